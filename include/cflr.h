@@ -1,0 +1,177 @@
+/*
+ * cflr.h - C ABI of the GB300 CFL-reachability solver.
+ *
+ * Problem (paper Sec. 2, Algorithm 1 "Data"/"Result"): given a context-free
+ * grammar Gr = (N, Sigma, P, S) in weak Chomsky normal form and a graph
+ * G = (V, E) whose edges carry terminal labels, compute for every
+ * non-terminal X the boolean |V| x |V| matrix
+ *     M_X(i, j) = 1  iff  some path i -> j has a label word derivable from X.
+ * The solver keeps one sparse boolean matrix per non-terminal (Algorithm 1,
+ * storage comment) and runs the closure loop of Algorithm 1 in the
+ * semi-naive form of optimisation 1:  every production c -> a b adds
+ * (dA . B) u (A_old . dB) to M_c, minus what M_c already holds, until no
+ * iteration adds a pair.  All device work runs in this library's own CUDA
+ * kernels for sm_103a; the arithmetic is boolean/integer and exact.
+ *
+ * Conventions for every entry point:
+ *   - The return value is a status: CFLR_OK (0) or a negative CFLR_E* code.
+ *     On error, cflr_last_error() describes it; the context stays usable
+ *     unless the code is CFLR_ECUDA (the CUDA context itself failed).
+ *   - Input buffers are host memory owned by the caller and are copied before
+ *     the call returns.  The context owns all device memory it allocates and
+ *     frees it in cflr_destroy().  Output buffers are host memory owned by
+ *     the caller.
+ *   - Call order: cflr_create -> cflr_load_grammar -> cflr_load_graph ->
+ *     cflr_solve -> cflr_get_pairs (any number of times).  Loading a new
+ *     graph discards the previous matrices; loading a new grammar discards
+ *     the graph.  Calls out of order return CFLR_ESTATE.
+ *   - A context belongs to one host thread at a time.  Contexts on different
+ *     streams may solve concurrently.
+ */
+#ifndef CFLR_H
+#define CFLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CFLR_OK = 0,
+    CFLR_EINVAL = -1,    /* bad argument (NULL pointer, size, capacity too small) */
+    CFLR_EGRAMMAR = -2,  /* grammar text is malformed or not in WCNF            */
+    CFLR_EGRAPH = -3,    /* vertex id out of range, or too many vertices        */
+    CFLR_ENOMEM = -4,    /* device memory exhausted or over mem_budget_bytes    */
+    CFLR_ECUDA = -5,     /* a CUDA runtime call failed                          */
+    CFLR_ELIMIT = -6,    /* max_iterations reached before the fixpoint          */
+    CFLR_ESTATE = -7,    /* call out of order                                   */
+    CFLR_ETIMEOUT = -8   /* a bounded device-side wait gave up                  */
+};
+
+/* Execution forms of the closure loop (all give identical pair sets). */
+enum {
+    CFLR_FORM_PLAIN = 0,    /* one launch sequence per production per iteration,
+                               the shape of one library mxm per production      */
+    CFLR_FORM_BATCHED = 1,  /* every production of an iteration in one launch
+                               sequence; the host checks convergence each time  */
+    CFLR_FORM_GRAPH = 2     /* the batched iteration captured in a CUDA graph and
+                               repeated on the device until no pair is added    */
+};
+
+typedef struct cflr_ctx cflr_ctx;
+
+typedef struct {
+    int device;                 /* CUDA device ordinal                              */
+    void *stream;               /* cudaStream_t to run on; NULL = a private stream  */
+    uint64_t mem_budget_bytes;  /* cap on device bytes this context may hold; 0 = none */
+    uint32_t max_iterations;    /* stop with CFLR_ELIMIT after this many; 0 = none  */
+    int form;                   /* CFLR_FORM_*                                      */
+    int profile;                /* nonzero: time every kernel launch with CUDA events
+                                   on the solve stream (see cflr_kernel_stats)      */
+    const char *autotune_cache; /* reserved; may be NULL                            */
+} cflr_config;
+
+typedef struct {
+    uint32_t iterations;        /* closure iterations run (the last one adds nothing) */
+    uint64_t total_pairs;       /* sum of pairs over the non-terminals named in the
+                                   grammar text (terminal wrappers excluded)        */
+    double solve_ms;            /* device time of cflr_solve (CUDA events)          */
+    uint64_t peak_device_bytes; /* high-water mark of this context's device memory  */
+    uint64_t ignored_edges;     /* edges whose label no production uses             */
+    uint64_t flops;             /* boolean OR operations of all products            */
+    uint64_t candidates;        /* pairs the products emitted after the mask        */
+    uint64_t regrows;           /* buffer growths that re-ran a phase               */
+} cflr_stats;
+
+/* Default configuration: device 0, private stream, no budget, no iteration
+ * limit, CFLR_FORM_BATCHED, profiling off. */
+void cflr_default_config(cflr_config *cfg);
+
+/* Create a context on cfg->device (cfg NULL = defaults).  *out receives the
+ * context; nothing is allocated on the device until a graph is loaded.
+ * Errors: CFLR_EINVAL (out NULL, bad form), CFLR_ECUDA (device unusable). */
+int cflr_create(cflr_ctx **out, const cflr_config *cfg);
+
+/* Load a grammar (paper Sec. 2, WCNF definition) from text of len bytes.
+ * Format: one production per line, "LHS -> X Y", "LHS -> x", "LHS -> eps"
+ * or "LHS -> X" (unit production); "|" separates alternatives; "#" starts a
+ * comment.  A symbol is a non-terminal iff it is the left-hand side of some
+ * production; all other symbols are terminals (edge labels).  A directive
+ * "%index v lo hi" makes each production mentioning "_{v}" stand for one copy
+ * per value lo..hi (the indexed non-terminals of the paper's appendix B).
+ * A terminal inside a binary production is replaced by a fresh non-terminal
+ * named "<x>" with the single production "<x> -> x".
+ * Errors: CFLR_EINVAL (NULL text), CFLR_EGRAMMAR (malformed; see
+ * cflr_last_error for the line). */
+int cflr_load_grammar(cflr_ctx *c, const char *text, size_t len);
+
+/* Look up a symbol of the loaded grammar.  Non-terminal ids are 0..nt-1 in
+ * order of first appearance as a left-hand side, wrappers "<x>" last;
+ * terminal ids are 0..t-1 in order of first appearance.
+ * Errors: CFLR_ESTATE (no grammar), CFLR_EINVAL (unknown name). */
+int cflr_symbol_id(const cflr_ctx *c, const char *name, uint32_t *id, int *is_terminal);
+
+/* Number of non-terminals (wrappers included), of those named in the text,
+ * and of terminals. */
+int cflr_grammar_sizes(const cflr_ctx *c, uint32_t *n_nonterminals, uint32_t *n_named,
+                       uint32_t *n_terminals);
+
+/* Load a graph: n_vertices vertices with ids 0..n_vertices-1 (the paper's
+ * 1..n shifted by one) and n_edges edges src[e] --label[e]--> dst[e], all
+ * host arrays of uint32.  Labels are terminal ids from cflr_symbol_id; a
+ * label id that is not a terminal of the grammar is legal, adds nothing
+ * (Algorithm 1 initialisation with the empty set) and is counted in
+ * cflr_stats.ignored_edges.  Duplicate edges are harmless.  The edges are
+ * copied to the device and turned into the initial matrices (Algorithm 1,
+ * terminal initialisation; the identity for every A -> eps).
+ * Errors: CFLR_ESTATE (no grammar), CFLR_EINVAL (NULL arrays with
+ * n_edges > 0), CFLR_EGRAPH (an id >= n_vertices, or n_vertices too large for
+ * the packed 64-bit pair keys: n_nonterminals * n_vertices^2 >= 2^62),
+ * CFLR_ENOMEM, CFLR_ECUDA. */
+int cflr_load_graph(cflr_ctx *c, uint32_t n_vertices, uint64_t n_edges,
+                    const uint32_t *src, const uint32_t *label, const uint32_t *dst);
+
+/* Run the closure loop of Algorithm 1 with optimisation 1 to its fixpoint.
+ * Blocks until the device finishes.  stats may be NULL.  Solving again
+ * without a new graph is a no-op that reports the same pairs.
+ * Errors: CFLR_ESTATE (no graph), CFLR_ELIMIT (max_iterations reached; the
+ * matrices hold every pair found so far), CFLR_ENOMEM, CFLR_ECUDA. */
+int cflr_solve(cflr_ctx *c, cflr_stats *stats);
+
+/* Copy the pairs of non-terminal `nonterminal` into host arrays src/dst,
+ * sorted by (src, dst).  *n_pairs receives the count.  With src == dst ==
+ * NULL only the count is returned.  If capacity < count, nothing is copied,
+ * *n_pairs holds the count and CFLR_EINVAL is returned.
+ * Errors: CFLR_ESTATE (not solved), CFLR_EINVAL (bad id, capacity). */
+int cflr_get_pairs(const cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint32_t *dst,
+                   uint64_t capacity, uint64_t *n_pairs);
+
+/* Solve n independent contexts together: each closure iteration runs the
+ * products of all unfinished contexts in one launch sequence.  Every
+ * context must hold a loaded graph and use the same device and stream as
+ * ctxs[0].  stats (nullable) is an array of n.  Results are identical to
+ * solving each context alone.
+ * Errors: as cflr_solve; CFLR_EINVAL for n <= 0 or mixed devices. */
+int cflr_solve_batch(cflr_ctx *const *ctxs, int n, cflr_stats *stats);
+
+/* Per-kernel timing of the last solve when cfg.profile was set: for kernel
+ * index k (0..count-1) its name, launches, total device milliseconds (CUDA
+ * events on the solve stream) and algorithmic bytes moved (the bytes the
+ * method must read and write, counted by the kernels themselves).
+ * cflr_kernel_stats(c, -1, ...) returns the number of kernels in *launches. */
+int cflr_kernel_stats(const cflr_ctx *c, int k, const char **name, uint64_t *launches,
+                      double *total_ms, uint64_t *alg_bytes);
+
+/* Description of the last error on this context (never NULL). */
+const char *cflr_last_error(const cflr_ctx *c);
+
+/* Free every device and host resource of the context.  NULL is a no-op. */
+void cflr_destroy(cflr_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFLR_H */
