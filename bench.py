@@ -1,0 +1,356 @@
+"""Benchmark: CFL-reachability solve throughput on one GB300 (pairs/s).
+
+One step is one pass of the whole hot path on the alias-analysis workload
+(Fig. "wcnf:fica" grammar, 200 000-vertex program-shaped graph with 400 000
+'a' and 150 000 'd' edges plus their reverses):
+  terminal initialisation from the device-resident edges (cflr_reset),
+  the semi-naive closure loop to its fixpoint (cflr_solve),
+  and the extraction of every non-terminal's sorted pairs into device
+  buffers (cflr_get_pairs_device).
+value = pairs of all named non-terminals / step time (CUDA events on the
+solve stream, L2 flushed between steps).  e2e repeats the step through the
+host-buffer API: grammar text and host edges in, host pair arrays out.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cflr|reference]
+
+Under torchrun (N > 1) every rank solves its own replica (different seed):
+the single-instance fixpoint has no exchange step that would let it shard,
+so multi-GPU runs are independent replicas (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2401_11029_gb300 import gen  # noqa: E402
+
+METRIC = "CFL-r solve throughput (pairs of all non-terminals / solve time)"
+UNIT = "pairs/s"
+WORKLOAD = {"workload": "fica_like alias analysis (Fig. wcnf:fica)", "n_vertices": 200_000,
+            "a_edges": 400_000, "d_edges": 150_000, "reverse_edges": True, "seed": 2}
+SAMPLE_N = 20_000     # oracle sample: same generator and ratios, 1/10 of the vertices
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def workload_graph(seed: int, n: int = None):
+    n = n or WORKLOAD["n_vertices"]
+    scale = n / WORKLOAD["n_vertices"]
+    return gen.fica_like(n=n, n_a=int(WORKLOAD["a_edges"] * scale),
+                         n_d=int(WORKLOAD["d_edges"] * scale), seed=seed)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profile(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if
+    the kernel source has not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_fica_like.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernels_cu_sha256:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+    if not m or not t:
+        return None
+    src = open(os.path.join(ROOT, "paper_2401_11029_gb300", "csrc", "kernels.cu"), "rb").read()
+    if hashlib.sha256(src).hexdigest() != m.group(1):
+        return None
+    return int(t.group(1))
+
+
+def cpu_oracle_sample(seed: int) -> dict:
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    g = workload_graph(seed, SAMPLE_N)
+    text = gen.grammar_text("fica")
+    res = oracle.solve(text, g)
+    pairs = res.total()
+    return {"value": pairs / res.seconds, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"fica_like n={SAMPLE_N} (same generator and ratios as the workload, "
+                      f"{g.n_edges} edges, {pairs} pairs), one worklist solve, "
+                      f"{res.seconds:.1f} s on 1 host core"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local, dist
+
+
+def run_reference(args):
+    world, rank, local, dist = dist_setup()
+    if rank != 0:
+        return
+    vals = []
+    info = None
+    for _ in range(args.warmup):
+        cpu_oracle_sample(WORKLOAD["seed"])
+    for _ in range(args.steps):
+        info = cpu_oracle_sample(WORKLOAD["seed"])
+        vals.append(info["value"])
+    v = statistics.mean(vals)
+    info["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism=f"replicas{args.gpus}"),
+            "cpu_baseline": info,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_cflr(args):
+    import torch
+    from paper_2401_11029_gb300 import cflr
+
+    world, rank, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    seed = WORKLOAD["seed"] + 1000 * rank
+    g = workload_graph(seed)
+    text = gen.grammar_text("fica")
+
+    ctx = cflr.cflr_create(device=local, stream=stream.cuda_stream, profile=1)
+    cflr.cflr_load_grammar(ctx, text)
+    n_nt, n_named, _ = cflr.cflr_grammar_sizes(ctx)
+    term = {}
+    for name in g.labels:
+        try:
+            i, is_t = cflr.cflr_symbol_id(ctx, name)
+            term[name] = i if is_t else 0xFFFFFFFF
+        except cflr.CflrError:
+            term[name] = 0xFFFFFFFF
+    lab = np.asarray([term[x] for x in g.labels], np.uint32)[g.lab]
+    # pinned host copies of the inputs for the end-to-end leg
+    h_src = torch.from_numpy(g.src.astype(np.uint32).view(np.int32)).pin_memory()
+    h_lab = torch.from_numpy(lab.view(np.int32)).pin_memory()
+    h_dst = torch.from_numpy(g.dst.astype(np.uint32).view(np.int32)).pin_memory()
+    cflr.cflr_load_graph(ctx, g.n, h_src.numpy().view(np.uint32), h_lab.numpy().view(np.uint32),
+                         h_dst.numpy().view(np.uint32))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    last = {}
+
+    def device_step(out=None):
+        cflr.cflr_reset(ctx)
+        last.update(cflr.cflr_solve(ctx))
+        total = 0
+        for x in range(n_named):
+            cnt = cflr.cflr_get_pairs(ctx, x, count_only=True)
+            if cnt and out is not None:
+                cflr.cflr_get_pairs_device(ctx, x, out[0].data_ptr(), out[1].data_ptr(), cnt)
+            total += cnt
+        return total
+
+    pairs = device_step()
+    cap = max(cflr.cflr_get_pairs(ctx, x, count_only=True) for x in range(n_named))
+    out = (torch.empty(cap, dtype=torch.int32, device=dev),
+           torch.empty(cap, dtype=torch.int32, device=dev))
+    for _ in range(max(0, args.warmup - 1)):
+        device_step(out)
+    before = {k["name"]: k for k in cflr.cflr_kernel_stats(ctx)}
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(rank + 1)                      # evict L2 between steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p = device_step(out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        assert p == pairs, "pair count changed between steps"
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    after = {k["name"]: k for k in cflr.cflr_kernel_stats(ctx)}
+
+    # end-to-end through the host-buffer API
+    h_out_s = torch.empty(cap, dtype=torch.int32).pin_memory()
+    h_out_d = torch.empty(cap, dtype=torch.int32).pin_memory()
+    e2e_s = []
+    for k in range(args.steps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        c2 = cflr.cflr_create(device=local, stream=stream.cuda_stream)
+        cflr.cflr_load_grammar(c2, text)
+        cflr.cflr_load_graph(c2, g.n, h_src.numpy().view(np.uint32),
+                             h_lab.numpy().view(np.uint32), h_dst.numpy().view(np.uint32))
+        cflr.cflr_solve(c2)
+        tot = 0
+        lib = cflr.load_library()
+        import ctypes
+        for x in range(n_named):
+            n_p = ctypes.c_uint64()
+            rc = lib.cflr_get_pairs(c2, x, h_out_s.data_ptr(), h_out_d.data_ptr(), cap,
+                                    ctypes.byref(n_p))
+            assert rc == 0
+            tot += n_p.value
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        cflr.cflr_destroy(c2)
+        if k > 0:                                   # first call warms the allocator
+            e2e_s.append(dt)
+        assert tot == pairs
+
+    ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([ms, pairs, statistics.mean(e2e_s)], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_all, pairs_all, e2e_all = float(mx[0]), float(sm[1]), float(mx[2])
+    else:
+        ms_all, pairs_all, e2e_all = ms, float(pairs), statistics.mean(e2e_s)
+
+    # roofline of the dominant kernel over the timed steps
+    rows = []
+    for name, a in after.items():
+        b = before.get(name, {"launches": 0, "ms": 0.0, "alg_bytes": 0})
+        rows.append((a["ms"] - b["ms"], a["launches"] - b["launches"],
+                     a["alg_bytes"] - b["alg_bytes"], name))
+    rows.sort(reverse=True)
+    kms, kl, kb, kname = rows[0]
+    pk = peaks()
+    achieved = (kb / 1e9) / (kms / 1e3) if kms > 0 else 0.0
+    traffic = traffic_from_profile(kname)
+    launches = sum(r[1] for r in rows) + args.steps * n_named * 6   # + extraction kernels
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": pairs_all / (ms_all / 1e3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": dict(WORKLOAD, pairs=int(pairs), parallelism=f"replicas{world}",
+                       l2="flushed between steps (256 MiB write)"),
+        "e2e": {"value": pairs_all / e2e_all, "unit": UNIT,
+                "h2d_bytes_per_step": int(12 * g.n_edges),
+                "d2h_bytes_per_step": int(8 * pairs)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                     "traffic": traffic, "kernel": kname,
+                     "launches": kl, "avg_launch_ms": kms / max(kl, 1),
+                     "peak_src": pk["src"]},
+        "kernels": [{"name": r[3], "ms": round(r[0], 4), "launches": r[1],
+                     "gbs": round((r[2] / 1e9) / (r[0] / 1e3), 1) if r[0] > 0 else None}
+                    for r in rows if r[1]],
+        "clocks": clk,
+        "solve": {"iterations": last["iterations"], "flops": last["flops"],
+                  "candidates": last["candidates"],
+                  "peak_device_bytes": last["peak_device_bytes"]},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(WORKLOAD["seed"])
+    print(json.dumps(line), flush=True)
+    cflr.cflr_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cflr", choices=["cflr", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cflr(args)
+
+
+if __name__ == "__main__":
+    main()

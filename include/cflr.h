@@ -71,6 +71,9 @@ typedef struct {
     int profile;                /* nonzero: time every kernel launch with CUDA events
                                    on the solve stream (see cflr_kernel_stats)      */
     const char *autotune_cache; /* reserved; may be NULL                            */
+    uint32_t initial_capacity;  /* entries of the first work buffers; 0 = sized from
+                                   the input.  Small values exercise the growth
+                                   paths (every phase re-runs after a growth).      */
 } cflr_config;
 
 typedef struct {
@@ -137,7 +140,9 @@ int cflr_load_graph(cflr_ctx *c, uint32_t n_vertices, uint64_t n_edges,
  * Blocks until the device finishes.  stats may be NULL.  Solving again
  * without a new graph is a no-op that reports the same pairs.
  * Errors: CFLR_ESTATE (no graph), CFLR_ELIMIT (max_iterations reached; the
- * matrices hold every pair found so far), CFLR_ENOMEM, CFLR_ECUDA. */
+ * matrices hold every pair found so far and a further cflr_solve continues
+ * from there), CFLR_ENOMEM (the matrices are dropped: load a graph again),
+ * CFLR_ECUDA. */
 int cflr_solve(cflr_ctx *c, cflr_stats *stats);
 
 /* Copy the pairs of non-terminal `nonterminal` into host arrays src/dst,
@@ -147,6 +152,19 @@ int cflr_solve(cflr_ctx *c, cflr_stats *stats);
  * Errors: CFLR_ESTATE (not solved), CFLR_EINVAL (bad id, capacity). */
 int cflr_get_pairs(const cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint32_t *dst,
                    uint64_t capacity, uint64_t *n_pairs);
+
+/* As cflr_get_pairs, but d_src/d_dst are device pointers (on this context's
+ * device) owned by the caller; the pairs never leave the GPU.  The call
+ * returns after the copy has finished on the context's stream. */
+int cflr_get_pairs_device(const cflr_ctx *c, uint32_t nonterminal, uint32_t *d_src,
+                          uint32_t *d_dst, uint64_t capacity, uint64_t *n_pairs);
+
+/* Restore the matrices of the loaded graph to Algorithm 1's terminal
+ * initialisation, from the copy of the edges cflr_load_graph keeps on the
+ * device (no host transfer).  Device buffers grown by earlier solves are
+ * kept, so a reset-solve cycle allocates nothing in steady state.
+ * Errors: CFLR_ESTATE (no graph), CFLR_ENOMEM, CFLR_ECUDA. */
+int cflr_reset(cflr_ctx *c);
 
 /* Solve n independent contexts together: each closure iteration runs the
  * products of all unfinished contexts in one launch sequence.  Every

@@ -1,0 +1,946 @@
+// CUDA kernels of the CFL-reachability closure loop (sm_103a).
+//
+// One closure iteration of Algorithm 1 with optimisation 1 is, for every
+// production c -> a b,  T_c = (dA . B) u (A_old . dB),  dC = T_c \ M_c,
+// M_c <- M_c u dC  (paper Sec. 3, optimisations 1 and 2).  The kernels below
+// split it into:
+//   k_symbolic   work list: one group per (production, delta row) with its
+//                product count, binned by the shared memory it needs
+//   k_spgemm_*   the boolean products of a group with the mask fused:
+//                a shared-memory set of the mask row plus the products;
+//                a product is emitted only when the set did not hold it
+//   k_commit     dedupe across groups into the per-non-terminal hash set;
+//                the winners are the new pairs dC
+//   k_reset_dnew / k_count / k_capacity / k_scatter
+//                the union M_c u dC: append dC to the row and column forms
+//                (rows keep slack and move when full, so a union touches
+//                only the rows that grow - the role optimisation 3 plays)
+// All work is integer; the result does not depend on thread timing.
+#include "kernels.cuh"
+
+#include <cstdio>
+
+namespace cflr {
+
+#define FULL_MASK 0xFFFFFFFFu
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+// 64-bit mixer (the MurmurHash3 64-bit finaliser).
+__device__ __forceinline__ unsigned long long hmix(unsigned long long k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t t = __shfl_up_sync(FULL_MASK, v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL_MASK, v, d);
+    return v;
+}
+
+// Insert v into a shared-memory open-addressing set of 2^lg slots.
+// Returns true when v was not present.  The caller keeps the load <= 1/2.
+__device__ __forceinline__ bool smem_insert(uint32_t *tab, int lg, uint32_t v) {
+    const uint32_t m = (1u << lg) - 1;
+    uint32_t s = (v * 2654435761u) >> (32 - lg);
+    for (;;) {
+        uint32_t old = atomicCAS(&tab[s], EMPTY32, v);
+        if (old == EMPTY32) return true;
+        if (old == v) return false;
+        s = (s + 1) & m;
+    }
+}
+
+__device__ __forceinline__ bool bitmap_insert(uint32_t *bm, uint32_t v) {
+    const uint32_t bit = 1u << (v & 31);
+    return (atomicOr(&bm[v >> 5], bit) & bit) == 0;
+}
+
+__device__ __forceinline__ bool htab_contains(const unsigned long long *tab,
+                                              unsigned long long m, unsigned long long key) {
+    unsigned long long h = hmix(key) & m;
+    for (;;) {
+        unsigned long long v = tab[h];
+        if (v == key) return true;
+        if (v == EMPTY_KEY) return false;
+        h = (h + 1) & m;
+    }
+}
+
+// Warp-collective append of flagged keys to the candidate buffer.  All 32
+// lanes must call it.  Returns (in every lane) the number appended.
+__device__ __forceinline__ uint32_t emit_candidates(bool flag, unsigned long long key,
+                                                    uint32_t slot, const WorkBufs &W,
+                                                    int lane) {
+    const unsigned m = __ballot_sync(FULL_MASK, flag);
+    if (!m) return 0;
+    const uint32_t cnt = __popc(m);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&W.cnt->cand, (unsigned long long)cnt);
+    base = __shfl_sync(FULL_MASK, base, 0);
+    if (flag) {
+        unsigned long long pos = base + __popc(m & ((1u << lane) - 1));
+        if (pos < W.cand_cap) {
+            W.cand_key[pos] = key;
+            W.cand_slot[pos] = slot;
+        }
+    }
+    if (lane == 0 && base + cnt > W.cand_cap) atomicOr(&W.cnt->overflow, OVF_CAND);
+    return cnt;
+}
+
+// ---------------------------------------------------------------------------
+// k_symbolic: groups of this iteration, binned by shared-memory need
+// ---------------------------------------------------------------------------
+
+constexpr int SYM_BUF = 16;   // per-warp staging of groups before one atomic
+
+// prod_only >= 0 restricts the work list to one production (the plain form).
+__global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs W,
+                                                  int prod_only) {
+    __shared__ uint2 stage[8][N_BINS][SYM_BUF];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned long long nw = (unsigned long long)gridDim.x * 8;
+    const unsigned long long n_in = *W.touched_in_n;
+    int fill[N_BINS] = {0, 0, 0, 0};
+    unsigned long long bytes[N_BINS] = {0, 0, 0, 0};
+    unsigned long long flops = 0, sym_bytes = 0;
+
+    auto flush = [&](int b) {   // lane 0 only
+        unsigned long long pos = atomicAdd(&W.cnt->groups[b], (unsigned long long)fill[b]);
+        for (int q = 0; q < fill[b]; q++) {
+            if (pos + q < W.group_cap[b]) W.groups[b][pos + q] = stage[wib][b][q];
+        }
+        if (pos + fill[b] > W.group_cap[b]) atomicOr(&W.cnt->overflow, OVF_GROUPS);
+        fill[b] = 0;
+    };
+
+    for (unsigned long long e = (unsigned long long)blockIdx.x * 8 + wib; e < n_in; e += nw) {
+        const uint2 t = W.touched_in[e];
+        const uint32_t xo = t.x, idx = t.y, slot = xo >> 1, o = xo & 1;
+        const uint32_t n = S.n[slot];
+        const uint4 dsc = S.desc[slot][(size_t)o * n + idx];
+        const uint32_t d = dsc.w, dstart = dsc.x + dsc.y - dsc.w;
+        const uint32_t *pool = S.pool[slot];
+        for (uint32_t u = P.use_off[xo]; u < P.use_off[xo + 1]; u++) {
+            const uint32_t code = P.use_code[u];
+            if (prod_only >= 0 && (code >> 2) != (uint32_t)prod_only) continue;
+            const uint32_t part = code & 3;
+            const uint4 pr = P.prod[code >> 2];
+            const uint32_t mlen = S.desc[pr.x][(size_t)o * n + idx].y;
+            unsigned long long f = 0;
+            if (part == PART_U) {
+                f = d;
+            } else {
+                const uint4 *dg = (part == PART_A) ? S.desc[pr.z] : S.desc[pr.y] + n;
+                for (uint32_t q = lane; q < d; q += 32) {
+                    const uint4 gd = dg[pool[dstart + q]];
+                    f += (part == PART_A) ? gd.y : (gd.y - gd.w);
+                }
+                f = warp_sum64(f);
+            }
+            if (lane == 0 && f > 0) {
+                bool probe = (unsigned long long)mlen > (unsigned long long)PROBE_RATIO * f;
+                unsigned long long need = probe ? f : f + mlen;
+                int b = need <= BIN0_LIMIT ? 0 : need <= BIN1_LIMIT ? 1
+                      : need <= BIN2_LIMIT ? 2 : 3;
+                if (b == 3) probe = false;       // the bitmap takes the whole mask row
+                stage[wib][b][fill[b]++] =
+                    make_uint2(((code >> 2) << 3) | (probe ? MODE_PROBE : 0u) | part, idx);
+                // algorithmic bytes: the delta row (4 B per entry), one 16-byte
+                // descriptor and 4 B per element of every referenced row, and
+                // the mask row when it is loaded
+                bytes[b] += 20ull * d + 4ull * f + (probe ? 0ull : 4ull * mlen + 16ull);
+                sym_bytes += 20ull * d + 32ull;
+                flops += f;
+                if (fill[b] == SYM_BUF) flush(b);
+            }
+        }
+    }
+    if (lane == 0) {
+        for (int b = 0; b < N_BINS; b++) {
+            if (fill[b]) flush(b);
+            if (bytes[b]) atomicAdd(&W.cnt->bytes_bin[b], bytes[b]);
+        }
+        if (flops) atomicAdd(&W.cnt->flops, flops);
+        if (sym_bytes) atomicAdd(&W.cnt->bytes_sym, sym_bytes);
+    }
+}
+
+// Group code layout: prod << 3 | probe bit (MODE_PROBE) | part.
+struct GroupInfo {
+    uint32_t part, c, a, b, idx, n, o;
+    bool probe;
+};
+
+__device__ __forceinline__ GroupInfo decode_group(const ProdTab &P, const SlotTab &S,
+                                                  uint2 g) {
+    GroupInfo gi;
+    gi.probe = (g.x & MODE_PROBE) != 0;
+    gi.part = g.x & 3;
+    const uint4 pr = P.prod[g.x >> 3];
+    gi.c = pr.x; gi.a = pr.y; gi.b = pr.z;
+    gi.idx = g.y;
+    gi.n = S.n[gi.c];
+    gi.o = (gi.part == PART_B) ? 1u : 0u;
+    return gi;
+}
+
+// The delta owner of a group: a's row form (PART_A, PART_U) or b's column form.
+__device__ __forceinline__ uint4 owner_desc(const SlotTab &S, const GroupInfo &gi) {
+    const uint32_t x = (gi.part == PART_B) ? gi.b : gi.a;
+    return S.desc[x][(size_t)gi.o * gi.n + gi.idx];
+}
+
+__device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uint32_t v) {
+    // row groups produce (idx, v); column groups produce (v, idx)
+    return gi.o ? (((unsigned long long)v << 32) | gi.idx)
+                : (((unsigned long long)gi.idx << 32) | v);
+}
+
+// Walk the delta entries [first, d) of a group in chunks of 32 (stride
+// `stride`), expand the referenced rows with a load-balanced warp loop and
+// insert every element into the accumulator `ins`; new elements that pass
+// the probe (if any) are emitted.  Warp-collective.
+template <class Ins>
+__device__ __forceinline__ uint32_t expand_group(const SlotTab &S, const WorkBufs &W,
+                                                 const GroupInfo &gi, uint4 own,
+                                                 uint32_t first, uint32_t stride, int lane,
+                                                 Ins ins) {
+    const uint32_t d = own.w, dstart = own.x + own.y - own.w;
+    const uint32_t *pool = S.pool[gi.c];
+    const uint4 *dg = (gi.part == PART_A) ? S.desc[gi.b]
+                    : (gi.part == PART_B) ? S.desc[gi.a] + gi.n : nullptr;
+    const unsigned long long *ht = S.htab[gi.c];
+    const unsigned long long hm = S.hmask[gi.c];
+    uint32_t emitted = 0;
+    for (uint32_t base = first; base < d; base += stride) {
+        const uint32_t t = base + lane;
+        uint32_t k = 0, goff = 0, glen = 0;
+        if (t < d) {
+            k = pool[dstart + t];
+            if (gi.part == PART_U) {
+                glen = 1;
+            } else {
+                const uint4 gd = dg[k];
+                goff = gd.x;
+                glen = (gi.part == PART_A) ? gd.y : gd.y - gd.w;   // B full, A_old prefix
+            }
+        }
+        const uint32_t incl = warp_incl_scan(glen, lane);
+        const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+        for (uint32_t fb = 0; fb < total; fb += 32) {
+            const uint32_t f = fb + lane;
+            const bool valid = f < total;
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int s = 0; s < 5; s++) {       // first lane whose inclusive sum > f
+                const int mid = (lo + hi) >> 1;
+                const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
+                if (f < v) hi = mid; else lo = mid + 1;
+            }
+            const int owner = lo > 31 ? 31 : lo;
+            const uint32_t o_off = __shfl_sync(FULL_MASK, goff, owner);
+            const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
+            const uint32_t o_len = __shfl_sync(FULL_MASK, glen, owner);
+            const uint32_t o_k = __shfl_sync(FULL_MASK, k, owner);
+            uint32_t v = 0;
+            bool isnew = false;
+            unsigned long long key = 0;
+            if (valid) {
+                v = (gi.part == PART_U) ? o_k : pool[o_off + (f - (o_incl - o_len))];
+                isnew = ins(v);
+                key = group_key(gi, v);
+                if (isnew && gi.probe) isnew = !htab_contains(ht, hm, key);
+            }
+            emitted += emit_candidates(isnew, key, gi.c, W, lane);
+        }
+    }
+    return emitted;
+}
+
+// Bins 0 and 1: one warp per group, a private shared-memory set per warp.
+template <int LG, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SlotTab S, ProdTab P, WorkBufs W,
+                                                            int bin) {
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *tab = smem + (size_t)wib * (1u << LG);
+    const unsigned long long n_groups =
+        min(W.cnt->groups[bin], W.group_cap[bin]);
+    const unsigned long long nw = (unsigned long long)gridDim.x * WARPS;
+    unsigned long long bytes = 0;
+    for (unsigned long long g = (unsigned long long)blockIdx.x * WARPS + wib; g < n_groups;
+         g += nw) {
+        const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
+        for (uint32_t s = lane; s < (1u << LG); s += 32) tab[s] = EMPTY32;
+        __syncwarp();
+        if (!gi.probe) {
+            const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
+            const uint32_t *pool = S.pool[gi.c];
+            for (uint32_t q = lane; q < md.y; q += 32) smem_insert(tab, LG, pool[md.x + q]);
+            __syncwarp();
+        }
+        const uint4 own = owner_desc(S, gi);
+        const uint32_t e = expand_group(S, W, gi, own, 0, 32, lane,
+                                        [&](uint32_t v) { return smem_insert(tab, LG, v); });
+        if (lane == 0 && e) {
+            atomicAdd(&S.cand[gi.c], (unsigned long long)e);
+            bytes += 12ull * e;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
+}
+
+// Bin 2: one CTA per group sharing a 2^LG-slot shared-memory set.
+template <int LG>
+__global__ void __launch_bounds__(256) k_spgemm_cta(SlotTab S, ProdTab P, WorkBufs W, int bin) {
+    extern __shared__ uint32_t smem[];
+    __shared__ uint32_t emitted_sh;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned long long n_groups = min(W.cnt->groups[bin], W.group_cap[bin]);
+    unsigned long long bytes = 0;
+    for (unsigned long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
+        for (uint32_t s = threadIdx.x; s < (1u << LG); s += blockDim.x) smem[s] = EMPTY32;
+        if (threadIdx.x == 0) emitted_sh = 0;
+        __syncthreads();
+        if (!gi.probe) {
+            const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
+            const uint32_t *pool = S.pool[gi.c];
+            for (uint32_t q = threadIdx.x; q < md.y; q += blockDim.x)
+                smem_insert(smem, LG, pool[md.x + q]);
+        }
+        __syncthreads();
+        const uint4 own = owner_desc(S, gi);
+        const uint32_t e = expand_group(S, W, gi, own, wib * 32, blockDim.x, lane,
+                                        [&](uint32_t v) { return smem_insert(smem, LG, v); });
+        if (lane == 0 && e) atomicAdd(&emitted_sh, e);
+        __syncthreads();
+        if (threadIdx.x == 0 && emitted_sh) {
+            atomicAdd(&S.cand[gi.c], (unsigned long long)emitted_sh);
+            bytes += 12ull * emitted_sh;
+        }
+    }
+    if (threadIdx.x == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
+}
+
+// Bin 3: one CTA per group with an n-bit bitmap of the output row (shared
+// memory when it fits, else a per-CTA slice of global scratch).
+__global__ void __launch_bounds__(256) k_spgemm_bitmap(SlotTab S, ProdTab P, WorkBufs W,
+                                                       int bin, int use_smem) {
+    extern __shared__ uint32_t smem[];
+    __shared__ uint32_t emitted_sh;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned long long n_groups = min(W.cnt->groups[bin], W.group_cap[bin]);
+    uint32_t *bm = use_smem ? smem : W.bitmap_scratch + (size_t)blockIdx.x * W.bitmap_words;
+    unsigned long long bytes = 0;
+    for (unsigned long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
+        const uint32_t words = (gi.n + 31) >> 5;
+        for (uint32_t s = threadIdx.x; s < words; s += blockDim.x) bm[s] = 0;
+        if (threadIdx.x == 0) emitted_sh = 0;
+        __syncthreads();
+        {
+            const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
+            const uint32_t *pool = S.pool[gi.c];
+            for (uint32_t q = threadIdx.x; q < md.y; q += blockDim.x) {
+                const uint32_t v = pool[md.x + q];
+                atomicOr(&bm[v >> 5], 1u << (v & 31));
+            }
+        }
+        __syncthreads();
+        const uint4 own = owner_desc(S, gi);
+        const uint32_t e = expand_group(S, W, gi, own, wib * 32, blockDim.x, lane,
+                                        [&](uint32_t v) { return bitmap_insert(bm, v); });
+        if (lane == 0 && e) atomicAdd(&emitted_sh, e);
+        __syncthreads();
+        if (threadIdx.x == 0 && emitted_sh) {
+            atomicAdd(&S.cand[gi.c], (unsigned long long)emitted_sh);
+            bytes += 12ull * emitted_sh;
+        }
+    }
+    if (threadIdx.x == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
+}
+
+// ---------------------------------------------------------------------------
+// k_commit: global dedupe of candidates into the per-slot pair sets
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nc = min(W.cnt->cand, W.cand_cap);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x +
+                                   (threadIdx.x & ~31u);
+         base < nc; base += stride) {
+        const unsigned long long t = base + lane;
+        bool isnew = false;
+        unsigned long long key = 0;
+        uint32_t slot = EMPTY32;
+        if (t < nc) {
+            key = W.cand_key[t];
+            slot = W.cand_slot[t];
+            unsigned long long *tab = S.htab[slot];
+            const unsigned long long m = S.hmask[slot];
+            unsigned long long h = hmix(key) & m;
+            for (;;) {
+                unsigned long long v = tab[h];
+                if (v == key) break;
+                if (v == EMPTY_KEY) {
+                    v = atomicCAS(&tab[h], EMPTY_KEY, key);
+                    if (v == EMPTY_KEY) { isnew = true; break; }
+                    if (v == key) break;
+                }
+                h = (h + 1) & m;
+            }
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, isnew);
+        if (m) {
+            unsigned long long pos = 0;
+            if (lane == 0) pos = atomicAdd(&W.cnt->delta, (unsigned long long)__popc(m));
+            pos = __shfl_sync(FULL_MASK, pos, 0);
+            if (isnew) {
+                pos += __popc(m & ((1u << lane) - 1));
+                W.delta_key[pos] = key;       // delta count <= candidate count <= cap
+                W.delta_slot[pos] = slot;
+            }
+            const unsigned same = __match_any_sync(FULL_MASK, isnew ? slot : EMPTY32);
+            if (isnew && lane == __ffs(same & m) - 1)
+                atomicAdd(&S.delta[slot], (unsigned long long)__popc(same & m));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// merge: M <- M u dC in the row and column forms
+// ---------------------------------------------------------------------------
+
+// Rows that received entries in the previous merge stop being "new".
+__global__ void k_reset_dnew(SlotTab S, WorkBufs W) {
+    const unsigned long long n_in = *W.touched_in_n;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         e < n_in; e += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint2 t = W.touched_in[e];
+        const uint32_t slot = t.x >> 1, o = t.x & 1;
+        S.desc[slot][(size_t)o * S.n[slot] + t.y].w = 0;
+    }
+}
+
+// Count the new entries of every row; list each row the first time.
+__global__ void __launch_bounds__(256) k_count(SlotTab S, WorkBufs W) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nd = W.cnt->delta;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x +
+                                   (threadIdx.x & ~31u);
+         base < nd; base += stride) {
+        const unsigned long long t = base + lane;
+        bool first_r = false, first_c = false;
+        uint32_t slot = 0, i = 0, j = 0;
+        if (t < nd) {
+            const unsigned long long key = W.delta_key[t];
+            slot = W.delta_slot[t];
+            i = (uint32_t)(key >> 32);
+            j = (uint32_t)key;
+            uint4 *dsc = S.desc[slot];
+            const uint32_t n = S.n[slot];
+            first_r = atomicAdd(&dsc[i].w, 1u) == 0;
+            first_c = atomicAdd(&dsc[(size_t)n + j].w, 1u) == 0;
+        }
+#pragma unroll
+        for (int o = 0; o < 2; o++) {
+            const bool f = o ? first_c : first_r;
+            const unsigned m = __ballot_sync(FULL_MASK, f);
+            if (!m) continue;
+            unsigned long long pos = 0;
+            if (lane == 0) pos = atomicAdd(W.touched_out_n, (unsigned long long)__popc(m));
+            pos = __shfl_sync(FULL_MASK, pos, 0);
+            if (f) {
+                pos += __popc(m & ((1u << lane) - 1));
+                if (pos < W.touched_cap) W.touched_out[pos] = make_uint2(slot * 2 + o, o ? j : i);
+                else atomicOr(&W.cnt->overflow, OVF_TOUCHED);
+            }
+        }
+    }
+}
+
+// Make room for every listed row (relocate to a larger segment if needed).
+// Idempotent: after a pool overflow the host grows the pool and runs it again.
+__global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs W) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long n_t = min(*W.touched_out_n, W.touched_cap);
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) +
+                                (threadIdx.x >> 5);
+         e < n_t; e += nw) {
+        const uint2 t = W.touched_out[e];
+        const uint32_t slot = t.x >> 1, o = t.x & 1;
+        uint4 *dp = &S.desc[slot][(size_t)o * S.n[slot] + t.y];
+        const uint4 dsc = *dp;
+        const unsigned long long need = (unsigned long long)dsc.y + dsc.w;
+        if (need <= dsc.z) continue;
+        unsigned long long cap = max(2ull * dsc.z, need);
+        cap = max((cap + 3) & ~3ull, 4ull);
+        const uint32_t inst = S.inst[slot];
+        unsigned long long off = 0;
+        if (lane == 0) {
+            off = atomicAdd(&I.pool_top[inst], cap);
+            if (off + cap > I.pool_cap[inst]) {
+                atomicOr(&W.cnt->overflow, OVF_POOL);
+                off = ~0ull;
+            }
+        }
+        off = __shfl_sync(FULL_MASK, off, 0);
+        if (off == ~0ull) continue;
+        uint32_t *pool = S.pool[slot];
+        for (uint32_t q = lane; q < dsc.y; q += 32) pool[off + q] = pool[dsc.x + q];
+        __syncwarp();
+        if (lane == 0) {
+            dp->x = (uint32_t)off;
+            dp->z = (uint32_t)cap;
+        }
+    }
+}
+
+// Append the new pairs: (i, j) goes to row i of the row form and row j of
+// the column form.
+__global__ void __launch_bounds__(256) k_scatter(SlotTab S, WorkBufs W) {
+    if (W.cnt->overflow & OVF_POOL) return;
+    const unsigned long long nd = W.cnt->delta;
+    for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         t < nd; t += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long key = W.delta_key[t];
+        const uint32_t slot = W.delta_slot[t];
+        const uint32_t i = (uint32_t)(key >> 32), j = (uint32_t)key;
+        uint4 *dsc = S.desc[slot];
+        uint32_t *pool = S.pool[slot];
+        const uint32_t n = S.n[slot];
+        const uint32_t pr = atomicAdd(&dsc[i].y, 1u);
+        pool[(size_t)dsc[i].x + pr] = j;
+        const uint32_t pc = atomicAdd(&dsc[(size_t)n + j].y, 1u);
+        pool[(size_t)dsc[(size_t)n + j].x + pc] = i;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// initialisation (Algorithm 1, terminal initialisation) and maintenance
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_init_edges(const uint32_t *src, const uint32_t *lab,
+                                                    const uint32_t *dst,
+                                                    unsigned long long n_edges,
+                                                    const uint32_t *term_off,
+                                                    const uint32_t *term_slot,
+                                                    uint32_t n_terms, WorkBufs W) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x +
+                                   (threadIdx.x & ~31u);
+         base < n_edges; base += stride) {
+        const unsigned long long e = base + lane;
+        uint32_t q0 = 0, q1 = 0;
+        unsigned long long key = 0;
+        if (e < n_edges) {
+            const uint32_t l = lab[e];
+            if (l < n_terms) { q0 = term_off[l]; q1 = term_off[l + 1]; }
+            key = ((unsigned long long)src[e] << 32) | dst[e];
+        }
+        // every terminal maps to few non-terminals: emit one round per target
+        uint32_t rounds = q1 - q0;
+        for (int d = 16; d > 0; d >>= 1) rounds = max(rounds, __shfl_xor_sync(FULL_MASK, rounds, d));
+        for (uint32_t r = 0; r < rounds; r++) {
+            const bool f = q0 + r < q1;
+            const uint32_t slot = f ? term_slot[q0 + r] : 0;
+            emit_candidates(f, key, slot, W, lane);
+        }
+    }
+}
+
+__global__ void k_init_eps(uint32_t slot, uint32_t n, WorkBufs W) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x +
+                                   (threadIdx.x & ~31u);
+         base < n; base += stride) {
+        const unsigned long long i = base + lane;
+        emit_candidates(i < n, (i << 32) | i, slot, W, lane);
+    }
+}
+
+__global__ void k_rehash(const unsigned long long *old_tab, unsigned long long old_cap,
+                         unsigned long long *new_tab, unsigned long long new_cap) {
+    const unsigned long long m = new_cap - 1;
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         s < old_cap; s += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long key = old_tab[s];
+        if (key == EMPTY_KEY) continue;
+        unsigned long long h = hmix(key) & m;
+        while (atomicCAS(&new_tab[h], EMPTY_KEY, key) != EMPTY_KEY) h = (h + 1) & m;
+    }
+}
+
+__global__ void k_fill_u64(unsigned long long *p, unsigned long long count,
+                           unsigned long long v) {
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         s < count; s += (unsigned long long)gridDim.x * blockDim.x)
+        p[s] = v;
+}
+
+__global__ void k_remap_touched(const uint2 *in, unsigned long long n, uint32_t slot_base,
+                                uint2 *out) {
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         s < n; s += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint2 t = in[s];
+        out[s] = make_uint2(t.x + 2 * slot_base, t.y);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// extraction: rows of the row form, each sorted, written in row order
+// ---------------------------------------------------------------------------
+
+__global__ void k_row_lengths(const uint4 *desc, uint32_t n, uint32_t *len) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        len[i] = desc[i].y;
+}
+
+constexpr int EXTRACT_WARP_MAX = 1024;
+
+// One warp per row: bitonic sort in shared memory for rows up to 1024
+// entries; longer rows are listed for k_extract_big.
+__global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const uint32_t *pool,
+                                                       uint32_t n,
+                                                       const unsigned long long *row_out,
+                                                       uint32_t *out_src, uint32_t *out_dst,
+                                                       uint32_t *big_rows,
+                                                       uint32_t *big_count) {
+    __shared__ uint32_t sbuf[8][EXTRACT_WARP_MAX];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *s = sbuf[wib];
+    for (uint32_t i = blockIdx.x * 8 + wib; i < n; i += gridDim.x * 8) {
+        const uint4 d = desc[i];
+        const uint32_t len = d.y;
+        if (len == 0) continue;
+        if (len > EXTRACT_WARP_MAX) {
+            if (lane == 0) big_rows[atomicAdd(big_count, 1u)] = i;
+            continue;
+        }
+        uint32_t P = 32;
+        while (P < len) P <<= 1;
+        for (uint32_t t = lane; t < P; t += 32) s[t] = t < len ? pool[d.x + t] : EMPTY32;
+        __syncwarp();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+                for (uint32_t t = lane; t < P; t += 32) {
+                    const uint32_t ixj = t ^ jj;
+                    if (ixj > t) {
+                        const uint32_t a = s[t], b = s[ixj];
+                        const bool up = (t & k) == 0;
+                        if ((a > b) == up) { s[t] = b; s[ixj] = a; }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        const unsigned long long o = row_out[i];
+        for (uint32_t t = lane; t < len; t += 32) {
+            out_src[o + t] = i;
+            out_dst[o + t] = s[t];
+        }
+        __syncwarp();
+    }
+}
+
+// One CTA per long row: mark the row's columns in an n-bit bitmap, then
+// write the set bits in increasing order.
+__global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const uint32_t *pool,
+                                                     uint32_t n,
+                                                     const unsigned long long *row_out,
+                                                     uint32_t *out_src, uint32_t *out_dst,
+                                                     const uint32_t *big_rows,
+                                                     const uint32_t *big_count,
+                                                     uint32_t *gbitmap, int use_smem) {
+    extern __shared__ uint32_t smem[];
+    __shared__ uint32_t scan[256];
+    const uint32_t words = (n + 31) >> 5;
+    uint32_t *bm = use_smem ? smem : gbitmap + (size_t)blockIdx.x * words;
+    const uint32_t per = (words + blockDim.x - 1) / blockDim.x;
+    const uint32_t nb = *big_count;
+    for (uint32_t r = blockIdx.x; r < nb; r += gridDim.x) {
+        const uint32_t i = big_rows[r];
+        const uint4 d = desc[i];
+        for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < d.y; t += blockDim.x) {
+            const uint32_t v = pool[d.x + t];
+            atomicOr(&bm[v >> 5], 1u << (v & 31));
+        }
+        __syncthreads();
+        const uint32_t w0 = threadIdx.x * per, w1 = min(words, w0 + per);
+        uint32_t cnt = 0;
+        for (uint32_t w = w0; w < w1; w++) cnt += __popc(bm[w]);
+        scan[threadIdx.x] = cnt;
+        __syncthreads();
+        for (uint32_t off = 1; off < blockDim.x; off <<= 1) {
+            const uint32_t v = threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
+            __syncthreads();
+            scan[threadIdx.x] += v;
+            __syncthreads();
+        }
+        unsigned long long o = row_out[i] + scan[threadIdx.x] - cnt;
+        for (uint32_t w = w0; w < w1; w++) {
+            uint32_t bits = bm[w];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                out_src[o] = i;
+                out_dst[o] = w * 32 + b;
+                o++;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 counts into uint64 offsets (three phases)
+// ---------------------------------------------------------------------------
+
+constexpr uint32_t SCAN_TILE = 1024;   // 256 threads x 4 elements
+
+__device__ __forceinline__ unsigned long long block_excl_scan256(unsigned long long v,
+                                                                 unsigned long long *sh,
+                                                                 unsigned long long &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        unsigned long long t = __shfl_up_sync(FULL_MASK, x, d);
+        if (lane >= d) x += t;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long y = lane < 8 ? sh[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            unsigned long long t = __shfl_up_sync(FULL_MASK, y, d);
+            if (lane >= d) y += t;
+        }
+        if (lane < 8) sh[8 + lane] = y;
+    }
+    __syncthreads();
+    total = sh[15];
+    const unsigned long long before = (w ? sh[8 + w - 1] : 0ull) + x - v;
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *in, uint32_t n,
+                                                     unsigned long long *bsum) {
+    __shared__ unsigned long long sh[16];
+    const unsigned long long base = (unsigned long long)blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    unsigned long long v = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (base + q < n) v += in[base + q];
+    unsigned long long total;
+    block_excl_scan256(v, sh, total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(256) k_scan_top(unsigned long long *bsum, uint32_t nb,
+                                                  unsigned long long *grand) {
+    __shared__ unsigned long long sh[16];
+    unsigned long long carry = 0;
+    for (uint32_t b0 = 0; b0 < nb; b0 += 256) {
+        const uint32_t i = b0 + threadIdx.x;
+        const unsigned long long v = i < nb ? bsum[i] : 0;
+        unsigned long long total;
+        const unsigned long long ex = block_excl_scan256(v, sh, total);
+        if (i < nb) bsum[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0 && grand) *grand = carry;
+}
+
+__global__ void __launch_bounds__(256) k_scan_down(const uint32_t *in, uint32_t n,
+                                                   const unsigned long long *bsum,
+                                                   unsigned long long *out) {
+    __shared__ unsigned long long sh[16];
+    const unsigned long long base = (unsigned long long)blockIdx.x * SCAN_TILE + threadIdx.x * 4;
+    uint32_t x[4];
+    unsigned long long v = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        x[q] = base + q < n ? in[base + q] : 0;
+        v += x[q];
+    }
+    unsigned long long total;
+    unsigned long long acc = bsum[blockIdx.x] + block_excl_scan256(v, sh, total);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (base + q < n) out[base + q] = acc;
+        acc += x[q];
+    }
+}
+
+void launch_exclusive_scan(const uint32_t *in, uint32_t n, unsigned long long *out,
+                           unsigned long long *bsum, unsigned long long *grand, cudaStream_t st) {
+    if (!n) return;
+    const uint32_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_reduce<<<nb, 256, 0, st>>>(in, n, bsum);
+    k_scan_top<<<1, 256, 0, st>>>(bsum, nb, grand);
+    k_scan_down<<<nb, 256, 0, st>>>(in, n, bsum, out);
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+// ---------------------------------------------------------------------------
+
+static inline int grid_for(unsigned long long work, int per_block, int sms, int mult) {
+    unsigned long long g = (work + per_block - 1) / per_block;
+    const unsigned long long cap = (unsigned long long)sms * mult;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+constexpr size_t BIN1_SMEM = 8 * 2048 * 4;     // 8 warps x 2048 slots
+constexpr size_t BIN2_SMEM = 16384 * 4;
+constexpr size_t SMEM_BITMAP_MAX = 200 * 1024;
+
+static void set_smem_attrs() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    cudaFuncSetAttribute(k_spgemm_warp<11, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)BIN1_SMEM);
+    cudaFuncSetAttribute(k_spgemm_cta<14>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)BIN2_SMEM);
+    cudaFuncSetAttribute(k_spgemm_bitmap, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SMEM_BITMAP_MAX);
+    cudaFuncSetAttribute(k_extract_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SMEM_BITMAP_MAX);
+}
+
+void launch_symbolic(const SlotTab &S, const ProdTab &P, const WorkBufs &W, int prod_only,
+                     int sms, cudaStream_t st) {
+    k_symbolic<<<sms * 8, 256, 0, st>>>(S, P, W, prod_only);
+}
+
+void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &W,
+                   uint32_t max_n, int sms, cudaStream_t st) {
+    set_smem_attrs();
+    switch (bin) {
+    case 0:
+        k_spgemm_warp<8, 8><<<sms * 8, 256, 8 * 256 * 4, st>>>(S, P, W, 0);
+        break;
+    case 1:
+        k_spgemm_warp<11, 8><<<sms * 3, 256, BIN1_SMEM, st>>>(S, P, W, 1);
+        break;
+    case 2:
+        k_spgemm_cta<14><<<sms * 3, 256, BIN2_SMEM, st>>>(S, P, W, 2);
+        break;
+    default: {
+        const size_t bm_bytes = (size_t)((max_n + 31) / 32) * 4;
+        const bool sm = bm_bytes <= SMEM_BITMAP_MAX;
+        int per_sm = sm ? (int)((220 * 1024) / (bm_bytes + 1024)) : 4;
+        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+        k_spgemm_bitmap<<<sms * per_sm, 256, sm ? bm_bytes : 0, st>>>(S, P, W, 3, sm ? 1 : 0);
+        break;
+    }
+    }
+}
+
+void launch_commit(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {
+    k_commit<<<sms * 8, 256, 0, st>>>(S, W);
+}
+
+void launch_reset_dnew(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {
+    k_reset_dnew<<<sms * 4, 256, 0, st>>>(S, W);
+}
+
+void launch_count(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {
+    k_count<<<sms * 8, 256, 0, st>>>(S, W);
+}
+
+void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, int sms,
+                     cudaStream_t st) {
+    k_capacity<<<sms * 8, 256, 0, st>>>(S, I, W);
+}
+
+void launch_scatter(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {
+    k_scatter<<<sms * 8, 256, 0, st>>>(S, W);
+}
+
+void launch_init_edges(const uint32_t *src, const uint32_t *lab, const uint32_t *dst,
+                       unsigned long long n_edges, const uint32_t *term_off,
+                       const uint32_t *term_slot, uint32_t n_terms, const WorkBufs &W,
+                       int sms, cudaStream_t st) {
+    if (!n_edges) return;
+    k_init_edges<<<grid_for(n_edges, 256, sms, 8), 256, 0, st>>>(src, lab, dst, n_edges,
+                                                                  term_off, term_slot, n_terms, W);
+}
+
+void launch_init_eps(uint32_t slot, uint32_t n, const WorkBufs &W, int sms, cudaStream_t st) {
+    if (!n) return;
+    k_init_eps<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(slot, n, W);
+}
+
+void launch_rehash(const unsigned long long *old_tab, unsigned long long old_cap,
+                   unsigned long long *new_tab, unsigned long long new_cap, int sms,
+                   cudaStream_t st) {
+    k_rehash<<<grid_for(old_cap, 256, sms, 8), 256, 0, st>>>(old_tab, old_cap, new_tab, new_cap);
+}
+
+void launch_fill_u64(unsigned long long *p, unsigned long long count, unsigned long long v,
+                     int sms, cudaStream_t st) {
+    if (!count) return;
+    k_fill_u64<<<grid_for(count, 256, sms, 8), 256, 0, st>>>(p, count, v);
+}
+
+void launch_remap_touched(const uint2 *in, unsigned long long n, uint32_t slot_base,
+                          uint2 *out, cudaStream_t st) {
+    if (!n) return;
+    k_remap_touched<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(in, n, slot_base, out);
+}
+
+void launch_row_lengths(const uint4 *desc, uint32_t n, uint32_t *len, cudaStream_t st) {
+    if (!n) return;
+    k_row_lengths<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(desc, n, len);
+}
+
+void launch_extract(const uint4 *desc, const uint32_t *pool, uint32_t n,
+                    const unsigned long long *row_out, uint32_t *out_src, uint32_t *out_dst,
+                    uint32_t *big_rows, uint32_t *big_count, uint32_t *bitmap, int sms,
+                    cudaStream_t st) {
+    if (!n) return;
+    set_smem_attrs();
+    cudaMemsetAsync(big_count, 0, sizeof(uint32_t), st);
+    k_extract_small<<<grid_for(n, 8, sms, 8), 256, 0, st>>>(desc, pool, n, row_out, out_src,
+                                                            out_dst, big_rows, big_count);
+    const size_t bm_bytes = (size_t)((n + 31) / 32) * 4;
+    const bool sm = bm_bytes <= SMEM_BITMAP_MAX;
+    k_extract_big<<<sms * 4, 256, sm ? bm_bytes : 0, st>>>(desc, pool, n, row_out, out_src,
+                                                           out_dst, big_rows, big_count, bitmap,
+                                                           sm ? 1 : 0);
+}
+
+}  // namespace cflr

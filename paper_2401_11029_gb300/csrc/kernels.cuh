@@ -1,0 +1,127 @@
+// Device data layout and kernel entry points of the CFL-r closure loop.
+//
+// Layout in HBM (one "slot" = one non-terminal of one solved instance):
+//   desc[s]     uint4 per row and orientation, 2*n entries per slot:
+//                 [0, n)  row form    (row i -> the j with M(i, j))
+//                 [n, 2n) column form (column j -> the i with M(i, j))
+//               .x = offset of the row in the instance pool (uint32 entries)
+//               .y = length, .z = capacity, .w = entries appended by the last
+//               merge ("dnew").  The row's last dnew entries are the delta of
+//               optimisation 1; the first len-dnew are M_old.
+//   pool        uint32 arena of row segments; rows grow by relocation.
+//   htab[s]     open-addressing set of 64-bit keys (i << 32 | j): every pair
+//               of M_s, used for the complement mask and for deduplication.
+// Work items refer to slots, so one launch covers many instances.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cflr {
+
+constexpr uint32_t PART_A = 0;      // dA . B     : row groups of a's delta
+constexpr uint32_t PART_B = 1;      // A_old . dB : column groups of b's delta
+constexpr uint32_t PART_U = 2;      // c -> a     : row groups of a's delta
+constexpr uint32_t MODE_PROBE = 4;  // group code bit: mask by probing htab[c]
+constexpr unsigned long long EMPTY_KEY = ~0ull;
+constexpr uint32_t EMPTY32 = 0xFFFFFFFFu;
+
+constexpr int N_BINS = 4;
+// Bin limits on a group's smem need (mask entries + products); a bin's table
+// holds twice its limit so the load factor stays <= 1/2.
+constexpr uint32_t BIN0_LIMIT = 128;    // warp per group, 256-slot table
+constexpr uint32_t BIN1_LIMIT = 1024;   // warp per group, 2048-slot table
+constexpr uint32_t BIN2_LIMIT = 8192;   // CTA per group, 16384-slot table
+                                        // bin 3: CTA per group, n-bit bitmap
+constexpr uint32_t PROBE_RATIO = 4;     // probe when mask_len > PROBE_RATIO*flops
+
+struct SlotTab {              // per slot (device arrays, length n_slots)
+    uint4 **desc;             // row descriptors (2*n per slot)
+    uint32_t **pool;          // instance pool of the slot
+    uint32_t *n;              // vertices of the slot's instance
+    uint32_t *inst;           // instance index of the slot
+    unsigned long long **htab;
+    unsigned long long *hmask;      // capacity - 1
+    unsigned long long *cand;       // candidates emitted for the slot (iteration)
+    unsigned long long *delta;      // new pairs of the slot (iteration)
+};
+
+struct InstTab {              // per instance
+    unsigned long long *pool_top;   // entries in use (device counters)
+    unsigned long long *pool_cap;
+};
+
+struct ProdTab {              // global production table of the batch
+    const uint4 *prod;        // {c_slot, a_slot, b_slot, kind(0 binary, 1 unit)}
+    const uint32_t *use_off;  // per slot*2+o: offsets into use_code
+    const uint32_t *use_code; // prod << 2 | part
+};
+
+struct Counters {
+    unsigned long long groups[N_BINS];
+    unsigned long long cand;
+    unsigned long long delta;
+    unsigned long long flops;
+    unsigned long long bytes_bin[N_BINS];
+    unsigned long long bytes_sym;
+    unsigned int overflow;          // OVF_* bits
+    unsigned int pad;
+};
+
+constexpr unsigned OVF_GROUPS = 1u;
+constexpr unsigned OVF_CAND = 2u;
+constexpr unsigned OVF_POOL = 4u;
+constexpr unsigned OVF_TOUCHED = 8u;
+
+struct WorkBufs {
+    // touched rows {slot*2+o, idx}: "in" = rows whose dnew > 0 (this
+    // iteration's deltas), "out" = rows the current merge appends to
+    uint2 *touched_in;  const unsigned long long *touched_in_n;   // device count
+    uint2 *touched_out; unsigned long long *touched_out_n; unsigned long long touched_cap;
+    uint2 *groups[N_BINS]; unsigned long long group_cap[N_BINS];   // {code, idx}
+    unsigned long long *cand_key; uint32_t *cand_slot; unsigned long long cand_cap;
+    unsigned long long *delta_key; uint32_t *delta_slot;
+    uint32_t *bitmap_scratch; unsigned long long bitmap_words;  // per CTA, global
+    Counters *cnt;
+};
+
+// ---- launch wrappers (kernels.cu) -------------------------------------
+void launch_symbolic(const SlotTab &S, const ProdTab &P, const WorkBufs &W, int prod_only,
+                     int sms, cudaStream_t st);
+void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &W,
+                   uint32_t max_n, int sms, cudaStream_t st);
+void launch_commit(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
+void launch_reset_dnew(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
+void launch_count(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
+void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, int sms,
+                     cudaStream_t st);
+void launch_scatter(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
+
+void launch_init_edges(const uint32_t *src, const uint32_t *lab, const uint32_t *dst,
+                       unsigned long long n_edges, const uint32_t *term_off,
+                       const uint32_t *term_slot, uint32_t n_terms, const WorkBufs &W,
+                       int sms, cudaStream_t st);
+void launch_init_eps(uint32_t slot, uint32_t n, const WorkBufs &W, int sms, cudaStream_t st);
+void launch_rehash(const unsigned long long *old_tab, unsigned long long old_cap,
+                   unsigned long long *new_tab, unsigned long long new_cap, int sms,
+                   cudaStream_t st);
+void launch_fill_u64(unsigned long long *p, unsigned long long count, unsigned long long v,
+                     int sms, cudaStream_t st);
+void launch_remap_touched(const uint2 *in, unsigned long long n, uint32_t slot_base,
+                          uint2 *out, cudaStream_t st);
+
+// out[i] = in[0] + ... + in[i-1]; bsum: ceil(n/1024) scratch; grand (nullable)
+// receives the total.
+void launch_exclusive_scan(const uint32_t *in, uint32_t n, unsigned long long *out,
+                           unsigned long long *bsum, unsigned long long *grand, cudaStream_t st);
+
+// Extraction of one non-terminal's pairs, sorted by (src, dst).
+void launch_row_lengths(const uint4 *desc, uint32_t n, uint32_t *len, cudaStream_t st);
+// big_rows: scratch of n uint32 plus one counter; bitmap: scratch of
+// sms*4*ceil(n/32) words used when a row bitmap does not fit shared memory.
+void launch_extract(const uint4 *desc, const uint32_t *pool, uint32_t n,
+                    const unsigned long long *row_out, uint32_t *out_src, uint32_t *out_dst,
+                    uint32_t *big_rows, uint32_t *big_count, uint32_t *bitmap, int sms,
+                    cudaStream_t st);
+
+}  // namespace cflr

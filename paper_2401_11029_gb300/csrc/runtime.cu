@@ -1,0 +1,1226 @@
+// Host runtime of the CFL-reachability library: contexts, device memory,
+// the closure-loop driver and the C ABI of include/cflr.h.
+//
+// The driver runs Algorithm 1's closure loop with optimisation 1 (paper
+// Sec. 2-3): per iteration it builds the work list from the rows that grew in
+// the last merge, runs the masked products, deduplicates the candidates into
+// the new pairs and appends them.  Every buffer whose size depends on data
+// (work list, candidates, hash sets, pool) is checked after the phase that
+// fills it; on overflow the phase is re-run with a larger buffer before any
+// matrix changes, so growth never loses or duplicates a pair.
+#include "cflr.h"
+#include "grammar.h"
+#include "kernels.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+using namespace cflr;
+
+namespace {
+
+enum { ST_CREATED = 0, ST_GRAMMAR = 1, ST_GRAPH = 2, ST_SOLVED = 3 };
+
+enum KernelId {
+    KID_SYMBOLIC = 0, KID_BIN0, KID_BIN1, KID_BIN2, KID_BIN3, KID_COMMIT, KID_RESET,
+    KID_COUNT, KID_CAPACITY, KID_SCATTER, KID_INIT, KID_REHASH, N_KID
+};
+const char *kKernelNames[N_KID] = {
+    "k_symbolic", "k_spgemm_bin0", "k_spgemm_bin1", "k_spgemm_bin2", "k_spgemm_bin3",
+    "k_commit", "k_reset_dnew", "k_count", "k_capacity", "k_scatter", "k_init", "k_rehash"};
+
+struct CudaError {
+    cudaError_t e;
+    const char *what;
+};
+
+inline void ck(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) throw CudaError{e, what};
+}
+
+struct Status {
+    int code;
+    std::string msg;
+};
+
+inline uint64_t next_pow2(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+struct Runner;
+
+}  // namespace
+
+struct cflr_ctx {
+    cflr_config cfg{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 152;
+    size_t smem_optin = 0;
+    std::string err;
+    int state = ST_CREATED;
+    Grammar g;
+    // graph and matrices
+    uint32_t n = 0;
+    uint64_t ignored = 0;
+    uint4 *desc = nullptr;              // n_nt * 2 * n descriptors
+    uint32_t *pool = nullptr;
+    uint64_t pool_cap = 0;
+    uint64_t pool_top = 0;              // host mirror between solves
+    std::vector<unsigned long long *> htab;
+    std::vector<uint64_t> hcap;
+    std::vector<uint64_t> nnz;
+    uint2 *touched = nullptr;           // rows with dnew > 0 (local slot ids)
+    uint64_t touched_n = 0;
+    uint64_t touched_cap = 0;
+    uint32_t iterations = 0;
+    // the graph as loaded (device copies, kept for cflr_reset)
+    uint64_t m_edges = 0, n_init = 0;
+    uint32_t *e_src = nullptr, *e_lab = nullptr, *e_dst = nullptr;
+    uint32_t *t_off = nullptr, *t_slot = nullptr;
+    size_t t_off_n = 0, t_slot_n = 0;
+    std::vector<uint64_t> init_cnt;
+    Runner *runner = nullptr;           // cached work buffers of solves led by this context
+    // extraction scratch
+    uint32_t *x_len = nullptr, *x_big = nullptr, *x_bm = nullptr;
+    unsigned long long *x_off = nullptr, *x_bsum = nullptr;
+    size_t x_n = 0, x_bm_n = 0;
+    uint32_t *x_src = nullptr, *x_dst = nullptr;
+    uint64_t x_out_cap = 0;
+    // accounting
+    uint64_t bytes_now = 0, bytes_peak = 0;
+    cflr_stats last{};
+    // profiling (per kernel)
+    uint64_t k_launches[N_KID] = {};
+    double k_ms[N_KID] = {};
+    uint64_t k_bytes[N_KID] = {};
+
+    int fail(int code, const std::string &m) {
+        err = m;
+        return code;
+    }
+
+    void *dalloc(size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        if (cfg.mem_budget_bytes && bytes_now + bytes > cfg.mem_budget_bytes)
+            throw Status{CFLR_ENOMEM, "device memory budget exceeded (" +
+                                          std::to_string(bytes_now + bytes) + " > " +
+                                          std::to_string(cfg.mem_budget_bytes) + " bytes)"};
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            throw Status{CFLR_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+        }
+        ck(e, "cudaMalloc");
+        bytes_now += bytes;
+        bytes_peak = std::max(bytes_peak, bytes_now);
+        return p;
+    }
+    void dfree(void *p, size_t bytes) {
+        if (!p) return;
+        if (bytes == 0) bytes = 16;
+        cudaFree(p);
+        bytes_now -= std::min(bytes_now, (uint64_t)bytes);
+    }
+
+    // extraction scratch (row lengths, offsets, long-row list, bitmaps)
+    void free_extract_scratch() {
+        if (x_len) dfree(x_len, x_n * 4);
+        if (x_big) dfree(x_big, (x_n + 1) * 4);
+        if (x_off) dfree(x_off, x_n * 8);
+        if (x_bsum) dfree(x_bsum, (x_n / 1024 + 2) * 8);
+        if (x_bm) dfree(x_bm, x_bm_n * 4);
+        x_len = x_big = x_bm = nullptr;
+        x_off = x_bsum = nullptr;
+        x_n = x_bm_n = 0;
+    }
+    // device staging of cflr_get_pairs's host output
+    void free_extract_out() {
+        if (x_src) dfree(x_src, x_out_cap * 4);
+        if (x_dst) dfree(x_dst, x_out_cap * 4);
+        x_src = x_dst = nullptr;
+        x_out_cap = 0;
+    }
+
+    void free_graph() {
+        free_extract_scratch();
+        free_extract_out();
+        if (e_src) dfree(e_src, m_edges * 4);
+        if (e_lab) dfree(e_lab, m_edges * 4);
+        if (e_dst) dfree(e_dst, m_edges * 4);
+        if (t_off) dfree(t_off, t_off_n * 4);
+        if (t_slot) dfree(t_slot, t_slot_n * 4);
+        e_src = e_lab = e_dst = t_off = t_slot = nullptr;
+        m_edges = n_init = 0;
+        t_off_n = t_slot_n = 0;
+        init_cnt.clear();
+        uint32_t nt = (uint32_t)g.nts.size();
+        if (desc) dfree(desc, (size_t)nt * 2 * n * sizeof(uint4));
+        desc = nullptr;
+        if (pool) dfree(pool, pool_cap * 4);
+        pool = nullptr;
+        pool_cap = pool_top = 0;
+        for (size_t s = 0; s < htab.size(); s++)
+            if (htab[s]) dfree(htab[s], hcap[s] * 8);
+        htab.clear();
+        hcap.clear();
+        nnz.clear();
+        if (touched) dfree(touched, touched_cap * sizeof(uint2));
+        touched = nullptr;
+        touched_n = touched_cap = 0;
+        n = 0;
+        iterations = 0;
+    }
+};
+
+namespace {
+
+// Per-kernel CUDA-event timing on the solve stream (profile mode).
+struct Prof {
+    cflr_ctx *owner;
+    bool on;
+    cudaStream_t st;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    std::vector<cudaEvent_t> free_ev;
+    cudaEvent_t get() {
+        if (!free_ev.empty()) {
+            cudaEvent_t e = free_ev.back();
+            free_ev.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        ck(cudaEventCreate(&e), "cudaEventCreate");
+        return e;
+    }
+    template <class F>
+    void run(int kid, F f) {
+        if (!on) {
+            f();
+            ck(cudaGetLastError(), kKernelNames[kid]);
+            return;
+        }
+        cudaEvent_t a = get(), b = get();
+        ck(cudaEventRecord(a, st), "cudaEventRecord");
+        f();
+        ck(cudaGetLastError(), kKernelNames[kid]);
+        ck(cudaEventRecord(b, st), "cudaEventRecord");
+        marks.push_back({kid, {a, b}});
+    }
+    void collect() {
+        for (auto &m : marks) {
+            float ms = 0;
+            ck(cudaEventSynchronize(m.second.second), "cudaEventSynchronize");
+            ck(cudaEventElapsedTime(&ms, m.second.first, m.second.second), "cudaEventElapsedTime");
+            owner->k_ms[m.first] += ms;
+            owner->k_launches[m.first] += 1;
+            free_ev.push_back(m.second.first);
+            free_ev.push_back(m.second.second);
+        }
+        marks.clear();
+    }
+    ~Prof() {
+        for (auto &m : marks) {
+            cudaEventDestroy(m.second.first);
+            cudaEventDestroy(m.second.second);
+        }
+        for (auto e : free_ev) cudaEventDestroy(e);
+    }
+};
+
+template <class T>
+struct DevArr {           // device array owned by a context's accounting
+    cflr_ctx *o = nullptr;
+    T *p = nullptr;
+    size_t n = 0;
+    void alloc(cflr_ctx *owner, size_t count) {
+        release();
+        o = owner;
+        n = count;
+        p = (T *)o->dalloc(std::max<size_t>(count, 1) * sizeof(T));
+    }
+    void release() {
+        if (p) o->dfree(p, std::max<size_t>(n, 1) * sizeof(T));
+        p = nullptr;
+        n = 0;
+    }
+    void ensure(cflr_ctx *owner, size_t count) {   // grow-only, contents dropped
+        if (!p || count > n) alloc(owner, count);
+    }
+    ~DevArr() { release(); }
+};
+
+// The closure-loop driver over one or more contexts (a batch).  Every
+// context's non-terminals get global slot ids; work items name slots, so
+// one launch sequence serves the whole batch.
+struct Runner {
+    std::vector<cflr_ctx *> cx;
+    cflr_ctx *own;
+    cudaStream_t st;
+    int sms;
+    Prof prof;
+    std::vector<uint32_t> base;        // first slot of each context
+    uint32_t n_slots = 0, n_prods = 0;
+    uint32_t max_n = 0;
+    std::vector<uint32_t> slot_ctx;    // slot -> context index
+    // device tables
+    DevArr<uint4 *> d_desc;
+    DevArr<uint32_t *> d_pool;
+    DevArr<uint32_t> d_n, d_inst;
+    DevArr<unsigned long long *> d_htab;
+    DevArr<unsigned long long> d_hmask, d_cand, d_delta;
+    DevArr<unsigned long long> d_pool_top, d_pool_cap;
+    DevArr<uint4> d_prod;
+    DevArr<uint32_t> d_use_off, d_use_code;
+    // work buffers
+    DevArr<uint2> d_touched[2];
+    DevArr<unsigned long long> d_touched_n;   // [2]
+    int cur = 0;                              // d_touched[cur] = this iteration's input
+    DevArr<uint2> d_groups[N_BINS];
+    DevArr<unsigned long long> d_cand_key, d_delta_key;
+    DevArr<uint32_t> d_cand_slot, d_delta_slot;
+    DevArr<uint32_t> d_bitmap;
+    DevArr<Counters> d_cnt;
+    Counters *h_cnt = nullptr;                // pinned
+    unsigned long long *h_small = nullptr;    // pinned scratch for small reads
+    size_t h_small_n = 0;
+    uint64_t cand_cap = 0, touched_cap = 0;
+    uint64_t group_cap[N_BINS] = {};
+    std::vector<uint64_t> host_slot_n;        // per slot: vertices
+    // per-iteration host copies
+    std::vector<unsigned long long> h_cand, h_delta;
+    uint64_t total_flops = 0, total_cand = 0, regrows = 0;
+
+    explicit Runner(cflr_ctx *owner) : own(owner), st(owner->stream), sms(owner->sms) {
+        prof.owner = own;
+        prof.on = own->cfg.profile != 0;
+        prof.st = st;
+        ck(cudaMallocHost(&h_cnt, sizeof(Counters)), "cudaMallocHost");
+    }
+    // Point the runner at a batch of contexts (their matrices must be loaded).
+    void bind(std::vector<cflr_ctx *> ctxs) {
+        cx = std::move(ctxs);
+        cur = 0;
+        total_flops = total_cand = regrows = 0;
+        build_tables();
+    }
+    ~Runner() {
+        if (h_cnt) cudaFreeHost(h_cnt);
+        if (h_small) cudaFreeHost(h_small);
+    }
+
+    unsigned long long *small(size_t n) {
+        if (n > h_small_n) {
+            if (h_small) cudaFreeHost(h_small);
+            h_small_n = std::max<size_t>(n, 64);
+            ck(cudaMallocHost(&h_small, h_small_n * 8), "cudaMallocHost");
+        }
+        return h_small;
+    }
+
+    // ---- tables ---------------------------------------------------------
+    void build_tables() {
+        base.clear();
+        slot_ctx.clear();
+        n_slots = 0;
+        max_n = 0;
+        for (size_t k = 0; k < cx.size(); k++) {
+            base.push_back(n_slots);
+            uint32_t nt = (uint32_t)cx[k]->g.nts.size();
+            for (uint32_t x = 0; x < nt; x++) slot_ctx.push_back((uint32_t)k);
+            n_slots += nt;
+            max_n = std::max(max_n, cx[k]->n);
+        }
+        std::vector<uint4 *> hd(n_slots);
+        std::vector<uint32_t *> hp(n_slots);
+        std::vector<uint32_t> hn(n_slots), hi(n_slots);
+        host_slot_n.assign(n_slots, 0);
+        std::vector<uint4> prods;
+        std::vector<std::vector<uint32_t>> uses((size_t)n_slots * 2);
+        for (size_t k = 0; k < cx.size(); k++) {
+            cflr_ctx *c = cx[k];
+            uint32_t nt = (uint32_t)c->g.nts.size(), b0 = base[k];
+            for (uint32_t x = 0; x < nt; x++) {
+                hd[b0 + x] = c->desc + (size_t)x * 2 * c->n;
+                hp[b0 + x] = c->pool;
+                hn[b0 + x] = c->n;
+                hi[b0 + x] = (uint32_t)k;
+                host_slot_n[b0 + x] = c->n;
+            }
+            const Grammar &g = c->g;
+            for (size_t p = 0; p < g.bin_c.size(); p++) {
+                uint32_t id = (uint32_t)prods.size();
+                prods.push_back(make_uint4(b0 + g.bin_c[p], b0 + g.bin_a[p], b0 + g.bin_b[p], 0));
+                uses[(size_t)(b0 + g.bin_a[p]) * 2 + 0].push_back(id << 2 | PART_A);
+                uses[(size_t)(b0 + g.bin_b[p]) * 2 + 1].push_back(id << 2 | PART_B);
+            }
+            for (size_t p = 0; p < g.unit_c.size(); p++) {
+                uint32_t id = (uint32_t)prods.size();
+                prods.push_back(make_uint4(b0 + g.unit_c[p], b0 + g.unit_a[p], 0, 1));
+                uses[(size_t)(b0 + g.unit_a[p]) * 2 + 0].push_back(id << 2 | PART_U);
+            }
+        }
+        n_prods = (uint32_t)prods.size();
+        std::vector<uint32_t> off(1, 0), codes;
+        for (auto &u : uses) {
+            codes.insert(codes.end(), u.begin(), u.end());
+            off.push_back((uint32_t)codes.size());
+        }
+        d_desc.ensure(own, n_slots);
+        d_pool.ensure(own, n_slots);
+        d_n.ensure(own, n_slots);
+        d_inst.ensure(own, n_slots);
+        d_htab.ensure(own, n_slots);
+        d_hmask.ensure(own, n_slots);
+        d_cand.ensure(own, n_slots);
+        d_delta.ensure(own, n_slots);
+        d_prod.ensure(own, prods.size());
+        d_use_off.ensure(own, off.size());
+        d_use_code.ensure(own, codes.size());
+        d_pool_top.ensure(own, cx.size());
+        d_pool_cap.ensure(own, cx.size());
+        ck(cudaMemcpyAsync(d_desc.p, hd.data(), n_slots * sizeof(uint4 *), cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_pool.p, hp.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_n.p, hn.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_inst.p, hi.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
+        if (!prods.empty())
+            ck(cudaMemcpyAsync(d_prod.p, prods.data(), prods.size() * sizeof(uint4), cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_use_off.p, off.data(), off.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
+        if (!codes.empty())
+            ck(cudaMemcpyAsync(d_use_code.p, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
+        upload_htabs();
+        upload_pools();
+        ck(cudaStreamSynchronize(st), "sync tables");
+    }
+
+    void upload_htabs() {
+        std::vector<unsigned long long *> ht(n_slots);
+        std::vector<unsigned long long> hm(n_slots);
+        for (uint32_t s = 0; s < n_slots; s++) {
+            cflr_ctx *c = cx[slot_ctx[s]];
+            uint32_t x = s - base[slot_ctx[s]];
+            ht[s] = c->htab[x];
+            hm[s] = c->hcap[x] - 1;
+        }
+        ck(cudaMemcpyAsync(d_htab.p, ht.data(), n_slots * 8, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_hmask.p, hm.data(), n_slots * 8, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaStreamSynchronize(st), "sync");
+    }
+
+    void upload_pools() {
+        std::vector<unsigned long long> top(cx.size()), cap(cx.size());
+        std::vector<uint32_t *> hp(n_slots);
+        for (size_t k = 0; k < cx.size(); k++) {
+            top[k] = cx[k]->pool_top;
+            cap[k] = cx[k]->pool_cap;
+        }
+        for (uint32_t s = 0; s < n_slots; s++) hp[s] = cx[slot_ctx[s]]->pool;
+        ck(cudaMemcpyAsync(d_pool_top.p, top.data(), cx.size() * 8, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_pool_cap.p, cap.data(), cx.size() * 8, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_pool.p, hp.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaStreamSynchronize(st), "sync");
+    }
+
+    void download_pool_tops() {
+        unsigned long long *h = small(cx.size());
+        ck(cudaMemcpyAsync(h, d_pool_top.p, cx.size() * 8, cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaStreamSynchronize(st), "sync");
+        for (size_t k = 0; k < cx.size(); k++) cx[k]->pool_top = h[k];
+    }
+
+    SlotTab slots() {
+        SlotTab S;
+        S.desc = d_desc.p; S.pool = d_pool.p; S.n = d_n.p; S.inst = d_inst.p;
+        S.htab = d_htab.p; S.hmask = d_hmask.p; S.cand = d_cand.p; S.delta = d_delta.p;
+        return S;
+    }
+    ProdTab prodtab() {
+        ProdTab P;
+        P.prod = d_prod.p; P.use_off = d_use_off.p; P.use_code = d_use_code.p;
+        return P;
+    }
+    InstTab insttab() {
+        InstTab I;
+        I.pool_top = d_pool_top.p; I.pool_cap = d_pool_cap.p;
+        return I;
+    }
+    WorkBufs work() {
+        WorkBufs W{};
+        W.touched_in = d_touched[cur].p;
+        W.touched_in_n = d_touched_n.p + cur;
+        W.touched_out = d_touched[cur ^ 1].p;
+        W.touched_out_n = d_touched_n.p + (cur ^ 1);
+        W.touched_cap = touched_cap;
+        for (int b = 0; b < N_BINS; b++) {
+            W.groups[b] = d_groups[b].p;
+            W.group_cap[b] = group_cap[b];
+        }
+        W.cand_key = d_cand_key.p; W.cand_slot = d_cand_slot.p; W.cand_cap = cand_cap;
+        W.delta_key = d_delta_key.p; W.delta_slot = d_delta_slot.p;
+        W.bitmap_scratch = d_bitmap.p;
+        W.bitmap_words = (max_n + 31) / 32;
+        W.cnt = d_cnt.p;
+        return W;
+    }
+
+    // ---- buffers ----------------------------------------------------------
+    // smallest first sizes; cfg.initial_capacity lowers them (growth tests)
+    uint64_t min_cap(uint64_t dflt) const {
+        return own->cfg.initial_capacity ? std::max<uint64_t>(own->cfg.initial_capacity, 32)
+                                         : dflt;
+    }
+    void size_cand(uint64_t cap) {
+        cap = std::max<uint64_t>(cap, min_cap(1 << 16));
+        if (cap <= cand_cap) return;
+        cand_cap = cap;
+        d_cand_key.alloc(own, cap);
+        d_cand_slot.alloc(own, cap);
+        d_delta_key.alloc(own, cap);
+        d_delta_slot.alloc(own, cap);
+    }
+    // touched lists must hold two rows per new pair (row and column form)
+    void size_touched(uint64_t cap, bool keep_in) {
+        cap = std::max<uint64_t>(cap, min_cap(1 << 16));
+        if (cap <= touched_cap) return;
+        DevArr<uint2> nin;
+        nin.alloc(own, cap);
+        if (keep_in && d_touched[cur].p) {
+            ck(cudaMemcpyAsync(nin.p, d_touched[cur].p, touched_cap * sizeof(uint2),
+                               cudaMemcpyDeviceToDevice, st), "D2D");
+            ck(cudaStreamSynchronize(st), "sync");
+        }
+        std::swap(d_touched[cur].p, nin.p);
+        std::swap(d_touched[cur].n, nin.n);
+        d_touched[cur].o = own;
+        nin.release();
+        d_touched[cur ^ 1].alloc(own, cap);
+        touched_cap = cap;
+    }
+    void size_groups(int b, uint64_t cap) {
+        cap = std::max<uint64_t>(cap, min_cap(1 << 14));
+        if (cap <= group_cap[b]) return;
+        group_cap[b] = cap;
+        d_groups[b].alloc(own, cap);
+    }
+    void init_buffers(uint64_t cand_hint, uint64_t touched_in) {
+        d_touched_n.ensure(own, 2);
+        d_cnt.ensure(own, 1);
+        const uint64_t ic = own->cfg.initial_capacity;
+        size_cand(ic ? std::max<uint64_t>(ic, 32) : cand_hint);
+        size_touched(std::max<uint64_t>(2 * cand_cap, touched_in), false);
+        for (int b = 0; b < N_BINS; b++) size_groups(b, ic ? ic : (b < 2 ? 1 << 18 : 1 << 14));
+        ck(cudaMemsetAsync(d_touched_n.p, 0, 16, st), "memset");
+        if (max_n > 200 * 1024 * 8) {   // bitmaps do not fit shared memory
+            uint64_t words = (max_n + 31) / 32;
+            d_bitmap.ensure(own, words * (uint64_t)sms * 8);
+        }
+    }
+
+    void grow_htab(uint32_t s, uint64_t need) {
+        cflr_ctx *c = cx[slot_ctx[s]];
+        uint32_t x = s - base[slot_ctx[s]];
+        uint64_t cap = next_pow2(std::max<uint64_t>(4 * need, 1024));
+        unsigned long long *nt = (unsigned long long *)c->dalloc(cap * 8);
+        ck(cudaMemsetAsync(nt, 0xFF, cap * 8, st), "memset");
+        prof.run(KID_REHASH, [&] { launch_rehash(c->htab[x], c->hcap[x], nt, cap, sms, st); });
+        own->k_bytes[KID_REHASH] += c->hcap[x] * 8 + nnz_of(s) * 8;
+        ck(cudaStreamSynchronize(st), "sync rehash");
+        c->dfree(c->htab[x], c->hcap[x] * 8);
+        c->htab[x] = nt;
+        c->hcap[x] = cap;
+    }
+    uint64_t &nnz_of(uint32_t s) { return cx[slot_ctx[s]]->nnz[s - base[slot_ctx[s]]]; }
+    uint64_t hcap_of(uint32_t s) { return cx[slot_ctx[s]]->hcap[s - base[slot_ctx[s]]]; }
+
+    void read_counters() {
+        ck(cudaMemcpyAsync(h_cnt, d_cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, st), "D2H");
+    }
+
+    // Commit the candidates in the buffer and merge the new pairs into the
+    // matrices.  Returns the number of new pairs.
+    uint64_t commit_and_merge(std::vector<unsigned long long> &slot_delta) {
+        // hash capacity: every slot's set must stay at most half full
+        unsigned long long *hc = small(n_slots);
+        ck(cudaMemcpyAsync(hc, d_cand.p, n_slots * 8, cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaStreamSynchronize(st), "sync");
+        bool grew = false;
+        for (uint32_t s = 0; s < n_slots; s++) {
+            uint64_t need = nnz_of(s) + hc[s];
+            if (2 * need > hcap_of(s)) {
+                grow_htab(s, need);
+                grew = true;
+            }
+        }
+        if (grew) upload_htabs();
+        const SlotTab S = slots();
+        const WorkBufs W = work();
+        uint64_t nc = std::min<uint64_t>(h_cnt->cand, cand_cap);
+        prof.run(KID_COMMIT, [&] { launch_commit(S, W, sms, st); });
+        prof.run(KID_RESET, [&] { launch_reset_dnew(S, W, sms, st); });
+        prof.run(KID_COUNT, [&] { launch_count(S, W, sms, st); });
+        prof.run(KID_CAPACITY, [&] { launch_capacity(S, insttab(), W, sms, st); });
+        read_counters();
+        unsigned long long *hs = small(2 + cx.size());
+        ck(cudaMemcpyAsync(hs, d_touched_n.p, 16, cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaMemcpyAsync(hs + 2, d_pool_top.p, cx.size() * 8, cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaStreamSynchronize(st), "sync merge");
+        uint64_t touched_in = hs[cur], touched_out = hs[cur ^ 1];
+        uint64_t nd = h_cnt->delta;
+        if (h_cnt->overflow & OVF_TOUCHED)
+            throw Status{CFLR_ECUDA, "internal: touched list overflow"};
+        int guard = 0;
+        while (h_cnt->overflow & OVF_POOL) {
+            if (++guard > 8) throw Status{CFLR_ENOMEM, "pool growth did not converge"};
+            for (size_t k = 0; k < cx.size(); k++) {
+                uint64_t top = hs[2 + k];
+                if (top > cx[k]->pool_cap) grow_pool(k, top);
+            }
+            upload_pools_caps_only();
+            unsigned zero = 0;
+            ck(cudaMemcpyAsync(&d_cnt.p->overflow, &zero, 4, cudaMemcpyHostToDevice, st), "H2D");
+            prof.run(KID_CAPACITY, [&] { launch_capacity(slots(), insttab(), work(), sms, st); });
+            read_counters();
+            ck(cudaMemcpyAsync(hs + 2, d_pool_top.p, cx.size() * 8, cudaMemcpyDeviceToHost, st), "D2H");
+            ck(cudaStreamSynchronize(st), "sync capacity");
+            regrows++;
+        }
+        prof.run(KID_SCATTER, [&] { launch_scatter(slots(), work(), sms, st); });
+        own->k_bytes[KID_COMMIT] += 20 * nc + 12 * nd;
+        own->k_bytes[KID_RESET] += 12 * touched_in;
+        own->k_bytes[KID_COUNT] += 20 * nd + 8 * touched_out;
+        own->k_bytes[KID_CAPACITY] += 24 * touched_out;
+        own->k_bytes[KID_SCATTER] += 52 * nd;
+        slot_delta.resize(n_slots);
+        ck(cudaMemcpyAsync(slot_delta.data(), d_delta.p, n_slots * 8, cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaStreamSynchronize(st), "sync scatter");
+        for (uint32_t s = 0; s < n_slots; s++) nnz_of(s) += slot_delta[s];
+        // the rows appended to become next iteration's delta rows
+        cur ^= 1;
+        ck(cudaMemsetAsync(d_touched_n.p + (cur ^ 1), 0, 8, st), "memset");
+        return nd;
+    }
+
+    // After a pool growth: new pool pointers and capacities; the device
+    // pool_top counters keep counting (they are ahead of any host copy).
+    void upload_pools_caps_only() {
+        std::vector<unsigned long long> cap(cx.size());
+        std::vector<uint32_t *> hp(n_slots);
+        for (size_t k = 0; k < cx.size(); k++) cap[k] = cx[k]->pool_cap;
+        for (uint32_t s = 0; s < n_slots; s++) hp[s] = cx[slot_ctx[s]]->pool;
+        ck(cudaMemcpyAsync(d_pool_cap.p, cap.data(), cx.size() * 8, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_pool.p, hp.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaStreamSynchronize(st), "sync");
+    }
+
+    void grow_pool(size_t k, uint64_t top) {
+        cflr_ctx *c = cx[k];
+        uint64_t cap = std::max<uint64_t>(2 * c->pool_cap, top + top / 2 + (1 << 20));
+        cap = std::min<uint64_t>(cap, 0xFFFFFFF0ull);
+        if (cap <= c->pool_cap || top > cap)
+            throw Status{CFLR_ENOMEM, "row pool exceeds 2^32 entries"};
+        uint32_t *np = (uint32_t *)c->dalloc(cap * 4);
+        ck(cudaMemcpyAsync(np, c->pool, c->pool_cap * 4, cudaMemcpyDeviceToDevice, st), "D2D");
+        ck(cudaStreamSynchronize(st), "sync pool");
+        c->dfree(c->pool, c->pool_cap * 4);
+        c->pool = np;
+        c->pool_cap = cap;
+        // descriptors of this context point into the old pool by offset only
+        regrows++;
+    }
+
+    // One closure iteration over every context of the batch.  Returns the
+    // number of new pairs; per-context counts in ctx_delta.
+    uint64_t iterate(std::vector<uint64_t> &ctx_delta) {
+        const SlotTab S = slots();
+        const ProdTab P = prodtab();
+        for (;;) {
+            ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(Counters), st), "memset");
+            ck(cudaMemsetAsync(d_cand.p, 0, n_slots * 8, st), "memset");
+            ck(cudaMemsetAsync(d_delta.p, 0, n_slots * 8, st), "memset");
+            const WorkBufs W = work();
+            if (own->cfg.form == CFLR_FORM_PLAIN) {
+                // one launch sequence per production, like one library mxm each
+                for (uint32_t p = 0; p < n_prods; p++) {
+                    prof.run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, (int)p, sms, st); });
+                    for (int b = 0; b < N_BINS; b++)
+                        prof.run(KID_BIN0 + b, [&] { launch_spgemm(b, S, P, W, max_n, sms, st); });
+                    ck(cudaMemsetAsync(d_cnt.p->groups, 0, sizeof(d_cnt.p->groups), st), "memset");
+                }
+            } else {
+                prof.run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, -1, sms, st); });
+                for (int b = 0; b < N_BINS; b++)
+                    prof.run(KID_BIN0 + b, [&] { launch_spgemm(b, S, P, W, max_n, sms, st); });
+            }
+            read_counters();
+            ck(cudaStreamSynchronize(st), "sync spgemm");
+            bool again = false;
+            if (h_cnt->overflow & OVF_GROUPS) {
+                for (int b = 0; b < N_BINS; b++) {
+                    uint64_t want = h_cnt->groups[b] > group_cap[b] ? h_cnt->groups[b] * 3 / 2 : 0;
+                    if (own->cfg.form == CFLR_FORM_PLAIN)   // counts were reset per production
+                        want = std::max<uint64_t>(want, 2 * group_cap[b]);
+                    if (want) size_groups(b, want);
+                }
+                again = true;
+            }
+            if (h_cnt->overflow & OVF_CAND) {
+                size_cand(h_cnt->cand * 3 / 2);
+                size_touched(2 * cand_cap, true);
+                again = true;
+            }
+            if (again) {
+                regrows++;
+                continue;
+            }
+            break;
+        }
+        total_flops += h_cnt->flops;
+        total_cand += h_cnt->cand;
+        own->k_bytes[KID_SYMBOLIC] += h_cnt->bytes_sym;
+        for (int b = 0; b < N_BINS; b++) own->k_bytes[KID_BIN0 + b] += h_cnt->bytes_bin[b];
+        std::vector<unsigned long long> sd;
+        uint64_t nd = commit_and_merge(sd);
+        ctx_delta.assign(cx.size(), 0);
+        for (uint32_t s = 0; s < n_slots; s++) ctx_delta[slot_ctx[s]] += sd[s];
+        prof.collect();
+        return nd;
+    }
+
+    // Import each context's pending delta rows into the work list.
+    void import_touched() {
+        uint64_t total = 0;
+        for (auto *c : cx) total += c->touched_n;
+        size_touched(std::max<uint64_t>(total, 2 * cand_cap), false);
+        uint64_t at = 0;
+        for (size_t k = 0; k < cx.size(); k++) {
+            cflr_ctx *c = cx[k];
+            if (c->touched_n)
+                launch_remap_touched(c->touched, c->touched_n, base[k], d_touched[cur].p + at, st);
+            ck(cudaGetLastError(), "remap");
+            at += c->touched_n;
+        }
+        unsigned long long *h = small(2);
+        h[0] = cur == 0 ? at : 0;
+        h[1] = cur == 1 ? at : 0;
+        ck(cudaMemcpyAsync(d_touched_n.p, h, 16, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaStreamSynchronize(st), "sync import");
+    }
+
+    // Save the pending delta rows of each context (local slot ids).
+    void export_touched() {
+        unsigned long long *h = small(2);
+        ck(cudaMemcpyAsync(h, d_touched_n.p, 16, cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaStreamSynchronize(st), "sync");
+        uint64_t n_in = h[cur];
+        std::vector<uint2> all(n_in);
+        if (n_in)
+            ck(cudaMemcpyAsync(all.data(), d_touched[cur].p, n_in * sizeof(uint2),
+                               cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaStreamSynchronize(st), "sync");
+        std::vector<std::vector<uint2>> per(cx.size());
+        for (auto &t : all) {
+            uint32_t s = t.x >> 1;
+            uint32_t k = slot_ctx[s];
+            per[k].push_back(make_uint2(t.x - 2 * base[k], t.y));
+        }
+        for (size_t k = 0; k < cx.size(); k++) {
+            cflr_ctx *c = cx[k];
+            if (per[k].size() > c->touched_cap) {
+                if (c->touched) c->dfree(c->touched, c->touched_cap * sizeof(uint2));
+                c->touched_cap = std::max<uint64_t>(per[k].size(), 1024);
+                c->touched = (uint2 *)c->dalloc(c->touched_cap * sizeof(uint2));
+            }
+            c->touched_n = per[k].size();
+            if (c->touched_n)
+                ck(cudaMemcpyAsync(c->touched, per[k].data(), c->touched_n * sizeof(uint2),
+                                   cudaMemcpyHostToDevice, st), "H2D");
+        }
+        ck(cudaStreamSynchronize(st), "sync");
+    }
+};
+
+Runner &runner_of(cflr_ctx *c) {
+    if (!c->runner) c->runner = new Runner(c);
+    c->runner->prof.on = c->cfg.profile != 0;
+    return *c->runner;
+}
+
+// Copy the graph to the device and size the matrices (cflr_load_graph).
+void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *lab,
+                  const uint32_t *dst) {
+    const Grammar &g = c->g;
+    const uint32_t nt = (uint32_t)g.nts.size(), nterm = (uint32_t)g.terms.size();
+    cudaStream_t st = c->stream;
+    // per-label edge counts -> per-non-terminal initial counts
+    std::vector<uint64_t> per_label(nterm, 0);
+    uint64_t ignored = 0;
+    for (uint64_t e = 0; e < m; e++) {
+        if (lab[e] < nterm && !g.term_nts[lab[e]].empty()) per_label[lab[e]]++;
+        else ignored++;
+    }
+    c->init_cnt.assign(nt, 0);
+    for (uint32_t l = 0; l < nterm; l++)
+        for (uint32_t A : g.term_nts[l]) c->init_cnt[A] += per_label[l];
+    for (uint32_t A : g.eps) c->init_cnt[A] += n;
+    c->n_init = 0;
+    for (uint32_t A = 0; A < nt; A++) c->n_init += c->init_cnt[A];
+    c->ignored = ignored;
+    c->n = n;
+    c->m_edges = m;
+    c->e_src = (uint32_t *)c->dalloc(m * 4);
+    c->e_lab = (uint32_t *)c->dalloc(m * 4);
+    c->e_dst = (uint32_t *)c->dalloc(m * 4);
+    if (m) {
+        ck(cudaMemcpyAsync(c->e_src, src, m * 4, cudaMemcpyHostToDevice, st), "H2D edges");
+        ck(cudaMemcpyAsync(c->e_lab, lab, m * 4, cudaMemcpyHostToDevice, st), "H2D edges");
+        ck(cudaMemcpyAsync(c->e_dst, dst, m * 4, cudaMemcpyHostToDevice, st), "H2D edges");
+    }
+    std::vector<uint32_t> toff(1, 0), tslot;
+    for (uint32_t l = 0; l < nterm; l++) {
+        tslot.insert(tslot.end(), g.term_nts[l].begin(), g.term_nts[l].end());
+        toff.push_back((uint32_t)tslot.size());
+    }
+    c->t_off_n = toff.size();
+    c->t_slot_n = std::max<size_t>(tslot.size(), 1);
+    c->t_off = (uint32_t *)c->dalloc(c->t_off_n * 4);
+    c->t_slot = (uint32_t *)c->dalloc(c->t_slot_n * 4);
+    ck(cudaMemcpyAsync(c->t_off, toff.data(), toff.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
+    if (!tslot.empty())
+        ck(cudaMemcpyAsync(c->t_slot, tslot.data(), tslot.size() * 4, cudaMemcpyHostToDevice, st),
+           "H2D");
+    c->desc = (uint4 *)c->dalloc((size_t)nt * 2 * n * sizeof(uint4));
+    c->pool_cap = std::min<uint64_t>(std::max<uint64_t>(16 * c->n_init, 1 << 16), 0xFFFFFFF0ull);
+    if (c->cfg.initial_capacity)   // small first pool: the growth path runs early
+        c->pool_cap = std::max<uint64_t>(8 * c->n_init / 5 + 4 * 2 * (uint64_t)nt, 64);
+    c->pool = (uint32_t *)c->dalloc(c->pool_cap * 4);
+    c->htab.assign(nt, nullptr);
+    c->hcap.assign(nt, 0);
+    c->nnz.assign(nt, 0);
+    for (uint32_t A = 0; A < nt; A++) {
+        c->hcap[A] = next_pow2(std::max<uint64_t>(4 * c->init_cnt[A], 1024));
+        c->htab[A] = (unsigned long long *)c->dalloc(c->hcap[A] * 8);
+    }
+}
+
+// Algorithm 1, terminal initialisation: M_A(i, j) = 1 for every edge
+// (i, x, j) and production A -> x, and the identity for every A -> eps.  The
+// initial pairs go through the same commit and merge as the closure loop, so
+// afterwards every row's entries are its delta (M_old is empty).
+void reset_matrices(cflr_ctx *c) {
+    const Grammar &g = c->g;
+    const uint32_t nt = (uint32_t)g.nts.size(), nterm = (uint32_t)g.terms.size();
+    const uint32_t n = c->n;
+    cudaStream_t st = c->stream;
+    ck(cudaMemsetAsync(c->desc, 0, (size_t)nt * 2 * n * sizeof(uint4), st), "memset");
+    for (uint32_t A = 0; A < nt; A++)
+        ck(cudaMemsetAsync(c->htab[A], 0xFF, c->hcap[A] * 8, st), "memset");
+    c->pool_top = 0;
+    std::fill(c->nnz.begin(), c->nnz.end(), 0);
+    c->iterations = 0;
+    c->touched_n = 0;
+    Runner &r = runner_of(c);
+    r.bind({c});
+    r.init_buffers(std::max<uint64_t>(c->n_init, 1), 0);
+    if (r.cand_cap < c->n_init) {      // the initial pairs are counted exactly
+        r.size_cand(c->n_init);
+        r.size_touched(2 * r.cand_cap, false);
+    }
+    ck(cudaMemsetAsync(r.d_cnt.p, 0, sizeof(Counters), st), "memset");
+    ck(cudaMemsetAsync(r.d_cand.p, 0, r.n_slots * 8, st), "memset");
+    ck(cudaMemsetAsync(r.d_delta.p, 0, r.n_slots * 8, st), "memset");
+    const WorkBufs W = r.work();
+    r.prof.run(KID_INIT, [&] {
+        launch_init_edges(c->e_src, c->e_lab, c->e_dst, c->m_edges, c->t_off, c->t_slot, nterm, W,
+                          c->sms, st);
+        for (uint32_t A : g.eps) launch_init_eps(A, n, W, c->sms, st);
+    });
+    c->k_bytes[KID_INIT] += 12 * c->m_edges + 12 * c->n_init;
+    r.read_counters();
+    ck(cudaStreamSynchronize(st), "sync init");
+    if (r.h_cnt->overflow & OVF_CAND) throw Status{CFLR_ECUDA, "internal: init overflow"};
+    // the hash sets were sized from the exact initial counts; per-slot
+    // candidate counts stay zero here, so commit directly
+    std::vector<unsigned long long> sd;
+    r.commit_and_merge(sd);
+    r.download_pool_tops();
+    r.export_touched();
+    r.prof.collect();
+}
+
+int finish_status(cflr_ctx *c, const Status &s) { return c->fail(s.code, s.msg); }
+
+int cuda_status(cflr_ctx *c, const CudaError &e) {
+    c->err = std::string(e.what) + ": " + cudaGetErrorString(e.e);
+    return CFLR_ECUDA;
+}
+
+int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
+    cflr_ctx *own = cx[0];
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    ck(cudaSetDevice(own->device), "cudaSetDevice");
+    std::vector<cflr_ctx *> active;
+    for (auto *c : cx)
+        if (c->touched_n) active.push_back(c);
+    std::vector<uint32_t> iters(cx.size(), 0);
+    std::vector<uint64_t> before(cx.size(), 0);
+    for (size_t k = 0; k < cx.size(); k++) {
+        cx[k]->k_launches[0] = cx[k]->k_launches[0];  // keep profile totals
+        iters[k] = cx[k]->iterations;
+    }
+    ck(cudaEventCreate(&ev0), "event");
+    ck(cudaEventCreate(&ev1), "event");
+    ck(cudaEventRecord(ev0, own->stream), "event");
+    int rc = CFLR_OK;
+    uint64_t flops = 0, cand = 0, regrows = 0;
+    if (!active.empty()) {
+        Runner &r = runner_of(own);
+        r.bind(active);
+        uint64_t hint = 0;
+        for (auto *c : active) hint += c->touched_n;
+        r.init_buffers(std::max<uint64_t>(hint * 4, 1 << 16), hint);
+        r.import_touched();
+        std::vector<uint64_t> cd;
+        std::vector<bool> done(active.size(), false);
+        uint32_t limit = own->cfg.max_iterations;
+        uint32_t it = 0;
+        for (;;) {
+            if (limit && it >= limit) {
+                rc = CFLR_ELIMIT;
+                break;
+            }
+            uint64_t nd = r.iterate(cd);
+            it++;
+            for (size_t k = 0; k < active.size(); k++) {
+                if (!done[k]) {
+                    active[k]->iterations++;
+                    if (cd[k] == 0) done[k] = true;
+                }
+            }
+            if (nd == 0) break;
+        }
+        r.download_pool_tops();
+        r.export_touched();
+        flops = r.total_flops;
+        cand = r.total_cand;
+        regrows = r.regrows;
+    }
+    ck(cudaEventRecord(ev1, own->stream), "event");
+    ck(cudaEventSynchronize(ev1), "event");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    for (size_t k = 0; k < cx.size(); k++) {
+        cflr_ctx *c = cx[k];
+        cflr_stats s{};
+        s.iterations = c->iterations;
+        for (uint32_t x = 0; x < c->g.n_named; x++) s.total_pairs += c->nnz[x];
+        s.solve_ms = ms;
+        s.peak_device_bytes = c->bytes_peak;
+        s.ignored_edges = c->ignored;
+        s.flops = flops;
+        s.candidates = cand;
+        s.regrows = regrows;
+        c->last = s;
+        if (stats) stats[k] = s;
+        if (rc == CFLR_OK) c->state = ST_SOLVED;
+    }
+    (void)before;
+    if (rc == CFLR_ELIMIT)
+        own->err = "max_iterations reached before the fixpoint";
+    return rc;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+void cflr_default_config(cflr_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->form = CFLR_FORM_BATCHED;
+}
+
+int cflr_create(cflr_ctx **out, const cflr_config *cfg) {
+    if (!out) return CFLR_EINVAL;
+    *out = nullptr;
+    cflr_config c;
+    if (cfg) c = *cfg;
+    else cflr_default_config(&c);
+    if (c.form < CFLR_FORM_PLAIN || c.form > CFLR_FORM_GRAPH) return CFLR_EINVAL;
+    std::unique_ptr<cflr_ctx> x(new cflr_ctx());
+    x->cfg = c;
+    x->device = c.device;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+        cudaGetLastError();
+        return CFLR_ECUDA;
+    }
+    if (cudaSetDevice(c.device) != cudaSuccess) return CFLR_ECUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c.device) != cudaSuccess) return CFLR_ECUDA;
+    x->sms = prop.multiProcessorCount;
+    x->smem_optin = prop.sharedMemPerBlockOptin;
+    if (c.stream) {
+        x->stream = (cudaStream_t)c.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&x->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return CFLR_ECUDA;
+        x->own_stream = true;
+    }
+    *out = x.release();
+    return CFLR_OK;
+}
+
+int cflr_load_grammar(cflr_ctx *c, const char *text, size_t len) {
+    if (!c) return CFLR_EINVAL;
+    if (!text) return c->fail(CFLR_EINVAL, "grammar text is NULL");
+    try {
+        cudaSetDevice(c->device);
+        Grammar g;
+        std::string err;
+        if (parse_grammar(text, len, g, err)) return c->fail(CFLR_EGRAMMAR, err);
+        if (g.nts.size() >= (1u << 20)) return c->fail(CFLR_EGRAMMAR, "too many non-terminals");
+        c->free_graph();
+        c->g = std::move(g);
+        c->state = ST_GRAMMAR;
+        c->err.clear();
+        return CFLR_OK;
+    } catch (const CudaError &e) {
+        return cuda_status(c, e);
+    }
+}
+
+int cflr_symbol_id(const cflr_ctx *c, const char *name, uint32_t *id, int *is_terminal) {
+    if (!c || !name || !id) return CFLR_EINVAL;
+    if (c->state < ST_GRAMMAR) return CFLR_ESTATE;
+    int k = c->g.find_nt(name);
+    if (k >= 0) {
+        *id = (uint32_t)k;
+        if (is_terminal) *is_terminal = 0;
+        return CFLR_OK;
+    }
+    k = c->g.find_term(name);
+    if (k >= 0) {
+        *id = (uint32_t)k;
+        if (is_terminal) *is_terminal = 1;
+        return CFLR_OK;
+    }
+    return CFLR_EINVAL;
+}
+
+int cflr_grammar_sizes(const cflr_ctx *c, uint32_t *n_nonterminals, uint32_t *n_named,
+                       uint32_t *n_terminals) {
+    if (!c) return CFLR_EINVAL;
+    if (c->state < ST_GRAMMAR) return CFLR_ESTATE;
+    if (n_nonterminals) *n_nonterminals = (uint32_t)c->g.nts.size();
+    if (n_named) *n_named = c->g.n_named;
+    if (n_terminals) *n_terminals = (uint32_t)c->g.terms.size();
+    return CFLR_OK;
+}
+
+int cflr_load_graph(cflr_ctx *c, uint32_t n_vertices, uint64_t n_edges, const uint32_t *src,
+                    const uint32_t *label, const uint32_t *dst) {
+    if (!c) return CFLR_EINVAL;
+    if (c->state < ST_GRAMMAR) return c->fail(CFLR_ESTATE, "load a grammar first");
+    if (n_edges && (!src || !label || !dst)) return c->fail(CFLR_EINVAL, "NULL edge array");
+    const uint64_t nt = c->g.nts.size();
+    const long double bound = (long double)nt * n_vertices * (long double)n_vertices;
+    if (bound >= 4.6e18L || n_vertices >= 0xFFFFFFF0u)
+        return c->fail(CFLR_EGRAPH, "too many vertices for 64-bit pair keys");
+    for (uint64_t e = 0; e < n_edges; e++)
+        if (src[e] >= n_vertices || dst[e] >= n_vertices)
+            return c->fail(CFLR_EGRAPH, "edge " + std::to_string(e) + " has a vertex id >= " +
+                                            std::to_string(n_vertices));
+    try {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        c->free_graph();
+        c->state = ST_GRAMMAR;
+        upload_graph(c, n_vertices, n_edges, src, label, dst);
+        reset_matrices(c);
+        c->state = ST_GRAPH;
+        c->err.clear();
+        return CFLR_OK;
+    } catch (const Status &s) {
+        c->free_graph();
+        return finish_status(c, s);
+    } catch (const CudaError &e) {
+        return cuda_status(c, e);
+    }
+}
+
+int cflr_solve(cflr_ctx *c, cflr_stats *stats) {
+    if (!c) return CFLR_EINVAL;
+    cflr_ctx *arr[1] = {c};
+    return cflr_solve_batch(arr, 1, stats);
+}
+
+int cflr_solve_batch(cflr_ctx *const *ctxs, int n, cflr_stats *stats) {
+    if (!ctxs || n <= 0) return CFLR_EINVAL;
+    std::vector<cflr_ctx *> cx;
+    for (int k = 0; k < n; k++) {
+        if (!ctxs[k]) return CFLR_EINVAL;
+        if (ctxs[k]->state < ST_GRAPH) return ctxs[k]->fail(CFLR_ESTATE, "load a graph first");
+        if (ctxs[k]->device != ctxs[0]->device)
+            return ctxs[0]->fail(CFLR_EINVAL, "contexts of one batch must share a device");
+        cx.push_back(ctxs[k]);
+    }
+    try {
+        return solve_many(cx, stats);
+    } catch (const Status &s) {
+        // A failed growth may strike between the commit and the merge of an
+        // iteration: the matrices are then incomplete, so they are dropped
+        // and the contexts need a new graph.
+        for (auto *c : cx) {
+            c->free_graph();
+            c->state = ST_GRAMMAR;
+        }
+        return finish_status(cx[0], s);
+    } catch (const CudaError &e) {
+        return cuda_status(cx[0], e);
+    }
+}
+
+int cflr_reset(cflr_ctx *c) {
+    if (!c) return CFLR_EINVAL;
+    if (c->state < ST_GRAPH) return c->fail(CFLR_ESTATE, "no graph loaded");
+    try {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        reset_matrices(c);
+        c->state = ST_GRAPH;
+        return CFLR_OK;
+    } catch (const Status &s) {
+        c->free_graph();
+        c->state = ST_GRAMMAR;
+        return finish_status(c, s);
+    } catch (const CudaError &e) {
+        return cuda_status(c, e);
+    }
+}
+
+}  // extern "C"
+
+namespace {
+
+// Write the pairs of one non-terminal, sorted by (src, dst), to device
+// arrays out_src/out_dst (row offsets by a device scan of the row lengths,
+// then one sort per row).
+void extract_device(cflr_ctx *c, uint32_t nt, uint32_t *out_src, uint32_t *out_dst) {
+    cudaStream_t st = c->stream;
+    const uint32_t n = c->n;
+    if (c->x_n < n || !c->x_len) {
+        c->free_extract_scratch();
+        c->x_n = n;
+        c->x_len = (uint32_t *)c->dalloc((size_t)n * 4);
+        c->x_big = (uint32_t *)c->dalloc(((size_t)n + 1) * 4);
+        c->x_off = (unsigned long long *)c->dalloc((size_t)n * 8);
+        c->x_bsum = (unsigned long long *)c->dalloc(((size_t)n / 1024 + 2) * 8);
+        const size_t words = ((size_t)n + 31) / 32;
+        if (words * 4 > 200 * 1024) {
+            c->x_bm_n = words * (size_t)c->sms * 4;
+            c->x_bm = (uint32_t *)c->dalloc(c->x_bm_n * 4);
+        }
+    }
+    const uint4 *desc = c->desc + (size_t)nt * 2 * n;
+    launch_row_lengths(desc, n, c->x_len, st);
+    launch_exclusive_scan(c->x_len, n, c->x_off, c->x_bsum, nullptr, st);
+    launch_extract(desc, c->pool, n, c->x_off, out_src, out_dst, c->x_big, c->x_big + n, c->x_bm,
+                   c->sms, st);
+    ck(cudaGetLastError(), "extract");
+}
+
+int get_pairs_common(cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint32_t *dst,
+                     uint64_t capacity, uint64_t *n_pairs, bool on_device) {
+    if (!c || !n_pairs) return CFLR_EINVAL;
+    if (c->state < ST_GRAPH) return c->fail(CFLR_ESTATE, "no graph loaded");
+    if (nonterminal >= c->g.nts.size()) return c->fail(CFLR_EINVAL, "bad non-terminal id");
+    const uint64_t cnt = c->nnz[nonterminal];
+    *n_pairs = cnt;
+    if (!src && !dst) return CFLR_OK;
+    if (!src || !dst) return c->fail(CFLR_EINVAL, "src and dst must both be given");
+    if (capacity < cnt) return c->fail(CFLR_EINVAL, "capacity smaller than the pair count");
+    if (cnt == 0) return CFLR_OK;
+    try {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        cudaStream_t st = c->stream;
+        if (on_device) {
+            extract_device(c, nonterminal, src, dst);
+            ck(cudaStreamSynchronize(st), "sync extract");
+            return CFLR_OK;
+        }
+        if (c->x_out_cap < cnt) {
+            c->free_extract_out();
+            c->x_src = (uint32_t *)c->dalloc(cnt * 4);
+            c->x_dst = (uint32_t *)c->dalloc(cnt * 4);
+            c->x_out_cap = cnt;
+        }
+        extract_device(c, nonterminal, c->x_src, c->x_dst);
+        ck(cudaMemcpyAsync(src, c->x_src, cnt * 4, cudaMemcpyDeviceToHost, st), "D2H pairs");
+        ck(cudaMemcpyAsync(dst, c->x_dst, cnt * 4, cudaMemcpyDeviceToHost, st), "D2H pairs");
+        ck(cudaStreamSynchronize(st), "sync extract");
+        return CFLR_OK;
+    } catch (const Status &s) {
+        return finish_status(c, s);
+    } catch (const CudaError &e) {
+        return cuda_status(c, e);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int cflr_get_pairs(const cflr_ctx *cc, uint32_t nonterminal, uint32_t *src, uint32_t *dst,
+                   uint64_t capacity, uint64_t *n_pairs) {
+    return get_pairs_common(const_cast<cflr_ctx *>(cc), nonterminal, src, dst, capacity, n_pairs,
+                            false);
+}
+
+int cflr_get_pairs_device(const cflr_ctx *cc, uint32_t nonterminal, uint32_t *d_src,
+                          uint32_t *d_dst, uint64_t capacity, uint64_t *n_pairs) {
+    return get_pairs_common(const_cast<cflr_ctx *>(cc), nonterminal, d_src, d_dst, capacity,
+                            n_pairs, true);
+}
+
+int cflr_kernel_stats(const cflr_ctx *c, int k, const char **name, uint64_t *launches,
+                      double *total_ms, uint64_t *alg_bytes) {
+    if (!c) return CFLR_EINVAL;
+    if (k < 0) {
+        if (launches) *launches = N_KID;
+        return CFLR_OK;
+    }
+    if (k >= N_KID) return CFLR_EINVAL;
+    if (name) *name = kKernelNames[k];
+    if (launches) *launches = c->k_launches[k];
+    if (total_ms) *total_ms = c->k_ms[k];
+    if (alg_bytes) *alg_bytes = c->k_bytes[k];
+    return CFLR_OK;
+}
+
+const char *cflr_last_error(const cflr_ctx *c) {
+    if (!c) return "NULL context";
+    return c->err.c_str();
+}
+
+void cflr_destroy(cflr_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    delete c->runner;
+    c->runner = nullptr;
+    c->free_graph();
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -28,7 +28,7 @@ _GRAMMAR_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "grammar
 # against the oracle; the values and the resulting closure sizes are recorded
 # with the workload recipe in the design notes).
 DEFAULT_WINDOW = 64
-DEFAULT_P_LONG = 0.01
+DEFAULT_P_LONG = 0.002
 DEFAULT_K_MAX = 1024
 ZIPF_S = 2.1
 
@@ -124,11 +124,13 @@ class _Locality:
     blocks of ``window`` vertices ("procedures").  Sources are drawn Chung-Lu
     style from Zipf(``s``) vertex weights truncated at ``k_max``.  A target is
     uniform over the later positions of the source's own block; with
-    probability ``p_long`` it is uniform over all later positions of the whole
-    order instead (an inter-procedural edge).  These edges therefore form a DAG, like the
-    cycle-eliminated graphs the paper evaluates on, and reachability stays
-    mostly inside a procedure and its few callees.
+    probability ``p_long`` it is uniform over the next ``LONG_BLOCKS`` blocks
+    instead (an inter-procedural edge).  These edges therefore form a DAG,
+    like the cycle-eliminated graphs the paper evaluates on, and reachability
+    stays mostly inside a procedure and its few callees at every graph size.
     """
+
+    LONG_BLOCKS = 64
 
     def __init__(self, rng, verts: np.ndarray, window: int, p_long: float, k_max: int,
                  s: float = ZIPF_S):
@@ -145,8 +147,8 @@ class _Locality:
 
     def sample(self, size: int):
         """``size`` draws of (src, dst); a draw is dropped when its source has
-        no later vertex in its block (a block-local draw) or in the whole order
-        (a long draw), so fewer may come back."""
+        no later vertex in its block (a block-local draw) or no block after
+        its own (a long draw), so fewer may come back."""
         rng, m, W = self.rng, self.verts.shape[0], self.window
         si = np.searchsorted(self.cw, rng.integers(0, int(self.cw[-1]), size=size,
                                                    dtype=np.int64), side="right")
@@ -155,10 +157,11 @@ class _Locality:
         p = self.pos[si]
         block_end = np.minimum((p // W + 1) * W, m)    # first position after the block
         in_block = block_end - 1 - p                   # later positions in the block
-        later = m - 1 - p                              # later positions overall
+        far_end = np.minimum(block_end + self.LONG_BLOCKS * W, m)
+        later = far_end - block_end                    # positions in the next blocks
         ok = np.where(longp, later > 0, in_block > 0)
         near = p + 1 + r % np.maximum(in_block, 1)
-        far = p + 1 + r % np.maximum(later, 1)
+        far = block_end + r % np.maximum(later, 1)
         tpos = np.minimum(np.where(longp, far, near), m - 1)
         ti = self.order[tpos]
         return self.verts[si[ok]], self.verts[ti[ok]]
@@ -252,8 +255,10 @@ def fsjpt_like(n: int = 500_000, n_edges: int = 2_000_000, fields: int = 64, see
                k_max: int = DEFAULT_K_MAX, field_s: float = 1.0) -> Graph:
     """Field-sensitive points-to workload (Fig. "wcnf:fsjpt" labels).
 
-    10 % of vertices are objects, the rest variables.  Forward edges: 40 %
-    assign (variable -> variable), 10 % alloc (variable -> object), 50 %
+    10 % of vertices are objects, the rest variables; variables fall into
+    procedures of ``window`` variables, each owning ``window``/9 objects.
+    Forward edges: 40 % assign (variable -> variable), 10 % alloc (variable
+    -> an object of its procedure, or any object with probability p_long), 50 %
     load_i / store_i split evenly (variable -> variable) with the field index i
     drawn Zipf(``field_s``) over ``fields`` fields.  Every edge also gets its
     reverse (alloc_r, assign_r, load_r_i, store_r_i).
@@ -274,13 +279,19 @@ def fsjpt_like(n: int = 500_000, n_edges: int = 2_000_000, fields: int = 64, see
     keys = [_distinct_edges(loc.sample, n_assign, n, L, 0)]
 
     obj_rank = rng.permutation(n_obj)
+    per_block = max(1, n_obj * window // max(1, vars_.shape[0]))   # objects per procedure
+    thr = int(round(p_long * (1 << 32)))
 
     def alloc_fn(size):
+        # a variable allocates one of its own procedure's objects; with
+        # probability p_long any object (a factory or global)
         s, _ = loc.sample(size)
-        vpos = loc.pos[np.searchsorted(vars_, s)]
-        base = vpos * n_obj // max(1, vars_.shape[0])
-        off = rng.integers(0, window, size=size, dtype=np.int64)
-        return s, objs[obj_rank[(base + off) % n_obj]]
+        blk = loc.pos[np.searchsorted(vars_, s)] // window
+        near = (blk * per_block + rng.integers(0, per_block, size=s.shape[0],
+                                               dtype=np.int64)) % n_obj
+        far = rng.integers(0, n_obj, size=s.shape[0], dtype=np.int64)
+        longp = rng.integers(0, 1 << 32, size=s.shape[0], dtype=np.int64) < thr
+        return s, objs[obj_rank[np.where(longp, far, near)]]
     keys.append(_distinct_edges(alloc_fn, n_alloc, n, L, 1))
 
     fcdf = zipf_cdf(field_s, fields)

@@ -1,0 +1,43 @@
+"""Shared test inputs and helpers (no oracle arithmetic, no CUDA calls)."""
+import numpy as np
+
+from paper_2401_11029_gb300 import gen
+
+FSJPT2_LABELS = ["alloc", "assign", "alloc_r", "assign_r", "load_0", "load_1", "store_0",
+                 "store_1", "load_r_0", "load_r_1", "store_r_0", "store_r_1"]
+
+GRAMMARS = {
+    "dyck1": (gen.grammar_text("dyck1"), ["a", "b"]),
+    "dyck3": (gen.grammar_text("dyck3"), ["a_1", "b_1", "a_2", "b_2", "a_3", "b_3"]),
+    "fica": (gen.grammar_text("fica"), ["a", "d", "a_r", "d_r"]),
+    "fica_cfg": (gen.grammar_text("fica_cfg"), ["a", "d", "a_r", "d_r"]),
+    "fsjpt2": (gen.grammar_text("fsjpt", index_hi=1), FSJPT2_LABELS),
+    "fsjpt2_cfg": (gen.grammar_text("fsjpt_cfg", index_hi=1), FSJPT2_LABELS),
+}
+
+# WCNF grammars with epsilon, unit and terminal-in-binary productions.
+RANDOM_GRAMMARS = [
+    "S -> S S | a | A b\nA -> eps | a A\n",
+    "X -> Y Z | b\nY -> X a | eps\nZ -> Y | c\n",
+    "P -> Q P | a\nQ -> P b | c Q | eps\nR -> P | Q Q\n",
+    "A -> B C | a\nB -> C A | b\nC -> A B | c | A\n",
+]
+
+
+def keys_of(src, dst) -> np.ndarray:
+    return (np.asarray(src, np.uint64) << np.uint64(32)) | np.asarray(dst, np.uint64)
+
+
+def fingerprint(keys: np.ndarray) -> str:
+    """Order-independent digest of a set of uint64 keys: count, xor and sum of
+    a 64-bit mix of every key."""
+    x = keys.astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        x ^= x >> np.uint64(31)
+        x *= np.uint64(0x7FB5D329728EA185)
+        x ^= x >> np.uint64(27)
+        x *= np.uint64(0x81DADEF4BC2DD44D)
+        x ^= x >> np.uint64(33)
+    xr = int(np.bitwise_xor.reduce(x)) if x.size else 0
+    sm = int(np.sum(x, dtype=np.uint64)) if x.size else 0
+    return "%d:%016x:%016x" % (keys.size, xr, sm)

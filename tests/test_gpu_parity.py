@@ -1,0 +1,290 @@
+"""Parity of the CUDA path with the CPU oracle (bit-exact pair sets).
+
+All calls go through the C ABI (the ctypes binding).  Sizes are chosen so the
+oracle finishes in seconds while the GPU work still spans many work-list
+groups, every shared-memory bin and ragged tails; the full-size workloads are
+compared through fingerprints the oracle wrote (tests/golden).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from common import GRAMMARS, RANDOM_GRAMMARS, fingerprint, keys_of
+from paper_2401_11029_gb300 import cflr, gen
+from paper_2401_11029_gb300.cflr import CflrError, Solver
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_pairs(text, g, names=None, **cfg):
+    with Solver(text, **cfg) as s:
+        s.load(g)
+        st = s.solve()
+        if names is None:
+            names = oracle.parse(text).nts
+        return {x: s.pairs(x) for x in names}, st
+
+
+def assert_parity(text, g, include_wrappers=True, **cfg):
+    want = oracle.solve(text, g)
+    pg = want.grammar
+    names = pg.nts if include_wrappers else pg.nts[:pg.n_user]
+    got, st = gpu_pairs(text, g, names, **cfg)
+    for x in names:
+        a, b = got[x], want.pairs[x]
+        if not np.array_equal(a, b):
+            extra = np.setdiff1d(a, b)[:5]
+            missing = np.setdiff1d(b, a)[:5]
+            raise AssertionError(f"{x}: gpu {a.size} vs oracle {b.size} pairs; "
+                                 f"extra {[(int(k >> 32), int(k & 0xFFFFFFFF)) for k in extra]} "
+                                 f"missing {[(int(k >> 32), int(k & 0xFFFFFFFF)) for k in missing]}")
+    assert st["total_pairs"] == want.total()
+    return st, want
+
+
+@pytest.mark.parametrize("name", list(GRAMMARS))
+@pytest.mark.parametrize("seed", [1, 2])
+@pytest.mark.parametrize("n,m", [(30, 70), (300, 900)])
+def test_paper_grammars_random_graphs(name, seed, n, m):
+    text, labels = GRAMMARS[name]
+    assert_parity(text, gen.random_graph(n=n, n_edges=m, labels=labels, seed=seed))
+
+
+@pytest.mark.parametrize("text", RANDOM_GRAMMARS)
+@pytest.mark.parametrize("seed", [3, 4])
+def test_epsilon_unit_and_terminal_operands(text, seed):
+    assert_parity(text, gen.random_graph(n=60, n_edges=150, labels=["a", "b", "c"], seed=seed))
+
+
+def test_dyck1_erdos_renyi_full_size():
+    """Dyck-1 on the 1000-vertex Erdos-Renyi graph (dense closure, bitmap bin)."""
+    st, want = assert_parity(gen.grammar_text("dyck1"), gen.dyck1_er())
+    assert want.pairs["S"].size > 100_000
+
+
+def test_fica_program_graph():
+    g = gen.fica_like(n=20_000, n_a=40_000, n_d=15_000, seed=2)
+    st, want = assert_parity(gen.grammar_text("fica"), g)
+    assert st["iterations"] > 3
+
+
+def test_fsjpt_program_graph_64_fields():
+    g = gen.fsjpt_like(n=12_000, n_edges=48_000, fields=64, seed=3)
+    st, want = assert_parity(gen.grammar_text("fsjpt"), g, include_wrappers=False)
+    assert want.pairs["PT"].size > 0
+
+
+def test_growth_paths_give_identical_pairs():
+    """Tiny first buffers force every re-run-after-growth path."""
+    g = gen.fica_like(n=5000, n_a=10_000, n_d=3750, seed=11)
+    st, _ = assert_parity(gen.grammar_text("fica"), g, initial_capacity=64)
+    assert st["regrows"] > 0
+
+
+def test_batch_equals_alone_and_oracle():
+    text = gen.grammar_text("dyck3")
+    graphs = gen.dyck3_batch(count=12, seed0=4000, n_lo=500, n_hi=5000)
+    solvers = [Solver(text) for _ in graphs]
+    try:
+        for s, g in zip(solvers, graphs):
+            s.load(g)
+        cflr.cflr_solve_batch([s.ctx for s in solvers])
+        for s, g in zip(solvers, graphs):
+            want = oracle.solve(text, g)
+            for x in want.grammar.nts:
+                assert np.array_equal(s.pairs(x), want.pairs[x]), x
+    finally:
+        for s in solvers:
+            s.close()
+
+
+# ---------------------------------------------------------------------------
+# edge cases and error handling
+# ---------------------------------------------------------------------------
+
+def test_empty_graph_and_isolated_vertices():
+    text = gen.grammar_text("fica")
+    g = gen.Graph(n=10, labels=["a"], src=np.zeros(0, np.uint32), lab=np.zeros(0, np.uint32),
+                  dst=np.zeros(0, np.uint32))
+    got, st = gpu_pairs(text, g, ["M", "N1"])
+    assert got["M"].size == 0 and st["total_pairs"] == 0
+
+
+def test_single_vertex_self_loops():
+    assert_parity("S -> S S | a\n", gen.Graph(n=1, labels=["a"], src=np.zeros(1, np.uint32),
+                                               lab=np.zeros(1, np.uint32),
+                                               dst=np.zeros(1, np.uint32)))
+
+
+def test_duplicate_edges_and_unknown_labels():
+    text, labels = GRAMMARS["dyck1"]
+    g = gen.random_graph(n=50, n_edges=120, labels=labels + ["zzz"], seed=5)
+    dup = gen.Graph(n=g.n, labels=g.labels, src=np.concatenate([g.src, g.src]),
+                    lab=np.concatenate([g.lab, g.lab]), dst=np.concatenate([g.dst, g.dst]))
+    want = oracle.solve(text, g)
+    got, st = gpu_pairs(text, dup, ["S", "S1"])
+    for x in ("S", "S1"):
+        assert np.array_equal(got[x], want.pairs[x])
+    assert st["ignored_edges"] == 2 * int((g.lab == 2).sum())
+
+
+def test_epsilon_identity_on_every_vertex():
+    got, _ = gpu_pairs("A -> eps\n", gen.Graph(n=1000, labels=["a"], src=np.zeros(0, np.uint32),
+                                               lab=np.zeros(0, np.uint32),
+                                               dst=np.zeros(0, np.uint32)), ["A"])
+    assert np.array_equal(got["A"], keys_of(np.arange(1000), np.arange(1000)))
+
+
+def test_call_order_and_argument_errors():
+    ctx = cflr.cflr_create()
+    try:
+        with pytest.raises(CflrError) as e:
+            cflr.cflr_load_graph(ctx, 3, [0], [0], [1])
+        assert e.value.code == cflr.CFLR_ESTATE
+        with pytest.raises(CflrError) as e:
+            cflr.cflr_load_grammar(ctx, "S -> a b c\n")
+        assert e.value.code == cflr.CFLR_EGRAMMAR
+        cflr.cflr_load_grammar(ctx, "S -> S S | a\n")
+        with pytest.raises(CflrError) as e:
+            cflr.cflr_solve(ctx)
+        assert e.value.code == cflr.CFLR_ESTATE
+        with pytest.raises(CflrError) as e:
+            cflr.cflr_load_graph(ctx, 3, [0], [0], [3])
+        assert e.value.code == cflr.CFLR_EGRAPH
+        cflr.cflr_load_graph(ctx, 3, [0, 1], [0, 0], [1, 2])
+        cflr.cflr_solve(ctx)
+        s, d = cflr.cflr_get_pairs(ctx, 0)
+        assert list(zip(s.tolist(), d.tolist())) == [(0, 1), (0, 2), (1, 2)]
+        with pytest.raises(CflrError) as e:
+            cflr.cflr_get_pairs(ctx, 7)
+        assert e.value.code == cflr.CFLR_EINVAL
+    finally:
+        cflr.cflr_destroy(ctx)
+
+
+def test_iteration_limit_then_resume_reaches_same_fixpoint():
+    text = gen.grammar_text("fica")
+    g = gen.fica_like(n=4000, n_a=8000, n_d=3000, seed=12)
+    want = oracle.solve(text, g)
+    with Solver(text, max_iterations=2) as s:
+        s.load(g)
+        with pytest.raises(CflrError) as e:
+            s.solve()
+        assert e.value.code == cflr.CFLR_ELIMIT
+        partial = s.count("M")
+        assert partial <= want.pairs["M"].size
+        for _ in range(1000):
+            try:
+                s.solve()
+                break
+            except CflrError as err:
+                assert err.code == cflr.CFLR_ELIMIT
+        assert np.array_equal(s.pairs("M"), want.pairs["M"])
+
+
+def test_memory_budget_is_enforced_and_context_survives():
+    text = gen.grammar_text("fica")
+    g = gen.fica_like(n=20_000, n_a=40_000, n_d=15_000, seed=2)
+    with Solver(text, mem_budget_bytes=48 << 20) as s:    # the 20k graph needs ~450 MB
+        with pytest.raises(CflrError) as e:
+            s.load(g)
+            s.solve()
+        assert e.value.code == cflr.CFLR_ENOMEM
+        small = gen.random_graph(n=20, n_edges=30, labels=["a", "d", "a_r", "d_r"], seed=1)
+        s.load(small)
+        s.solve()
+        want = oracle.solve(text, small)
+        assert np.array_equal(s.pairs("M"), want.pairs["M"])
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads against the oracle's stored fingerprints
+# ---------------------------------------------------------------------------
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, name + ".json")
+    if not os.path.exists(path):
+        pytest.skip(f"no stored oracle fingerprints for {name}")
+    with open(path) as f:
+        return json.load(f)
+
+
+def _check_full(name, grammar, g, **cfg):
+    gold = _golden(name)
+    if g.edge_digest() != gold["edge_digest"]:
+        pytest.skip("the generator made a different graph on this machine")
+    with Solver(gen.grammar_text(grammar), **cfg) as s:
+        s.load(g)
+        st = s.solve()
+        for x, fp in gold["pairs"].items():
+            assert fingerprint(s.pairs(x)) == fp, x
+    assert st["total_pairs"] == gold["total_pairs"]
+    return st
+
+
+def test_full_size_dyck1_er():
+    _check_full("dyck1_er_1000", "dyck1", gen.dyck1_er())
+
+
+def test_full_size_fica_200k():
+    _check_full("fica_like_200k", "fica", gen.fica_like())
+
+
+def test_full_size_fica_200k_launch_config_of_bench():
+    """The bench's call sequence: reset from device-resident edges, solve,
+    extract to device buffers, read back and compare."""
+    import torch
+    gold = _golden("fica_like_200k")
+    g = gen.fica_like()
+    if g.edge_digest() != gold["edge_digest"]:
+        pytest.skip("the generator made a different graph on this machine")
+    with Solver(gen.grammar_text("fica"), profile=1) as s:
+        s.load(g)
+        for _ in range(2):                       # second pass runs on reused buffers
+            cflr.cflr_reset(s.ctx)
+            s.solve()
+        for x, fp in gold["pairs"].items():
+            i = s.nt_id(x)
+            cnt = cflr.cflr_get_pairs(s.ctx, i, count_only=True)
+            d_s = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
+            d_d = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
+            cflr.cflr_get_pairs_device(s.ctx, i, d_s.data_ptr(), d_d.data_ptr(), cnt)
+            keys = keys_of(d_s[:cnt].cpu().numpy().view(np.uint32),
+                           d_d[:cnt].cpu().numpy().view(np.uint32))
+            assert np.all(keys[1:] > keys[:-1]), "pairs not sorted by (src, dst)"
+            assert fingerprint(keys) == fp, x
+
+
+def test_full_size_fsjpt_500k():
+    _check_full("fsjpt_like_500k", "fsjpt", gen.fsjpt_like())
+
+
+def test_full_size_dyck3_batch_256():
+    gold = _golden("dyck3_batch_256")
+    text = gen.grammar_text("dyck3")
+    graphs = gen.dyck3_batch(count=256, seed0=4000)
+    solvers = [Solver(text) for _ in graphs]
+    try:
+        for s, g, gi in zip(solvers, graphs, gold["instances"]):
+            assert g.edge_digest() == gi["edge_digest"]
+            s.load(g)
+        cflr.cflr_solve_batch([s.ctx for s in solvers])
+        for s, gi in zip(solvers, gold["instances"]):
+            for x, fp in gi["pairs"].items():
+                assert fingerprint(s.pairs(x)) == fp, (gi["seed"], x)
+    finally:
+        for s in solvers:
+            s.close()
+
+
+@pytest.mark.parametrize("form", [cflr.CFLR_FORM_PLAIN, cflr.CFLR_FORM_BATCHED])
+def test_execution_forms_agree(form):
+    text = gen.grammar_text("fica")
+    g = gen.fica_like(n=8000, n_a=16_000, n_d=6000, seed=21)
+    assert_parity(text, g, form=form)
