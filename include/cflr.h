@@ -159,6 +159,29 @@ int cflr_get_pairs(const cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint3
 int cflr_get_pairs_device(const cflr_ctx *c, uint32_t nonterminal, uint32_t *d_src,
                           uint32_t *d_dst, uint64_t capacity, uint64_t *n_pairs);
 
+/* Largest graph (vertices) cflr_get_pairs_device_noalloc accepts. */
+#define CFLR_NOALLOC_MAX_VERTICES 1048576u
+
+/* As cflr_get_pairs_device, but allocates no device memory.  (The paper has
+ * no counterpart; this serves callers that may not allocate when they read
+ * results: code that runs against a fixed device-memory plan made at
+ * start-up, embedders whose own allocator owns the whole device, and paths
+ * that must not risk the device synchronisation cudaMalloc/cudaFree can
+ * cause.)  Its scratch lives in one static device array of about 16 MiB
+ * inside this library, which every GPU that loads the library holds until
+ * the process exits.
+ *   - Graphs with more than CFLR_NOALLOC_MAX_VERTICES vertices are rejected
+ *     with CFLR_EINVAL; nothing is launched.
+ *   - The first call for a device looks up the array's device address on
+ *     that device (cudaGetSymbolAddress); make that first call before any
+ *     stream capture.
+ *   - All calls share the one array per device: calls whose work overlaps
+ *     on the GPU (other host threads, or contexts on other streams) race and
+ *     may return wrong pairs.  Serialise them.
+ *   - Arguments, output format and other errors as cflr_get_pairs_device. */
+int cflr_get_pairs_device_noalloc(const cflr_ctx *c, uint32_t nonterminal, uint32_t *d_src,
+                                  uint32_t *d_dst, uint64_t capacity, uint64_t *n_pairs);
+
 /* Restore the matrices of the loaded graph to Algorithm 1's terminal
  * initialisation, from the copy of the edges cflr_load_graph keeps on the
  * device (no host transfer).  Device buffers grown by earlier solves are

@@ -36,8 +36,11 @@ CFLR_FORM_GRAPH = 2
 # Every symbol include/cflr.h declares (checked by the CPU tests).
 EXPORTS = ["cflr_default_config", "cflr_create", "cflr_load_grammar", "cflr_symbol_id",
            "cflr_grammar_sizes", "cflr_load_graph", "cflr_solve", "cflr_get_pairs",
-           "cflr_get_pairs_device", "cflr_reset", "cflr_solve_batch", "cflr_kernel_stats",
-           "cflr_last_error", "cflr_destroy"]
+           "cflr_get_pairs_device", "cflr_get_pairs_device_noalloc", "cflr_reset",
+           "cflr_solve_batch", "cflr_kernel_stats", "cflr_last_error", "cflr_destroy"]
+
+# Largest graph the allocation-free extraction accepts (CFLR_NOALLOC_MAX_VERTICES).
+CFLR_NOALLOC_MAX_VERTICES = 1048576
 
 
 class CflrError(RuntimeError):
@@ -97,6 +100,8 @@ def load_library(path: str = LIB_PATH):
     lib.cflr_get_pairs.restype = i32
     lib.cflr_get_pairs_device.argtypes = [vp, u32, vp, vp, u64, ctypes.POINTER(u64)]
     lib.cflr_get_pairs_device.restype = i32
+    lib.cflr_get_pairs_device_noalloc.argtypes = [vp, u32, vp, vp, u64, ctypes.POINTER(u64)]
+    lib.cflr_get_pairs_device_noalloc.restype = i32
     lib.cflr_reset.argtypes = [vp]
     lib.cflr_reset.restype = i32
     lib.cflr_solve_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(cflr_stats)]
@@ -209,6 +214,19 @@ def cflr_get_pairs_device(ctx, nonterminal: int, d_src: int, d_dst: int, capacit
     _check(ctx, load_library().cflr_get_pairs_device(ctx, int(nonterminal), ctypes.c_void_p(d_src),
                                                      ctypes.c_void_p(d_dst), int(capacity),
                                                      ctypes.byref(n)))
+    return int(n.value)
+
+
+def cflr_get_pairs_device_noalloc(ctx, nonterminal: int, d_src: int, d_dst: int,
+                                  capacity: int) -> int:
+    """As cflr_get_pairs_device, for callers that may not allocate device
+    memory: the scratch lives in a static device array inside the library, so
+    the graph may have at most CFLR_NOALLOC_MAX_VERTICES vertices and calls
+    that overlap on the GPU must not be issued.  Returns the pair count."""
+    n = ctypes.c_uint64()
+    _check(ctx, load_library().cflr_get_pairs_device_noalloc(
+        ctx, int(nonterminal), ctypes.c_void_p(d_src), ctypes.c_void_p(d_dst), int(capacity),
+        ctypes.byref(n)))
     return int(n.value)
 
 

@@ -1224,3 +1224,96 @@ void cflr_destroy(cflr_ctx *c) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free extraction (cflr_get_pairs_device_noalloc)
+//
+// Some callers may not allocate device memory at the point where they read
+// results: code that runs against a fixed device-memory plan made at start-up,
+// embedders whose own allocator owns the whole device, or paths that must not
+// risk the implicit device synchronisation a cudaMalloc/cudaFree can cause.
+// For them this variant of the extraction keeps its scratch (row lengths, row
+// offsets, scan block sums and the list of long rows) in one file-scope
+// device array instead of context-owned buffers.  The array is sized for
+// graphs of up to CFLR_NOALLOC_MAX_VERTICES vertices (about 16 MiB) and, like
+// any __device__ variable, is held by every GPU that loads this library until
+// the process exits.
+// ===========================================================================
+
+#include <mutex>
+
+namespace {
+
+constexpr uint64_t NA_MAX = CFLR_NOALLOC_MAX_VERTICES;
+// word layout (8-byte words): offsets | scan block sums | lengths | long rows
+constexpr uint64_t NA_OFF_WORDS = NA_MAX;
+constexpr uint64_t NA_BSUM_WORDS = NA_MAX / 1024 + 2;
+constexpr uint64_t NA_LEN_WORDS = NA_MAX / 2;
+constexpr uint64_t NA_BIG_WORDS = (NA_MAX + 2) / 2;
+constexpr uint64_t NA_WORDS = NA_OFF_WORDS + NA_BSUM_WORDS + NA_LEN_WORDS + NA_BIG_WORDS;
+
+// In host code this name is only a stand-in for the device variable: its
+// device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[NA_WORDS];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NA_MAX_DEVICES] = {};
+
+// Device address of the scratch array on `device`, which must be current.
+// Looked up once per device, on the first call made for that device.
+cudaError_t noalloc_scratch(int device, void **out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (device < 0 || device >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = p;
+    }
+    *out = g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int cflr_get_pairs_device_noalloc(const cflr_ctx *cc, uint32_t nonterminal,
+                                             uint32_t *d_src, uint32_t *d_dst,
+                                             uint64_t capacity, uint64_t *n_pairs) {
+    cflr_ctx *c = const_cast<cflr_ctx *>(cc);
+    if (!c || !n_pairs) return CFLR_EINVAL;
+    if (c->state < ST_GRAPH) return c->fail(CFLR_ESTATE, "no graph loaded");
+    if (nonterminal >= c->g.nts.size()) return c->fail(CFLR_EINVAL, "bad non-terminal id");
+    const uint64_t cnt = c->nnz[nonterminal];
+    *n_pairs = cnt;
+    if (!d_src && !d_dst) return CFLR_OK;
+    if (!d_src || !d_dst) return c->fail(CFLR_EINVAL, "d_src and d_dst must both be given");
+    if (capacity < cnt) return c->fail(CFLR_EINVAL, "capacity smaller than the pair count");
+    if (c->n > NA_MAX)
+        return c->fail(CFLR_EINVAL, "graph has " + std::to_string(c->n) +
+                                        " vertices; the allocation-free extraction supports at "
+                                        "most " + std::to_string(NA_MAX));
+    if (cnt == 0) return CFLR_OK;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_status(c, CudaError{e, "cudaSetDevice"});
+    void *base = nullptr;
+    e = noalloc_scratch(c->device, &base);
+    if (e != cudaSuccess) return cuda_status(c, CudaError{e, "cudaGetSymbolAddress"});
+    unsigned long long *w = (unsigned long long *)base;
+    unsigned long long *off = w;
+    unsigned long long *bsum = w + NA_OFF_WORDS;
+    uint32_t *len = (uint32_t *)(bsum + NA_BSUM_WORDS);
+    uint32_t *big = (uint32_t *)(w + NA_OFF_WORDS + NA_BSUM_WORDS + NA_LEN_WORDS);
+    const uint32_t n = c->n;
+    const uint4 *desc = c->desc + (size_t)nonterminal * 2 * n;
+    cudaStream_t st = c->stream;
+    // Every scratch word used below is written before it is read (lengths,
+    // offsets, block sums) or cleared first (the long-row counter).
+    launch_row_lengths(desc, n, len, st);
+    launch_exclusive_scan(len, n, off, bsum, nullptr, st);
+    launch_extract(desc, c->pool, n, off, d_src, d_dst, big, big + n, nullptr, c->sms, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(c, CudaError{e, "extract (no-alloc)"});
+    return CFLR_OK;
+}
