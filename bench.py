@@ -190,10 +190,11 @@ def run_cflr(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     seed = WORKLOAD["seed"] + 1000 * rank
-    g = workload_graph(seed)
+    g = workload_graph(seed, args.vertices)
     text = gen.grammar_text("fica")
 
-    ctx = cflr.cflr_create(device=local, stream=stream.cuda_stream, profile=1)
+    # timed context: the device-driven loop (one CUDA graph per solve)
+    ctx = cflr.cflr_create(device=local, stream=stream.cuda_stream, form=cflr.CFLR_FORM_GRAPH)
     cflr.cflr_load_grammar(ctx, text)
     n_nt, n_named, _ = cflr.cflr_grammar_sizes(ctx)
     term = {}
@@ -211,17 +212,26 @@ def run_cflr(args):
     cflr.cflr_load_graph(ctx, g.n, h_src.numpy().view(np.uint32), h_lab.numpy().view(np.uint32),
                          h_dst.numpy().view(np.uint32))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # profiled context: the same iterations launched one by one from the host
+    # with CUDA events around every kernel (events cannot sit inside the
+    # graph's loop body); it supplies the per-kernel times of the roofline
+    pctx = cflr.cflr_create(device=local, stream=stream.cuda_stream,
+                            form=cflr.CFLR_FORM_BATCHED, profile=1)
+    cflr.cflr_load_grammar(pctx, text)
+    cflr.cflr_load_graph(pctx, g.n, h_src.numpy().view(np.uint32), h_lab.numpy().view(np.uint32),
+                         h_dst.numpy().view(np.uint32))
 
     last = {}
 
-    def device_step(out=None):
-        cflr.cflr_reset(ctx)
-        last.update(cflr.cflr_solve(ctx))
+    def device_step(out=None, c=None):
+        c = c or ctx
+        cflr.cflr_reset(c)
+        last.update(cflr.cflr_solve(c))
         total = 0
         for x in range(n_named):
-            cnt = cflr.cflr_get_pairs(ctx, x, count_only=True)
+            cnt = cflr.cflr_get_pairs(c, x, count_only=True)
             if cnt and out is not None:
-                cflr.cflr_get_pairs_device(ctx, x, out[0].data_ptr(), out[1].data_ptr(), cnt)
+                cflr.cflr_get_pairs_device(c, x, out[0].data_ptr(), out[1].data_ptr(), cnt)
             total += cnt
         return total
 
@@ -231,7 +241,6 @@ def run_cflr(args):
            torch.empty(cap, dtype=torch.int32, device=dev))
     for _ in range(max(0, args.warmup - 1)):
         device_step(out)
-    before = {k["name"]: k for k in cflr.cflr_kernel_stats(ctx)}
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -253,7 +262,18 @@ def run_cflr(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    after = {k["name"]: k for k in cflr.cflr_kernel_stats(ctx)}
+    solve_stats = dict(last)
+
+    # per-kernel event times: the same steps on the profiled context
+    for _ in range(args.warmup):
+        device_step(out, pctx)
+    before = {k["name"]: k for k in cflr.cflr_kernel_stats(pctx)}
+    for _ in range(args.steps):
+        flush.fill_(rank + 1)
+        assert device_step(out, pctx) == pairs
+    torch.cuda.synchronize(dev)
+    after = {k["name"]: k for k in cflr.cflr_kernel_stats(pctx)}
+    cflr.cflr_destroy(pctx)
 
     # end-to-end through the host-buffer API
     h_out_s = torch.empty(cap, dtype=torch.int32).pin_memory()
@@ -328,14 +348,146 @@ def run_cflr(args):
                      "gbs": round((r[2] / 1e9) / (r[0] / 1e3), 1) if r[0] > 0 else None}
                     for r in rows if r[1]],
         "clocks": clk,
-        "solve": {"iterations": last["iterations"], "flops": last["flops"],
-                  "candidates": last["candidates"],
-                  "peak_device_bytes": last["peak_device_bytes"]},
+        "solve": {"form": "graph", "iterations": solve_stats["iterations"],
+                  "flops": solve_stats["flops"], "candidates": solve_stats["candidates"],
+                  "peak_device_bytes": solve_stats["peak_device_bytes"]},
+        "roofline_note": "kernel times from the same steps replayed with per-kernel CUDA "
+                         "events (host-launched iterations) right after the timed region",
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(WORKLOAD["seed"])
     print(json.dumps(line), flush=True)
     cflr.cflr_destroy(ctx)
+
+
+def run_dyck3_batch(args):
+    """Config 4: 256 independent Dyck-3 instances.  Times the solve of all of
+    them as one batch (every production of every instance in one launch
+    sequence per iteration, the iterations looping inside one CUDA graph)
+    against solving each alone in the plain per-production form; both after
+    cflr_reset from device-resident edges."""
+    import torch
+    from paper_2401_11029_gb300 import cflr
+
+    world, rank, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    text = gen.grammar_text("dyck3")
+    graphs = gen.dyck3_batch(count=args.instances, seed0=4000 + 100000 * rank)
+
+    def make(form):
+        out = []
+        for g in graphs:
+            c = cflr.cflr_create(device=local, stream=stream.cuda_stream, form=form)
+            cflr.cflr_load_grammar(c, text)
+            ids = {}
+            for name in g.labels:
+                i, _ = cflr.cflr_symbol_id(c, name)
+                ids[name] = i
+            lab = np.asarray([ids[x] for x in g.labels], np.uint32)[g.lab]
+            cflr.cflr_load_graph(c, g.n, g.src, lab, g.dst)
+            out.append(c)
+        return out
+
+    batched = make(cflr.CFLR_FORM_GRAPH)
+    plain = make(cflr.CFLR_FORM_PLAIN)
+
+    def timed(fn, ctxs):
+        ts = []
+        for k in range(args.warmup + args.steps):
+            for c in ctxs:
+                cflr.cflr_reset(c)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(ctxs)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts)
+
+    ms_b = timed(lambda cs: cflr.cflr_solve_batch(cs), batched)
+    ms_p = timed(lambda cs: [cflr.cflr_solve(c) for c in cs], plain)
+    named = None
+    pairs = 0
+    for c in batched:
+        n_nt, n_named, _ = cflr.cflr_grammar_sizes(c)
+        pairs += sum(cflr.cflr_get_pairs(c, x, count_only=True) for x in range(n_named))
+    pairs_p = 0
+    for c in plain:
+        n_nt, n_named, _ = cflr.cflr_grammar_sizes(c)
+        pairs_p += sum(cflr.cflr_get_pairs(c, x, count_only=True) for x in range(n_named))
+    assert pairs == pairs_p
+    if rank == 0:
+        line = {"metric": "batched CFL-r solve throughput (pairs / solve time)",
+                "value": pairs / (ms_b / 1e3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic",
+                "config": {"workload": f"dyck3 x{args.instances} (seeds 4000..)",
+                           "vertices": int(sum(g.n for g in graphs)),
+                           "edges": int(sum(g.n_edges for g in graphs)), "pairs": pairs},
+                "plain_form": {"ms_per_step": ms_p, "value": pairs / (ms_p / 1e3),
+                               "form": "each instance alone, one launch sequence per "
+                                       "production"},
+                "batched_over_plain": ms_p / ms_b}
+        print(json.dumps(line), flush=True)
+    for c in batched + plain:
+        cflr.cflr_destroy(c)
+
+
+def _gen_request(args):
+    n, seed = args
+    return gen.fica_like(n=n, n_a=2 * n, n_d=(3 * n) // 4, seed=seed)
+
+
+def run_serving(args):
+    """Config 5: a Poisson stream of alias-analysis solves (sizes log-uniform
+    in [5k, 300k] vertices) served with continuous batching; p50/p99 latency
+    from arrival to result on the host, after a warm-up window."""
+    import multiprocessing as mp
+    reqs = gen.serving_stream(n_req=args.requests, rate=args.rate, seed=5)
+    # graphs are made before the first GPU call, in spawned workers
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        graphs = pool.map(_gen_request, [(r.n, r.seed) for r in reqs], chunksize=4)
+    import torch
+    from paper_2401_11029_gb300 import cflr
+    from paper_2401_11029_gb300.serve import Server, summarize
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    text = gen.grammar_text("fica")
+    # warm the library and the allocator on a small request
+    w = Server(text, stream=stream.cuda_stream)
+    w.run([(0, 0.0, _gen_request((20_000, 99)))])
+    w.close()
+    srv = Server(text, mem_budget_bytes=args.serve_budget_gb << 30, max_active=args.max_active,
+                 stream=stream.cuda_stream)
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    done = srv.run([(r.rid, r.arrival_s, g) for r, g in zip(reqs, graphs)])
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    srv.close()
+    summ = summarize(done, warmup_s=args.serve_warmup)
+    line = {"metric": "served CFL-r solves: throughput (pairs/s) with p50/p99 latency",
+            "value": summ["pairs_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": len(done), "warmup": args.serve_warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals of fica_like solves",
+                       "rate_per_s": args.rate, "requests": args.requests,
+                       "vertices": "log-uniform [5000, 300000]",
+                       "mem_budget_gb": args.serve_budget_gb, "max_active": args.max_active},
+            "serving": dict(summ, wall_s=wall, warmup_s=args.serve_warmup),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -344,10 +496,24 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cflr", choices=["cflr", "reference"])
+    ap.add_argument("--workload", default="fica", choices=["fica", "dyck3_batch", "serving"])
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--serve-warmup", type=float, default=5.0)
+    ap.add_argument("--serve-budget-gb", type=int, default=96)
+    ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--vertices", type=int, default=None,
+                    help="scale the workload to this many vertices (same generator and "
+                         "ratios; for profiling runs, not for bench lines)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "dyck3_batch":
+        run_dyck3_batch(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_cflr(args)
 

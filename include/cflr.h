@@ -86,6 +86,7 @@ typedef struct {
     uint64_t flops;             /* boolean OR operations of all products            */
     uint64_t candidates;        /* pairs the products emitted after the mask        */
     uint64_t regrows;           /* buffer growths that re-ran a phase               */
+    uint32_t converged;         /* 1 when the context has reached its fixpoint      */
 } cflr_stats;
 
 /* Default configuration: device 0, private stream, no budget, no iteration
@@ -193,7 +194,13 @@ int cflr_reset(cflr_ctx *c);
  * products of all unfinished contexts in one launch sequence.  Every
  * context must hold a loaded graph and use the same device and stream as
  * ctxs[0].  stats (nullable) is an array of n.  Results are identical to
- * solving each context alone.
+ * solving each context alone.  The iteration limit and the work buffers are
+ * those of ctxs[0], which may be a context whose solve has already finished
+ * (it then only lends its buffers): with max_iterations = 1 every call
+ * advances each unfinished context by one closure iteration, and contexts
+ * may join or leave between calls (continuous batching).  stats[k].converged
+ * tells which contexts are done; the call returns CFLR_ELIMIT while any is
+ * not.
  * Errors: as cflr_solve; CFLR_EINVAL for n <= 0 or mixed devices. */
 int cflr_solve_batch(cflr_ctx *const *ctxs, int n, cflr_stats *stats);
 

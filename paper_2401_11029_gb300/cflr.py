@@ -61,7 +61,8 @@ class cflr_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_uint32), ("total_pairs", ctypes.c_uint64),
                 ("solve_ms", ctypes.c_double), ("peak_device_bytes", ctypes.c_uint64),
                 ("ignored_edges", ctypes.c_uint64), ("flops", ctypes.c_uint64),
-                ("candidates", ctypes.c_uint64), ("regrows", ctypes.c_uint64)]
+                ("candidates", ctypes.c_uint64), ("regrows", ctypes.c_uint64),
+                ("converged", ctypes.c_uint32)]
 
     def to_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -184,11 +185,14 @@ def cflr_solve(ctx) -> dict:
     return st.to_dict()
 
 
-def cflr_solve_batch(ctxs) -> list:
+def cflr_solve_batch(ctxs, allow_limit: bool = False) -> list:
+    """Solve contexts together; with allow_limit, CFLR_ELIMIT is not an error
+    (each stats dict then says whether its context converged)."""
     arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
     stats = (cflr_stats * len(ctxs))()
     rc = load_library().cflr_solve_batch(arr, len(ctxs), stats)
-    _check(ctxs[0] if ctxs else None, rc)
+    if not (allow_limit and rc == CFLR_ELIMIT):
+        _check(ctxs[0] if ctxs else None, rc)
     return [s.to_dict() for s in stats]
 
 

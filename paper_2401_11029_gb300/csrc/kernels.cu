@@ -104,6 +104,35 @@ __device__ __forceinline__ uint32_t emit_candidates(bool flag, unsigned long lon
     return cnt;
 }
 
+// Exclusive scan over the 256 threads of a block; `total` gets the block sum.
+__device__ __forceinline__ unsigned long long block_excl_scan256(unsigned long long v,
+                                                                 unsigned long long *sh,
+                                                                 unsigned long long &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        unsigned long long t = __shfl_up_sync(FULL_MASK, x, d);
+        if (lane >= d) x += t;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long y = lane < 8 ? sh[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            unsigned long long t = __shfl_up_sync(FULL_MASK, y, d);
+            if (lane >= d) y += t;
+        }
+        if (lane < 8) sh[8 + lane] = y;
+    }
+    __syncthreads();
+    total = sh[15];
+    const unsigned long long before = (w ? sh[8 + w - 1] : 0ull) + x - v;
+    __syncthreads();
+    return before;
+}
+
 // ---------------------------------------------------------------------------
 // k_symbolic: groups of this iteration, binned by shared-memory need
 // ---------------------------------------------------------------------------
@@ -116,7 +145,9 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
     __shared__ uint2 stage[8][N_BINS][SYM_BUF];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned long long nw = (unsigned long long)gridDim.x * 8;
-    const unsigned long long n_in = *W.touched_in_n;
+    const int par = *W.parity;
+    const unsigned long long n_in = W.touched_n[par];
+    const uint2 *t_in = W.touched[par];
     int fill[N_BINS] = {0, 0, 0, 0};
     unsigned long long bytes[N_BINS] = {0, 0, 0, 0};
     unsigned long long flops = 0, sym_bytes = 0;
@@ -131,7 +162,7 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
     };
 
     for (unsigned long long e = (unsigned long long)blockIdx.x * 8 + wib; e < n_in; e += nw) {
-        const uint2 t = W.touched_in[e];
+        const uint2 t = t_in[e];
         const uint32_t xo = t.x, idx = t.y, slot = xo >> 1, o = xo & 1;
         const uint32_t n = S.n[slot];
         const uint4 dsc = S.desc[slot][(size_t)o * n + idx];
@@ -155,13 +186,15 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                 f = warp_sum64(f);
             }
             if (lane == 0 && f > 0) {
-                bool probe = (unsigned long long)mlen > (unsigned long long)PROBE_RATIO * f;
-                unsigned long long need = probe ? f : f + mlen;
-                int b = need <= BIN0_LIMIT ? 0 : need <= BIN1_LIMIT ? 1
-                      : need <= BIN2_LIMIT ? 2 : 3;
-                if (b == 3) probe = false;       // the bitmap takes the whole mask row
-                stage[wib][b][fill[b]++] =
-                    make_uint2(((code >> 2) << 3) | (probe ? MODE_PROBE : 0u) | part, idx);
+                const bool probe = (unsigned long long)mlen > (unsigned long long)PROBE_RATIO * f;
+                const unsigned long long need = probe ? f : f + mlen;
+                const int b = need <= BIN0_LIMIT ? 0 : need <= BIN1_LIMIT ? 1
+                            : need <= BIN2_LIMIT ? 2 : 3;
+                // table of the smallest power of two >= 2*need slots (>= 32)
+                uint32_t lg = 5;
+                while (b < 3 && (1ull << lg) < 2 * need) lg++;
+                stage[wib][b][fill[b]++] = make_uint2(
+                    ((code >> 2) << 8) | (lg << 3) | (probe ? MODE_PROBE : 0u) | part, idx);
                 // algorithmic bytes: the delta row (4 B per entry), one 16-byte
                 // descriptor and 4 B per element of every referenced row, and
                 // the mask row when it is loaded
@@ -182,9 +215,9 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
     }
 }
 
-// Group code layout: prod << 3 | probe bit (MODE_PROBE) | part.
+// Group code layout: prod << 8 | log2(table slots) << 3 | probe bit (MODE_PROBE) | part.
 struct GroupInfo {
-    uint32_t part, c, a, b, idx, n, o;
+    uint32_t part, c, a, b, idx, n, o, lg;
     bool probe;
 };
 
@@ -193,7 +226,8 @@ __device__ __forceinline__ GroupInfo decode_group(const ProdTab &P, const SlotTa
     GroupInfo gi;
     gi.probe = (g.x & MODE_PROBE) != 0;
     gi.part = g.x & 3;
-    const uint4 pr = P.prod[g.x >> 3];
+    gi.lg = (g.x >> 3) & 31;
+    const uint4 pr = P.prod[g.x >> 8];
     gi.c = pr.x; gi.a = pr.y; gi.b = pr.z;
     gi.idx = g.y;
     gi.n = S.n[gi.c];
@@ -213,15 +247,18 @@ __device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uin
                 : (((unsigned long long)gi.idx << 32) | v);
 }
 
-// Walk the delta entries [first, d) of a group in chunks of 32 (stride
-// `stride`), expand the referenced rows with a load-balanced warp loop and
-// insert every element into the accumulator `ins`; new elements that pass
-// the probe (if any) are emitted.  Warp-collective.
+// Expand the products of a group's delta entries into the accumulator
+// `ins` and emit the ones that are new (warp-collective).  Warp `warp_id` of
+// `nwarps` takes the entries warp_id + nwarps*l (lane l) of every block of
+// 32*nwarps entries, so all warps of a CTA get work even for short deltas.
+// A referenced row of 32 or more elements is walked by the whole warp
+// (coalesced, two loads in flight); shorter rows are packed 32 products per
+// step with a per-lane search of the owning row.  Returns the emitted count.
 template <class Ins>
-__device__ __forceinline__ uint32_t expand_group(const SlotTab &S, const WorkBufs &W,
-                                                 const GroupInfo &gi, uint4 own,
-                                                 uint32_t first, uint32_t stride, int lane,
-                                                 Ins ins) {
+__device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs &W,
+                                                const GroupInfo &gi, uint4 own,
+                                                uint32_t warp_id, uint32_t nwarps, int lane,
+                                                Ins ins) {
     const uint32_t d = own.w, dstart = own.x + own.y - own.w;
     const uint32_t *pool = S.pool[gi.c];
     const uint4 *dg = (gi.part == PART_A) ? S.desc[gi.b]
@@ -229,46 +266,68 @@ __device__ __forceinline__ uint32_t expand_group(const SlotTab &S, const WorkBuf
     const unsigned long long *ht = S.htab[gi.c];
     const unsigned long long hm = S.hmask[gi.c];
     uint32_t emitted = 0;
-    for (uint32_t base = first; base < d; base += stride) {
-        const uint32_t t = base + lane;
-        uint32_t k = 0, goff = 0, glen = 0;
-        if (t < d) {
-            k = pool[dstart + t];
+    auto consume = [&](bool valid, uint32_t v) {
+        bool isnew = false;
+        unsigned long long key = 0;
+        if (valid) {
+            isnew = ins(v);
+            key = group_key(gi, v);
+            if (isnew && gi.probe) isnew = !htab_contains(ht, hm, key);
+        }
+        emitted += emit_candidates(isnew, key, gi.c, W, lane);
+    };
+    for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
+        const uint32_t e = cb + lane * nwarps;
+        uint32_t k = 0, off = 0, len = 0;
+        if (e < d) {
+            k = pool[dstart + e];
             if (gi.part == PART_U) {
-                glen = 1;
+                len = 1;
             } else {
                 const uint4 gd = dg[k];
-                goff = gd.x;
-                glen = (gi.part == PART_A) ? gd.y : gd.y - gd.w;   // B full, A_old prefix
+                off = gd.x;
+                len = (gi.part == PART_A) ? gd.y : gd.y - gd.w;   // B full, A_old prefix
             }
         }
-        const uint32_t incl = warp_incl_scan(glen, lane);
+        // long rows: the warp strides over one row at a time
+        unsigned lm = __ballot_sync(FULL_MASK, len >= 32);
+        while (lm) {
+            const int l = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const uint32_t roff = __shfl_sync(FULL_MASK, off, l);
+            const uint32_t rlen = __shfl_sync(FULL_MASK, len, l);
+            for (uint32_t qb = 0; qb < rlen; qb += 64) {
+                const uint32_t q0 = qb + lane, q1 = q0 + 32;
+                const bool v0ok = q0 < rlen, v1ok = q1 < rlen;
+                const uint32_t v0 = v0ok ? pool[roff + q0] : 0;
+                const uint32_t v1 = v1ok ? pool[roff + q1] : 0;
+                consume(v0ok, v0);
+                if (qb + 32 < rlen) consume(v1ok, v1);
+            }
+        }
+        // short rows: packed, 32 products per step
+        const uint32_t slen = len < 32 ? len : 0;
+        const uint32_t incl = warp_incl_scan(slen, lane);
         const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
         for (uint32_t fb = 0; fb < total; fb += 32) {
             const uint32_t f = fb + lane;
             const bool valid = f < total;
             int lo = 0, hi = 31;
 #pragma unroll
-            for (int s = 0; s < 5; s++) {       // first lane whose inclusive sum > f
+            for (int st = 0; st < 5; st++) {     // first lane whose inclusive sum > f
                 const int mid = (lo + hi) >> 1;
                 const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
                 if (f < v) hi = mid; else lo = mid + 1;
             }
             const int owner = lo > 31 ? 31 : lo;
-            const uint32_t o_off = __shfl_sync(FULL_MASK, goff, owner);
+            const uint32_t o_off = __shfl_sync(FULL_MASK, off, owner);
             const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
-            const uint32_t o_len = __shfl_sync(FULL_MASK, glen, owner);
+            const uint32_t o_len = __shfl_sync(FULL_MASK, slen, owner);
             const uint32_t o_k = __shfl_sync(FULL_MASK, k, owner);
             uint32_t v = 0;
-            bool isnew = false;
-            unsigned long long key = 0;
-            if (valid) {
+            if (valid)
                 v = (gi.part == PART_U) ? o_k : pool[o_off + (f - (o_incl - o_len))];
-                isnew = ins(v);
-                key = group_key(gi, v);
-                if (isnew && gi.probe) isnew = !htab_contains(ht, hm, key);
-            }
-            emitted += emit_candidates(isnew, key, gi.c, W, lane);
+            consume(valid, v);
         }
     }
     return emitted;
@@ -288,17 +347,18 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SlotTab S, ProdTab P
     for (unsigned long long g = (unsigned long long)blockIdx.x * WARPS + wib; g < n_groups;
          g += nw) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
-        for (uint32_t s = lane; s < (1u << LG); s += 32) tab[s] = EMPTY32;
+        const int lg = min((int)gi.lg, LG);
+        for (uint32_t s = lane; s < (1u << lg); s += 32) tab[s] = EMPTY32;
         __syncwarp();
         if (!gi.probe) {
             const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
             const uint32_t *pool = S.pool[gi.c];
-            for (uint32_t q = lane; q < md.y; q += 32) smem_insert(tab, LG, pool[md.x + q]);
+            for (uint32_t q = lane; q < md.y; q += 32) smem_insert(tab, lg, pool[md.x + q]);
             __syncwarp();
         }
         const uint4 own = owner_desc(S, gi);
-        const uint32_t e = expand_group(S, W, gi, own, 0, 32, lane,
-                                        [&](uint32_t v) { return smem_insert(tab, LG, v); });
+        const uint32_t e = expand_rows(S, W, gi, own, 0, 1, lane,
+                                       [&](uint32_t v) { return smem_insert(tab, lg, v); });
         if (lane == 0 && e) {
             atomicAdd(&S.cand[gi.c], (unsigned long long)e);
             bytes += 12ull * e;
@@ -318,19 +378,20 @@ __global__ void __launch_bounds__(256) k_spgemm_cta(SlotTab S, ProdTab P, WorkBu
     unsigned long long bytes = 0;
     for (unsigned long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
-        for (uint32_t s = threadIdx.x; s < (1u << LG); s += blockDim.x) smem[s] = EMPTY32;
+        const int lg = min((int)gi.lg, LG);
+        for (uint32_t s = threadIdx.x; s < (1u << lg); s += blockDim.x) smem[s] = EMPTY32;
         if (threadIdx.x == 0) emitted_sh = 0;
         __syncthreads();
         if (!gi.probe) {
             const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
             const uint32_t *pool = S.pool[gi.c];
             for (uint32_t q = threadIdx.x; q < md.y; q += blockDim.x)
-                smem_insert(smem, LG, pool[md.x + q]);
+                smem_insert(smem, lg, pool[md.x + q]);
         }
         __syncthreads();
         const uint4 own = owner_desc(S, gi);
-        const uint32_t e = expand_group(S, W, gi, own, wib * 32, blockDim.x, lane,
-                                        [&](uint32_t v) { return smem_insert(smem, LG, v); });
+        const uint32_t e = expand_rows(S, W, gi, own, wib, blockDim.x >> 5, lane,
+                                       [&](uint32_t v) { return smem_insert(smem, lg, v); });
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
@@ -342,7 +403,9 @@ __global__ void __launch_bounds__(256) k_spgemm_cta(SlotTab S, ProdTab P, WorkBu
 }
 
 // Bin 3: one CTA per group with an n-bit bitmap of the output row (shared
-// memory when it fits, else a per-CTA slice of global scratch).
+// memory when it fits, else a per-CTA slice of global scratch).  In mask mode
+// the mask row's bits are set first; in probe mode new bits are checked
+// against the non-terminal's hash set instead.
 __global__ void __launch_bounds__(256) k_spgemm_bitmap(SlotTab S, ProdTab P, WorkBufs W,
                                                        int bin, int use_smem) {
     extern __shared__ uint32_t smem[];
@@ -357,7 +420,7 @@ __global__ void __launch_bounds__(256) k_spgemm_bitmap(SlotTab S, ProdTab P, Wor
         for (uint32_t s = threadIdx.x; s < words; s += blockDim.x) bm[s] = 0;
         if (threadIdx.x == 0) emitted_sh = 0;
         __syncthreads();
-        {
+        if (!gi.probe) {
             const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
             const uint32_t *pool = S.pool[gi.c];
             for (uint32_t q = threadIdx.x; q < md.y; q += blockDim.x) {
@@ -367,8 +430,8 @@ __global__ void __launch_bounds__(256) k_spgemm_bitmap(SlotTab S, ProdTab P, Wor
         }
         __syncthreads();
         const uint4 own = owner_desc(S, gi);
-        const uint32_t e = expand_group(S, W, gi, own, wib * 32, blockDim.x, lane,
-                                        [&](uint32_t v) { return bitmap_insert(bm, v); });
+        const uint32_t e = expand_rows(S, W, gi, own, wib, blockDim.x >> 5, lane,
+                                       [&](uint32_t v) { return bitmap_insert(bm, v); });
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
@@ -384,6 +447,7 @@ __global__ void __launch_bounds__(256) k_spgemm_bitmap(SlotTab S, ProdTab P, Wor
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
+    if (W.cnt->overflow & OVF_PRE) return;     // the iteration is re-run after a growth
     const int lane = threadIdx.x & 31;
     const unsigned long long nc = min(W.cnt->cand, W.cand_cap);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -434,10 +498,13 @@ __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
 
 // Rows that received entries in the previous merge stop being "new".
 __global__ void k_reset_dnew(SlotTab S, WorkBufs W) {
-    const unsigned long long n_in = *W.touched_in_n;
+    if (W.cnt->overflow & OVF_PRE) return;
+    const int par = *W.parity;
+    const unsigned long long n_in = W.touched_n[par];
+    const uint2 *t_in = W.touched[par];
     for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
          e < n_in; e += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint2 t = W.touched_in[e];
+        const uint2 t = t_in[e];
         const uint32_t slot = t.x >> 1, o = t.x & 1;
         S.desc[slot][(size_t)o * S.n[slot] + t.y].w = 0;
     }
@@ -445,7 +512,11 @@ __global__ void k_reset_dnew(SlotTab S, WorkBufs W) {
 
 // Count the new entries of every row; list each row the first time.
 __global__ void __launch_bounds__(256) k_count(SlotTab S, WorkBufs W) {
+    if (W.cnt->overflow & OVF_PRE) return;
     const int lane = threadIdx.x & 31;
+    const int par = *W.parity;
+    unsigned long long *out_n = &W.touched_n[par ^ 1];
+    uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long nd = W.cnt->delta;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x +
@@ -470,11 +541,11 @@ __global__ void __launch_bounds__(256) k_count(SlotTab S, WorkBufs W) {
             const unsigned m = __ballot_sync(FULL_MASK, f);
             if (!m) continue;
             unsigned long long pos = 0;
-            if (lane == 0) pos = atomicAdd(W.touched_out_n, (unsigned long long)__popc(m));
+            if (lane == 0) pos = atomicAdd(out_n, (unsigned long long)__popc(m));
             pos = __shfl_sync(FULL_MASK, pos, 0);
             if (f) {
                 pos += __popc(m & ((1u << lane) - 1));
-                if (pos < W.touched_cap) W.touched_out[pos] = make_uint2(slot * 2 + o, o ? j : i);
+                if (pos < W.touched_cap) t_out[pos] = make_uint2(slot * 2 + o, o ? j : i);
                 else atomicOr(&W.cnt->overflow, OVF_TOUCHED);
             }
         }
@@ -484,13 +555,16 @@ __global__ void __launch_bounds__(256) k_count(SlotTab S, WorkBufs W) {
 // Make room for every listed row (relocate to a larger segment if needed).
 // Idempotent: after a pool overflow the host grows the pool and runs it again.
 __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs W) {
+    if (W.cnt->overflow & OVF_PRE) return;
     const int lane = threadIdx.x & 31;
-    const unsigned long long n_t = min(*W.touched_out_n, W.touched_cap);
+    const int par = *W.parity;
+    const uint2 *t_out = W.touched[par ^ 1];
+    const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
     const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) +
                                 (threadIdx.x >> 5);
          e < n_t; e += nw) {
-        const uint2 t = W.touched_out[e];
+        const uint2 t = t_out[e];
         const uint32_t slot = t.x >> 1, o = t.x & 1;
         uint4 *dp = &S.desc[slot][(size_t)o * S.n[slot] + t.y];
         const uint4 dsc = *dp;
@@ -522,7 +596,7 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
 // Append the new pairs: (i, j) goes to row i of the row form and row j of
 // the column form.
 __global__ void __launch_bounds__(256) k_scatter(SlotTab S, WorkBufs W) {
-    if (W.cnt->overflow & OVF_POOL) return;
+    if (W.cnt->overflow & (OVF_PRE | OVF_POOL)) return;
     const unsigned long long nd = W.cnt->delta;
     for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
          t < nd; t += (unsigned long long)gridDim.x * blockDim.x) {
@@ -536,6 +610,82 @@ __global__ void __launch_bounds__(256) k_scatter(SlotTab S, WorkBufs W) {
         pool[(size_t)dsc[i].x + pr] = j;
         const uint32_t pc = atomicAdd(&dsc[(size_t)n + j].y, 1u);
         pool[(size_t)dsc[(size_t)n + j].x + pc] = i;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// iteration frame (device-side checks; lets the loop run inside a CUDA graph)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_iter_begin(SlotTab S, InstTab I, WorkBufs W,
+                                                    uint32_t n_slots, uint32_t n_inst) {
+    const int par = *W.parity;
+    if (threadIdx.x == 0) {
+        *W.cnt = Counters{};
+        W.touched_n[par ^ 1] = 0;
+    }
+    for (uint32_t s = threadIdx.x; s < n_slots; s += blockDim.x) {
+        S.cand[s] = 0;
+        S.delta[s] = 0;
+    }
+    for (uint32_t k = threadIdx.x; k < n_inst; k += blockDim.x) I.delta[k] = 0;
+}
+
+// Before the commit: stop the iteration if a buffer overflowed or if some
+// pair set could pass half full with this iteration's candidates.
+__global__ void __launch_bounds__(256) k_check(SlotTab S, WorkBufs W, uint32_t n_slots) {
+    bool grow = false;
+    for (uint32_t s = threadIdx.x; s < n_slots; s += blockDim.x)
+        grow |= 2 * (S.nnz[s] + S.cand[s]) > S.hmask[s] + 1;
+    if (__syncthreads_or(grow) && threadIdx.x == 0) atomicOr(&W.cnt->overflow, OVF_HASH);
+}
+
+// After the merge: add the new pairs to the counts, advance every
+// instance's iteration count, flip the touched-list parity and decide
+// whether the closure loop goes on (Algorithm 1: while M is changing).
+__global__ void __launch_bounds__(256) k_iter_end(SlotTab S, InstTab I, WorkBufs W, LoopCtl *ctl,
+                                                  uint32_t n_slots, uint32_t n_inst,
+                                                  int count_iteration,
+                                                  cudaGraphConditionalHandle handle,
+                                                  int in_graph) {
+    const unsigned flags = W.cnt->overflow & (OVF_PRE | OVF_POOL);
+    if (flags) {                        // the host grows a buffer and finishes the iteration
+        if (threadIdx.x == 0) {
+            ctl->status = flags;
+            if (in_graph) cudaGraphSetConditional(handle, 0);
+        }
+        return;
+    }
+    for (uint32_t s = threadIdx.x; s < n_slots; s += blockDim.x) {
+        const unsigned long long d = S.delta[s];
+        S.nnz[s] += d;
+        if (d) atomicAdd(&I.delta[S.inst[s]], d);
+    }
+    __syncthreads();
+    if (count_iteration) {
+        for (uint32_t k = threadIdx.x; k < n_inst; k += blockDim.x) {
+            if (I.active[k]) I.iters[k] += 1;
+            I.active[k] = I.delta[k] > 0 ? 1u : 0u;
+        }
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long total = W.cnt->delta;
+        const int par = *W.parity;
+        if (count_iteration) {
+            ctl->total_flops += W.cnt->flops;
+            ctl->total_cand += W.cnt->cand;
+            ctl->total_delta += total;
+            ctl->total_touched_in += W.touched_n[par];
+            ctl->total_touched_out += W.touched_n[par ^ 1];
+            for (int b = 0; b < N_BINS; b++) ctl->bytes_bin[b] += W.cnt->bytes_bin[b];
+            ctl->bytes_sym += W.cnt->bytes_sym;
+        }
+        *W.parity = par ^ 1;
+        ctl->status = 0;
+        ctl->last_delta = total;
+        if (count_iteration) ctl->iter += 1;
+        const bool more = total > 0 && ctl->iter < ctl->limit;
+        if (in_graph) cudaGraphSetConditional(handle, more ? 1u : 0u);
     }
 }
 
@@ -725,34 +875,6 @@ __global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const ui
 
 constexpr uint32_t SCAN_TILE = 1024;   // 256 threads x 4 elements
 
-__device__ __forceinline__ unsigned long long block_excl_scan256(unsigned long long v,
-                                                                 unsigned long long *sh,
-                                                                 unsigned long long &total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned long long x = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        unsigned long long t = __shfl_up_sync(FULL_MASK, x, d);
-        if (lane >= d) x += t;
-    }
-    if (lane == 31) sh[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        unsigned long long y = lane < 8 ? sh[lane] : 0;
-#pragma unroll
-        for (int d = 1; d < 8; d <<= 1) {
-            unsigned long long t = __shfl_up_sync(FULL_MASK, y, d);
-            if (lane >= d) y += t;
-        }
-        if (lane < 8) sh[8 + lane] = y;
-    }
-    __syncthreads();
-    total = sh[15];
-    const unsigned long long before = (w ? sh[8 + w - 1] : 0ull) + x - v;
-    __syncthreads();
-    return before;
-}
-
 __global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *in, uint32_t n,
                                                      unsigned long long *bsum) {
     __shared__ unsigned long long sh[16];
@@ -823,8 +945,11 @@ static inline int grid_for(unsigned long long work, int per_block, int sms, int 
 }
 
 constexpr size_t BIN1_SMEM = 8 * 2048 * 4;     // 8 warps x 2048 slots
-constexpr size_t BIN2_SMEM = 16384 * 4;
+constexpr size_t BIN2_SMEM = 8192 * 4;
 constexpr size_t SMEM_BITMAP_MAX = 200 * 1024;
+
+static void set_smem_attrs();
+void prepare_launch_attributes() { set_smem_attrs(); }
 
 static void set_smem_attrs() {
     static bool done = false;
@@ -832,7 +957,7 @@ static void set_smem_attrs() {
     done = true;
     cudaFuncSetAttribute(k_spgemm_warp<11, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)BIN1_SMEM);
-    cudaFuncSetAttribute(k_spgemm_cta<14>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_spgemm_cta<13>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)BIN2_SMEM);
     cudaFuncSetAttribute(k_spgemm_bitmap, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)SMEM_BITMAP_MAX);
@@ -856,7 +981,7 @@ void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &
         k_spgemm_warp<11, 8><<<sms * 3, 256, BIN1_SMEM, st>>>(S, P, W, 1);
         break;
     case 2:
-        k_spgemm_cta<14><<<sms * 3, 256, BIN2_SMEM, st>>>(S, P, W, 2);
+        k_spgemm_cta<13><<<sms * 3, 256, BIN2_SMEM, st>>>(S, P, W, 2);
         break;
     default: {
         const size_t bm_bytes = (size_t)((max_n + 31) / 32) * 4;
@@ -871,6 +996,22 @@ void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &
 
 void launch_commit(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {
     k_commit<<<sms * 8, 256, 0, st>>>(S, W);
+}
+
+void launch_iter_begin(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t n_slots,
+                       uint32_t n_inst, cudaStream_t st) {
+    k_iter_begin<<<1, 256, 0, st>>>(S, I, W, n_slots, n_inst);
+}
+
+void launch_check(const SlotTab &S, const WorkBufs &W, uint32_t n_slots, cudaStream_t st) {
+    k_check<<<1, 256, 0, st>>>(S, W, n_slots);
+}
+
+void launch_iter_end(const SlotTab &S, const InstTab &I, const WorkBufs &W, LoopCtl *ctl,
+                     uint32_t n_slots, uint32_t n_inst, bool count_iteration,
+                     cudaGraphConditionalHandle handle, bool in_graph, cudaStream_t st) {
+    k_iter_end<<<1, 256, 0, st>>>(S, I, W, ctl, n_slots, n_inst, count_iteration ? 1 : 0, handle,
+                                  in_graph ? 1 : 0);
 }
 
 void launch_reset_dnew(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {

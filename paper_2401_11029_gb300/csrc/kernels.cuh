@@ -23,6 +23,7 @@ constexpr uint32_t PART_A = 0;      // dA . B     : row groups of a's delta
 constexpr uint32_t PART_B = 1;      // A_old . dB : column groups of b's delta
 constexpr uint32_t PART_U = 2;      // c -> a     : row groups of a's delta
 constexpr uint32_t MODE_PROBE = 4;  // group code bit: mask by probing htab[c]
+                                    // group code: prod << 8 | lg << 3 | probe | part
 constexpr unsigned long long EMPTY_KEY = ~0ull;
 constexpr uint32_t EMPTY32 = 0xFFFFFFFFu;
 
@@ -31,7 +32,7 @@ constexpr int N_BINS = 4;
 // holds twice its limit so the load factor stays <= 1/2.
 constexpr uint32_t BIN0_LIMIT = 128;    // warp per group, 256-slot table
 constexpr uint32_t BIN1_LIMIT = 1024;   // warp per group, 2048-slot table
-constexpr uint32_t BIN2_LIMIT = 8192;   // CTA per group, 16384-slot table
+constexpr uint32_t BIN2_LIMIT = 4096;   // CTA per group, 8192-slot table
                                         // bin 3: CTA per group, n-bit bitmap
 constexpr uint32_t PROBE_RATIO = 4;     // probe when mask_len > PROBE_RATIO*flops
 
@@ -44,11 +45,29 @@ struct SlotTab {              // per slot (device arrays, length n_slots)
     unsigned long long *hmask;      // capacity - 1
     unsigned long long *cand;       // candidates emitted for the slot (iteration)
     unsigned long long *delta;      // new pairs of the slot (iteration)
+    unsigned long long *nnz;        // pairs of the slot so far
 };
 
 struct InstTab {              // per instance
     unsigned long long *pool_top;   // entries in use (device counters)
     unsigned long long *pool_cap;
+    unsigned long long *delta;      // new pairs of the instance (iteration)
+    uint32_t *active;               // 1 while the instance still has delta rows
+    uint32_t *iters;                // closure iterations the instance has run
+};
+
+// Closure-loop control in device memory (one per batch).
+struct LoopCtl {
+    uint32_t iter;                  // iterations finished since the solve began
+    uint32_t limit;                 // stop after this many (0xFFFFFFFF = none)
+    uint32_t status;                // overflow bits that stopped the last iteration
+    uint32_t pad;
+    unsigned long long last_delta;  // new pairs of the last finished iteration
+    // totals over the finished iterations (work and algorithmic bytes)
+    unsigned long long total_flops, total_cand, total_delta;
+    unsigned long long total_touched_in, total_touched_out;
+    unsigned long long bytes_bin[N_BINS];
+    unsigned long long bytes_sym;
 };
 
 struct ProdTab {              // global production table of the batch
@@ -68,16 +87,23 @@ struct Counters {
     unsigned int pad;
 };
 
-constexpr unsigned OVF_GROUPS = 1u;
-constexpr unsigned OVF_CAND = 2u;
-constexpr unsigned OVF_POOL = 4u;
-constexpr unsigned OVF_TOUCHED = 8u;
+constexpr unsigned OVF_GROUPS = 1u;    // work list overflow        (before the commit)
+constexpr unsigned OVF_CAND = 2u;      // candidate buffer overflow (before the commit)
+constexpr unsigned OVF_POOL = 4u;      // row pool exhausted        (inside the merge)
+constexpr unsigned OVF_TOUCHED = 8u;   // touched list overflow (cannot happen: sized 2x)
+constexpr unsigned OVF_HASH = 16u;     // a pair set would pass half full (before the commit)
+constexpr unsigned OVF_PRE = OVF_GROUPS | OVF_CAND | OVF_HASH;   // iteration not committed
 
 struct WorkBufs {
-    // touched rows {slot*2+o, idx}: "in" = rows whose dnew > 0 (this
-    // iteration's deltas), "out" = rows the current merge appends to
-    uint2 *touched_in;  const unsigned long long *touched_in_n;   // device count
-    uint2 *touched_out; unsigned long long *touched_out_n; unsigned long long touched_cap;
+    // touched rows {slot*2+o, idx}: touched[*parity] lists the rows whose
+    // dnew > 0 (this iteration's deltas, "in"); touched[*parity ^ 1] gets the
+    // rows the current merge appends to ("out").  The end-of-iteration
+    // kernel flips the parity, so the same launch sequence serves every
+    // iteration (and can be captured once in a CUDA graph).
+    uint2 *touched[2];
+    unsigned long long *touched_n;     // [2], device counts
+    int *parity;                       // device
+    unsigned long long touched_cap;
     uint2 *groups[N_BINS]; unsigned long long group_cap[N_BINS];   // {code, idx}
     unsigned long long *cand_key; uint32_t *cand_slot; unsigned long long cand_cap;
     unsigned long long *delta_key; uint32_t *delta_slot;
@@ -86,11 +112,23 @@ struct WorkBufs {
 };
 
 // ---- launch wrappers (kernels.cu) -------------------------------------
+// Set the kernels' shared-memory limits (done by the first launch anyway;
+// call it before capturing launches into a graph).
+void prepare_launch_attributes();
 void launch_symbolic(const SlotTab &S, const ProdTab &P, const WorkBufs &W, int prod_only,
                      int sms, cudaStream_t st);
 void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &W,
                    uint32_t max_n, int sms, cudaStream_t st);
 void launch_commit(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
+// Iteration frame: zero the per-iteration counters; check the pre-commit
+// conditions (buffer overflow, pair-set load); finish the iteration (pair
+// counts, per-instance iteration counts, parity flip, loop condition).
+void launch_iter_begin(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t n_slots,
+                       uint32_t n_inst, cudaStream_t st);
+void launch_check(const SlotTab &S, const WorkBufs &W, uint32_t n_slots, cudaStream_t st);
+void launch_iter_end(const SlotTab &S, const InstTab &I, const WorkBufs &W, LoopCtl *ctl,
+                     uint32_t n_slots, uint32_t n_inst, bool count_iteration,
+                     cudaGraphConditionalHandle handle, bool in_graph, cudaStream_t st);
 void launch_reset_dnew(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
 void launch_count(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
 void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, int sms,

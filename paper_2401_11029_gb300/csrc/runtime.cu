@@ -275,58 +275,76 @@ struct Runner {
     DevArr<uint32_t *> d_pool;
     DevArr<uint32_t> d_n, d_inst;
     DevArr<unsigned long long *> d_htab;
-    DevArr<unsigned long long> d_hmask, d_cand, d_delta;
-    DevArr<unsigned long long> d_pool_top, d_pool_cap;
+    DevArr<unsigned long long> d_hmask, d_cand, d_delta, d_nnz;
+    DevArr<unsigned long long> d_pool_top, d_pool_cap, d_inst_delta;
+    DevArr<uint32_t> d_inst_active, d_inst_iters;
     DevArr<uint4> d_prod;
     DevArr<uint32_t> d_use_off, d_use_code;
     // work buffers
     DevArr<uint2> d_touched[2];
     DevArr<unsigned long long> d_touched_n;   // [2]
-    int cur = 0;                              // d_touched[cur] = this iteration's input
     DevArr<uint2> d_groups[N_BINS];
     DevArr<unsigned long long> d_cand_key, d_delta_key;
     DevArr<uint32_t> d_cand_slot, d_delta_slot;
     DevArr<uint32_t> d_bitmap;
     DevArr<Counters> d_cnt;
+    DevArr<LoopCtl> d_ctl;
+    DevArr<int> d_parity;
     Counters *h_cnt = nullptr;                // pinned
+    LoopCtl *h_ctl = nullptr;                 // pinned
+    int *h_parity = nullptr;                  // pinned
     unsigned long long *h_small = nullptr;    // pinned scratch for small reads
     size_t h_small_n = 0;
     uint64_t cand_cap = 0, touched_cap = 0;
     uint64_t group_cap[N_BINS] = {};
-    std::vector<uint64_t> host_slot_n;        // per slot: vertices
-    // per-iteration host copies
-    std::vector<unsigned long long> h_cand, h_delta;
-    uint64_t total_flops = 0, total_cand = 0, regrows = 0;
+    uint64_t regrows = 0;
+    // the iteration as one CUDA graph: a while-loop node around the body
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphConditionalHandle handle = 0;
+    bool graph_valid = false;
 
     explicit Runner(cflr_ctx *owner) : own(owner), st(owner->stream), sms(owner->sms) {
         prof.owner = own;
         prof.on = own->cfg.profile != 0;
         prof.st = st;
         ck(cudaMallocHost(&h_cnt, sizeof(Counters)), "cudaMallocHost");
-    }
-    // Point the runner at a batch of contexts (their matrices must be loaded).
-    void bind(std::vector<cflr_ctx *> ctxs) {
-        cx = std::move(ctxs);
-        cur = 0;
-        total_flops = total_cand = regrows = 0;
-        build_tables();
+        ck(cudaMallocHost(&h_ctl, sizeof(LoopCtl)), "cudaMallocHost");
+        ck(cudaMallocHost(&h_parity, sizeof(int)), "cudaMallocHost");
     }
     ~Runner() {
+        drop_graph();
         if (h_cnt) cudaFreeHost(h_cnt);
+        if (h_ctl) cudaFreeHost(h_ctl);
+        if (h_parity) cudaFreeHost(h_parity);
         if (h_small) cudaFreeHost(h_small);
+    }
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+        graph_valid = false;
     }
 
     unsigned long long *small(size_t n) {
         if (n > h_small_n) {
             if (h_small) cudaFreeHost(h_small);
+            h_small = nullptr;
             h_small_n = std::max<size_t>(n, 64);
             ck(cudaMallocHost(&h_small, h_small_n * 8), "cudaMallocHost");
         }
         return h_small;
     }
+    void sync(const char *what) { ck(cudaStreamSynchronize(st), what); }
 
     // ---- tables ---------------------------------------------------------
-    void build_tables() {
+    // Point the runner at a batch of contexts (their matrices are loaded):
+    // global slot ids, production and use tables, pair counts.
+    void bind(std::vector<cflr_ctx *> ctxs) {
+        cx = std::move(ctxs);
+        regrows = 0;
+        drop_graph();
         base.clear();
         slot_ctx.clear();
         n_slots = 0;
@@ -339,9 +357,8 @@ struct Runner {
             max_n = std::max(max_n, cx[k]->n);
         }
         std::vector<uint4 *> hd(n_slots);
-        std::vector<uint32_t *> hp(n_slots);
         std::vector<uint32_t> hn(n_slots), hi(n_slots);
-        host_slot_n.assign(n_slots, 0);
+        std::vector<unsigned long long> hz(n_slots);
         std::vector<uint4> prods;
         std::vector<std::vector<uint32_t>> uses((size_t)n_slots * 2);
         for (size_t k = 0; k < cx.size(); k++) {
@@ -349,10 +366,9 @@ struct Runner {
             uint32_t nt = (uint32_t)c->g.nts.size(), b0 = base[k];
             for (uint32_t x = 0; x < nt; x++) {
                 hd[b0 + x] = c->desc + (size_t)x * 2 * c->n;
-                hp[b0 + x] = c->pool;
                 hn[b0 + x] = c->n;
                 hi[b0 + x] = (uint32_t)k;
-                host_slot_n[b0 + x] = c->n;
+                hz[b0 + x] = c->nnz[x];
             }
             const Grammar &g = c->g;
             for (size_t p = 0; p < g.bin_c.size(); p++) {
@@ -373,6 +389,7 @@ struct Runner {
             codes.insert(codes.end(), u.begin(), u.end());
             off.push_back((uint32_t)codes.size());
         }
+        const size_t ni = cx.size();
         d_desc.ensure(own, n_slots);
         d_pool.ensure(own, n_slots);
         d_n.ensure(own, n_slots);
@@ -381,23 +398,42 @@ struct Runner {
         d_hmask.ensure(own, n_slots);
         d_cand.ensure(own, n_slots);
         d_delta.ensure(own, n_slots);
+        d_nnz.ensure(own, n_slots);
         d_prod.ensure(own, prods.size());
         d_use_off.ensure(own, off.size());
         d_use_code.ensure(own, codes.size());
-        d_pool_top.ensure(own, cx.size());
-        d_pool_cap.ensure(own, cx.size());
+        d_pool_top.ensure(own, ni);
+        d_pool_cap.ensure(own, ni);
+        d_inst_delta.ensure(own, ni);
+        d_inst_active.ensure(own, ni);
+        d_inst_iters.ensure(own, ni);
+        d_touched_n.ensure(own, 2);
+        d_cnt.ensure(own, 1);
+        d_ctl.ensure(own, 1);
+        d_parity.ensure(own, 1);
         ck(cudaMemcpyAsync(d_desc.p, hd.data(), n_slots * sizeof(uint4 *), cudaMemcpyHostToDevice, st), "H2D");
-        ck(cudaMemcpyAsync(d_pool.p, hp.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_n.p, hn.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_inst.p, hi.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_nnz.p, hz.data(), n_slots * 8, cudaMemcpyHostToDevice, st), "H2D");
         if (!prods.empty())
             ck(cudaMemcpyAsync(d_prod.p, prods.data(), prods.size() * sizeof(uint4), cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_use_off.p, off.data(), off.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
         if (!codes.empty())
             ck(cudaMemcpyAsync(d_use_code.p, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
+        // loop state: parity 0, no touched rows, iteration count 0
+        std::vector<uint32_t> act(ni);
+        for (size_t k = 0; k < ni; k++) act[k] = cx[k]->touched_n ? 1u : 0u;
+        ck(cudaMemcpyAsync(d_inst_active.p, act.data(), ni * 4, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemsetAsync(d_inst_iters.p, 0, ni * 4, st), "memset");
+        ck(cudaMemsetAsync(d_touched_n.p, 0, 16, st), "memset");
+        ck(cudaMemsetAsync(d_parity.p, 0, sizeof(int), st), "memset");
+        LoopCtl ctl{};
+        ctl.limit = own->cfg.max_iterations ? own->cfg.max_iterations : 0xFFFFFFFFu;
+        *h_ctl = ctl;
+        ck(cudaMemcpyAsync(d_ctl.p, h_ctl, sizeof(LoopCtl), cudaMemcpyHostToDevice, st), "H2D");
         upload_htabs();
         upload_pools();
-        ck(cudaStreamSynchronize(st), "sync tables");
+        sync("bind");
     }
 
     void upload_htabs() {
@@ -411,10 +447,11 @@ struct Runner {
         }
         ck(cudaMemcpyAsync(d_htab.p, ht.data(), n_slots * 8, cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_hmask.p, hm.data(), n_slots * 8, cudaMemcpyHostToDevice, st), "H2D");
-        ck(cudaStreamSynchronize(st), "sync");
+        sync("upload htabs");
     }
 
-    void upload_pools() {
+    // Pool pointers, capacities and (at bind only) the bump counters.
+    void upload_pools(bool tops = true) {
         std::vector<unsigned long long> top(cx.size()), cap(cx.size());
         std::vector<uint32_t *> hp(n_slots);
         for (size_t k = 0; k < cx.size(); k++) {
@@ -422,23 +459,35 @@ struct Runner {
             cap[k] = cx[k]->pool_cap;
         }
         for (uint32_t s = 0; s < n_slots; s++) hp[s] = cx[slot_ctx[s]]->pool;
-        ck(cudaMemcpyAsync(d_pool_top.p, top.data(), cx.size() * 8, cudaMemcpyHostToDevice, st), "H2D");
+        if (tops)
+            ck(cudaMemcpyAsync(d_pool_top.p, top.data(), cx.size() * 8, cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_pool_cap.p, cap.data(), cx.size() * 8, cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_pool.p, hp.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
-        ck(cudaStreamSynchronize(st), "sync");
+        sync("upload pools");
     }
 
-    void download_pool_tops() {
-        unsigned long long *h = small(cx.size());
-        ck(cudaMemcpyAsync(h, d_pool_top.p, cx.size() * 8, cudaMemcpyDeviceToHost, st), "D2H");
-        ck(cudaStreamSynchronize(st), "sync");
-        for (size_t k = 0; k < cx.size(); k++) cx[k]->pool_top = h[k];
+    // After a solve: pool counters, pair counts and iteration counts back to
+    // the contexts.
+    void download_state(bool add_iterations) {
+        const size_t ni = cx.size();
+        std::vector<unsigned long long> top(ni), nz(n_slots);
+        std::vector<uint32_t> it(ni);
+        ck(cudaMemcpyAsync(top.data(), d_pool_top.p, ni * 8, cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaMemcpyAsync(nz.data(), d_nnz.p, n_slots * 8, cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaMemcpyAsync(it.data(), d_inst_iters.p, ni * 4, cudaMemcpyDeviceToHost, st), "D2H");
+        sync("download state");
+        for (size_t k = 0; k < ni; k++) {
+            cx[k]->pool_top = top[k];
+            if (add_iterations) cx[k]->iterations += it[k];
+        }
+        for (uint32_t s = 0; s < n_slots; s++) cx[slot_ctx[s]]->nnz[s - base[slot_ctx[s]]] = nz[s];
     }
 
     SlotTab slots() {
         SlotTab S;
         S.desc = d_desc.p; S.pool = d_pool.p; S.n = d_n.p; S.inst = d_inst.p;
         S.htab = d_htab.p; S.hmask = d_hmask.p; S.cand = d_cand.p; S.delta = d_delta.p;
+        S.nnz = d_nnz.p;
         return S;
     }
     ProdTab prodtab() {
@@ -448,15 +497,16 @@ struct Runner {
     }
     InstTab insttab() {
         InstTab I;
-        I.pool_top = d_pool_top.p; I.pool_cap = d_pool_cap.p;
+        I.pool_top = d_pool_top.p; I.pool_cap = d_pool_cap.p; I.delta = d_inst_delta.p;
+        I.active = d_inst_active.p; I.iters = d_inst_iters.p;
         return I;
     }
     WorkBufs work() {
         WorkBufs W{};
-        W.touched_in = d_touched[cur].p;
-        W.touched_in_n = d_touched_n.p + cur;
-        W.touched_out = d_touched[cur ^ 1].p;
-        W.touched_out_n = d_touched_n.p + (cur ^ 1);
+        W.touched[0] = d_touched[0].p;
+        W.touched[1] = d_touched[1].p;
+        W.touched_n = d_touched_n.p;
+        W.parity = d_parity.p;
         W.touched_cap = touched_cap;
         for (int b = 0; b < N_BINS; b++) {
             W.groups[b] = d_groups[b].p;
@@ -484,42 +534,45 @@ struct Runner {
         d_cand_slot.alloc(own, cap);
         d_delta_key.alloc(own, cap);
         d_delta_slot.alloc(own, cap);
+        graph_valid = false;
     }
-    // touched lists must hold two rows per new pair (row and column form)
-    void size_touched(uint64_t cap, bool keep_in) {
+    // Both touched lists; the list touched[parity] keeps its rows.  Each must
+    // hold two rows per new pair (row and column form).
+    void size_touched(uint64_t cap, int parity) {
         cap = std::max<uint64_t>(cap, min_cap(1 << 16));
         if (cap <= touched_cap) return;
-        DevArr<uint2> nin;
-        nin.alloc(own, cap);
-        if (keep_in && d_touched[cur].p) {
-            ck(cudaMemcpyAsync(nin.p, d_touched[cur].p, touched_cap * sizeof(uint2),
+        DevArr<uint2> keep;
+        keep.alloc(own, cap);
+        if (parity >= 0 && d_touched[parity].p) {
+            ck(cudaMemcpyAsync(keep.p, d_touched[parity].p, touched_cap * sizeof(uint2),
                                cudaMemcpyDeviceToDevice, st), "D2D");
-            ck(cudaStreamSynchronize(st), "sync");
+            sync("touched copy");
         }
-        std::swap(d_touched[cur].p, nin.p);
-        std::swap(d_touched[cur].n, nin.n);
-        d_touched[cur].o = own;
-        nin.release();
-        d_touched[cur ^ 1].alloc(own, cap);
+        const int pin = parity >= 0 ? parity : 0;
+        std::swap(d_touched[pin].p, keep.p);
+        std::swap(d_touched[pin].n, keep.n);
+        d_touched[pin].o = own;
+        keep.release();
+        d_touched[pin ^ 1].alloc(own, cap);
         touched_cap = cap;
+        graph_valid = false;
     }
     void size_groups(int b, uint64_t cap) {
         cap = std::max<uint64_t>(cap, min_cap(1 << 14));
         if (cap <= group_cap[b]) return;
         group_cap[b] = cap;
         d_groups[b].alloc(own, cap);
+        graph_valid = false;
     }
     void init_buffers(uint64_t cand_hint, uint64_t touched_in) {
-        d_touched_n.ensure(own, 2);
-        d_cnt.ensure(own, 1);
         const uint64_t ic = own->cfg.initial_capacity;
         size_cand(ic ? std::max<uint64_t>(ic, 32) : cand_hint);
-        size_touched(std::max<uint64_t>(2 * cand_cap, touched_in), false);
+        size_touched(std::max<uint64_t>(2 * cand_cap, touched_in), -1);
         for (int b = 0; b < N_BINS; b++) size_groups(b, ic ? ic : (b < 2 ? 1 << 18 : 1 << 14));
-        ck(cudaMemsetAsync(d_touched_n.p, 0, 16, st), "memset");
         if (max_n > 200 * 1024 * 8) {   // bitmaps do not fit shared memory
             uint64_t words = (max_n + 31) / 32;
             d_bitmap.ensure(own, words * (uint64_t)sms * 8);
+            graph_valid = false;
         }
     }
 
@@ -530,93 +583,12 @@ struct Runner {
         unsigned long long *nt = (unsigned long long *)c->dalloc(cap * 8);
         ck(cudaMemsetAsync(nt, 0xFF, cap * 8, st), "memset");
         prof.run(KID_REHASH, [&] { launch_rehash(c->htab[x], c->hcap[x], nt, cap, sms, st); });
-        own->k_bytes[KID_REHASH] += c->hcap[x] * 8 + nnz_of(s) * 8;
-        ck(cudaStreamSynchronize(st), "sync rehash");
+        own->k_bytes[KID_REHASH] += c->hcap[x] * 8 + need * 8;
+        sync("rehash");
         c->dfree(c->htab[x], c->hcap[x] * 8);
         c->htab[x] = nt;
         c->hcap[x] = cap;
-    }
-    uint64_t &nnz_of(uint32_t s) { return cx[slot_ctx[s]]->nnz[s - base[slot_ctx[s]]]; }
-    uint64_t hcap_of(uint32_t s) { return cx[slot_ctx[s]]->hcap[s - base[slot_ctx[s]]]; }
-
-    void read_counters() {
-        ck(cudaMemcpyAsync(h_cnt, d_cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, st), "D2H");
-    }
-
-    // Commit the candidates in the buffer and merge the new pairs into the
-    // matrices.  Returns the number of new pairs.
-    uint64_t commit_and_merge(std::vector<unsigned long long> &slot_delta) {
-        // hash capacity: every slot's set must stay at most half full
-        unsigned long long *hc = small(n_slots);
-        ck(cudaMemcpyAsync(hc, d_cand.p, n_slots * 8, cudaMemcpyDeviceToHost, st), "D2H");
-        ck(cudaStreamSynchronize(st), "sync");
-        bool grew = false;
-        for (uint32_t s = 0; s < n_slots; s++) {
-            uint64_t need = nnz_of(s) + hc[s];
-            if (2 * need > hcap_of(s)) {
-                grow_htab(s, need);
-                grew = true;
-            }
-        }
-        if (grew) upload_htabs();
-        const SlotTab S = slots();
-        const WorkBufs W = work();
-        uint64_t nc = std::min<uint64_t>(h_cnt->cand, cand_cap);
-        prof.run(KID_COMMIT, [&] { launch_commit(S, W, sms, st); });
-        prof.run(KID_RESET, [&] { launch_reset_dnew(S, W, sms, st); });
-        prof.run(KID_COUNT, [&] { launch_count(S, W, sms, st); });
-        prof.run(KID_CAPACITY, [&] { launch_capacity(S, insttab(), W, sms, st); });
-        read_counters();
-        unsigned long long *hs = small(2 + cx.size());
-        ck(cudaMemcpyAsync(hs, d_touched_n.p, 16, cudaMemcpyDeviceToHost, st), "D2H");
-        ck(cudaMemcpyAsync(hs + 2, d_pool_top.p, cx.size() * 8, cudaMemcpyDeviceToHost, st), "D2H");
-        ck(cudaStreamSynchronize(st), "sync merge");
-        uint64_t touched_in = hs[cur], touched_out = hs[cur ^ 1];
-        uint64_t nd = h_cnt->delta;
-        if (h_cnt->overflow & OVF_TOUCHED)
-            throw Status{CFLR_ECUDA, "internal: touched list overflow"};
-        int guard = 0;
-        while (h_cnt->overflow & OVF_POOL) {
-            if (++guard > 8) throw Status{CFLR_ENOMEM, "pool growth did not converge"};
-            for (size_t k = 0; k < cx.size(); k++) {
-                uint64_t top = hs[2 + k];
-                if (top > cx[k]->pool_cap) grow_pool(k, top);
-            }
-            upload_pools_caps_only();
-            unsigned zero = 0;
-            ck(cudaMemcpyAsync(&d_cnt.p->overflow, &zero, 4, cudaMemcpyHostToDevice, st), "H2D");
-            prof.run(KID_CAPACITY, [&] { launch_capacity(slots(), insttab(), work(), sms, st); });
-            read_counters();
-            ck(cudaMemcpyAsync(hs + 2, d_pool_top.p, cx.size() * 8, cudaMemcpyDeviceToHost, st), "D2H");
-            ck(cudaStreamSynchronize(st), "sync capacity");
-            regrows++;
-        }
-        prof.run(KID_SCATTER, [&] { launch_scatter(slots(), work(), sms, st); });
-        own->k_bytes[KID_COMMIT] += 20 * nc + 12 * nd;
-        own->k_bytes[KID_RESET] += 12 * touched_in;
-        own->k_bytes[KID_COUNT] += 20 * nd + 8 * touched_out;
-        own->k_bytes[KID_CAPACITY] += 24 * touched_out;
-        own->k_bytes[KID_SCATTER] += 52 * nd;
-        slot_delta.resize(n_slots);
-        ck(cudaMemcpyAsync(slot_delta.data(), d_delta.p, n_slots * 8, cudaMemcpyDeviceToHost, st), "D2H");
-        ck(cudaStreamSynchronize(st), "sync scatter");
-        for (uint32_t s = 0; s < n_slots; s++) nnz_of(s) += slot_delta[s];
-        // the rows appended to become next iteration's delta rows
-        cur ^= 1;
-        ck(cudaMemsetAsync(d_touched_n.p + (cur ^ 1), 0, 8, st), "memset");
-        return nd;
-    }
-
-    // After a pool growth: new pool pointers and capacities; the device
-    // pool_top counters keep counting (they are ahead of any host copy).
-    void upload_pools_caps_only() {
-        std::vector<unsigned long long> cap(cx.size());
-        std::vector<uint32_t *> hp(n_slots);
-        for (size_t k = 0; k < cx.size(); k++) cap[k] = cx[k]->pool_cap;
-        for (uint32_t s = 0; s < n_slots; s++) hp[s] = cx[slot_ctx[s]]->pool;
-        ck(cudaMemcpyAsync(d_pool_cap.p, cap.data(), cx.size() * 8, cudaMemcpyHostToDevice, st), "H2D");
-        ck(cudaMemcpyAsync(d_pool.p, hp.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
-        ck(cudaStreamSynchronize(st), "sync");
+        regrows++;
     }
 
     void grow_pool(size_t k, uint64_t top) {
@@ -627,103 +599,199 @@ struct Runner {
             throw Status{CFLR_ENOMEM, "row pool exceeds 2^32 entries"};
         uint32_t *np = (uint32_t *)c->dalloc(cap * 4);
         ck(cudaMemcpyAsync(np, c->pool, c->pool_cap * 4, cudaMemcpyDeviceToDevice, st), "D2D");
-        ck(cudaStreamSynchronize(st), "sync pool");
+        sync("pool copy");
         c->dfree(c->pool, c->pool_cap * 4);
-        c->pool = np;
+        c->pool = np;       // rows address the pool by offset, so they stay valid
         c->pool_cap = cap;
-        // descriptors of this context point into the old pool by offset only
         regrows++;
     }
 
-    // One closure iteration over every context of the batch.  Returns the
-    // number of new pairs; per-context counts in ctx_delta.
-    uint64_t iterate(std::vector<uint64_t> &ctx_delta) {
+    // ---- the iteration --------------------------------------------------
+    // Products of one iteration (symbolic pass and the four bins).
+    void launch_products(const SlotTab &S, const ProdTab &P, const WorkBufs &W, bool timed) {
+        auto run = [&](int kid, auto f) { if (timed) prof.run(kid, f); else f(); };
+        if (own->cfg.form == CFLR_FORM_PLAIN) {
+            // one launch sequence per production, like one library mxm each
+            for (uint32_t p = 0; p < n_prods; p++) {
+                run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, (int)p, sms, st); });
+                for (int b = 0; b < N_BINS; b++)
+                    run(KID_BIN0 + b, [&] { launch_spgemm(b, S, P, W, max_n, sms, st); });
+                ck(cudaMemsetAsync(d_cnt.p->groups, 0, sizeof(d_cnt.p->groups), st), "memset");
+            }
+        } else {
+            run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, -1, sms, st); });
+            for (int b = 0; b < N_BINS; b++)
+                run(KID_BIN0 + b, [&] { launch_spgemm(b, S, P, W, max_n, sms, st); });
+        }
+    }
+    // Commit and union, from the dedupe (stage 0), the capacity pass
+    // (stage 1) or the scatter (stage 2), then the end of the iteration.
+    void launch_merge(const SlotTab &S, const InstTab &I, const WorkBufs &W, int stage,
+                      bool count_iteration, bool in_graph, bool timed) {
+        auto run = [&](int kid, auto f) { if (timed) prof.run(kid, f); else f(); };
+        if (stage <= 0) {
+            run(KID_COMMIT, [&] { launch_commit(S, W, sms, st); });
+            run(KID_RESET, [&] { launch_reset_dnew(S, W, sms, st); });
+            run(KID_COUNT, [&] { launch_count(S, W, sms, st); });
+        }
+        if (stage <= 1) run(KID_CAPACITY, [&] { launch_capacity(S, I, W, sms, st); });
+        run(KID_SCATTER, [&] { launch_scatter(S, W, sms, st); });
+        launch_iter_end(S, I, W, d_ctl.p, n_slots, (uint32_t)cx.size(), count_iteration,
+                        handle, in_graph, st);
+        ck(cudaGetLastError(), "k_iter_end");
+    }
+    // One whole iteration as a launch sequence (also the graph's body).
+    void launch_iteration(bool in_graph, bool timed) {
         const SlotTab S = slots();
         const ProdTab P = prodtab();
-        for (;;) {
-            ck(cudaMemsetAsync(d_cnt.p, 0, sizeof(Counters), st), "memset");
-            ck(cudaMemsetAsync(d_cand.p, 0, n_slots * 8, st), "memset");
-            ck(cudaMemsetAsync(d_delta.p, 0, n_slots * 8, st), "memset");
-            const WorkBufs W = work();
-            if (own->cfg.form == CFLR_FORM_PLAIN) {
-                // one launch sequence per production, like one library mxm each
-                for (uint32_t p = 0; p < n_prods; p++) {
-                    prof.run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, (int)p, sms, st); });
-                    for (int b = 0; b < N_BINS; b++)
-                        prof.run(KID_BIN0 + b, [&] { launch_spgemm(b, S, P, W, max_n, sms, st); });
-                    ck(cudaMemsetAsync(d_cnt.p->groups, 0, sizeof(d_cnt.p->groups), st), "memset");
-                }
-            } else {
-                prof.run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, -1, sms, st); });
-                for (int b = 0; b < N_BINS; b++)
-                    prof.run(KID_BIN0 + b, [&] { launch_spgemm(b, S, P, W, max_n, sms, st); });
-            }
-            read_counters();
-            ck(cudaStreamSynchronize(st), "sync spgemm");
-            bool again = false;
-            if (h_cnt->overflow & OVF_GROUPS) {
-                for (int b = 0; b < N_BINS; b++) {
-                    uint64_t want = h_cnt->groups[b] > group_cap[b] ? h_cnt->groups[b] * 3 / 2 : 0;
-                    if (own->cfg.form == CFLR_FORM_PLAIN)   // counts were reset per production
-                        want = std::max<uint64_t>(want, 2 * group_cap[b]);
-                    if (want) size_groups(b, want);
-                }
-                again = true;
-            }
-            if (h_cnt->overflow & OVF_CAND) {
-                size_cand(h_cnt->cand * 3 / 2);
-                size_touched(2 * cand_cap, true);
-                again = true;
-            }
-            if (again) {
-                regrows++;
-                continue;
-            }
-            break;
-        }
-        total_flops += h_cnt->flops;
-        total_cand += h_cnt->cand;
-        own->k_bytes[KID_SYMBOLIC] += h_cnt->bytes_sym;
-        for (int b = 0; b < N_BINS; b++) own->k_bytes[KID_BIN0 + b] += h_cnt->bytes_bin[b];
-        std::vector<unsigned long long> sd;
-        uint64_t nd = commit_and_merge(sd);
-        ctx_delta.assign(cx.size(), 0);
-        for (uint32_t s = 0; s < n_slots; s++) ctx_delta[slot_ctx[s]] += sd[s];
-        prof.collect();
-        return nd;
+        const InstTab I = insttab();
+        const WorkBufs W = work();
+        launch_iter_begin(S, I, W, n_slots, (uint32_t)cx.size(), st);
+        launch_products(S, P, W, timed);
+        launch_check(S, W, n_slots, st);
+        launch_merge(S, I, W, 0, true, in_graph, timed);
     }
 
-    // Import each context's pending delta rows into the work list.
+    void ensure_graph() {
+        if (graph_valid) return;
+        drop_graph();
+        prepare_launch_attributes();
+        ck(cudaGraphCreate(&graph, 0), "cudaGraphCreate");
+        ck(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault),
+           "cudaGraphConditionalHandleCreate");
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        ck(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp), "cudaGraphAddNode");
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ck(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal),
+           "cudaStreamBeginCaptureToGraph");
+        launch_iteration(true, false);
+        cudaGraph_t captured = nullptr;
+        ck(cudaStreamEndCapture(st, &captured), "cudaStreamEndCapture");
+        ck(cudaGraphInstantiate(&gexec, graph, 0), "cudaGraphInstantiate");
+        graph_valid = true;
+    }
+
+    void read_status() {
+        ck(cudaMemcpyAsync(h_cnt, d_cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaMemcpyAsync(h_ctl, d_ctl.p, sizeof(LoopCtl), cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaMemcpyAsync(h_parity, d_parity.p, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H");
+        sync("status");
+    }
+    void clear_overflow() {
+        ck(cudaMemsetAsync(&d_cnt.p->overflow, 0, sizeof(unsigned), st), "memset");
+    }
+
+    // Grow what the last (stopped) iteration overflowed and finish it.
+    // Returns false when the iteration must be run again from its start.
+    bool recover() {
+        const unsigned st_bits = h_ctl->status;
+        if (st_bits & (OVF_GROUPS | OVF_CAND)) {       // nothing was committed
+            for (int b = 0; b < N_BINS; b++) {
+                uint64_t want = h_cnt->groups[b] > group_cap[b] ? h_cnt->groups[b] * 3 / 2 : 0;
+                if ((st_bits & OVF_GROUPS) && own->cfg.form == CFLR_FORM_PLAIN)
+                    want = std::max<uint64_t>(want, 2 * group_cap[b]);   // counts reset per production
+                if (want) size_groups(b, want);
+            }
+            if (st_bits & OVF_CAND) {
+                size_cand(h_cnt->cand * 3 / 2);
+                size_touched(2 * cand_cap, *h_parity);
+            }
+            regrows++;
+            return false;
+        }
+        const SlotTab S = slots();
+        const InstTab I = insttab();
+        const WorkBufs W = work();
+        if (st_bits & OVF_HASH) {                      // grow pair sets, then commit
+            std::vector<unsigned long long> nz(n_slots), cd(n_slots);
+            ck(cudaMemcpyAsync(nz.data(), d_nnz.p, n_slots * 8, cudaMemcpyDeviceToHost, st), "D2H");
+            ck(cudaMemcpyAsync(cd.data(), d_cand.p, n_slots * 8, cudaMemcpyDeviceToHost, st), "D2H");
+            sync("hash sizes");
+            for (uint32_t s = 0; s < n_slots; s++) {
+                cflr_ctx *c = cx[slot_ctx[s]];
+                uint32_t x = s - base[slot_ctx[s]];
+                if (2 * (nz[s] + cd[s]) > c->hcap[x]) grow_htab(s, nz[s] + cd[s]);
+            }
+            upload_htabs();
+            clear_overflow();
+            launch_merge(S, I, W, 0, true, false, true);
+            read_status();
+        }
+        for (int guard = 0; h_ctl->status & OVF_POOL; guard++) {   // grow pools, redo the union
+            if (guard > 8) throw Status{CFLR_ENOMEM, "pool growth did not converge"};
+            std::vector<unsigned long long> top(cx.size());
+            ck(cudaMemcpyAsync(top.data(), d_pool_top.p, cx.size() * 8, cudaMemcpyDeviceToHost, st), "D2H");
+            sync("pool tops");
+            for (size_t k = 0; k < cx.size(); k++)
+                if (top[k] > cx[k]->pool_cap) grow_pool(k, top[k]);
+            upload_pools(false);
+            clear_overflow();
+            launch_merge(S, I, W, 1, true, false, true);
+            read_status();
+        }
+        if (h_ctl->status) throw Status{CFLR_ECUDA, "internal: unexpected loop status"};
+        return true;
+    }
+
+    // Run closure iterations until the fixpoint (true) or the iteration
+    // limit (false).
+    bool run_loop() {
+        const bool use_graph = own->cfg.form == CFLR_FORM_GRAPH && !prof.on;
+        for (;;) {
+            if (use_graph) {
+                ensure_graph();
+                ck(cudaGraphLaunch(gexec, st), "cudaGraphLaunch");
+            } else {
+                launch_iteration(false, true);
+            }
+            read_status();
+            prof.collect();
+            if (h_ctl->status && !recover()) continue;
+            if (h_ctl->last_delta == 0) return true;
+            if (h_ctl->iter >= h_ctl->limit) return false;
+        }
+    }
+
+    // Pending delta rows of each context into the "in" touched list.
     void import_touched() {
         uint64_t total = 0;
         for (auto *c : cx) total += c->touched_n;
-        size_touched(std::max<uint64_t>(total, 2 * cand_cap), false);
+        size_touched(std::max<uint64_t>(total, 2 * cand_cap), -1);
         uint64_t at = 0;
         for (size_t k = 0; k < cx.size(); k++) {
             cflr_ctx *c = cx[k];
             if (c->touched_n)
-                launch_remap_touched(c->touched, c->touched_n, base[k], d_touched[cur].p + at, st);
+                launch_remap_touched(c->touched, c->touched_n, base[k], d_touched[0].p + at, st);
             ck(cudaGetLastError(), "remap");
             at += c->touched_n;
         }
         unsigned long long *h = small(2);
-        h[0] = cur == 0 ? at : 0;
-        h[1] = cur == 1 ? at : 0;
+        h[0] = at;
+        h[1] = 0;
         ck(cudaMemcpyAsync(d_touched_n.p, h, 16, cudaMemcpyHostToDevice, st), "H2D");
-        ck(cudaStreamSynchronize(st), "sync import");
+        ck(cudaMemsetAsync(d_parity.p, 0, sizeof(int), st), "memset");
+        sync("import");
     }
 
     // Save the pending delta rows of each context (local slot ids).
     void export_touched() {
         unsigned long long *h = small(2);
         ck(cudaMemcpyAsync(h, d_touched_n.p, 16, cudaMemcpyDeviceToHost, st), "D2H");
-        ck(cudaStreamSynchronize(st), "sync");
-        uint64_t n_in = h[cur];
+        ck(cudaMemcpyAsync(h_parity, d_parity.p, sizeof(int), cudaMemcpyDeviceToHost, st), "D2H");
+        sync("export");
+        const int par = *h_parity;
+        const uint64_t n_in = h[par];
         std::vector<uint2> all(n_in);
         if (n_in)
-            ck(cudaMemcpyAsync(all.data(), d_touched[cur].p, n_in * sizeof(uint2),
+            ck(cudaMemcpyAsync(all.data(), d_touched[par].p, n_in * sizeof(uint2),
                                cudaMemcpyDeviceToHost, st), "D2H");
-        ck(cudaStreamSynchronize(st), "sync");
+        sync("export");
         std::vector<std::vector<uint2>> per(cx.size());
         for (auto &t : all) {
             uint32_t s = t.x >> 1;
@@ -734,6 +802,7 @@ struct Runner {
             cflr_ctx *c = cx[k];
             if (per[k].size() > c->touched_cap) {
                 if (c->touched) c->dfree(c->touched, c->touched_cap * sizeof(uint2));
+                c->touched = nullptr;
                 c->touched_cap = std::max<uint64_t>(per[k].size(), 1024);
                 c->touched = (uint2 *)c->dalloc(c->touched_cap * sizeof(uint2));
             }
@@ -742,7 +811,19 @@ struct Runner {
                 ck(cudaMemcpyAsync(c->touched, per[k].data(), c->touched_n * sizeof(uint2),
                                    cudaMemcpyHostToDevice, st), "H2D");
         }
-        ck(cudaStreamSynchronize(st), "sync");
+        sync("export");
+    }
+
+    // Byte and work totals of the finished solve, from the loop control.
+    void account() {
+        read_status();
+        own->k_bytes[KID_SYMBOLIC] += h_ctl->bytes_sym;
+        for (int b = 0; b < N_BINS; b++) own->k_bytes[KID_BIN0 + b] += h_ctl->bytes_bin[b];
+        own->k_bytes[KID_COMMIT] += 20 * h_ctl->total_cand + 12 * h_ctl->total_delta;
+        own->k_bytes[KID_RESET] += 12 * h_ctl->total_touched_in;
+        own->k_bytes[KID_COUNT] += 20 * h_ctl->total_delta + 8 * h_ctl->total_touched_out;
+        own->k_bytes[KID_CAPACITY] += 24 * h_ctl->total_touched_out;
+        own->k_bytes[KID_SCATTER] += 52 * h_ctl->total_delta;
     }
 };
 
@@ -830,26 +911,25 @@ void reset_matrices(cflr_ctx *c) {
     r.init_buffers(std::max<uint64_t>(c->n_init, 1), 0);
     if (r.cand_cap < c->n_init) {      // the initial pairs are counted exactly
         r.size_cand(c->n_init);
-        r.size_touched(2 * r.cand_cap, false);
+        r.size_touched(2 * r.cand_cap, -1);
     }
-    ck(cudaMemsetAsync(r.d_cnt.p, 0, sizeof(Counters), st), "memset");
-    ck(cudaMemsetAsync(r.d_cand.p, 0, r.n_slots * 8, st), "memset");
-    ck(cudaMemsetAsync(r.d_delta.p, 0, r.n_slots * 8, st), "memset");
+    const SlotTab S = r.slots();
+    const InstTab I = r.insttab();
     const WorkBufs W = r.work();
+    launch_iter_begin(S, I, W, r.n_slots, 1, st);
     r.prof.run(KID_INIT, [&] {
         launch_init_edges(c->e_src, c->e_lab, c->e_dst, c->m_edges, c->t_off, c->t_slot, nterm, W,
                           c->sms, st);
         for (uint32_t A : g.eps) launch_init_eps(A, n, W, c->sms, st);
     });
     c->k_bytes[KID_INIT] += 12 * c->m_edges + 12 * c->n_init;
-    r.read_counters();
-    ck(cudaStreamSynchronize(st), "sync init");
+    // the pair sets were sized from the exact initial counts, so the commit
+    // needs no capacity check; the pool may still grow
+    r.launch_merge(S, I, W, 0, false, false, true);
+    r.read_status();
     if (r.h_cnt->overflow & OVF_CAND) throw Status{CFLR_ECUDA, "internal: init overflow"};
-    // the hash sets were sized from the exact initial counts; per-slot
-    // candidate counts stay zero here, so commit directly
-    std::vector<unsigned long long> sd;
-    r.commit_and_merge(sd);
-    r.download_pool_tops();
+    if (r.h_ctl->status) r.recover();
+    r.download_state(false);
     r.export_touched();
     r.prof.collect();
 }
@@ -868,12 +948,6 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
     std::vector<cflr_ctx *> active;
     for (auto *c : cx)
         if (c->touched_n) active.push_back(c);
-    std::vector<uint32_t> iters(cx.size(), 0);
-    std::vector<uint64_t> before(cx.size(), 0);
-    for (size_t k = 0; k < cx.size(); k++) {
-        cx[k]->k_launches[0] = cx[k]->k_launches[0];  // keep profile totals
-        iters[k] = cx[k]->iterations;
-    }
     ck(cudaEventCreate(&ev0), "event");
     ck(cudaEventCreate(&ev1), "event");
     ck(cudaEventRecord(ev0, own->stream), "event");
@@ -886,29 +960,12 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
         for (auto *c : active) hint += c->touched_n;
         r.init_buffers(std::max<uint64_t>(hint * 4, 1 << 16), hint);
         r.import_touched();
-        std::vector<uint64_t> cd;
-        std::vector<bool> done(active.size(), false);
-        uint32_t limit = own->cfg.max_iterations;
-        uint32_t it = 0;
-        for (;;) {
-            if (limit && it >= limit) {
-                rc = CFLR_ELIMIT;
-                break;
-            }
-            uint64_t nd = r.iterate(cd);
-            it++;
-            for (size_t k = 0; k < active.size(); k++) {
-                if (!done[k]) {
-                    active[k]->iterations++;
-                    if (cd[k] == 0) done[k] = true;
-                }
-            }
-            if (nd == 0) break;
-        }
-        r.download_pool_tops();
+        if (!r.run_loop()) rc = CFLR_ELIMIT;
+        r.account();
+        r.download_state(true);
         r.export_touched();
-        flops = r.total_flops;
-        cand = r.total_cand;
+        flops = r.h_ctl->total_flops;
+        cand = r.h_ctl->total_cand;
         regrows = r.regrows;
     }
     ck(cudaEventRecord(ev1, own->stream), "event");
@@ -928,11 +985,11 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
         s.flops = flops;
         s.candidates = cand;
         s.regrows = regrows;
+        s.converged = c->touched_n == 0 ? 1u : 0u;
         c->last = s;
         if (stats) stats[k] = s;
-        if (rc == CFLR_OK) c->state = ST_SOLVED;
+        if (s.converged) c->state = ST_SOLVED;
     }
-    (void)before;
     if (rc == CFLR_ELIMIT)
         own->err = "max_iterations reached before the fixpoint";
     return rc;

@@ -283,8 +283,56 @@ def test_full_size_dyck3_batch_256():
             s.close()
 
 
-@pytest.mark.parametrize("form", [cflr.CFLR_FORM_PLAIN, cflr.CFLR_FORM_BATCHED])
+@pytest.mark.parametrize("form", [cflr.CFLR_FORM_PLAIN, cflr.CFLR_FORM_BATCHED,
+                                  cflr.CFLR_FORM_GRAPH])
 def test_execution_forms_agree(form):
     text = gen.grammar_text("fica")
     g = gen.fica_like(n=8000, n_a=16_000, n_d=6000, seed=21)
-    assert_parity(text, g, form=form)
+    st, want = assert_parity(text, g, form=form)
+    # one more solve of a finished context is a no-op with the same pairs
+    with Solver(text, form=form) as s:
+        s.load(g)
+        first = s.solve()
+        again = s.solve()
+        assert again["total_pairs"] == first["total_pairs"] == want.total()
+        assert first["iterations"] == st["iterations"]
+
+
+def test_graph_form_growth_and_limit_paths():
+    """The device-driven loop stops for every growth and for the iteration
+    limit, and the host finishes the iteration."""
+    text = gen.grammar_text("fica")
+    g = gen.fica_like(n=5000, n_a=10_000, n_d=3750, seed=11)
+    st, _ = assert_parity(text, g, form=cflr.CFLR_FORM_GRAPH, initial_capacity=64)
+    assert st["regrows"] > 0
+    want = oracle.solve(text, g)
+    with Solver(text, form=cflr.CFLR_FORM_GRAPH, max_iterations=3) as s:
+        s.load(g)
+        for _ in range(1000):
+            try:
+                s.solve()
+                break
+            except CflrError as err:
+                assert err.code == cflr.CFLR_ELIMIT
+        assert np.array_equal(s.pairs("M"), want.pairs["M"])
+
+
+def test_graph_form_batch_of_instances():
+    text = gen.grammar_text("dyck3")
+    graphs = gen.dyck3_batch(count=8, seed0=4100, n_lo=500, n_hi=4000)
+    solvers = [Solver(text, form=cflr.CFLR_FORM_GRAPH) for _ in graphs]
+    try:
+        for s, g in zip(solvers, graphs):
+            s.load(g)
+        stats = cflr.cflr_solve_batch([s.ctx for s in solvers])
+        for s, g, st in zip(solvers, graphs, stats):
+            want = oracle.solve(text, g)
+            for x in want.grammar.nts:
+                assert np.array_equal(s.pairs(x), want.pairs[x]), x
+            alone = Solver(text)
+            alone.load(g)
+            assert alone.solve()["iterations"] == st["iterations"]
+            alone.close()
+    finally:
+        for s in solvers:
+            s.close()
