@@ -158,6 +158,21 @@ def dist_setup():
     return world, rank, local, dist
 
 
+def aggregate(dist, device, ms: float, pairs: int, e2e_s: float):
+    """Whole-job figures over the ranks: the slowest rank's step time and
+    end-to-end time, and the pairs of all ranks (each rank solves its own
+    replica, so the work adds up)."""
+    if dist is None:
+        return ms, float(pairs), e2e_s
+    import torch
+    t = torch.tensor([ms, float(pairs), e2e_s], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(mx[2])
+
+
 def run_reference(args):
     world, rank, local, dist = dist_setup()
     if rank != 0:
@@ -304,15 +319,7 @@ def run_cflr(args):
         assert tot == pairs
 
     ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([ms, pairs, statistics.mean(e2e_s)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_all, pairs_all, e2e_all = float(mx[0]), float(sm[1]), float(mx[2])
-    else:
-        ms_all, pairs_all, e2e_all = ms, float(pairs), statistics.mean(e2e_s)
+    ms_all, pairs_all, e2e_all = aggregate(dist, dev, ms, pairs, statistics.mean(e2e_s))
 
     # roofline of the dominant kernel over the timed steps
     rows = []

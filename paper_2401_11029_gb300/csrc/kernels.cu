@@ -55,19 +55,26 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
 
 // Insert v into a shared-memory open-addressing set of 2^lg slots.
 // Returns true when v was not present.  The caller keeps the load <= 1/2.
+// Most products are already present (masked or repeated), so each slot is
+// read first and the atomic is issued only on an empty slot.
 __device__ __forceinline__ bool smem_insert(uint32_t *tab, int lg, uint32_t v) {
     const uint32_t m = (1u << lg) - 1;
     uint32_t s = (v * 2654435761u) >> (32 - lg);
     for (;;) {
-        uint32_t old = atomicCAS(&tab[s], EMPTY32, v);
-        if (old == EMPTY32) return true;
-        if (old == v) return false;
+        const uint32_t cur = ((volatile uint32_t *)tab)[s];
+        if (cur == v) return false;
+        if (cur == EMPTY32) {
+            const uint32_t old = atomicCAS(&tab[s], EMPTY32, v);
+            if (old == EMPTY32) return true;
+            if (old == v) return false;
+        }
         s = (s + 1) & m;
     }
 }
 
 __device__ __forceinline__ bool bitmap_insert(uint32_t *bm, uint32_t v) {
     const uint32_t bit = 1u << (v & 31);
+    if (((volatile uint32_t *)bm)[v >> 5] & bit) return false;
     return (atomicOr(&bm[v >> 5], bit) & bit) == 0;
 }
 

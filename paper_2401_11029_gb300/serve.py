@@ -1,0 +1,164 @@
+"""Continuous-batching CFL-reachability server over the C ABI.
+
+Requests (a graph each, all under one grammar) arrive over time.  The
+server keeps every admitted request's matrices resident on the GPU and
+advances all of them together: each tick is one closure iteration of
+Algorithm 1 for every unfinished request, run as one batched launch
+sequence (cflr_solve_batch with a one-iteration limit).  Between ticks it
+retires the requests that reached their fixpoint (their pairs are copied
+out and their device memory freed) and admits newly arrived ones while
+their estimated device footprint fits the memory budget.  A request's
+result is the same whether it is solved alone or in the mix: the batch
+only interleaves independent fixpoints.
+
+This module only schedules; all CFL-r work runs in libcflr.so.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import cflr
+
+
+@dataclass
+class Finished:
+    rid: int
+    n: int
+    edges: int
+    pairs: int
+    iterations: int
+    arrival_s: float
+    admitted_s: float
+    done_s: float
+    keys: dict = field(default_factory=dict)   # non-terminal -> sorted uint64 keys
+
+    @property
+    def latency_s(self) -> float:
+        return self.done_s - self.arrival_s
+
+
+class Server:
+    """Admission by device-memory footprint, resident state, one batched
+    closure iteration per tick."""
+
+    # device bytes per input edge and per vertex-nonterminal, measured on the
+    # alias-analysis workload (peak bytes / edges of a 200k-vertex solve),
+    # used to admit requests before their closure size is known
+    BYTES_PER_EDGE = 8192
+    BYTES_PER_VERTEX_NT = 40
+
+    def __init__(self, grammar_text: str, mem_budget_bytes: int = 64 << 30,
+                 max_active: int = 128, device: int = 0, stream=None,
+                 keep_pairs: bool = False, form: int = cflr.CFLR_FORM_GRAPH):
+        self.text = grammar_text
+        self.budget = int(mem_budget_bytes)
+        self.max_active = max_active
+        self.device = device
+        self.stream = stream
+        self.keep_pairs = keep_pairs
+        self.form = form
+        # the leader holds the shared work buffers and the one-iteration limit;
+        # its own (empty) graph is solved at once, so it never does work
+        self.leader = cflr.cflr_create(device=device, stream=stream, max_iterations=1,
+                                       form=form)
+        cflr.cflr_load_grammar(self.leader, grammar_text)
+        cflr.cflr_load_graph(self.leader, 1, [], [], [])
+        cflr.cflr_solve(self.leader)
+        self.n_nt, self.n_named, _ = cflr.cflr_grammar_sizes(self.leader)
+        self.term = {}
+
+    def close(self):
+        cflr.cflr_destroy(self.leader)
+        self.leader = None
+
+    def footprint(self, graph) -> int:
+        return (self.BYTES_PER_EDGE * graph.n_edges +
+                self.BYTES_PER_VERTEX_NT * graph.n * self.n_nt + (32 << 20))
+
+    def _label_ids(self, ctx, labels):
+        out = []
+        for name in labels:
+            if name not in self.term:
+                try:
+                    i, is_t = cflr.cflr_symbol_id(ctx, name)
+                    self.term[name] = i if is_t else 0xFFFFFFFF
+                except cflr.CflrError:
+                    self.term[name] = 0xFFFFFFFF
+            out.append(self.term[name])
+        return np.asarray(out, dtype=np.uint32)
+
+    def _admit(self, graph):
+        ctx = cflr.cflr_create(device=self.device, stream=self.stream, form=self.form)
+        cflr.cflr_load_grammar(ctx, self.text)
+        ids = self._label_ids(ctx, graph.labels)
+        cflr.cflr_load_graph(ctx, graph.n, graph.src, ids[graph.lab], graph.dst)
+        return ctx
+
+    def _retire(self, ctx, rec) -> dict:
+        keys = {}
+        total = 0
+        for x in range(self.n_named):
+            if self.keep_pairs:
+                s, d = cflr.cflr_get_pairs(ctx, x)
+                keys[x] = (s.astype(np.uint64) << np.uint64(32)) | d.astype(np.uint64)
+                total += s.size
+            else:
+                total += cflr.cflr_get_pairs(ctx, x, count_only=True)
+        cflr.cflr_destroy(ctx)
+        return total, keys
+
+    def run(self, requests, clock=time.perf_counter) -> list:
+        """Serve ``requests``: an iterable of (rid, arrival_s, graph), sorted
+        by arrival.  Returns a list of ``Finished``."""
+        pending = collections.deque(requests)
+        active = []          # [ctx, rid, graph, arrival, admitted, footprint, iterations]
+        used = 0
+        done = []
+        t0 = clock()
+        while pending or active:
+            now = clock() - t0
+            while (pending and pending[0][1] <= now and len(active) < self.max_active):
+                rid, arr, g = pending[0]
+                fp = self.footprint(g)
+                if active and used + fp > self.budget:
+                    break                                  # wait for memory to free up
+                pending.popleft()
+                ctx = self._admit(g)
+                active.append([ctx, rid, g, arr, clock() - t0, fp, 0])
+                used += fp
+            if not active:
+                wait = pending[0][1] - (clock() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.05))
+                continue
+            stats = cflr.cflr_solve_batch([self.leader] + [a[0] for a in active],
+                                          allow_limit=True)
+            still = []
+            for a, st in zip(active, stats[1:]):
+                a[6] = st["iterations"]
+                if st["converged"]:
+                    pairs, keys = self._retire(a[0], a)
+                    used -= a[5]
+                    done.append(Finished(rid=a[1], n=a[2].n, edges=a[2].n_edges, pairs=pairs,
+                                         iterations=a[6], arrival_s=a[3], admitted_s=a[4],
+                                         done_s=clock() - t0, keys=keys))
+                else:
+                    still.append(a)
+            active = still
+        return done
+
+
+def summarize(done: list, warmup_s: float = 0.0) -> dict:
+    """Latency percentiles and throughput of the requests that arrived after
+    ``warmup_s``."""
+    kept = [f for f in done if f.arrival_s >= warmup_s] or done
+    lat = np.asarray([f.latency_s for f in kept])
+    span = max(f.done_s for f in kept) - min(f.arrival_s for f in kept)
+    return {"requests": len(kept), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+            "req_per_s": len(kept) / span if span > 0 else None,
+            "pairs_per_s": sum(f.pairs for f in kept) / span if span > 0 else None}

@@ -13,6 +13,12 @@ GRAMMARS = {
     "fica_cfg": (gen.grammar_text("fica_cfg"), ["a", "d", "a_r", "d_r"]),
     "fsjpt2": (gen.grammar_text("fsjpt", index_hi=1), FSJPT2_LABELS),
     "fsjpt2_cfg": (gen.grammar_text("fsjpt_cfg", index_hi=1), FSJPT2_LABELS),
+    # the grammars of Figs. wcnf:fsca and wcnf:cscvf (epsilon, unit
+    # productions, indexed families), two indices each
+    "fsca2": (gen.grammar_text("fsca", index_hi=1),
+              ["d", "d_r", "a", "a_r", "f_0", "f_1", "f_r_0", "f_r_1"]),
+    "cscvf2": (gen.grammar_text("cscvf", index_hi=1),
+               ["a", "call_0", "call_1", "ret_0", "ret_1"]),
 }
 
 # WCNF grammars with epsilon, unit and terminal-in-binary productions.

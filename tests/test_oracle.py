@@ -14,26 +14,7 @@ from oracle.grammar import GrammarError, parse
 from paper_2401_11029_gb300 import gen
 from pins import bfs_reach, brute_force, dyck_balanced, naive_alg1, read_grammar
 
-GRAMMARS = {
-    "dyck1": (gen.grammar_text("dyck1"), ["a", "b"]),
-    "dyck3": (gen.grammar_text("dyck3"), ["a_1", "b_1", "a_2", "b_2", "a_3", "b_3"]),
-    "fica": (gen.grammar_text("fica"), ["a", "d", "a_r", "d_r"]),
-    "fica_cfg": (gen.grammar_text("fica_cfg"), ["a", "d", "a_r", "d_r"]),
-    "fsjpt2": (gen.grammar_text("fsjpt", index_hi=1),
-               ["alloc", "assign", "alloc_r", "assign_r", "load_0", "load_1", "store_0",
-                "store_1", "load_r_0", "load_r_1", "store_r_0", "store_r_1"]),
-    "fsjpt2_cfg": (gen.grammar_text("fsjpt_cfg", index_hi=1),
-                   ["alloc", "assign", "alloc_r", "assign_r", "load_0", "load_1", "store_0",
-                    "store_1", "load_r_0", "load_r_1", "store_r_0", "store_r_1"]),
-}
-
-# Random WCNF grammars with epsilon, unit and terminal-in-binary productions.
-RANDOM_GRAMMARS = [
-    "S -> S S | a | A b\nA -> eps | a A\n",
-    "X -> Y Z | b\nY -> X a | eps\nZ -> Y | c\n",
-    "P -> Q P | a\nQ -> P b | c Q | eps\nR -> P | Q Q\n",
-    "A -> B C | a\nB -> C A | b\nC -> A B | c | A\n",
-]
+from common import GRAMMARS, RANDOM_GRAMMARS  # noqa: E402
 
 
 def dense_of(res, name, n):
@@ -80,7 +61,7 @@ def _tiny_dag(seed, labels, n=6, m=10):
                      lab=np.array(lab, np.uint32), dst=np.array(dst, np.uint32))
 
 
-@pytest.mark.parametrize("name", ["dyck1", "dyck3", "fica", "fica_cfg", "fsjpt2"])
+@pytest.mark.parametrize("name", ["dyck1", "dyck3", "fica", "fica_cfg", "fsjpt2", "fsca2", "cscvf2"])
 @pytest.mark.parametrize("seed", [5, 6])
 def test_oracle_equals_brute_force_on_dags(name, seed):
     text, labels = GRAMMARS[name]
