@@ -43,6 +43,7 @@ UNIT = "pairs/s"
 WORKLOAD = {"workload": "fica_like alias analysis (Fig. wcnf:fica)", "n_vertices": 200_000,
             "a_edges": 400_000, "d_edges": 150_000, "reverse_edges": True, "seed": 2}
 SAMPLE_N = 20_000     # oracle sample: same generator and ratios, 1/10 of the vertices
+TUNING_CACHE = os.path.join(ROOT, "paper_2401_11029_gb300", "tuning", "gb300.txt")
 
 
 def peaks() -> dict:
@@ -208,8 +209,10 @@ def run_cflr(args):
     g = workload_graph(seed, args.vertices)
     text = gen.grammar_text("fica")
 
-    # timed context: the device-driven loop (one CUDA graph per solve)
-    ctx = cflr.cflr_create(device=local, stream=stream.cuda_stream, form=cflr.CFLR_FORM_GRAPH)
+    # timed context: the device-driven loop (one CUDA graph per solve), with
+    # the product schedule picked by cflr_autotune (cached per grammar and size)
+    ctx = cflr.cflr_create(device=local, stream=stream.cuda_stream, form=cflr.CFLR_FORM_GRAPH,
+                           autotune_cache=TUNING_CACHE.encode())
     cflr.cflr_load_grammar(ctx, text)
     n_nt, n_named, _ = cflr.cflr_grammar_sizes(ctx)
     term = {}
@@ -226,6 +229,7 @@ def run_cflr(args):
     h_dst = torch.from_numpy(g.dst.astype(np.uint32).view(np.int32)).pin_memory()
     cflr.cflr_load_graph(ctx, g.n, h_src.numpy().view(np.uint32), h_lab.numpy().view(np.uint32),
                          h_dst.numpy().view(np.uint32))
+    tuning = cflr.cflr_autotune(ctx) if not args.no_autotune else cflr.cflr_get_tuning(ctx)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     # profiled context: the same iterations launched one by one from the host
     # with CUDA events around every kernel (events cannot sit inside the
@@ -233,6 +237,7 @@ def run_cflr(args):
     pctx = cflr.cflr_create(device=local, stream=stream.cuda_stream,
                             form=cflr.CFLR_FORM_BATCHED, profile=1)
     cflr.cflr_load_grammar(pctx, text)
+    cflr.cflr_set_tuning(pctx, tuning["probe_ratio"], tuning["bin_limit"], tuning["ctas_per_sm"])
     cflr.cflr_load_graph(pctx, g.n, h_src.numpy().view(np.uint32), h_lab.numpy().view(np.uint32),
                          h_dst.numpy().view(np.uint32))
 
@@ -355,6 +360,7 @@ def run_cflr(args):
                      "gbs": round((r[2] / 1e9) / (r[0] / 1e3), 1) if r[0] > 0 else None}
                     for r in rows if r[1]],
         "clocks": clk,
+        "tuning": tuning,
         "solve": {"form": "graph", "iterations": solve_stats["iterations"],
                   "flops": solve_stats["flops"], "candidates": solve_stats["candidates"],
                   "peak_device_bytes": solve_stats["peak_device_bytes"]},
@@ -511,6 +517,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=int, default=96)
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--vertices", type=int, default=None,
                     help="scale the workload to this many vertices (same generator and "
                          "ratios; for profiling runs, not for bench lines)")

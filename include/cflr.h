@@ -89,6 +89,19 @@ typedef struct {
     uint32_t converged;         /* 1 when the context has reached its fixpoint      */
 } cflr_stats;
 
+/* Schedule of the product kernels.  Each (production, delta row) group goes
+ * to the first bin whose limit holds its accumulator need (mask entries plus
+ * products, or products alone when it probes the pair set instead of
+ * loading the mask row, which it does when mask_len > probe_ratio *
+ * products); bin 3 takes the rest with an n-bit bitmap.  Limits must
+ * increase and stay within 128, 1024 and 4096 (the bins' table sizes). */
+typedef struct {
+    uint32_t probe_ratio;       /* >= 1                                             */
+    uint32_t bin_limit[3];      /* accumulator need bounds of bins 0, 1, 2          */
+    uint32_t ctas_per_sm[4];    /* grid of each bin in CTAs per SM (1..32); for bin 3
+                                   an upper bound under the shared-memory limit     */
+} cflr_tuning;
+
 /* Default configuration: device 0, private stream, no budget, no iteration
  * limit, CFLR_FORM_BATCHED, profiling off. */
 void cflr_default_config(cflr_config *cfg);
@@ -211,6 +224,23 @@ int cflr_solve_batch(cflr_ctx *const *ctxs, int n, cflr_stats *stats);
  * cflr_kernel_stats(c, -1, ...) returns the number of kernels in *launches. */
 int cflr_kernel_stats(const cflr_ctx *c, int k, const char **name, uint64_t *launches,
                       double *total_ms, uint64_t *alg_bytes);
+
+/* Read or set the product-kernel schedule of a context (also used for
+ * batches it leads).  Errors: CFLR_EINVAL (NULL, or a schedule outside the
+ * limits above). */
+int cflr_get_tuning(const cflr_ctx *c, cflr_tuning *t);
+int cflr_set_tuning(cflr_ctx *c, const cflr_tuning *t);
+
+/* Pick the schedule for the loaded graph by measurement: starting from the
+ * current one, try candidate values of each field in turn (coordinate
+ * descent), timing a reset-and-solve of the loaded graph for each, and keep
+ * the fastest.  At most max_trials solves (0 = 24).  When cfg.autotune_cache
+ * names a file, a schedule stored there for the same grammar text and graph
+ * size is used without measuring, and a measured one is added to it.
+ * Afterwards the matrices are back at the terminal initialisation (as after
+ * cflr_reset) and *best (nullable) holds the schedule now in use.
+ * Errors: CFLR_ESTATE (no graph), and those of cflr_solve. */
+int cflr_autotune(cflr_ctx *c, uint32_t max_trials, cflr_tuning *best);
 
 /* Description of the last error on this context (never NULL). */
 const char *cflr_last_error(const cflr_ctx *c);

@@ -37,7 +37,8 @@ CFLR_FORM_GRAPH = 2
 EXPORTS = ["cflr_default_config", "cflr_create", "cflr_load_grammar", "cflr_symbol_id",
            "cflr_grammar_sizes", "cflr_load_graph", "cflr_solve", "cflr_get_pairs",
            "cflr_get_pairs_device", "cflr_get_pairs_device_noalloc", "cflr_reset",
-           "cflr_solve_batch", "cflr_kernel_stats", "cflr_last_error", "cflr_destroy"]
+           "cflr_solve_batch", "cflr_kernel_stats", "cflr_get_tuning", "cflr_set_tuning",
+           "cflr_autotune", "cflr_last_error", "cflr_destroy"]
 
 # Largest graph the allocation-free extraction accepts (CFLR_NOALLOC_MAX_VERTICES).
 CFLR_NOALLOC_MAX_VERTICES = 1048576
@@ -55,6 +56,15 @@ class cflr_config(ctypes.Structure):
                 ("mem_budget_bytes", ctypes.c_uint64), ("max_iterations", ctypes.c_uint32),
                 ("form", ctypes.c_int), ("profile", ctypes.c_int),
                 ("autotune_cache", ctypes.c_char_p), ("initial_capacity", ctypes.c_uint32)]
+
+
+class cflr_tuning(ctypes.Structure):
+    _fields_ = [("probe_ratio", ctypes.c_uint32), ("bin_limit", ctypes.c_uint32 * 3),
+                ("ctas_per_sm", ctypes.c_uint32 * 4)]
+
+    def to_dict(self) -> dict:
+        return {"probe_ratio": self.probe_ratio, "bin_limit": list(self.bin_limit),
+                "ctas_per_sm": list(self.ctas_per_sm)}
 
 
 class cflr_stats(ctypes.Structure):
@@ -111,6 +121,13 @@ def load_library(path: str = LIB_PATH):
                                       ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(u64)]
     lib.cflr_kernel_stats.restype = i32
+    tp = ctypes.POINTER(cflr_tuning)
+    lib.cflr_get_tuning.argtypes = [vp, tp]
+    lib.cflr_get_tuning.restype = i32
+    lib.cflr_set_tuning.argtypes = [vp, tp]
+    lib.cflr_set_tuning.restype = i32
+    lib.cflr_autotune.argtypes = [vp, u32, tp]
+    lib.cflr_autotune.restype = i32
     lib.cflr_last_error.argtypes = [vp]
     lib.cflr_last_error.restype = ctypes.c_char_p
     lib.cflr_destroy.argtypes = [vp]
@@ -251,6 +268,26 @@ def cflr_kernel_stats(ctx) -> list:
         out.append({"name": name.value.decode(), "launches": int(launches.value),
                     "ms": float(ms.value), "alg_bytes": int(by.value)})
     return out
+
+
+def cflr_get_tuning(ctx) -> dict:
+    t = cflr_tuning()
+    _check(ctx, load_library().cflr_get_tuning(ctx, ctypes.byref(t)))
+    return t.to_dict()
+
+
+def cflr_set_tuning(ctx, probe_ratio: int, bin_limit, ctas_per_sm):
+    t = cflr_tuning(probe_ratio, (ctypes.c_uint32 * 3)(*bin_limit),
+                    (ctypes.c_uint32 * 4)(*ctas_per_sm))
+    _check(ctx, load_library().cflr_set_tuning(ctx, ctypes.byref(t)))
+
+
+def cflr_autotune(ctx, max_trials: int = 0) -> dict:
+    """Measure and set the product-kernel schedule for the loaded graph;
+    returns it.  The matrices are left at the terminal initialisation."""
+    t = cflr_tuning()
+    _check(ctx, load_library().cflr_autotune(ctx, int(max_trials), ctypes.byref(t)))
+    return t.to_dict()
 
 
 def cflr_last_error(ctx) -> str:

@@ -148,7 +148,7 @@ constexpr int SYM_BUF = 16;   // per-warp staging of groups before one atomic
 
 // prod_only >= 0 restricts the work list to one production (the plain form).
 __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs W,
-                                                  int prod_only) {
+                                                  int prod_only, Tuning T) {
     __shared__ uint2 stage[8][N_BINS][SYM_BUF];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned long long nw = (unsigned long long)gridDim.x * 8;
@@ -193,10 +193,10 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                 f = warp_sum64(f);
             }
             if (lane == 0 && f > 0) {
-                const bool probe = (unsigned long long)mlen > (unsigned long long)PROBE_RATIO * f;
+                const bool probe = (unsigned long long)mlen > (unsigned long long)T.probe_ratio * f;
                 const unsigned long long need = probe ? f : f + mlen;
-                const int b = need <= BIN0_LIMIT ? 0 : need <= BIN1_LIMIT ? 1
-                            : need <= BIN2_LIMIT ? 2 : 3;
+                const int b = need <= T.limit[0] ? 0 : need <= T.limit[1] ? 1
+                            : need <= T.limit[2] ? 2 : 3;
                 // table of the smallest power of two >= 2*need slots (>= 32)
                 uint32_t lg = 5;
                 while (b < 3 && (1ull << lg) < 2 * need) lg++;
@@ -296,45 +296,55 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
                 len = (gi.part == PART_A) ? gd.y : gd.y - gd.w;   // B full, A_old prefix
             }
         }
-        // long rows: the warp strides over one row at a time
+        // long rows: the warp strides over one row at a time, four coalesced
+        // loads in flight per lane
         unsigned lm = __ballot_sync(FULL_MASK, len >= 32);
         while (lm) {
             const int l = __ffs(lm) - 1;
             lm &= lm - 1;
             const uint32_t roff = __shfl_sync(FULL_MASK, off, l);
             const uint32_t rlen = __shfl_sync(FULL_MASK, len, l);
-            for (uint32_t qb = 0; qb < rlen; qb += 64) {
-                const uint32_t q0 = qb + lane, q1 = q0 + 32;
-                const bool v0ok = q0 < rlen, v1ok = q1 < rlen;
-                const uint32_t v0 = v0ok ? pool[roff + q0] : 0;
-                const uint32_t v1 = v1ok ? pool[roff + q1] : 0;
-                consume(v0ok, v0);
-                if (qb + 32 < rlen) consume(v1ok, v1);
+            for (uint32_t qb = 0; qb < rlen; qb += 128) {
+                uint32_t v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t q = qb + 32 * u + lane;
+                    v[u] = q < rlen ? pool[roff + q] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (qb + 32 * u < rlen) consume(qb + 32 * u + lane < rlen, v[u]);
             }
         }
-        // short rows: packed, 32 products per step
+        // short rows: packed 32 products per step, two steps per round
         const uint32_t slen = len < 32 ? len : 0;
         const uint32_t incl = warp_incl_scan(slen, lane);
         const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
-        for (uint32_t fb = 0; fb < total; fb += 32) {
-            const uint32_t f = fb + lane;
-            const bool valid = f < total;
-            int lo = 0, hi = 31;
+        for (uint32_t fb = 0; fb < total; fb += 64) {
+            uint32_t v[2];
+            bool ok[2];
 #pragma unroll
-            for (int st = 0; st < 5; st++) {     // first lane whose inclusive sum > f
-                const int mid = (lo + hi) >> 1;
-                const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
-                if (f < v) hi = mid; else lo = mid + 1;
+            for (int u = 0; u < 2; u++) {
+                const uint32_t f = fb + 32 * u + lane;
+                ok[u] = f < total;
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int st = 0; st < 5; st++) {     // first lane whose inclusive sum > f
+                    const int mid = (lo + hi) >> 1;
+                    const uint32_t x = __shfl_sync(FULL_MASK, incl, mid);
+                    if (f < x) hi = mid; else lo = mid + 1;
+                }
+                const int owner = lo > 31 ? 31 : lo;
+                const uint32_t o_off = __shfl_sync(FULL_MASK, off, owner);
+                const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
+                const uint32_t o_len = __shfl_sync(FULL_MASK, slen, owner);
+                const uint32_t o_k = __shfl_sync(FULL_MASK, k, owner);
+                v[u] = 0;
+                if (ok[u])
+                    v[u] = (gi.part == PART_U) ? o_k : pool[o_off + (f - (o_incl - o_len))];
             }
-            const int owner = lo > 31 ? 31 : lo;
-            const uint32_t o_off = __shfl_sync(FULL_MASK, off, owner);
-            const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
-            const uint32_t o_len = __shfl_sync(FULL_MASK, slen, owner);
-            const uint32_t o_k = __shfl_sync(FULL_MASK, k, owner);
-            uint32_t v = 0;
-            if (valid)
-                v = (gi.part == PART_U) ? o_k : pool[o_off + (f - (o_incl - o_len))];
-            consume(valid, v);
+            consume(ok[0], v[0]);
+            if (fb + 32 < total) consume(ok[1], v[1]);
         }
     }
     return emitted;
@@ -560,6 +570,8 @@ __global__ void __launch_bounds__(256) k_count(SlotTab S, WorkBufs W) {
 }
 
 // Make room for every listed row (relocate to a larger segment if needed).
+// A lane per listed row checks its capacity; the warp then copies the rows
+// that move, one after the other, with coalesced loads and stores.
 // Idempotent: after a pool overflow the host grows the pool and runs it again.
 __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs W) {
     if (W.cnt->overflow & OVF_PRE) return;
@@ -567,33 +579,45 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
     const int par = *W.parity;
     const uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
-    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) +
-                                (threadIdx.x >> 5);
-         e < n_t; e += nw) {
-        const uint2 t = t_out[e];
-        const uint32_t slot = t.x >> 1, o = t.x & 1;
-        uint4 *dp = &S.desc[slot][(size_t)o * S.n[slot] + t.y];
-        const uint4 dsc = *dp;
-        const unsigned long long need = (unsigned long long)dsc.y + dsc.w;
-        if (need <= dsc.z) continue;
-        unsigned long long cap = max(2ull * dsc.z, need);
-        cap = max((cap + 3) & ~3ull, 4ull);
-        const uint32_t inst = S.inst[slot];
-        unsigned long long off = 0;
-        if (lane == 0) {
-            off = atomicAdd(&I.pool_top[inst], cap);
-            if (off + cap > I.pool_cap[inst]) {
-                atomicOr(&W.cnt->overflow, OVF_POOL);
-                off = ~0ull;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x +
+                                   (threadIdx.x & ~31u);
+         base < n_t; base += stride) {
+        const unsigned long long e = base + lane;
+        uint4 *dp = nullptr;
+        uint4 dsc = make_uint4(0, 0, 0, 0);
+        uint32_t *pool = nullptr;
+        unsigned long long off = 0, cap = 0;
+        bool move = false;
+        if (e < n_t) {
+            const uint2 t = t_out[e];
+            const uint32_t slot = t.x >> 1, o = t.x & 1;
+            dp = &S.desc[slot][(size_t)o * S.n[slot] + t.y];
+            dsc = *dp;
+            const unsigned long long need = (unsigned long long)dsc.y + dsc.w;
+            if (need > dsc.z) {
+                cap = max(2ull * dsc.z, need);
+                cap = max((cap + 3) & ~3ull, 4ull);
+                const uint32_t inst = S.inst[slot];
+                off = atomicAdd(&I.pool_top[inst], cap);
+                if (off + cap > I.pool_cap[inst]) atomicOr(&W.cnt->overflow, OVF_POOL);
+                else move = true;
+                pool = S.pool[slot];
             }
         }
-        off = __shfl_sync(FULL_MASK, off, 0);
-        if (off == ~0ull) continue;
-        uint32_t *pool = S.pool[slot];
-        for (uint32_t q = lane; q < dsc.y; q += 32) pool[off + q] = pool[dsc.x + q];
+        unsigned m = __ballot_sync(FULL_MASK, move);
+        while (m) {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t *src = (const uint32_t *)__shfl_sync(FULL_MASK, (unsigned long long)pool, l)
+                                  + __shfl_sync(FULL_MASK, dsc.x, l);
+            uint32_t *dst = (uint32_t *)__shfl_sync(FULL_MASK, (unsigned long long)pool, l)
+                            + __shfl_sync(FULL_MASK, off, l);
+            const uint32_t len = __shfl_sync(FULL_MASK, dsc.y, l);
+            for (uint32_t q = lane; q < len; q += 32) dst[q] = src[q];
+        }
         __syncwarp();
-        if (lane == 0) {
+        if (move) {
             dp->x = (uint32_t)off;
             dp->z = (uint32_t)cap;
         }
@@ -758,6 +782,27 @@ __global__ void k_fill_u64(unsigned long long *p, unsigned long long count,
     for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
          s < count; s += (unsigned long long)gridDim.x * blockDim.x)
         p[s] = v;
+}
+
+// Split a batch's touched list back into per-instance lists with local
+// slot ids: first count the entries of every instance, then scatter.
+__global__ void k_touched_count(const uint2 *in, unsigned long long n, const uint32_t *slot_inst,
+                                unsigned long long *cnt) {
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         s < n; s += (unsigned long long)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[slot_inst[in[s].x >> 1]], 1ull);
+}
+
+__global__ void k_touched_split(const uint2 *in, unsigned long long n, const uint32_t *slot_inst,
+                                const uint32_t *inst_base, uint2 *const *out,
+                                unsigned long long *cursor) {
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         s < n; s += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint2 t = in[s];
+        const uint32_t k = slot_inst[t.x >> 1];
+        const unsigned long long pos = atomicAdd(&cursor[k], 1ull);
+        out[k][pos] = make_uint2(t.x - 2 * inst_base[k], t.y);
+    }
 }
 
 __global__ void k_remap_touched(const uint2 *in, unsigned long long n, uint32_t slot_base,
@@ -973,28 +1018,28 @@ static void set_smem_attrs() {
 }
 
 void launch_symbolic(const SlotTab &S, const ProdTab &P, const WorkBufs &W, int prod_only,
-                     int sms, cudaStream_t st) {
-    k_symbolic<<<sms * 8, 256, 0, st>>>(S, P, W, prod_only);
+                     const Tuning &T, int sms, cudaStream_t st) {
+    k_symbolic<<<sms * 8, 256, 0, st>>>(S, P, W, prod_only, T);
 }
 
 void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &W,
-                   uint32_t max_n, int sms, cudaStream_t st) {
+                   uint32_t max_n, const Tuning &T, int sms, cudaStream_t st) {
     set_smem_attrs();
     switch (bin) {
     case 0:
-        k_spgemm_warp<8, 8><<<sms * 8, 256, 8 * 256 * 4, st>>>(S, P, W, 0);
+        k_spgemm_warp<8, 8><<<sms * T.ctas_per_sm[0], 256, 8 * 256 * 4, st>>>(S, P, W, 0);
         break;
     case 1:
-        k_spgemm_warp<11, 8><<<sms * 3, 256, BIN1_SMEM, st>>>(S, P, W, 1);
+        k_spgemm_warp<11, 8><<<sms * T.ctas_per_sm[1], 256, BIN1_SMEM, st>>>(S, P, W, 1);
         break;
     case 2:
-        k_spgemm_cta<13><<<sms * 3, 256, BIN2_SMEM, st>>>(S, P, W, 2);
+        k_spgemm_cta<13><<<sms * T.ctas_per_sm[2], 256, BIN2_SMEM, st>>>(S, P, W, 2);
         break;
     default: {
         const size_t bm_bytes = (size_t)((max_n + 31) / 32) * 4;
         const bool sm = bm_bytes <= SMEM_BITMAP_MAX;
         int per_sm = sm ? (int)((220 * 1024) / (bm_bytes + 1024)) : 4;
-        per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+        per_sm = per_sm < 1 ? 1 : (per_sm > (int)T.ctas_per_sm[3] ? (int)T.ctas_per_sm[3] : per_sm);
         k_spgemm_bitmap<<<sms * per_sm, 256, sm ? bm_bytes : 0, st>>>(S, P, W, 3, sm ? 1 : 0);
         break;
     }
@@ -1068,6 +1113,20 @@ void launch_remap_touched(const uint2 *in, unsigned long long n, uint32_t slot_b
                           uint2 *out, cudaStream_t st) {
     if (!n) return;
     k_remap_touched<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(in, n, slot_base, out);
+}
+
+void launch_touched_count(const uint2 *in, unsigned long long n, const uint32_t *slot_inst,
+                          unsigned long long *cnt, cudaStream_t st) {
+    if (!n) return;
+    k_touched_count<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(in, n, slot_inst, cnt);
+}
+
+void launch_touched_split(const uint2 *in, unsigned long long n, const uint32_t *slot_inst,
+                          const uint32_t *inst_base, uint2 *const *out,
+                          unsigned long long *cursor, cudaStream_t st) {
+    if (!n) return;
+    k_touched_split<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(in, n, slot_inst, inst_base, out,
+                                                              cursor);
 }
 
 void launch_row_lengths(const uint4 *desc, uint32_t n, uint32_t *len, cudaStream_t st) {

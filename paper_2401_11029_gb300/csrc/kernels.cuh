@@ -36,6 +36,13 @@ constexpr uint32_t BIN2_LIMIT = 4096;   // CTA per group, 8192-slot table
                                         // bin 3: CTA per group, n-bit bitmap
 constexpr uint32_t PROBE_RATIO = 4;     // probe when mask_len > PROBE_RATIO*flops
 
+// Run-time schedule of the product kernels (picked by cflr_autotune).
+struct Tuning {
+    uint32_t probe_ratio = PROBE_RATIO;          // see PROBE_RATIO
+    uint32_t limit[3] = {BIN0_LIMIT, BIN1_LIMIT, BIN2_LIMIT};   // need bounds of bins 0-2
+    uint32_t ctas_per_sm[4] = {8, 3, 3, 8};      // grids (bin 3: upper bound)
+};
+
 struct SlotTab {              // per slot (device arrays, length n_slots)
     uint4 **desc;             // row descriptors (2*n per slot)
     uint32_t **pool;          // instance pool of the slot
@@ -116,9 +123,9 @@ struct WorkBufs {
 // call it before capturing launches into a graph).
 void prepare_launch_attributes();
 void launch_symbolic(const SlotTab &S, const ProdTab &P, const WorkBufs &W, int prod_only,
-                     int sms, cudaStream_t st);
+                     const Tuning &T, int sms, cudaStream_t st);
 void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &W,
-                   uint32_t max_n, int sms, cudaStream_t st);
+                   uint32_t max_n, const Tuning &T, int sms, cudaStream_t st);
 void launch_commit(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
 // Iteration frame: zero the per-iteration counters; check the pre-commit
 // conditions (buffer overflow, pair-set load); finish the iteration (pair
@@ -147,6 +154,13 @@ void launch_fill_u64(unsigned long long *p, unsigned long long count, unsigned l
                      int sms, cudaStream_t st);
 void launch_remap_touched(const uint2 *in, unsigned long long n, uint32_t slot_base,
                           uint2 *out, cudaStream_t st);
+// Per-instance split of a batch touched list (counts, then scatter with
+// local slot ids); slot_inst maps a slot to its instance.
+void launch_touched_count(const uint2 *in, unsigned long long n, const uint32_t *slot_inst,
+                          unsigned long long *cnt, cudaStream_t st);
+void launch_touched_split(const uint2 *in, unsigned long long n, const uint32_t *slot_inst,
+                          const uint32_t *inst_base, uint2 *const *out,
+                          unsigned long long *cursor, cudaStream_t st);
 
 // out[i] = in[0] + ... + in[i-1]; bsum: ceil(n/1024) scratch; grand (nullable)
 // receives the total.

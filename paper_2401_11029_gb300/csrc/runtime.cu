@@ -97,6 +97,8 @@ struct cflr_ctx {
     // accounting
     uint64_t bytes_now = 0, bytes_peak = 0;
     cflr_stats last{};
+    Tuning tuning;                      // product-kernel schedule (cflr_autotune)
+    std::string grammar_text;           // as loaded (key of the autotune cache)
     // profiling (per kernel)
     uint64_t k_launches[N_KID] = {};
     double k_ms[N_KID] = {};
@@ -277,7 +279,9 @@ struct Runner {
     DevArr<unsigned long long *> d_htab;
     DevArr<unsigned long long> d_hmask, d_cand, d_delta, d_nnz;
     DevArr<unsigned long long> d_pool_top, d_pool_cap, d_inst_delta;
-    DevArr<uint32_t> d_inst_active, d_inst_iters;
+    DevArr<uint32_t> d_inst_active, d_inst_iters, d_inst_base;
+    DevArr<unsigned long long> d_inst_cnt;
+    DevArr<uint2 *> d_inst_out;
     DevArr<uint4> d_prod;
     DevArr<uint32_t> d_use_off, d_use_code;
     // work buffers
@@ -607,21 +611,23 @@ struct Runner {
     }
 
     // ---- the iteration --------------------------------------------------
+    const Tuning &tuning() const { return own->tuning; }
     // Products of one iteration (symbolic pass and the four bins).
     void launch_products(const SlotTab &S, const ProdTab &P, const WorkBufs &W, bool timed) {
         auto run = [&](int kid, auto f) { if (timed) prof.run(kid, f); else f(); };
         if (own->cfg.form == CFLR_FORM_PLAIN) {
             // one launch sequence per production, like one library mxm each
             for (uint32_t p = 0; p < n_prods; p++) {
-                run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, (int)p, sms, st); });
+                run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, (int)p, tuning(), sms, st); });
                 for (int b = 0; b < N_BINS; b++)
-                    run(KID_BIN0 + b, [&] { launch_spgemm(b, S, P, W, max_n, sms, st); });
+                    run(KID_BIN0 + b,
+                        [&] { launch_spgemm(b, S, P, W, max_n, tuning(), sms, st); });
                 ck(cudaMemsetAsync(d_cnt.p->groups, 0, sizeof(d_cnt.p->groups), st), "memset");
             }
         } else {
-            run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, -1, sms, st); });
+            run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, -1, tuning(), sms, st); });
             for (int b = 0; b < N_BINS; b++)
-                run(KID_BIN0 + b, [&] { launch_spgemm(b, S, P, W, max_n, sms, st); });
+                run(KID_BIN0 + b, [&] { launch_spgemm(b, S, P, W, max_n, tuning(), sms, st); });
         }
     }
     // Commit and union, from the dedupe (stage 0), the capacity pass
@@ -779,7 +785,8 @@ struct Runner {
         sync("import");
     }
 
-    // Save the pending delta rows of each context (local slot ids).
+    // Save the pending delta rows of each context (local slot ids), split
+    // on the device.
     void export_touched() {
         unsigned long long *h = small(2);
         ck(cudaMemcpyAsync(h, d_touched_n.p, 16, cudaMemcpyDeviceToHost, st), "D2H");
@@ -787,31 +794,41 @@ struct Runner {
         sync("export");
         const int par = *h_parity;
         const uint64_t n_in = h[par];
-        std::vector<uint2> all(n_in);
-        if (n_in)
-            ck(cudaMemcpyAsync(all.data(), d_touched[par].p, n_in * sizeof(uint2),
-                               cudaMemcpyDeviceToHost, st), "D2H");
-        sync("export");
-        std::vector<std::vector<uint2>> per(cx.size());
-        for (auto &t : all) {
-            uint32_t s = t.x >> 1;
-            uint32_t k = slot_ctx[s];
-            per[k].push_back(make_uint2(t.x - 2 * base[k], t.y));
+        const size_t ni = cx.size();
+        if (n_in == 0) {
+            for (auto *c : cx) c->touched_n = 0;
+            return;
         }
-        for (size_t k = 0; k < cx.size(); k++) {
+        d_inst_cnt.ensure(own, ni);
+        d_inst_base.ensure(own, ni);
+        d_inst_out.ensure(own, ni);
+        ck(cudaMemsetAsync(d_inst_cnt.p, 0, ni * 8, st), "memset");
+        launch_touched_count(d_touched[par].p, n_in, d_inst.p, d_inst_cnt.p, st);
+        ck(cudaGetLastError(), "touched count");
+        std::vector<unsigned long long> cnt(ni);
+        ck(cudaMemcpyAsync(cnt.data(), d_inst_cnt.p, ni * 8, cudaMemcpyDeviceToHost, st), "D2H");
+        sync("export counts");
+        std::vector<uint2 *> outp(ni);
+        std::vector<uint32_t> b(ni);
+        for (size_t k = 0; k < ni; k++) {
             cflr_ctx *c = cx[k];
-            if (per[k].size() > c->touched_cap) {
+            if (cnt[k] > c->touched_cap) {
                 if (c->touched) c->dfree(c->touched, c->touched_cap * sizeof(uint2));
                 c->touched = nullptr;
-                c->touched_cap = std::max<uint64_t>(per[k].size(), 1024);
+                c->touched_cap = std::max<uint64_t>(cnt[k] + cnt[k] / 4, 1024);
                 c->touched = (uint2 *)c->dalloc(c->touched_cap * sizeof(uint2));
             }
-            c->touched_n = per[k].size();
-            if (c->touched_n)
-                ck(cudaMemcpyAsync(c->touched, per[k].data(), c->touched_n * sizeof(uint2),
-                                   cudaMemcpyHostToDevice, st), "H2D");
+            c->touched_n = cnt[k];
+            outp[k] = c->touched;
+            b[k] = base[k];
         }
-        sync("export");
+        ck(cudaMemcpyAsync(d_inst_out.p, outp.data(), ni * sizeof(uint2 *), cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_inst_base.p, b.data(), ni * 4, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemsetAsync(d_inst_cnt.p, 0, ni * 8, st), "memset");
+        launch_touched_split(d_touched[par].p, n_in, d_inst.p, d_inst_base.p, d_inst_out.p,
+                             d_inst_cnt.p, st);
+        ck(cudaGetLastError(), "touched split");
+        sync("export split");
     }
 
     // Byte and work totals of the finished solve, from the loop control.
@@ -1051,6 +1068,7 @@ int cflr_load_grammar(cflr_ctx *c, const char *text, size_t len) {
         if (g.nts.size() >= (1u << 20)) return c->fail(CFLR_EGRAMMAR, "too many non-terminals");
         c->free_graph();
         c->g = std::move(g);
+        c->grammar_text.assign(text, len);
         c->state = ST_GRAMMAR;
         c->err.clear();
         return CFLR_OK;
@@ -1248,6 +1266,154 @@ int cflr_get_pairs_device(const cflr_ctx *cc, uint32_t nonterminal, uint32_t *d_
                           uint32_t *d_dst, uint64_t capacity, uint64_t *n_pairs) {
     return get_pairs_common(const_cast<cflr_ctx *>(cc), nonterminal, d_src, d_dst, capacity,
                             n_pairs, true);
+}
+
+int cflr_get_tuning(const cflr_ctx *c, cflr_tuning *t) {
+    if (!c || !t) return CFLR_EINVAL;
+    t->probe_ratio = c->tuning.probe_ratio;
+    for (int b = 0; b < 3; b++) t->bin_limit[b] = c->tuning.limit[b];
+    for (int b = 0; b < 4; b++) t->ctas_per_sm[b] = c->tuning.ctas_per_sm[b];
+    return CFLR_OK;
+}
+
+int cflr_set_tuning(cflr_ctx *c, const cflr_tuning *t) {
+    if (!c || !t) return CFLR_EINVAL;
+    const uint32_t cap[3] = {BIN0_LIMIT, BIN1_LIMIT, BIN2_LIMIT};
+    if (t->probe_ratio < 1) return c->fail(CFLR_EINVAL, "probe_ratio must be >= 1");
+    for (int b = 0; b < 3; b++) {
+        if (t->bin_limit[b] < 1 || t->bin_limit[b] > cap[b] ||
+            (b && t->bin_limit[b] <= t->bin_limit[b - 1]))
+            return c->fail(CFLR_EINVAL, "bin limits must increase within 128, 1024, 4096");
+    }
+    for (int b = 0; b < 4; b++)
+        if (t->ctas_per_sm[b] < 1 || t->ctas_per_sm[b] > 32)
+            return c->fail(CFLR_EINVAL, "ctas_per_sm must be in 1..32");
+    Tuning n;
+    n.probe_ratio = t->probe_ratio;
+    for (int b = 0; b < 3; b++) n.limit[b] = t->bin_limit[b];
+    for (int b = 0; b < 4; b++) n.ctas_per_sm[b] = t->ctas_per_sm[b];
+    c->tuning = n;
+    if (c->runner) c->runner->drop_graph();   // the graph holds the old grids
+    return CFLR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+std::string autotune_key(const cflr_ctx *c) {
+    uint64_t h = 1469598103934665603ull;                     // FNV-1a of the grammar text
+    for (unsigned char ch : c->grammar_text) h = (h ^ ch) * 1099511628211ull;
+    char buf[96];
+    snprintf(buf, sizeof buf, "%016llx_%u_%llu", (unsigned long long)h, c->n,
+             (unsigned long long)c->m_edges);
+    return buf;
+}
+
+bool cache_lookup(const char *path, const std::string &key, Tuning &t) {
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char k[128];
+    Tuning r;
+    bool found = false;
+    while (fscanf(f, "%127s %u %u %u %u %u %u %u %u", k, &r.probe_ratio, &r.limit[0],
+                  &r.limit[1], &r.limit[2], &r.ctas_per_sm[0], &r.ctas_per_sm[1],
+                  &r.ctas_per_sm[2], &r.ctas_per_sm[3]) == 9) {
+        if (key == k) {
+            t = r;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, const Tuning &t) {
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %u %u %u %u %u %u %u %u\n", key.c_str(), t.probe_ratio, t.limit[0], t.limit[1],
+            t.limit[2], t.ctas_per_sm[0], t.ctas_per_sm[1], t.ctas_per_sm[2], t.ctas_per_sm[3]);
+    fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cflr_autotune(cflr_ctx *c, uint32_t max_trials, cflr_tuning *best) {
+    if (!c) return CFLR_EINVAL;
+    if (c->state < ST_GRAPH) return c->fail(CFLR_ESTATE, "load a graph first");
+    const std::string key = autotune_key(c);
+    const char *cache = c->cfg.autotune_cache;
+    Tuning found;
+    if (cache && cache_lookup(cache, key, found)) {
+        c->tuning = found;
+        if (c->runner) c->runner->drop_graph();
+        int rc = cflr_reset(c);
+        if (rc == CFLR_OK && best) cflr_get_tuning(c, best);
+        return rc;
+    }
+    if (!max_trials) max_trials = 24;
+    auto trial = [&](const Tuning &t, double &ms) -> int {
+        c->tuning = t;
+        if (c->runner) c->runner->drop_graph();
+        int rc = cflr_reset(c);
+        if (rc != CFLR_OK) return rc;
+        cflr_stats st;
+        rc = cflr_solve(c, &st);
+        if (rc != CFLR_OK && rc != CFLR_ELIMIT) return rc;
+        ms = st.solve_ms;
+        return CFLR_OK;
+    };
+    Tuning cur = c->tuning;
+    double cur_ms = 0;
+    int rc = trial(cur, cur_ms);            // warms the buffers too
+    if (rc != CFLR_OK) return rc;
+    rc = trial(cur, cur_ms);
+    if (rc != CFLR_OK) return rc;
+    uint32_t used = 2;
+    // candidate values per field, tried in this order
+    const std::vector<std::pair<int, std::vector<uint32_t>>> fields = {
+        {0, {1, 2, 8, 16, 64}},             // probe_ratio
+        {5, {4, 6, 8}},                     // ctas_per_sm[3] (bitmap bin)
+        {3, {1024, 2048, 3072}},            // limit[2]
+        {2, {256, 512}},                    // limit[1]
+        {4, {2, 4}},                        // ctas_per_sm[2]
+        {6, {2, 4, 6}},                     // ctas_per_sm[1]
+    };
+    auto with = [](Tuning t, int field, uint32_t v) {
+        switch (field) {
+        case 0: t.probe_ratio = v; break;
+        case 2: t.limit[1] = v; break;
+        case 3: t.limit[2] = v; break;
+        case 4: t.ctas_per_sm[2] = v; break;
+        case 5: t.ctas_per_sm[3] = v; break;
+        case 6: t.ctas_per_sm[1] = v; break;
+        }
+        return t;
+    };
+    for (const auto &fv : fields) {
+        for (uint32_t v : fv.second) {
+            if (used >= max_trials) break;
+            Tuning t = with(cur, fv.first, v);
+            if (t.limit[1] >= t.limit[2] || t.limit[0] >= t.limit[1]) continue;
+            double ms = 0;
+            rc = trial(t, ms);
+            used++;
+            if (rc != CFLR_OK) return rc;
+            if (ms < cur_ms) {
+                cur = t;
+                cur_ms = ms;
+            }
+        }
+    }
+    c->tuning = cur;
+    if (c->runner) c->runner->drop_graph();
+    rc = cflr_reset(c);
+    if (rc != CFLR_OK) return rc;
+    if (cache) cache_store(cache, key, cur);
+    if (best) cflr_get_tuning(c, best);
+    return CFLR_OK;
 }
 
 int cflr_kernel_stats(const cflr_ctx *c, int k, const char **name, uint64_t *launches,

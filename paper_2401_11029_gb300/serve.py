@@ -53,7 +53,7 @@ class Server:
 
     def __init__(self, grammar_text: str, mem_budget_bytes: int = 64 << 30,
                  max_active: int = 128, device: int = 0, stream=None,
-                 keep_pairs: bool = False, form: int = cflr.CFLR_FORM_GRAPH):
+                 keep_pairs: bool = False, form: int = cflr.CFLR_FORM_BATCHED):
         self.text = grammar_text
         self.budget = int(mem_budget_bytes)
         self.max_active = max_active

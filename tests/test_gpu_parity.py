@@ -336,3 +336,58 @@ def test_graph_form_batch_of_instances():
     finally:
         for s in solvers:
             s.close()
+
+
+# ---------------------------------------------------------------------------
+# product-kernel schedules
+# ---------------------------------------------------------------------------
+
+def test_tuning_roundtrip_and_validation():
+    with Solver("S -> S S | a\n") as s:
+        t = cflr.cflr_get_tuning(s.ctx)
+        assert t["bin_limit"] == [128, 1024, 4096]
+        cflr.cflr_set_tuning(s.ctx, 2, [64, 512, 2048], [4, 2, 2, 4])
+        assert cflr.cflr_get_tuning(s.ctx) == {"probe_ratio": 2, "bin_limit": [64, 512, 2048],
+                                               "ctas_per_sm": [4, 2, 2, 4]}
+        for bad in ((0, [64, 512, 2048], [4, 2, 2, 4]), (2, [256, 512, 2048], [4, 2, 2, 4]),
+                    (2, [64, 32, 2048], [4, 2, 2, 4]), (2, [64, 512, 2048], [0, 2, 2, 4])):
+            with pytest.raises(CflrError) as e:
+                cflr.cflr_set_tuning(s.ctx, *bad)
+            assert e.value.code == cflr.CFLR_EINVAL
+
+
+@pytest.mark.parametrize("tuning", [(1, [16, 64, 256], [1, 1, 1, 1]),
+                                    (1000, [128, 1024, 4096], [32, 8, 8, 8]),
+                                    (1, [128, 129, 130], [8, 3, 3, 2])])
+def test_extreme_schedules_give_identical_pairs(tuning):
+    """Groups pushed into other bins and accumulator modes still give the
+    oracle's pairs."""
+    text = gen.grammar_text("fica")
+    g = gen.fica_like(n=6000, n_a=12_000, n_d=4500, seed=31)
+    want = oracle.solve(text, g)
+    with Solver(text, form=cflr.CFLR_FORM_GRAPH) as s:
+        cflr.cflr_set_tuning(s.ctx, *tuning)
+        s.load(g)
+        s.solve()
+        for x in want.grammar.nts:
+            assert np.array_equal(s.pairs(x), want.pairs[x]), x
+
+
+def test_autotune_measures_caches_and_stays_exact(tmp_path):
+    text = gen.grammar_text("fica")
+    g = gen.fica_like(n=20_000, n_a=40_000, n_d=15_000, seed=2)
+    want = oracle.solve(text, g)
+    cache = str(tmp_path / "tuning.txt")
+    with Solver(text, autotune_cache=cache.encode()) as s:
+        s.load(g)
+        best = cflr.cflr_autotune(s.ctx, 10)
+        s.solve()
+        for x in want.grammar.nts[:want.grammar.n_user]:
+            assert np.array_equal(s.pairs(x), want.pairs[x]), x
+    assert open(cache).read().count("\n") == 1
+    with Solver(text, autotune_cache=cache.encode()) as s2:
+        s2.load(g)
+        assert cflr.cflr_autotune(s2.ctx, 10) == best      # read from the cache
+        s2.solve()
+        assert np.array_equal(s2.pairs("M"), want.pairs["M"])
+    assert open(cache).read().count("\n") == 1
