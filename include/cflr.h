@@ -74,6 +74,14 @@ typedef struct {
     uint32_t initial_capacity;  /* entries of the first work buffers; 0 = sized from
                                    the input.  Small values exercise the growth
                                    paths (every phase re-runs after a growth).      */
+    uint32_t size_hint;         /* expected pairs per input edge of the finished
+                                   closure over all non-terminals (0 = unknown): the
+                                   pair sets and the row pool start at that size, so
+                                   a fresh graph grows them rarely                  */
+    int stop_on_first_converged;/* nonzero: a batch led by this context stops after
+                                   the first iteration in which some context reaches
+                                   its fixpoint (CFLR_ELIMIT while others remain), so
+                                   a server can retire and admit between iterations  */
 } cflr_config;
 
 typedef struct {

@@ -273,15 +273,36 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
     const unsigned long long *ht = S.htab[gi.c];
     const unsigned long long hm = S.hmask[gi.c];
     uint32_t emitted = 0;
-    auto consume = [&](bool valid, uint32_t v) {
-        bool isnew = false;
+    // Nearly every product is already present (masked or repeated), so the
+    // common path is one accumulator test and one vote; keys, probes and the
+    // append only run when some lane found a new element.
+    auto emit_one = [&](bool hit, uint32_t v) {
+        bool isnew = hit;
         unsigned long long key = 0;
-        if (valid) {
-            isnew = ins(v);
+        if (hit) {
             key = group_key(gi, v);
-            if (isnew && gi.probe) isnew = !htab_contains(ht, hm, key);
+            if (gi.probe) isnew = !htab_contains(ht, hm, key);
         }
         emitted += emit_candidates(isnew, key, gi.c, W, lane);
+    };
+    auto consume = [&](bool valid, uint32_t v) {
+        const bool hit = valid && ins(v);
+        if (__any_sync(FULL_MASK, hit)) emit_one(hit, v);
+    };
+    auto consume4 = [&](uint4 w, uint32_t nv) {
+        const bool h0 = nv > 0 && ins(w.x);
+        const bool h1 = nv > 1 && ins(w.y);
+        const bool h2 = nv > 2 && ins(w.z);
+        const bool h3 = nv > 3 && ins(w.w);
+        if (__any_sync(FULL_MASK, h0 || h1 || h2 || h3)) {
+            const uint32_t hits = (uint32_t)h0 | ((uint32_t)h1 << 1) | ((uint32_t)h2 << 2) |
+                                  ((uint32_t)h3 << 3);
+#pragma unroll 1
+            for (int u = 0; u < 4; u++) {
+                const uint32_t v = u == 0 ? w.x : u == 1 ? w.y : u == 2 ? w.z : w.w;
+                emit_one((hits >> u) & 1u, v);
+            }
+        }
     };
     for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
         const uint32_t e = cb + lane * nwarps;
@@ -296,55 +317,53 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
                 len = (gi.part == PART_A) ? gd.y : gd.y - gd.w;   // B full, A_old prefix
             }
         }
-        // long rows: the warp strides over one row at a time, four coalesced
-        // loads in flight per lane
+        // long rows: the warp strides over one row at a time, 16-byte loads
+        // (row segments start at multiples of 4 entries), 128 products a step
         unsigned lm = __ballot_sync(FULL_MASK, len >= 32);
         while (lm) {
             const int l = __ffs(lm) - 1;
             lm &= lm - 1;
-            const uint32_t roff = __shfl_sync(FULL_MASK, off, l);
+            const uint32_t *row = pool + __shfl_sync(FULL_MASK, off, l);
             const uint32_t rlen = __shfl_sync(FULL_MASK, len, l);
             for (uint32_t qb = 0; qb < rlen; qb += 128) {
-                uint32_t v[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const uint32_t q = qb + 32 * u + lane;
-                    v[u] = q < rlen ? pool[roff + q] : 0;
+                const uint32_t q = qb + 4 * lane;
+                uint4 w = make_uint4(0, 0, 0, 0);
+                uint32_t nv = 0;
+                if (q + 4 <= rlen) {
+                    w = *reinterpret_cast<const uint4 *>(row + q);
+                    nv = 4;
+                } else if (q < rlen) {
+                    nv = rlen - q;
+                    w.x = row[q];
+                    if (nv > 1) w.y = row[q + 1];
+                    if (nv > 2) w.z = row[q + 2];
                 }
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (qb + 32 * u < rlen) consume(qb + 32 * u + lane < rlen, v[u]);
+                consume4(w, nv);
             }
         }
-        // short rows: packed 32 products per step, two steps per round
+        // short rows: packed, 32 products per step
         const uint32_t slen = len < 32 ? len : 0;
         const uint32_t incl = warp_incl_scan(slen, lane);
         const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
-        for (uint32_t fb = 0; fb < total; fb += 64) {
-            uint32_t v[2];
-            bool ok[2];
+        for (uint32_t fb = 0; fb < total; fb += 32) {
+            const uint32_t f = fb + lane;
+            const bool valid = f < total;
+            int lo = 0, hi = 31;
 #pragma unroll
-            for (int u = 0; u < 2; u++) {
-                const uint32_t f = fb + 32 * u + lane;
-                ok[u] = f < total;
-                int lo = 0, hi = 31;
-#pragma unroll
-                for (int st = 0; st < 5; st++) {     // first lane whose inclusive sum > f
-                    const int mid = (lo + hi) >> 1;
-                    const uint32_t x = __shfl_sync(FULL_MASK, incl, mid);
-                    if (f < x) hi = mid; else lo = mid + 1;
-                }
-                const int owner = lo > 31 ? 31 : lo;
-                const uint32_t o_off = __shfl_sync(FULL_MASK, off, owner);
-                const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
-                const uint32_t o_len = __shfl_sync(FULL_MASK, slen, owner);
-                const uint32_t o_k = __shfl_sync(FULL_MASK, k, owner);
-                v[u] = 0;
-                if (ok[u])
-                    v[u] = (gi.part == PART_U) ? o_k : pool[o_off + (f - (o_incl - o_len))];
+            for (int st = 0; st < 5; st++) {     // first lane whose inclusive sum > f
+                const int mid = (lo + hi) >> 1;
+                const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
+                if (f < v) hi = mid; else lo = mid + 1;
             }
-            consume(ok[0], v[0]);
-            if (fb + 32 < total) consume(ok[1], v[1]);
+            const int owner = lo > 31 ? 31 : lo;
+            const uint32_t o_off = __shfl_sync(FULL_MASK, off, owner);
+            const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
+            const uint32_t o_len = __shfl_sync(FULL_MASK, slen, owner);
+            const uint32_t o_k = __shfl_sync(FULL_MASK, k, owner);
+            uint32_t v = 0;
+            if (valid)
+                v = (gi.part == PART_U) ? o_k : pool[o_off + (f - (o_incl - o_len))];
+            consume(valid, v);
         }
     }
     return emitted;
@@ -387,7 +406,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SlotTab S, ProdTab P
 
 // Bin 2: one CTA per group sharing a 2^LG-slot shared-memory set.
 template <int LG>
-__global__ void __launch_bounds__(256) k_spgemm_cta(SlotTab S, ProdTab P, WorkBufs W, int bin) {
+__global__ void __launch_bounds__(256, 4) k_spgemm_cta(SlotTab S, ProdTab P, WorkBufs W, int bin) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t emitted_sh;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -423,7 +442,7 @@ __global__ void __launch_bounds__(256) k_spgemm_cta(SlotTab S, ProdTab P, WorkBu
 // memory when it fits, else a per-CTA slice of global scratch).  In mask mode
 // the mask row's bits are set first; in probe mode new bits are checked
 // against the non-terminal's hash set instead.
-__global__ void __launch_bounds__(256) k_spgemm_bitmap(SlotTab S, ProdTab P, WorkBufs W,
+__global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, WorkBufs W,
                                                        int bin, int use_smem) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t emitted_sh;
@@ -570,8 +589,6 @@ __global__ void __launch_bounds__(256) k_count(SlotTab S, WorkBufs W) {
 }
 
 // Make room for every listed row (relocate to a larger segment if needed).
-// A lane per listed row checks its capacity; the warp then copies the rows
-// that move, one after the other, with coalesced loads and stores.
 // Idempotent: after a pool overflow the host grows the pool and runs it again.
 __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs W) {
     if (W.cnt->overflow & OVF_PRE) return;
@@ -579,45 +596,33 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
     const int par = *W.parity;
     const uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x +
-                                   (threadIdx.x & ~31u);
-         base < n_t; base += stride) {
-        const unsigned long long e = base + lane;
-        uint4 *dp = nullptr;
-        uint4 dsc = make_uint4(0, 0, 0, 0);
-        uint32_t *pool = nullptr;
-        unsigned long long off = 0, cap = 0;
-        bool move = false;
-        if (e < n_t) {
-            const uint2 t = t_out[e];
-            const uint32_t slot = t.x >> 1, o = t.x & 1;
-            dp = &S.desc[slot][(size_t)o * S.n[slot] + t.y];
-            dsc = *dp;
-            const unsigned long long need = (unsigned long long)dsc.y + dsc.w;
-            if (need > dsc.z) {
-                cap = max(2ull * dsc.z, need);
-                cap = max((cap + 3) & ~3ull, 4ull);
-                const uint32_t inst = S.inst[slot];
-                off = atomicAdd(&I.pool_top[inst], cap);
-                if (off + cap > I.pool_cap[inst]) atomicOr(&W.cnt->overflow, OVF_POOL);
-                else move = true;
-                pool = S.pool[slot];
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) +
+                                (threadIdx.x >> 5);
+         e < n_t; e += nw) {
+        const uint2 t = t_out[e];
+        const uint32_t slot = t.x >> 1, o = t.x & 1;
+        uint4 *dp = &S.desc[slot][(size_t)o * S.n[slot] + t.y];
+        const uint4 dsc = *dp;
+        const unsigned long long need = (unsigned long long)dsc.y + dsc.w;
+        if (need <= dsc.z) continue;
+        unsigned long long cap = max(2ull * dsc.z, need);
+        cap = max((cap + 3) & ~3ull, 4ull);
+        const uint32_t inst = S.inst[slot];
+        unsigned long long off = 0;
+        if (lane == 0) {
+            off = atomicAdd(&I.pool_top[inst], cap);
+            if (off + cap > I.pool_cap[inst]) {
+                atomicOr(&W.cnt->overflow, OVF_POOL);
+                off = ~0ull;
             }
         }
-        unsigned m = __ballot_sync(FULL_MASK, move);
-        while (m) {
-            const int l = __ffs(m) - 1;
-            m &= m - 1;
-            const uint32_t *src = (const uint32_t *)__shfl_sync(FULL_MASK, (unsigned long long)pool, l)
-                                  + __shfl_sync(FULL_MASK, dsc.x, l);
-            uint32_t *dst = (uint32_t *)__shfl_sync(FULL_MASK, (unsigned long long)pool, l)
-                            + __shfl_sync(FULL_MASK, off, l);
-            const uint32_t len = __shfl_sync(FULL_MASK, dsc.y, l);
-            for (uint32_t q = lane; q < len; q += 32) dst[q] = src[q];
-        }
+        off = __shfl_sync(FULL_MASK, off, 0);
+        if (off == ~0ull) continue;
+        uint32_t *pool = S.pool[slot];
+        for (uint32_t q = lane; q < dsc.y; q += 32) pool[off + q] = pool[dsc.x + q];
         __syncwarp();
-        if (move) {
+        if (lane == 0) {
             dp->x = (uint32_t)off;
             dp->z = (uint32_t)cap;
         }
@@ -693,12 +698,17 @@ __global__ void __launch_bounds__(256) k_iter_end(SlotTab S, InstTab I, WorkBufs
         if (d) atomicAdd(&I.delta[S.inst[s]], d);
     }
     __syncthreads();
+    int finished = 0;                   // some instance reached its fixpoint now
     if (count_iteration) {
         for (uint32_t k = threadIdx.x; k < n_inst; k += blockDim.x) {
-            if (I.active[k]) I.iters[k] += 1;
+            if (I.active[k]) {
+                I.iters[k] += 1;
+                if (I.delta[k] == 0) finished = 1;
+            }
             I.active[k] = I.delta[k] > 0 ? 1u : 0u;
         }
     }
+    finished = __syncthreads_or(finished);
     if (threadIdx.x == 0) {
         const unsigned long long total = W.cnt->delta;
         const int par = *W.parity;
@@ -715,7 +725,8 @@ __global__ void __launch_bounds__(256) k_iter_end(SlotTab S, InstTab I, WorkBufs
         ctl->status = 0;
         ctl->last_delta = total;
         if (count_iteration) ctl->iter += 1;
-        const bool more = total > 0 && ctl->iter < ctl->limit;
+        const bool more = total > 0 && ctl->iter < ctl->limit &&
+                          !(ctl->stop_on_converge && finished);
         if (in_graph) cudaGraphSetConditional(handle, more ? 1u : 0u);
     }
 }

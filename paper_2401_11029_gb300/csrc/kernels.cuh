@@ -68,7 +68,7 @@ struct LoopCtl {
     uint32_t iter;                  // iterations finished since the solve began
     uint32_t limit;                 // stop after this many (0xFFFFFFFF = none)
     uint32_t status;                // overflow bits that stopped the last iteration
-    uint32_t pad;
+    uint32_t stop_on_converge;      // stop once some instance reaches its fixpoint
     unsigned long long last_delta;  // new pairs of the last finished iteration
     // totals over the finished iterations (work and algorithmic bytes)
     unsigned long long total_flops, total_cand, total_delta;

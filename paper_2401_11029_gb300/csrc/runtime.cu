@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -55,6 +56,33 @@ inline uint64_t next_pow2(uint64_t x) {
 
 struct Runner;
 
+// One stream-ordered memory pool per device for all contexts of this
+// library.  Freed blocks stay in the pool (release threshold: none), so
+// loading, solving and dropping graphs repeatedly does not map and unmap
+// device memory or synchronise the device the way cudaMalloc/cudaFree do.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+
+cudaError_t library_pool(int device, cudaMemPool_t *out) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (!g_pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p;
+        cudaError_t e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return e;
+        g_pools[device] = p;
+    }
+    *out = g_pools[device];
+    return cudaSuccess;
+}
+
 }  // namespace
 
 struct cflr_ctx {
@@ -62,6 +90,7 @@ struct cflr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaMemPool_t mpool = nullptr;      // the library's stream-ordered pool on `device`
     int sms = 152;
     size_t smem_optin = 0;
     std::string err;
@@ -116,12 +145,13 @@ struct cflr_ctx {
                                           std::to_string(bytes_now + bytes) + " > " +
                                           std::to_string(cfg.mem_budget_bytes) + " bytes)"};
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, bytes);
+        cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, mpool, stream);
         if (e == cudaErrorMemoryAllocation) {
             cudaGetLastError();
-            throw Status{CFLR_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+            throw Status{CFLR_ENOMEM, "device allocation of " + std::to_string(bytes) +
+                                          " bytes failed"};
         }
-        ck(e, "cudaMalloc");
+        ck(e, "cudaMallocFromPoolAsync");
         bytes_now += bytes;
         bytes_peak = std::max(bytes_peak, bytes_now);
         return p;
@@ -129,7 +159,7 @@ struct cflr_ctx {
     void dfree(void *p, size_t bytes) {
         if (!p) return;
         if (bytes == 0) bytes = 16;
-        cudaFree(p);
+        cudaFreeAsync(p, stream);
         bytes_now -= std::min(bytes_now, (uint64_t)bytes);
     }
 
@@ -331,6 +361,14 @@ struct Runner {
         graph_valid = false;
     }
 
+    // A context's allocation (stream-ordered on the context's stream) made
+    // ready for use on the batch stream.
+    void *alloc_for(cflr_ctx *c, size_t bytes) {
+        void *p = c->dalloc(bytes);
+        if (c->stream != st) ck(cudaStreamSynchronize(c->stream), "allocation");
+        return p;
+    }
+
     unsigned long long *small(size_t n) {
         if (n > h_small_n) {
             if (h_small) cudaFreeHost(h_small);
@@ -433,6 +471,7 @@ struct Runner {
         ck(cudaMemsetAsync(d_parity.p, 0, sizeof(int), st), "memset");
         LoopCtl ctl{};
         ctl.limit = own->cfg.max_iterations ? own->cfg.max_iterations : 0xFFFFFFFFu;
+        ctl.stop_on_converge = own->cfg.stop_on_first_converged ? 1u : 0u;
         *h_ctl = ctl;
         ck(cudaMemcpyAsync(d_ctl.p, h_ctl, sizeof(LoopCtl), cudaMemcpyHostToDevice, st), "H2D");
         upload_htabs();
@@ -584,7 +623,7 @@ struct Runner {
         cflr_ctx *c = cx[slot_ctx[s]];
         uint32_t x = s - base[slot_ctx[s]];
         uint64_t cap = next_pow2(std::max<uint64_t>(4 * need, 1024));
-        unsigned long long *nt = (unsigned long long *)c->dalloc(cap * 8);
+        unsigned long long *nt = (unsigned long long *)alloc_for(c, cap * 8);
         ck(cudaMemsetAsync(nt, 0xFF, cap * 8, st), "memset");
         prof.run(KID_REHASH, [&] { launch_rehash(c->htab[x], c->hcap[x], nt, cap, sms, st); });
         own->k_bytes[KID_REHASH] += c->hcap[x] * 8 + need * 8;
@@ -601,7 +640,7 @@ struct Runner {
         cap = std::min<uint64_t>(cap, 0xFFFFFFF0ull);
         if (cap <= c->pool_cap || top > cap)
             throw Status{CFLR_ENOMEM, "row pool exceeds 2^32 entries"};
-        uint32_t *np = (uint32_t *)c->dalloc(cap * 4);
+        uint32_t *np = (uint32_t *)alloc_for(c, cap * 4);
         ck(cudaMemcpyAsync(np, c->pool, c->pool_cap * 4, cudaMemcpyDeviceToDevice, st), "D2D");
         sync("pool copy");
         c->dfree(c->pool, c->pool_cap * 4);
@@ -761,7 +800,18 @@ struct Runner {
             if (h_ctl->status && !recover()) continue;
             if (h_ctl->last_delta == 0) return true;
             if (h_ctl->iter >= h_ctl->limit) return false;
+            if (h_ctl->stop_on_converge && first_converged()) return false;
         }
+    }
+
+    // True when some instance of the batch reached its fixpoint.
+    bool first_converged() {
+        std::vector<uint32_t> act(cx.size());
+        ck(cudaMemcpyAsync(act.data(), d_inst_active.p, cx.size() * 4, cudaMemcpyDeviceToHost, st), "D2H");
+        sync("active");
+        for (uint32_t a : act)
+            if (!a) return true;
+        return false;
     }
 
     // Pending delta rows of each context into the "in" touched list.
@@ -816,7 +866,7 @@ struct Runner {
                 if (c->touched) c->dfree(c->touched, c->touched_cap * sizeof(uint2));
                 c->touched = nullptr;
                 c->touched_cap = std::max<uint64_t>(cnt[k] + cnt[k] / 4, 1024);
-                c->touched = (uint2 *)c->dalloc(c->touched_cap * sizeof(uint2));
+                c->touched = (uint2 *)alloc_for(c, c->touched_cap * sizeof(uint2));
             }
             c->touched_n = cnt[k];
             outp[k] = c->touched;
@@ -897,12 +947,21 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
     c->pool_cap = std::min<uint64_t>(std::max<uint64_t>(16 * c->n_init, 1 << 16), 0xFFFFFFF0ull);
     if (c->cfg.initial_capacity)   // small first pool: the growth path runs early
         c->pool_cap = std::max<uint64_t>(8 * c->n_init / 5 + 4 * 2 * (uint64_t)nt, 64);
+    // with a size hint, named non-terminals start with an even share of the
+    // expected closure (terminal wrappers only ever hold their edges)
+    const uint64_t expect = (uint64_t)c->cfg.size_hint * m;
+    const uint64_t share = g.n_named ? expect / g.n_named : 0;
+    if (expect && !c->cfg.initial_capacity)
+        c->pool_cap = std::min<uint64_t>(std::max<uint64_t>(c->pool_cap, 3 * expect),
+                                         0xFFFFFFF0ull);
     c->pool = (uint32_t *)c->dalloc(c->pool_cap * 4);
     c->htab.assign(nt, nullptr);
     c->hcap.assign(nt, 0);
     c->nnz.assign(nt, 0);
     for (uint32_t A = 0; A < nt; A++) {
-        c->hcap[A] = next_pow2(std::max<uint64_t>(4 * c->init_cnt[A], 1024));
+        uint64_t want = std::max<uint64_t>(4 * c->init_cnt[A], 1024);
+        if (A < g.n_named) want = std::max<uint64_t>(want, 2 * share);
+        c->hcap[A] = next_pow2(want);
         c->htab[A] = (unsigned long long *)c->dalloc(c->hcap[A] * 8);
     }
 }
@@ -1046,6 +1105,10 @@ int cflr_create(cflr_ctx **out, const cflr_config *cfg) {
     if (cudaGetDeviceProperties(&prop, c.device) != cudaSuccess) return CFLR_ECUDA;
     x->sms = prop.multiProcessorCount;
     x->smem_optin = prop.sharedMemPerBlockOptin;
+    if (library_pool(c.device, &x->mpool) != cudaSuccess) {
+        cudaGetLastError();
+        return CFLR_ECUDA;
+    }
     if (c.stream) {
         x->stream = (cudaStream_t)c.stream;
     } else {
@@ -1442,6 +1505,7 @@ void cflr_destroy(cflr_ctx *c) {
     delete c->runner;
     c->runner = nullptr;
     c->free_graph();
+    if (c->stream) cudaStreamSynchronize(c->stream);   // the frees above are stream-ordered
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

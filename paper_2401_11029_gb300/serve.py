@@ -2,14 +2,16 @@
 
 Requests (a graph each, all under one grammar) arrive over time.  The
 server keeps every admitted request's matrices resident on the GPU and
-advances all of them together: each tick is one closure iteration of
-Algorithm 1 for every unfinished request, run as one batched launch
-sequence (cflr_solve_batch with a one-iteration limit).  Between ticks it
-retires the requests that reached their fixpoint (their pairs are copied
-out and their device memory freed) and admits newly arrived ones while
-their estimated device footprint fits the memory budget.  A request's
-result is the same whether it is solved alone or in the mix: the batch
-only interleaves independent fixpoints.
+advances all of them together: a tick runs closure iterations of
+Algorithm 1 for every unfinished request as one batched launch sequence
+per iteration (inside one CUDA graph), until some request reaches its
+fixpoint or the tick's iteration cap is hit (cflr_solve_batch led by a
+context with stop_on_first_converged).  Between ticks the server retires
+the finished requests (their pairs are copied out and their device memory
+freed) and admits newly arrived ones while their estimated device footprint
+fits the memory budget.  A request's result is the same whether it is
+solved alone or in the mix: the batch only interleaves independent
+fixpoints.
 
 This module only schedules; all CFL-r work runs in libcflr.so.
 """
@@ -53,7 +55,8 @@ class Server:
 
     def __init__(self, grammar_text: str, mem_budget_bytes: int = 64 << 30,
                  max_active: int = 128, device: int = 0, stream=None,
-                 keep_pairs: bool = False, form: int = cflr.CFLR_FORM_BATCHED):
+                 keep_pairs: bool = False, form: int = cflr.CFLR_FORM_GRAPH,
+                 tick_iterations: int = 16, size_hint: int = 0):
         self.text = grammar_text
         self.budget = int(mem_budget_bytes)
         self.max_active = max_active
@@ -61,15 +64,18 @@ class Server:
         self.stream = stream
         self.keep_pairs = keep_pairs
         self.form = form
-        # the leader holds the shared work buffers and the one-iteration limit;
-        # its own (empty) graph is solved at once, so it never does work
-        self.leader = cflr.cflr_create(device=device, stream=stream, max_iterations=1,
-                                       form=form)
+        self.size_hint = size_hint
+        # the leader holds the shared work buffers and the tick's iteration
+        # limit; its own (empty) graph is solved at once, so it never does work
+        self.leader = cflr.cflr_create(device=device, stream=stream,
+                                       max_iterations=tick_iterations,
+                                       stop_on_first_converged=1, form=form)
         cflr.cflr_load_grammar(self.leader, grammar_text)
         cflr.cflr_load_graph(self.leader, 1, [], [], [])
         cflr.cflr_solve(self.leader)
         self.n_nt, self.n_named, _ = cflr.cflr_grammar_sizes(self.leader)
         self.term = {}
+        self.time = {"admit_s": 0.0, "tick_s": 0.0, "retire_s": 0.0, "ticks": 0, "regrows": 0}
 
     def close(self):
         cflr.cflr_destroy(self.leader)
@@ -92,7 +98,8 @@ class Server:
         return np.asarray(out, dtype=np.uint32)
 
     def _admit(self, graph):
-        ctx = cflr.cflr_create(device=self.device, stream=self.stream, form=self.form)
+        ctx = cflr.cflr_create(device=self.device, stream=self.stream, form=self.form,
+                               size_hint=self.size_hint)
         cflr.cflr_load_grammar(ctx, self.text)
         ids = self._label_ids(ctx, graph.labels)
         cflr.cflr_load_graph(ctx, graph.n, graph.src, ids[graph.lab], graph.dst)
@@ -127,7 +134,9 @@ class Server:
                 if active and used + fp > self.budget:
                     break                                  # wait for memory to free up
                 pending.popleft()
+                ta = clock()
                 ctx = self._admit(g)
+                self.time["admit_s"] += clock() - ta
                 active.append([ctx, rid, g, arr, clock() - t0, fp, 0])
                 used += fp
             if not active:
@@ -135,13 +144,19 @@ class Server:
                 if wait > 0:
                     time.sleep(min(wait, 0.05))
                 continue
+            tt = clock()
             stats = cflr.cflr_solve_batch([self.leader] + [a[0] for a in active],
                                           allow_limit=True)
+            self.time["tick_s"] += clock() - tt
+            self.time["ticks"] += 1
             still = []
+            self.time["regrows"] += stats[0]["regrows"]
             for a, st in zip(active, stats[1:]):
                 a[6] = st["iterations"]
                 if st["converged"]:
+                    tr = clock()
                     pairs, keys = self._retire(a[0], a)
+                    self.time["retire_s"] += clock() - tr
                     used -= a[5]
                     done.append(Finished(rid=a[1], n=a[2].n, edges=a[2].n_edges, pairs=pairs,
                                          iterations=a[6], arrival_s=a[3], admitted_s=a[4],

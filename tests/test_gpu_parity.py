@@ -391,3 +391,11 @@ def test_autotune_measures_caches_and_stays_exact(tmp_path):
         s2.solve()
         assert np.array_equal(s2.pairs("M"), want.pairs["M"])
     assert open(cache).read().count("\n") == 1
+
+
+def test_size_hint_presizes_and_stays_exact():
+    text = gen.grammar_text("fica")
+    g = gen.fica_like(n=8000, n_a=16_000, n_d=6000, seed=41)
+    st_hint, _ = assert_parity(text, g, size_hint=100)
+    st_none, _ = assert_parity(text, g)
+    assert st_hint["regrows"] <= st_none["regrows"]
