@@ -55,11 +55,24 @@ def peaks() -> dict:
         return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-def workload_graph(seed: int, n: int = None):
+FSJPT = {"workload": "fsjpt_like field-sensitive points-to (Fig. wcnf:fsjpt, 64 fields)",
+         "n_vertices": 500_000, "forward_edges": 2_000_000, "reverse_edges": True, "seed": 3,
+         "productions": 514}
+
+
+def workload_graph(seed: int, n: int = None, kind: str = "fica"):
+    if kind == "fsjpt":
+        n = n or FSJPT["n_vertices"]
+        return gen.fsjpt_like(n=n, n_edges=FSJPT["forward_edges"] * n // FSJPT["n_vertices"],
+                              seed=seed)
     n = n or WORKLOAD["n_vertices"]
     scale = n / WORKLOAD["n_vertices"]
     return gen.fica_like(n=n, n_a=int(WORKLOAD["a_edges"] * scale),
                          n_d=int(WORKLOAD["d_edges"] * scale), seed=seed)
+
+
+def grammar_of(kind: str) -> str:
+    return gen.grammar_text("fsjpt" if kind == "fsjpt" else "fica")
 
 
 class ClockSampler:
@@ -135,15 +148,16 @@ def traffic_from_profile(kernel: str):
     return int(t.group(1))
 
 
-def cpu_oracle_sample(seed: int) -> dict:
+def cpu_oracle_sample(seed: int, kind: str = "fica") -> dict:
     """The oracle, as it stands, on a bounded sample of the workload."""
     import oracle
-    g = workload_graph(seed, SAMPLE_N)
-    text = gen.grammar_text("fica")
+    g = workload_graph(seed, SAMPLE_N, kind)
+    text = grammar_of(kind)
     res = oracle.solve(text, g)
     pairs = res.total()
+    name = "fsjpt_like" if kind == "fsjpt" else "fica_like"
     return {"value": pairs / res.seconds, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"fica_like n={SAMPLE_N} (same generator and ratios as the workload, "
+            "sample": f"{name} n={SAMPLE_N} (same generator and ratios as the workload, "
                       f"{g.n_edges} edges, {pairs} pairs), one worklist solve, "
                       f"{res.seconds:.1f} s on 1 host core"}
 
@@ -205,9 +219,11 @@ def run_cflr(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    seed = WORKLOAD["seed"] + 1000 * rank
-    g = workload_graph(seed, args.vertices)
-    text = gen.grammar_text("fica")
+    kind = args.workload
+    wl = FSJPT if kind == "fsjpt" else WORKLOAD
+    seed = wl["seed"] + 1000 * rank
+    g = workload_graph(seed, args.vertices, kind)
+    text = grammar_of(kind)
 
     # timed context: the device-driven loop (one CUDA graph per solve), with
     # the product schedule picked by cflr_autotune (cached per grammar and size)
@@ -345,7 +361,8 @@ def run_cflr(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": dict(WORKLOAD, pairs=int(pairs), parallelism=f"replicas{world}",
+        "config": dict(wl, n_vertices=int(g.n), edges=int(g.n_edges), pairs=int(pairs),
+                       parallelism=f"replicas{world}",
                        l2="flushed between steps (256 MiB write)"),
         "e2e": {"value": pairs_all / e2e_all, "unit": UNIT,
                 "h2d_bytes_per_step": int(12 * g.n_edges),
@@ -368,7 +385,7 @@ def run_cflr(args):
                          "events (host-launched iterations) right after the timed region",
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(WORKLOAD["seed"])
+        line["cpu_baseline"] = cpu_oracle_sample(wl["seed"], kind)
     print(json.dumps(line), flush=True)
     cflr.cflr_destroy(ctx)
 
@@ -512,7 +529,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cflr", choices=["cflr", "reference"])
-    ap.add_argument("--workload", default="fica", choices=["fica", "dyck3_batch", "serving"])
+    ap.add_argument("--workload", default="fica",
+                    choices=["fica", "fsjpt", "dyck3_batch", "serving"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--rate", type=float, default=50.0)

@@ -185,10 +185,20 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
             if (part == PART_U) {
                 f = d;
             } else {
-                const uint4 *dg = (part == PART_A) ? S.desc[pr.z] : S.desc[pr.y] + n;
+                // gathered rows: b's row form (PART_A) or a's column form
+                // (PART_B), both in orientation o; a row's descriptor is read
+                // only when its occupancy bit says it is non-empty
+                const uint32_t xg = (part == PART_A) ? pr.z : pr.y;
+                const uint4 *dg = (part == PART_A) ? S.desc[xg] : S.desc[xg] + n;
+                const uint32_t *oc = S.occ[xg];
+                const uint32_t ow = S.occ_w[xg], lx = S.local[xg];
+                const uint32_t bit = 1u << (lx & 31);
                 for (uint32_t q = lane; q < d; q += 32) {
-                    const uint4 gd = dg[pool[dstart + q]];
-                    f += (part == PART_A) ? gd.y : (gd.y - gd.w);
+                    const uint32_t k = pool[dstart + q];
+                    if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
+                        const uint4 gd = dg[k];
+                        f += (part == PART_A) ? gd.y : (gd.y - gd.w);
+                    }
                 }
                 f = warp_sum64(f);
             }
@@ -604,6 +614,11 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
         const uint32_t slot = t.x >> 1, o = t.x & 1;
         uint4 *dp = &S.desc[slot][(size_t)o * S.n[slot] + t.y];
         const uint4 dsc = *dp;
+        if (dsc.y == 0 && lane == 0) {           // the row gets its first entries
+            const uint32_t lx = S.local[slot];
+            atomicOr(&S.occ[slot][((size_t)o * S.n[slot] + t.y) * S.occ_w[slot] + (lx >> 5)],
+                     1u << (lx & 31));
+        }
         const unsigned long long need = (unsigned long long)dsc.y + dsc.w;
         if (need <= dsc.z) continue;
         unsigned long long cap = max(2ull * dsc.z, need);

@@ -53,6 +53,12 @@ struct SlotTab {              // per slot (device arrays, length n_slots)
     unsigned long long *cand;       // candidates emitted for the slot (iteration)
     unsigned long long *delta;      // new pairs of the slot (iteration)
     unsigned long long *nnz;        // pairs of the slot so far
+    // occupancy: occ[s][(o*n + k)*occ_w[s] + local[s]/32] has bit local[s]%32
+    // set once row k of orientation o of slot s is non-empty (one bit per
+    // non-terminal of the instance, all of a vertex's bits in one line)
+    uint32_t **occ;
+    uint32_t *occ_w;                // words per vertex and orientation
+    uint32_t *local;                // non-terminal id of the slot in its instance
 };
 
 struct InstTab {              // per instance

@@ -100,6 +100,8 @@ struct cflr_ctx {
     uint32_t n = 0;
     uint64_t ignored = 0;
     uint4 *desc = nullptr;              // n_nt * 2 * n descriptors
+    uint32_t *occ = nullptr;            // occupancy bits: 2 * n * occ_w words
+    uint32_t occ_w = 0;
     uint32_t *pool = nullptr;
     uint64_t pool_cap = 0;
     uint64_t pool_top = 0;              // host mirror between solves
@@ -197,6 +199,9 @@ struct cflr_ctx {
         uint32_t nt = (uint32_t)g.nts.size();
         if (desc) dfree(desc, (size_t)nt * 2 * n * sizeof(uint4));
         desc = nullptr;
+        if (occ) dfree(occ, (size_t)2 * n * occ_w * 4);
+        occ = nullptr;
+        occ_w = 0;
         if (pool) dfree(pool, pool_cap * 4);
         pool = nullptr;
         pool_cap = pool_top = 0;
@@ -305,7 +310,8 @@ struct Runner {
     // device tables
     DevArr<uint4 *> d_desc;
     DevArr<uint32_t *> d_pool;
-    DevArr<uint32_t> d_n, d_inst;
+    DevArr<uint32_t> d_n, d_inst, d_occw, d_local;
+    DevArr<uint32_t *> d_occ;
     DevArr<unsigned long long *> d_htab;
     DevArr<unsigned long long> d_hmask, d_cand, d_delta, d_nnz;
     DevArr<unsigned long long> d_pool_top, d_pool_cap, d_inst_delta;
@@ -399,7 +405,8 @@ struct Runner {
             max_n = std::max(max_n, cx[k]->n);
         }
         std::vector<uint4 *> hd(n_slots);
-        std::vector<uint32_t> hn(n_slots), hi(n_slots);
+        std::vector<uint32_t *> hoc(n_slots);
+        std::vector<uint32_t> hn(n_slots), hi(n_slots), how(n_slots), hl(n_slots);
         std::vector<unsigned long long> hz(n_slots);
         std::vector<uint4> prods;
         std::vector<std::vector<uint32_t>> uses((size_t)n_slots * 2);
@@ -408,6 +415,9 @@ struct Runner {
             uint32_t nt = (uint32_t)c->g.nts.size(), b0 = base[k];
             for (uint32_t x = 0; x < nt; x++) {
                 hd[b0 + x] = c->desc + (size_t)x * 2 * c->n;
+                hoc[b0 + x] = c->occ;
+                how[b0 + x] = c->occ_w;
+                hl[b0 + x] = x;
                 hn[b0 + x] = c->n;
                 hi[b0 + x] = (uint32_t)k;
                 hz[b0 + x] = c->nnz[x];
@@ -433,6 +443,9 @@ struct Runner {
         }
         const size_t ni = cx.size();
         d_desc.ensure(own, n_slots);
+        d_occ.ensure(own, n_slots);
+        d_occw.ensure(own, n_slots);
+        d_local.ensure(own, n_slots);
         d_pool.ensure(own, n_slots);
         d_n.ensure(own, n_slots);
         d_inst.ensure(own, n_slots);
@@ -454,6 +467,9 @@ struct Runner {
         d_ctl.ensure(own, 1);
         d_parity.ensure(own, 1);
         ck(cudaMemcpyAsync(d_desc.p, hd.data(), n_slots * sizeof(uint4 *), cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_occ.p, hoc.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_occw.p, how.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_local.p, hl.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_n.p, hn.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_inst.p, hi.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_nnz.p, hz.data(), n_slots * 8, cudaMemcpyHostToDevice, st), "H2D");
@@ -531,6 +547,7 @@ struct Runner {
         S.desc = d_desc.p; S.pool = d_pool.p; S.n = d_n.p; S.inst = d_inst.p;
         S.htab = d_htab.p; S.hmask = d_hmask.p; S.cand = d_cand.p; S.delta = d_delta.p;
         S.nnz = d_nnz.p;
+        S.occ = d_occ.p; S.occ_w = d_occw.p; S.local = d_local.p;
         return S;
     }
     ProdTab prodtab() {
@@ -944,6 +961,8 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
         ck(cudaMemcpyAsync(c->t_slot, tslot.data(), tslot.size() * 4, cudaMemcpyHostToDevice, st),
            "H2D");
     c->desc = (uint4 *)c->dalloc((size_t)nt * 2 * n * sizeof(uint4));
+    c->occ_w = (nt + 31) / 32;
+    c->occ = (uint32_t *)c->dalloc((size_t)2 * n * c->occ_w * 4);
     c->pool_cap = std::min<uint64_t>(std::max<uint64_t>(16 * c->n_init, 1 << 16), 0xFFFFFFF0ull);
     if (c->cfg.initial_capacity)   // small first pool: the growth path runs early
         c->pool_cap = std::max<uint64_t>(8 * c->n_init / 5 + 4 * 2 * (uint64_t)nt, 64);
@@ -976,6 +995,7 @@ void reset_matrices(cflr_ctx *c) {
     const uint32_t n = c->n;
     cudaStream_t st = c->stream;
     ck(cudaMemsetAsync(c->desc, 0, (size_t)nt * 2 * n * sizeof(uint4), st), "memset");
+    ck(cudaMemsetAsync(c->occ, 0, (size_t)2 * n * c->occ_w * 4, st), "memset");
     for (uint32_t A = 0; A < nt; A++)
         ck(cudaMemsetAsync(c->htab[A], 0xFF, c->hcap[A] * 8, st), "memset");
     c->pool_top = 0;
