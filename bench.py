@@ -379,6 +379,7 @@ def run_cflr(args):
         "clocks": clk,
         "tuning": tuning,
         "solve": {"form": "graph", "iterations": solve_stats["iterations"],
+                  "groups_per_bin": solve_stats["groups"],
                   "flops": solve_stats["flops"], "candidates": solve_stats["candidates"],
                   "peak_device_bytes": solve_stats["peak_device_bytes"]},
         "roofline_note": "kernel times from the same steps replayed with per-kernel CUDA "

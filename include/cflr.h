@@ -95,6 +95,7 @@ typedef struct {
     uint64_t candidates;        /* pairs the products emitted after the mask        */
     uint64_t regrows;           /* buffer growths that re-ran a phase               */
     uint32_t converged;         /* 1 when the context has reached its fixpoint      */
+    uint64_t groups[4];         /* work-list groups run by each product bin         */
 } cflr_stats;
 
 /* Schedule of the product kernels.  Each (production, delta row) group goes

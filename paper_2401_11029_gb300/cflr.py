@@ -73,10 +73,12 @@ class cflr_stats(ctypes.Structure):
                 ("solve_ms", ctypes.c_double), ("peak_device_bytes", ctypes.c_uint64),
                 ("ignored_edges", ctypes.c_uint64), ("flops", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("regrows", ctypes.c_uint64),
-                ("converged", ctypes.c_uint32)]
+                ("converged", ctypes.c_uint32), ("groups", ctypes.c_uint64 * 4)]
 
     def to_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "groups"}
+        d["groups"] = list(self.groups)
+        return d
 
 
 _lib = None

@@ -168,6 +168,25 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         fill[b] = 0;
     };
 
+    // classify one (production, delta row) group of product count f: mode,
+    // bin and table size; returns the bin and fills the group record
+    auto classify = [&](uint32_t code, uint32_t part, uint32_t idx, uint32_t d, uint32_t mlen,
+                        unsigned long long f, uint2 &grp) -> int {
+        const bool probe = (unsigned long long)mlen > (unsigned long long)T.probe_ratio * f;
+        const unsigned long long need = probe ? f : f + mlen;
+        const int b = need <= T.limit[0] ? 0 : need <= T.limit[1] ? 1 : need <= T.limit[2] ? 2 : 3;
+        // table of the smallest power of two >= 2*need slots (>= 32)
+        uint32_t lg = 5;
+        while (b < 3 && (1ull << lg) < 2 * need) lg++;
+        grp = make_uint2(((code >> 2) << 8) | (lg << 3) | (probe ? MODE_PROBE : 0u) | part, idx);
+        // algorithmic bytes: the delta row (4 B per entry), one 16-byte
+        // descriptor and 4 B per element of every referenced row, and the
+        // mask row when it is loaded
+        bytes[b] += 20ull * d + 4ull * f + (probe ? 0ull : 4ull * mlen + 16ull);
+        sym_bytes += 20ull * d + 32ull;
+        flops += f;
+        return b;
+    };
     for (unsigned long long e = (unsigned long long)blockIdx.x * 8 + wib; e < n_in; e += nw) {
         const uint2 t = t_in[e];
         const uint32_t xo = t.x, idx = t.y, slot = xo >> 1, o = xo & 1;
@@ -175,7 +194,58 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         const uint4 dsc = S.desc[slot][(size_t)o * n + idx];
         const uint32_t d = dsc.w, dstart = dsc.x + dsc.y - dsc.w;
         const uint32_t *pool = S.pool[slot];
-        for (uint32_t u = P.use_off[xo]; u < P.use_off[xo + 1]; u++) {
+        const uint32_t u0 = P.use_off[xo], u1 = P.use_off[xo + 1];
+        if (u1 - u0 >= 32 && d <= 16) {
+            // many productions read this row, each with few products: one
+            // lane per production, groups appended with one atomic per bin
+            for (uint32_t ub = u0; ub < u1; ub += 32) {
+                const uint32_t u = ub + lane;
+                int b = -1;
+                uint2 grp = make_uint2(0, 0);
+                if (u < u1) {
+                    const uint32_t code = P.use_code[u];
+                    if (prod_only < 0 || (code >> 2) == (uint32_t)prod_only) {
+                        const uint32_t part = code & 3;
+                        const uint4 pr = P.prod[code >> 2];
+                        const uint32_t mlen = S.desc[pr.x][(size_t)o * n + idx].y;
+                        unsigned long long f = 0;
+                        if (part == PART_U) {
+                            f = d;
+                        } else {
+                            const uint32_t xg = (part == PART_A) ? pr.z : pr.y;
+                            const uint4 *dg = (part == PART_A) ? S.desc[xg] : S.desc[xg] + n;
+                            const uint32_t *oc = S.occ[xg];
+                            const uint32_t ow = S.occ_w[xg], lx = S.local[xg];
+                            const uint32_t bit = 1u << (lx & 31);
+                            for (uint32_t q = 0; q < d; q++) {
+                                const uint32_t k = pool[dstart + q];
+                                if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
+                                    const uint4 gd = dg[k];
+                                    f += (part == PART_A) ? gd.y : (gd.y - gd.w);
+                                }
+                            }
+                        }
+                        if (f > 0) b = classify(code, part, idx, d, mlen, f, grp);
+                    }
+                }
+#pragma unroll
+                for (int bb = 0; bb < N_BINS; bb++) {
+                    const unsigned m = __ballot_sync(FULL_MASK, b == bb);
+                    if (!m) continue;
+                    const int leader = __ffs(m) - 1;
+                    unsigned long long pos = 0;
+                    if (lane == leader) pos = atomicAdd(&W.cnt->groups[bb], (unsigned long long)__popc(m));
+                    pos = __shfl_sync(FULL_MASK, pos, leader);
+                    if (b == bb) {
+                        pos += __popc(m & ((1u << lane) - 1));
+                        if (pos < W.group_cap[bb]) W.groups[bb][pos] = grp;
+                        else atomicOr(&W.cnt->overflow, OVF_GROUPS);
+                    }
+                }
+            }
+            continue;
+        }
+        for (uint32_t u = u0; u < u1; u++) {
             const uint32_t code = P.use_code[u];
             if (prod_only >= 0 && (code >> 2) != (uint32_t)prod_only) continue;
             const uint32_t part = code & 3;
@@ -203,25 +273,17 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                 f = warp_sum64(f);
             }
             if (lane == 0 && f > 0) {
-                const bool probe = (unsigned long long)mlen > (unsigned long long)T.probe_ratio * f;
-                const unsigned long long need = probe ? f : f + mlen;
-                const int b = need <= T.limit[0] ? 0 : need <= T.limit[1] ? 1
-                            : need <= T.limit[2] ? 2 : 3;
-                // table of the smallest power of two >= 2*need slots (>= 32)
-                uint32_t lg = 5;
-                while (b < 3 && (1ull << lg) < 2 * need) lg++;
-                stage[wib][b][fill[b]++] = make_uint2(
-                    ((code >> 2) << 8) | (lg << 3) | (probe ? MODE_PROBE : 0u) | part, idx);
-                // algorithmic bytes: the delta row (4 B per entry), one 16-byte
-                // descriptor and 4 B per element of every referenced row, and
-                // the mask row when it is loaded
-                bytes[b] += 20ull * d + 4ull * f + (probe ? 0ull : 4ull * mlen + 16ull);
-                sym_bytes += 20ull * d + 32ull;
-                flops += f;
+                uint2 grp;
+                const int b = classify(code, part, idx, d, mlen, f, grp);
+                stage[wib][b][fill[b]++] = grp;
                 if (fill[b] == SYM_BUF) flush(b);
             }
         }
     }
+    // every lane may hold byte and work counts (lane-per-production mode)
+    for (int b = 0; b < N_BINS; b++) bytes[b] = warp_sum64(bytes[b]);
+    flops = warp_sum64(flops);
+    sym_bytes = warp_sum64(sym_bytes);
     if (lane == 0) {
         for (int b = 0; b < N_BINS; b++) {
             if (fill[b]) flush(b);
@@ -733,7 +795,10 @@ __global__ void __launch_bounds__(256) k_iter_end(SlotTab S, InstTab I, WorkBufs
             ctl->total_delta += total;
             ctl->total_touched_in += W.touched_n[par];
             ctl->total_touched_out += W.touched_n[par ^ 1];
-            for (int b = 0; b < N_BINS; b++) ctl->bytes_bin[b] += W.cnt->bytes_bin[b];
+            for (int b = 0; b < N_BINS; b++) {
+                ctl->bytes_bin[b] += W.cnt->bytes_bin[b];
+                ctl->total_groups[b] += min(W.cnt->groups[b], W.group_cap[b]);
+            }
             ctl->bytes_sym += W.cnt->bytes_sym;
         }
         *W.parity = par ^ 1;

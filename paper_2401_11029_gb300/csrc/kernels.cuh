@@ -81,6 +81,7 @@ struct LoopCtl {
     unsigned long long total_touched_in, total_touched_out;
     unsigned long long bytes_bin[N_BINS];
     unsigned long long bytes_sym;
+    unsigned long long total_groups[N_BINS];
 };
 
 struct ProdTab {              // global production table of the batch

@@ -1048,7 +1048,7 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
     ck(cudaEventCreate(&ev1), "event");
     ck(cudaEventRecord(ev0, own->stream), "event");
     int rc = CFLR_OK;
-    uint64_t flops = 0, cand = 0, regrows = 0;
+    uint64_t flops = 0, cand = 0, regrows = 0, groups[4] = {0, 0, 0, 0};
     if (!active.empty()) {
         Runner &r = runner_of(own);
         r.bind(active);
@@ -1062,6 +1062,7 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
         r.export_touched();
         flops = r.h_ctl->total_flops;
         cand = r.h_ctl->total_cand;
+        for (int b = 0; b < 4; b++) groups[b] = r.h_ctl->total_groups[b];
         regrows = r.regrows;
     }
     ck(cudaEventRecord(ev1, own->stream), "event");
@@ -1082,6 +1083,7 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
         s.candidates = cand;
         s.regrows = regrows;
         s.converged = c->touched_n == 0 ? 1u : 0u;
+        for (int b = 0; b < 4; b++) s.groups[b] = groups[b];
         c->last = s;
         if (stats) stats[k] = s;
         if (s.converged) c->state = ST_SOLVED;
