@@ -397,20 +397,27 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
             lm &= lm - 1;
             const uint32_t *row = pool + __shfl_sync(FULL_MASK, off, l);
             const uint32_t rlen = __shfl_sync(FULL_MASK, len, l);
-            for (uint32_t qb = 0; qb < rlen; qb += 128) {
-                const uint32_t q = qb + 4 * lane;
-                uint4 w = make_uint4(0, 0, 0, 0);
-                uint32_t nv = 0;
-                if (q + 4 <= rlen) {
-                    w = *reinterpret_cast<const uint4 *>(row + q);
-                    nv = 4;
-                } else if (q < rlen) {
-                    nv = rlen - q;
-                    w.x = row[q];
-                    if (nv > 1) w.y = row[q + 1];
-                    if (nv > 2) w.z = row[q + 2];
+            for (uint32_t qb = 0; qb < rlen; qb += 256) {
+                // two 16-byte loads in flight per lane, then their products
+                uint4 w[2];
+                uint32_t nv[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t q = qb + 128 * h + 4 * lane;
+                    w[h] = make_uint4(0, 0, 0, 0);
+                    nv[h] = 0;
+                    if (q + 4 <= rlen) {
+                        w[h] = *reinterpret_cast<const uint4 *>(row + q);
+                        nv[h] = 4;
+                    } else if (q < rlen) {
+                        nv[h] = rlen - q;
+                        w[h].x = row[q];
+                        if (nv[h] > 1) w[h].y = row[q + 1];
+                        if (nv[h] > 2) w[h].z = row[q + 2];
+                    }
                 }
-                consume4(w, nv);
+                consume4(w[0], nv[0]);
+                if (qb + 128 < rlen) consume4(w[1], nv[1]);
             }
         }
         // short rows: packed, 32 products per step
