@@ -82,6 +82,12 @@ typedef struct {
                                    the first iteration in which some context reaches
                                    its fixpoint (CFLR_ELIMIT while others remain), so
                                    a server can retire and admit between iterations  */
+    int keep_vertex_order;      /* nonzero: store vertex v as row v.  0 (default):
+                                   the library renumbers the vertices internally in
+                                   breadth-first order of the undirected input edges,
+                                   so a row's entries fall into few 32-bit words (the
+                                   bit-packed tiles of the row storage); results
+                                   always use the caller's ids                      */
 } cflr_config;
 
 typedef struct {

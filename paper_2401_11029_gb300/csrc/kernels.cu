@@ -53,30 +53,45 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
     return v;
 }
 
-// Insert v into a shared-memory open-addressing set of 2^lg slots.
-// Returns true when v was not present.  The caller keeps the load <= 1/2.
-// Most products are already present (masked or repeated), so each slot is
-// read first and the atomic is issued only on an empty slot.
-__device__ __forceinline__ bool smem_insert(uint32_t *tab, int lg, uint32_t v) {
-    const uint32_t m = (1u << lg) - 1;
-    uint32_t s = (v * 2654435761u) >> (32 - lg);
-    for (;;) {
-        const uint32_t cur = ((volatile uint32_t *)tab)[s];
-        if (cur == v) return false;
-        if (cur == EMPTY32) {
-            const uint32_t old = atomicCAS(&tab[s], EMPTY32, v);
-            if (old == EMPTY32) return true;
-            if (old == v) return false;
-        }
-        s = (s + 1) & m;
-    }
-}
+// Accumulators of one output row.  Products arrive as 32-bit tiles (word w,
+// bits b: the columns 32w + i for every set bit i of b); a single column v is
+// the one-bit tile (v >> 5, 1 << (v & 31)).  ins() adds a tile and returns
+// the bits that were not present yet.  Nearly every product is already
+// present (masked or repeated), so a tile is tested with a plain
+// shared-memory read first and the atomic runs only when a bit is missing.
 
-__device__ __forceinline__ bool bitmap_insert(uint32_t *bm, uint32_t v) {
-    const uint32_t bit = 1u << (v & 31);
-    if (((volatile uint32_t *)bm)[v >> 5] & bit) return false;
-    return (atomicOr(&bm[v >> 5], bit) & bit) == 0;
-}
+// Open-addressing table of 2^lg words with their bits; the caller clears
+// keys to EMPTY32 and bits to 0 and keeps the load <= 1/2.
+struct HashAcc {
+    uint32_t *keys, *bits;
+    int lg;
+    __device__ __forceinline__ uint32_t ins(uint32_t w, uint32_t b) const {
+        const uint32_t m = (1u << lg) - 1;
+        uint32_t s = (w * 2654435761u) >> (32 - lg);
+        for (;;) {
+            const uint32_t cur = ((volatile uint32_t *)keys)[s];
+            if (cur == w) break;
+            if (cur == EMPTY32) {
+                const uint32_t old = atomicCAS(&keys[s], EMPTY32, w);
+                if (old == EMPTY32 || old == w) break;
+            }
+            s = (s + 1) & m;
+        }
+        const uint32_t ob = ((volatile uint32_t *)bits)[s];
+        if ((ob & b) == b) return 0;
+        return b & ~atomicOr(&bits[s], b);
+    }
+};
+
+// n-bit bitmap of the row (bin 3).
+struct BitmapAcc {
+    uint32_t *bm;
+    __device__ __forceinline__ uint32_t ins(uint32_t w, uint32_t b) const {
+        const uint32_t ob = ((volatile uint32_t *)bm)[w];
+        if ((ob & b) == b) return 0;
+        return b & ~atomicOr(&bm[w], b);
+    }
+};
 
 __device__ __forceinline__ bool htab_contains(const unsigned long long *tab,
                                               unsigned long long m, unsigned long long key) {
@@ -171,7 +186,8 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
     // classify one (production, delta row) group of product count f: mode,
     // bin and table size; returns the bin and fills the group record
     auto classify = [&](uint32_t code, uint32_t part, uint32_t idx, uint32_t d, uint32_t mlen,
-                        unsigned long long f, uint2 &grp) -> int {
+                        unsigned long long mbytes, unsigned long long f,
+                        unsigned long long fbytes, uint2 &grp) -> int {
         const bool probe = (unsigned long long)mlen > (unsigned long long)T.probe_ratio * f;
         const unsigned long long need = probe ? f : f + mlen;
         const int b = need <= T.limit[0] ? 0 : need <= T.limit[1] ? 1 : need <= T.limit[2] ? 2 : 3;
@@ -179,11 +195,11 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         uint32_t lg = 5;
         while (b < 3 && (1ull << lg) < 2 * need) lg++;
         grp = make_uint2(((code >> 2) << 8) | (lg << 3) | (probe ? MODE_PROBE : 0u) | part, idx);
-        // algorithmic bytes: the delta row (4 B per entry), one 16-byte
-        // descriptor and 4 B per element of every referenced row, and the
-        // mask row when it is loaded
-        bytes[b] += 20ull * d + 4ull * f + (probe ? 0ull : 4ull * mlen + 16ull);
-        sym_bytes += 20ull * d + 32ull;
+        // algorithmic bytes: the delta row (4 B per entry), the 20 bytes of
+        // descriptor and tile count of every referenced row, its tiles (8 B)
+        // and single entries (4 B), and the mask row when it is loaded
+        bytes[b] += 24ull * d + fbytes + (probe ? 0ull : mbytes + 20ull);
+        sym_bytes += 24ull * d + 40ull;
         flops += f;
         return b;
     };
@@ -207,13 +223,16 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                     if (prod_only < 0 || (code >> 2) == (uint32_t)prod_only) {
                         const uint32_t part = code & 3;
                         const uint4 pr = P.prod[code >> 2];
-                        const uint32_t mlen = S.desc[pr.x][(size_t)o * n + idx].y;
-                        unsigned long long f = 0;
+                        const size_t mr = (size_t)o * n + idx;
+                        const uint32_t my = S.desc[pr.x][mr].y, mt = S.tcnt[pr.x][mr];
+                        unsigned long long f = 0, fb = 0;
                         if (part == PART_U) {
                             f = d;
+                            fb = 4ull * d;
                         } else {
                             const uint32_t xg = (part == PART_A) ? pr.z : pr.y;
                             const uint4 *dg = (part == PART_A) ? S.desc[xg] : S.desc[xg] + n;
+                            const uint32_t *tg = (part == PART_A) ? S.tcnt[xg] : S.tcnt[xg] + n;
                             const uint32_t *oc = S.occ[xg];
                             const uint32_t ow = S.occ_w[xg], lx = S.local[xg];
                             const uint32_t bit = 1u << (lx & 31);
@@ -221,11 +240,16 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                                 const uint32_t k = pool[dstart + q];
                                 if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
                                     const uint4 gd = dg[k];
-                                    f += (part == PART_A) ? gd.y : (gd.y - gd.w);
+                                    const uint32_t nt = tg[k];
+                                    const uint32_t ne = (part == PART_A) ? gd.y : (gd.y - gd.w);
+                                    f += nt + ne;
+                                    fb += 8ull * nt + 4ull * ne;
                                 }
                             }
                         }
-                        if (f > 0) b = classify(code, part, idx, d, mlen, f, grp);
+                        if (f > 0)
+                            b = classify(code, part, idx, d, my + mt, 4ull * my + 8ull * mt, f,
+                                         fb, grp);
                     }
                 }
 #pragma unroll
@@ -250,16 +274,19 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
             if (prod_only >= 0 && (code >> 2) != (uint32_t)prod_only) continue;
             const uint32_t part = code & 3;
             const uint4 pr = P.prod[code >> 2];
-            const uint32_t mlen = S.desc[pr.x][(size_t)o * n + idx].y;
-            unsigned long long f = 0;
+            const size_t mr = (size_t)o * n + idx;
+            const uint32_t my = S.desc[pr.x][mr].y, mt = S.tcnt[pr.x][mr];
+            unsigned long long f = 0, fb = 0;
             if (part == PART_U) {
                 f = d;
+                fb = 4ull * d;
             } else {
                 // gathered rows: b's row form (PART_A) or a's column form
                 // (PART_B), both in orientation o; a row's descriptor is read
                 // only when its occupancy bit says it is non-empty
                 const uint32_t xg = (part == PART_A) ? pr.z : pr.y;
                 const uint4 *dg = (part == PART_A) ? S.desc[xg] : S.desc[xg] + n;
+                const uint32_t *tg = (part == PART_A) ? S.tcnt[xg] : S.tcnt[xg] + n;
                 const uint32_t *oc = S.occ[xg];
                 const uint32_t ow = S.occ_w[xg], lx = S.local[xg];
                 const uint32_t bit = 1u << (lx & 31);
@@ -267,14 +294,19 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                     const uint32_t k = pool[dstart + q];
                     if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
                         const uint4 gd = dg[k];
-                        f += (part == PART_A) ? gd.y : (gd.y - gd.w);
+                        const uint32_t nt = tg[k];
+                        const uint32_t ne = (part == PART_A) ? gd.y : (gd.y - gd.w);
+                        f += nt + ne;
+                        fb += 8ull * nt + 4ull * ne;
                     }
                 }
                 f = warp_sum64(f);
+                fb = warp_sum64(fb);
             }
             if (lane == 0 && f > 0) {
                 uint2 grp;
-                const int b = classify(code, part, idx, d, mlen, f, grp);
+                const int b = classify(code, part, idx, d, my + mt, 4ull * my + 8ull * mt, f, fb,
+                                       grp);
                 stage[wib][b][fill[b]++] = grp;
                 if (fill[b] == SYM_BUF) flush(b);
             }
@@ -327,27 +359,32 @@ __device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uin
 }
 
 // Expand the products of a group's delta entries into the accumulator
-// `ins` and emit the ones that are new (warp-collective).  Warp `warp_id` of
+// `acc` and emit the ones that are new (warp-collective).  Warp `warp_id` of
 // `nwarps` takes the entries warp_id + nwarps*l (lane l) of every block of
 // 32*nwarps entries, so all warps of a CTA get work even for short deltas.
-// A referenced row of 32 or more elements is walked by the whole warp
-// (coalesced, two loads in flight); shorter rows are packed 32 products per
-// step with a per-lane search of the owning row.  Returns the emitted count.
-template <class Ins>
+// A referenced row is its tiles, then its single entries.  A tile list of
+// 32 or more, or a run of 32 or more single entries, is walked by the whole
+// warp (coalesced 16-byte loads, two in flight per lane); shorter ones are
+// packed 32 per step with a per-lane search of the owning row.  Returns the
+// emitted count.
+template <class Acc>
 __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs &W,
                                                 const GroupInfo &gi, uint4 own,
                                                 uint32_t warp_id, uint32_t nwarps, int lane,
-                                                Ins ins) {
+                                                const Acc &acc) {
     const uint32_t d = own.w, dstart = own.x + own.y - own.w;
     const uint32_t *pool = S.pool[gi.c];
+    const size_t oo = (gi.part == PART_B) ? gi.n : 0;
     const uint4 *dg = (gi.part == PART_A) ? S.desc[gi.b]
-                    : (gi.part == PART_B) ? S.desc[gi.a] + gi.n : nullptr;
+                    : (gi.part == PART_B) ? S.desc[gi.a] + oo : nullptr;
+    const uint32_t *tg = (gi.part == PART_A) ? S.tcnt[gi.b]
+                       : (gi.part == PART_B) ? S.tcnt[gi.a] + oo : nullptr;
     const unsigned long long *ht = S.htab[gi.c];
     const unsigned long long hm = S.hmask[gi.c];
     uint32_t emitted = 0;
-    // Nearly every product is already present (masked or repeated), so the
-    // common path is one accumulator test and one vote; keys, probes and the
-    // append only run when some lane found a new element.
+    // Nearly every product is already present, so the common path is one
+    // accumulator test and one vote; keys, probes and the append only run
+    // when some lane found a new element.
     auto emit_one = [&](bool hit, uint32_t v) {
         bool isnew = hit;
         unsigned long long key = 0;
@@ -357,15 +394,43 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
         }
         emitted += emit_candidates(isnew, key, gi.c, W, lane);
     };
+    // the new bits nb of word wd (any number per lane)
+    auto emit_bits = [&](uint32_t nb, uint32_t wd) {
+        if (gi.probe) {
+            uint32_t keep = 0;
+            for (uint32_t r = nb; r; r &= r - 1) {
+                const uint32_t i = __ffs(r) - 1;
+                if (!htab_contains(ht, hm, group_key(gi, wd * 32 + i))) keep |= 1u << i;
+            }
+            nb = keep;
+        }
+        const uint32_t cnt = __popc(nb);
+        const uint32_t incl = warp_incl_scan(cnt, lane);
+        const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+        if (!total) return;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&W.cnt->cand, (unsigned long long)total);
+        base = __shfl_sync(FULL_MASK, base, 0);
+        unsigned long long pos = base + incl - cnt;
+        for (uint32_t r = nb; r; r &= r - 1, pos++) {
+            if (pos < W.cand_cap) {
+                W.cand_key[pos] = group_key(gi, wd * 32 + (__ffs(r) - 1));
+                W.cand_slot[pos] = gi.c;
+            }
+        }
+        if (lane == 0 && base + total > W.cand_cap) atomicOr(&W.cnt->overflow, OVF_CAND);
+        emitted += total;
+    };
+    auto ins1 = [&](uint32_t v) -> bool { return acc.ins(v >> 5, 1u << (v & 31)) != 0; };
     auto consume = [&](bool valid, uint32_t v) {
-        const bool hit = valid && ins(v);
+        const bool hit = valid && ins1(v);
         if (__any_sync(FULL_MASK, hit)) emit_one(hit, v);
     };
     auto consume4 = [&](uint4 w, uint32_t nv) {
-        const bool h0 = nv > 0 && ins(w.x);
-        const bool h1 = nv > 1 && ins(w.y);
-        const bool h2 = nv > 2 && ins(w.z);
-        const bool h3 = nv > 3 && ins(w.w);
+        const bool h0 = nv > 0 && ins1(w.x);
+        const bool h1 = nv > 1 && ins1(w.y);
+        const bool h2 = nv > 2 && ins1(w.z);
+        const bool h3 = nv > 3 && ins1(w.w);
         if (__any_sync(FULL_MASK, h0 || h1 || h2 || h3)) {
             const uint32_t hits = (uint32_t)h0 | ((uint32_t)h1 << 1) | ((uint32_t)h2 << 2) |
                                   ((uint32_t)h3 << 3);
@@ -376,22 +441,92 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
             }
         }
     };
+    // two tiles (w.x, w.y) and (w.z, w.w), nv of them valid
+    auto consume_tiles = [&](uint4 w, uint32_t nv) {
+        const uint32_t n0 = nv > 0 ? acc.ins(w.x, w.y) : 0u;
+        const uint32_t n1 = nv > 1 ? acc.ins(w.z, w.w) : 0u;
+        if (__any_sync(FULL_MASK, (n0 | n1) != 0)) {
+            emit_bits(n0, w.x);
+            emit_bits(n1, w.z);
+        }
+    };
     for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
         const uint32_t e = cb + lane * nwarps;
-        uint32_t k = 0, off = 0, len = 0;
+        uint32_t k = 0, off = 0, len = 0, toff = 0, tn = 0;
         if (e < d) {
             k = pool[dstart + e];
             if (gi.part == PART_U) {
                 len = 1;
             } else {
                 const uint4 gd = dg[k];
+                tn = tg[k];
                 off = gd.x;
+                toff = gd.x - tile_words(tn);
                 len = (gi.part == PART_A) ? gd.y : gd.y - gd.w;   // B full, A_old prefix
             }
         }
-        // long rows: the warp strides over one row at a time, 16-byte loads
-        // (row segments start at multiples of 4 entries), 128 products a step
-        unsigned lm = __ballot_sync(FULL_MASK, len >= 32);
+        // long tile lists: the warp strides over one list at a time
+        unsigned lm = __ballot_sync(FULL_MASK, tn >= 32);
+        while (lm) {
+            const int l = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const uint32_t *tl = pool + __shfl_sync(FULL_MASK, toff, l);
+            const uint32_t T = __shfl_sync(FULL_MASK, tn, l);
+            for (uint32_t qb = 0; qb < T; qb += 128) {
+                uint4 w[2];
+                uint32_t nv[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t q = qb + 64 * h + 2 * lane;
+                    w[h] = make_uint4(0, 0, 0, 0);
+                    nv[h] = 0;
+                    if (q + 2 <= T) {
+                        w[h] = *reinterpret_cast<const uint4 *>(tl + 2 * q);
+                        nv[h] = 2;
+                    } else if (q < T) {
+                        const uint2 t = *reinterpret_cast<const uint2 *>(tl + 2 * q);
+                        w[h].x = t.x;
+                        w[h].y = t.y;
+                        nv[h] = 1;
+                    }
+                }
+                consume_tiles(w[0], nv[0]);
+                if (qb + 64 < T) consume_tiles(w[1], nv[1]);
+            }
+        }
+        // short tile lists: packed, 32 tiles per step
+        {
+            const uint32_t stn = tn < 32 ? tn : 0;
+            const uint32_t incl = warp_incl_scan(stn, lane);
+            const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+            for (uint32_t fb = 0; fb < total; fb += 32) {
+                const uint32_t f = fb + lane;
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int st = 0; st < 5; st++) {
+                    const int mid = (lo + hi) >> 1;
+                    const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
+                    if (f < v) hi = mid; else lo = mid + 1;
+                }
+                const int owner = lo > 31 ? 31 : lo;
+                const uint32_t o_toff = __shfl_sync(FULL_MASK, toff, owner);
+                const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
+                const uint32_t o_len = __shfl_sync(FULL_MASK, stn, owner);
+                uint4 w = make_uint4(0, 0, 0, 0);
+                uint32_t nv = 0;
+                if (f < total) {
+                    const uint2 t = *reinterpret_cast<const uint2 *>(
+                        pool + o_toff + 2 * (f - (o_incl - o_len)));
+                    w.x = t.x;
+                    w.y = t.y;
+                    nv = 1;
+                }
+                consume_tiles(w, nv);
+            }
+        }
+        // long runs of single entries: the warp strides over one row at a
+        // time, 16-byte loads (segments start at multiples of 4 entries)
+        lm = __ballot_sync(FULL_MASK, len >= 32);
         while (lm) {
             const int l = __ffs(lm) - 1;
             lm &= lm - 1;
@@ -420,7 +555,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
                 if (qb + 128 < rlen) consume4(w[1], nv[1]);
             }
         }
-        // short rows: packed, 32 products per step
+        // short runs: packed, 32 products per step
         const uint32_t slen = len < 32 ? len : 0;
         const uint32_t incl = warp_incl_scan(slen, lane);
         const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
@@ -448,13 +583,35 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
     return emitted;
 }
 
-// Bins 0 and 1: one warp per group, a private shared-memory set per warp.
+// Load the mask row (the output row of c as it stands) into the accumulator:
+// thread tid of nth takes every nth tile and single entry.
+template <class Acc>
+__device__ __forceinline__ void preload_mask(const SlotTab &S, const GroupInfo &gi,
+                                             const Acc &acc, uint32_t tid, uint32_t nth) {
+    const size_t r = (size_t)gi.o * gi.n + gi.idx;
+    const uint4 md = S.desc[gi.c][r];
+    const uint32_t nt = S.tcnt[gi.c][r];
+    const uint32_t *pool = S.pool[gi.c];
+    const uint32_t *tl = pool + md.x - tile_words(nt);
+    for (uint32_t q = tid; q < nt; q += nth) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(tl + 2 * q);
+        acc.ins(t.x, t.y);
+    }
+    for (uint32_t q = tid; q < md.y; q += nth) {
+        const uint32_t v = pool[md.x + q];
+        acc.ins(v >> 5, 1u << (v & 31));
+    }
+}
+
+// Bins 0 and 1: one warp per group, a private shared-memory table per warp
+// (2^LG words and their bits).
 template <int LG, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SlotTab S, ProdTab P, WorkBufs W,
+__global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(SlotTab S, ProdTab P, WorkBufs W,
                                                             int bin) {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *tab = smem + (size_t)wib * (1u << LG);
+    uint32_t *keys = smem + (size_t)wib * (2u << LG);
+    uint32_t *bits = keys + (1u << LG);
     const unsigned long long n_groups =
         min(W.cnt->groups[bin], W.group_cap[bin]);
     const unsigned long long nw = (unsigned long long)gridDim.x * WARPS;
@@ -463,17 +620,18 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SlotTab S, ProdTab P
          g += nw) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
         const int lg = min((int)gi.lg, LG);
-        for (uint32_t s = lane; s < (1u << lg); s += 32) tab[s] = EMPTY32;
+        for (uint32_t s = lane; s < (1u << lg); s += 32) {
+            keys[s] = EMPTY32;
+            bits[s] = 0;
+        }
         __syncwarp();
+        const HashAcc acc{keys, bits, lg};
         if (!gi.probe) {
-            const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
-            const uint32_t *pool = S.pool[gi.c];
-            for (uint32_t q = lane; q < md.y; q += 32) smem_insert(tab, lg, pool[md.x + q]);
+            preload_mask(S, gi, acc, lane, 32);
             __syncwarp();
         }
         const uint4 own = owner_desc(S, gi);
-        const uint32_t e = expand_rows(S, W, gi, own, 0, 1, lane,
-                                       [&](uint32_t v) { return smem_insert(tab, lg, v); });
+        const uint32_t e = expand_rows(S, W, gi, own, 0, 1, lane, acc);
         if (lane == 0 && e) {
             atomicAdd(&S.cand[gi.c], (unsigned long long)e);
             bytes += 12ull * e;
@@ -483,30 +641,29 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_warp(SlotTab S, ProdTab P
     if (lane == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
 }
 
-// Bin 2: one CTA per group sharing a 2^LG-slot shared-memory set.
+// Bin 2: one CTA per group sharing a 2^LG-word shared-memory table.
 template <int LG>
-__global__ void __launch_bounds__(256, 4) k_spgemm_cta(SlotTab S, ProdTab P, WorkBufs W, int bin) {
+__global__ void __launch_bounds__(256, 3) k_spgemm_cta(SlotTab S, ProdTab P, WorkBufs W, int bin) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t emitted_sh;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned long long n_groups = min(W.cnt->groups[bin], W.group_cap[bin]);
+    uint32_t *keys = smem, *bits = smem + (1u << LG);
     unsigned long long bytes = 0;
     for (unsigned long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
         const int lg = min((int)gi.lg, LG);
-        for (uint32_t s = threadIdx.x; s < (1u << lg); s += blockDim.x) smem[s] = EMPTY32;
+        for (uint32_t s = threadIdx.x; s < (1u << lg); s += blockDim.x) {
+            keys[s] = EMPTY32;
+            bits[s] = 0;
+        }
         if (threadIdx.x == 0) emitted_sh = 0;
         __syncthreads();
-        if (!gi.probe) {
-            const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
-            const uint32_t *pool = S.pool[gi.c];
-            for (uint32_t q = threadIdx.x; q < md.y; q += blockDim.x)
-                smem_insert(smem, lg, pool[md.x + q]);
-        }
+        const HashAcc acc{keys, bits, lg};
+        if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
         const uint4 own = owner_desc(S, gi);
-        const uint32_t e = expand_rows(S, W, gi, own, wib, blockDim.x >> 5, lane,
-                                       [&](uint32_t v) { return smem_insert(smem, lg, v); });
+        const uint32_t e = expand_rows(S, W, gi, own, wib, blockDim.x >> 5, lane, acc);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
@@ -522,12 +679,13 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_cta(SlotTab S, ProdTab P, Wor
 // the mask row's bits are set first; in probe mode new bits are checked
 // against the non-terminal's hash set instead.
 __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, WorkBufs W,
-                                                       int bin, int use_smem) {
+                                                          int bin, int use_smem) {
     extern __shared__ uint32_t smem[];
     __shared__ uint32_t emitted_sh;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned long long n_groups = min(W.cnt->groups[bin], W.group_cap[bin]);
     uint32_t *bm = use_smem ? smem : W.bitmap_scratch + (size_t)blockIdx.x * W.bitmap_words;
+    const BitmapAcc acc{bm};
     unsigned long long bytes = 0;
     for (unsigned long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
@@ -535,18 +693,10 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
         for (uint32_t s = threadIdx.x; s < words; s += blockDim.x) bm[s] = 0;
         if (threadIdx.x == 0) emitted_sh = 0;
         __syncthreads();
-        if (!gi.probe) {
-            const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
-            const uint32_t *pool = S.pool[gi.c];
-            for (uint32_t q = threadIdx.x; q < md.y; q += blockDim.x) {
-                const uint32_t v = pool[md.x + q];
-                atomicOr(&bm[v >> 5], 1u << (v & 31));
-            }
-        }
+        if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
         const uint4 own = owner_desc(S, gi);
-        const uint32_t e = expand_rows(S, W, gi, own, wib, blockDim.x >> 5, lane,
-                                       [&](uint32_t v) { return bitmap_insert(bm, v); });
+        const uint32_t e = expand_rows(S, W, gi, own, wib, blockDim.x >> 5, lane, acc);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
@@ -667,48 +817,229 @@ __global__ void __launch_bounds__(256) k_count(SlotTab S, WorkBufs W) {
     }
 }
 
-// Make room for every listed row (relocate to a larger segment if needed).
-// Idempotent: after a pool overflow the host grows the pool and runs it again.
+constexpr uint32_t TILE_WARP_MAX = 256;   // tiles + entries one warp folds in k_capacity
+
+// Capacity for single entries after a move: room for this merge's entries
+// twice over, and for half the row's size, so a row that keeps growing
+// moves a logarithmic number of times.
+__device__ __forceinline__ uint32_t entry_cap_after_fold(uint32_t incoming, uint32_t units) {
+    const uint32_t c = max(incoming + 4u, units / 8);
+    return (c + 3) & ~3u;
+}
+__device__ __forceinline__ unsigned long long entry_cap_plain(uint32_t cap, unsigned long long need) {
+    unsigned long long c = max(2ull * cap, need);
+    return max((c + 3) & ~3ull, 4ull);
+}
+
+// Make room for every listed row.  A row that must grow moves to a new
+// segment: its tiles and single entries are folded into tiles when that
+// takes no more pool words than before (each distinct word once), else
+// copied as they are.  Rows with more than TILE_WARP_MAX tiles and entries
+// are left to k_capacity_big.  Idempotent: after a pool overflow the host
+// grows the pool and runs it again.
 __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs W) {
+    __shared__ uint32_t tab[8][4 * TILE_WARP_MAX];   // per warp: words, then bits
     if (W.cnt->overflow & OVF_PRE) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *keys = tab[wib], *bits = tab[wib] + 2 * TILE_WARP_MAX;
     const int par = *W.parity;
     const uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
     const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) +
-                                (threadIdx.x >> 5);
+    for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + wib;
          e < n_t; e += nw) {
         const uint2 t = t_out[e];
         const uint32_t slot = t.x >> 1, o = t.x & 1;
-        uint4 *dp = &S.desc[slot][(size_t)o * S.n[slot] + t.y];
+        const size_t r = (size_t)o * S.n[slot] + t.y;
+        uint4 *dp = &S.desc[slot][r];
         const uint4 dsc = *dp;
-        if (dsc.y == 0 && lane == 0) {           // the row gets its first entries
+        const uint32_t nt = S.tcnt[slot][r];
+        if (dsc.y == 0 && nt == 0 && lane == 0) {   // the row gets its first entries
             const uint32_t lx = S.local[slot];
-            atomicOr(&S.occ[slot][((size_t)o * S.n[slot] + t.y) * S.occ_w[slot] + (lx >> 5)],
-                     1u << (lx & 31));
+            atomicOr(&S.occ[slot][r * S.occ_w[slot] + (lx >> 5)], 1u << (lx & 31));
         }
         const unsigned long long need = (unsigned long long)dsc.y + dsc.w;
         if (need <= dsc.z) continue;
-        unsigned long long cap = max(2ull * dsc.z, need);
-        cap = max((cap + 3) & ~3ull, 4ull);
+        const uint32_t units = nt + dsc.y;
+        if (units > TILE_WARP_MAX) continue;
+        uint32_t *pool = S.pool[slot];
+        const uint32_t toff = dsc.x - tile_words(nt);
+        uint32_t lg = 5;
+        while ((1u << lg) < 2 * units) lg++;
+        for (uint32_t s = lane; s < (1u << lg); s += 32) {
+            keys[s] = EMPTY32;
+            bits[s] = 0;
+        }
+        __syncwarp();
+        const HashAcc acc{keys, bits, (int)lg};
+        for (uint32_t q = lane; q < nt; q += 32) {
+            const uint2 tl = *reinterpret_cast<const uint2 *>(pool + toff + 2 * q);
+            acc.ins(tl.x, tl.y);
+        }
+        for (uint32_t q = lane; q < dsc.y; q += 32) {
+            const uint32_t v = pool[dsc.x + q];
+            acc.ins(v >> 5, 1u << (v & 31));
+        }
+        __syncwarp();
+        uint32_t D = 0;
+        for (uint32_t s = lane; s < (1u << lg); s += 32) D += keys[s] != EMPTY32;
+        for (int dd = 16; dd > 0; dd >>= 1) D += __shfl_xor_sync(FULL_MASK, D, dd);
+        const bool fold = 2 * D <= 2 * nt + dsc.y;
+        const unsigned long long cap = fold ? entry_cap_after_fold(dsc.w, units)
+                                            : entry_cap_plain(dsc.z, need);
+        const uint32_t ntn = fold ? D : nt;
+        const unsigned long long size = tile_words(ntn) + cap;
         const uint32_t inst = S.inst[slot];
         unsigned long long off = 0;
         if (lane == 0) {
-            off = atomicAdd(&I.pool_top[inst], cap);
-            if (off + cap > I.pool_cap[inst]) {
+            off = atomicAdd(&I.pool_top[inst], size);
+            if (off + size > I.pool_cap[inst]) {
                 atomicOr(&W.cnt->overflow, OVF_POOL);
                 off = ~0ull;
             }
         }
         off = __shfl_sync(FULL_MASK, off, 0);
-        if (off == ~0ull) continue;
-        uint32_t *pool = S.pool[slot];
-        for (uint32_t q = lane; q < dsc.y; q += 32) pool[off + q] = pool[dsc.x + q];
+        if (off == ~0ull) {
+            __syncwarp();
+            continue;
+        }
+        uint32_t *np = pool + off;
+        if (fold) {
+            uint32_t base = 0;
+            for (uint32_t sb = 0; sb < (1u << lg); sb += 32) {
+                const uint32_t s = sb + lane;
+                const bool has = keys[s] != EMPTY32;
+                const unsigned m = __ballot_sync(FULL_MASK, has);
+                if (has) {
+                    const uint32_t pos = base + __popc(m & ((1u << lane) - 1));
+                    np[2 * pos] = keys[s];
+                    np[2 * pos + 1] = bits[s];
+                }
+                base += __popc(m);
+            }
+        } else {
+            for (uint32_t q = lane; q < 2 * nt; q += 32) np[q] = pool[toff + q];
+            const uint32_t tw = tile_words(nt);
+            for (uint32_t q = lane; q < dsc.y; q += 32) np[tw + q] = pool[dsc.x + q];
+        }
         __syncwarp();
         if (lane == 0) {
-            dp->x = (uint32_t)off;
+            dp->x = (uint32_t)off + tile_words(ntn);
+            dp->y = fold ? 0u : dsc.y;
             dp->z = (uint32_t)cap;
+            S.tcnt[slot][r] = ntn;
+        }
+        __syncwarp();
+    }
+}
+
+// The rows k_capacity leaves (more than TILE_WARP_MAX tiles and entries):
+// the CTA lists the large rows among 256 touched rows at a time, then folds
+// each through an n-bit bitmap in shared memory, so its tiles come out in
+// word order.  Without room for the bitmap (use_smem 0) the rows are copied
+// as they are.  Idempotent like k_capacity.
+__global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, WorkBufs W,
+                                                      int use_smem) {
+    extern __shared__ uint32_t bm[];
+    __shared__ uint32_t list[256];
+    __shared__ uint32_t list_n;
+    __shared__ unsigned long long sh[16];
+    __shared__ unsigned long long off_sh;
+    if (W.cnt->overflow & OVF_PRE) return;
+    const int par = *W.parity;
+    const uint2 *t_out = W.touched[par ^ 1];
+    const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
+    for (unsigned long long cb = (unsigned long long)blockIdx.x * 256; cb < n_t;
+         cb += (unsigned long long)gridDim.x * 256) {
+        if (threadIdx.x == 0) list_n = 0;
+        __syncthreads();
+        const unsigned long long e = cb + threadIdx.x;
+        if (e < n_t) {
+            const uint2 t = t_out[e];
+            const uint32_t slot = t.x >> 1, o = t.x & 1;
+            const size_t r = (size_t)o * S.n[slot] + t.y;
+            const uint4 dsc = S.desc[slot][r];
+            const uint32_t nt = S.tcnt[slot][r];
+            if ((unsigned long long)dsc.y + dsc.w > dsc.z && nt + dsc.y > TILE_WARP_MAX)
+                list[atomicAdd(&list_n, 1u)] = threadIdx.x;
+        }
+        __syncthreads();
+        const uint32_t ln = list_n;
+        for (uint32_t li = 0; li < ln; li++) {
+            const uint2 t = t_out[cb + list[li]];
+            const uint32_t slot = t.x >> 1, o = t.x & 1;
+            const uint32_t n = S.n[slot];
+            const size_t r = (size_t)o * n + t.y;
+            uint4 *dp = &S.desc[slot][r];
+            const uint4 dsc = *dp;
+            const uint32_t nt = S.tcnt[slot][r];
+            uint32_t *pool = S.pool[slot];
+            const uint32_t toff = dsc.x - tile_words(nt);
+            const uint32_t words = (n + 31) >> 5;
+            const uint32_t per = (words + blockDim.x - 1) / blockDim.x;
+            const uint32_t w0 = min(words, threadIdx.x * per), w1 = min(words, w0 + per);
+            uint32_t cnt = 0;
+            bool fold = false;
+            if (use_smem) {
+                for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+                __syncthreads();
+                for (uint32_t q = threadIdx.x; q < nt; q += blockDim.x) {
+                    const uint2 tl = *reinterpret_cast<const uint2 *>(pool + toff + 2 * q);
+                    atomicOr(&bm[tl.x], tl.y);
+                }
+                for (uint32_t q = threadIdx.x; q < dsc.y; q += blockDim.x) {
+                    const uint32_t v = pool[dsc.x + q];
+                    atomicOr(&bm[v >> 5], 1u << (v & 31));
+                }
+                __syncthreads();
+                for (uint32_t w = w0; w < w1; w++) cnt += bm[w] != 0;
+            }
+            unsigned long long D = 0;
+            const unsigned long long before = block_excl_scan256(cnt, sh, D);
+            if (use_smem) fold = 2 * D <= 2ull * nt + dsc.y;
+            const unsigned long long need = (unsigned long long)dsc.y + dsc.w;
+            const unsigned long long cap = fold ? entry_cap_after_fold(dsc.w, nt + dsc.y)
+                                                : entry_cap_plain(dsc.z, need);
+            const uint32_t ntn = fold ? (uint32_t)D : nt;
+            const unsigned long long size = tile_words(ntn) + cap;
+            if (threadIdx.x == 0) {
+                unsigned long long off = atomicAdd(&I.pool_top[S.inst[slot]], size);
+                if (off + size > I.pool_cap[S.inst[slot]]) {
+                    atomicOr(&W.cnt->overflow, OVF_POOL);
+                    off = ~0ull;
+                }
+                off_sh = off;
+            }
+            __syncthreads();
+            const unsigned long long off = off_sh;
+            if (off != ~0ull) {
+                uint32_t *np = pool + off;
+                if (fold) {
+                    unsigned long long pos = before;
+                    for (uint32_t w = w0; w < w1; w++) {
+                        const uint32_t b = bm[w];
+                        if (b) {
+                            np[2 * pos] = w;
+                            np[2 * pos + 1] = b;
+                            pos++;
+                        }
+                    }
+                } else {
+                    for (uint32_t q = threadIdx.x; q < 2 * nt; q += blockDim.x)
+                        np[q] = pool[toff + q];
+                    const uint32_t tw = tile_words(nt);
+                    for (uint32_t q = threadIdx.x; q < dsc.y; q += blockDim.x)
+                        np[tw + q] = pool[dsc.x + q];
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    dp->x = (uint32_t)off + tile_words(ntn);
+                    dp->y = fold ? 0u : dsc.y;
+                    dp->z = (uint32_t)cap;
+                    S.tcnt[slot][r] = ntn;
+                }
+            }
+            __syncthreads();
         }
     }
 }
@@ -916,17 +1247,42 @@ __global__ void k_remap_touched(const uint2 *in, unsigned long long n, uint32_t 
 // extraction: rows of the row form, each sorted, written in row order
 // ---------------------------------------------------------------------------
 
-__global__ void k_row_lengths(const uint4 *desc, uint32_t n, uint32_t *len) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        len[i] = desc[i].y;
+// Extraction walks the rows in the caller's vertex order: row i of the
+// output is stored row perm[i], and a stored column v is the caller's
+// vertex iperm[v] (both null when the vertices were kept in input order).
+__device__ __forceinline__ uint32_t stored_row(const uint32_t *perm, uint32_t i) {
+    return perm ? perm[i] : i;
+}
+
+// Pairs in a row: its single entries plus the set bits of its tiles.
+__global__ void k_row_lengths(const uint4 *desc, const uint32_t *tcnt, const uint32_t *pool,
+                              uint32_t n, const uint32_t *perm, uint32_t *len) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t r = stored_row(perm, i);
+        const uint4 d = desc[r];
+        const uint32_t nt = tcnt[r];
+        const uint32_t *tl = pool + d.x - tile_words(nt);
+        uint32_t c = d.y;
+        for (uint32_t q = 0; q < nt; q++) c += __popc(tl[2 * q + 1]);
+        len[i] = c;
+    }
+}
+
+// Renumber vertex ids in place: a[e] <- perm[a[e]].
+__global__ void k_permute_ids(uint32_t *a, unsigned long long m, const uint32_t *perm) {
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (unsigned long long)gridDim.x * blockDim.x)
+        a[e] = perm[a[e]];
 }
 
 constexpr int EXTRACT_WARP_MAX = 1024;
 
 // One warp per row: bitonic sort in shared memory for rows up to 1024
 // entries; longer rows are listed for k_extract_big.
-__global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const uint32_t *pool,
-                                                       uint32_t n,
+__global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const uint32_t *tcnt,
+                                                       const uint32_t *pool,
+                                                       uint32_t n, const uint32_t *perm,
+                                                       const uint32_t *iperm,
                                                        const unsigned long long *row_out,
                                                        uint32_t *out_src, uint32_t *out_dst,
                                                        uint32_t *big_rows,
@@ -935,8 +1291,14 @@ __global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *s = sbuf[wib];
     for (uint32_t i = blockIdx.x * 8 + wib; i < n; i += gridDim.x * 8) {
-        const uint4 d = desc[i];
-        const uint32_t len = d.y;
+        const uint32_t r = stored_row(perm, i);
+        const uint4 d = desc[r];
+        const uint32_t nt = tcnt[r];
+        const uint32_t *tl = pool + d.x - tile_words(nt);
+        uint32_t pc = 0;
+        for (uint32_t q = lane; q < nt; q += 32) pc += __popc(tl[2 * q + 1]);
+        for (int dd = 16; dd > 0; dd >>= 1) pc += __shfl_xor_sync(FULL_MASK, pc, dd);
+        const uint32_t len = d.y + pc;
         if (len == 0) continue;
         if (len > EXTRACT_WARP_MAX) {
             if (lane == 0) big_rows[atomicAdd(big_count, 1u)] = i;
@@ -944,7 +1306,29 @@ __global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const 
         }
         uint32_t P = 32;
         while (P < len) P <<= 1;
-        for (uint32_t t = lane; t < P; t += 32) s[t] = t < len ? pool[d.x + t] : EMPTY32;
+        // tiles first: each lane decodes one tile per round at its scan position
+        uint32_t base = 0;
+        for (uint32_t qb = 0; qb < nt; qb += 32) {
+            const uint32_t q = qb + lane;
+            const uint32_t w = q < nt ? tl[2 * q] : 0, b = q < nt ? tl[2 * q + 1] : 0;
+            const uint32_t c = __popc(b);
+            const uint32_t incl = warp_incl_scan(c, lane);
+            uint32_t pos = base + incl - c;
+            for (uint32_t rb = b; rb; rb &= rb - 1) {
+                uint32_t v = w * 32 + (__ffs(rb) - 1);
+                if (iperm) v = iperm[v];
+                s[pos++] = v;
+            }
+            base += __shfl_sync(FULL_MASK, incl, 31);
+        }
+        for (uint32_t t = pc + lane; t < P; t += 32) {
+            uint32_t v = EMPTY32;
+            if (t < len) {
+                v = pool[d.x + (t - pc)];
+                if (iperm) v = iperm[v];
+            }
+            s[t] = v;
+        }
         __syncwarp();
         for (uint32_t k = 2; k <= P; k <<= 1) {
             for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
@@ -970,8 +1354,10 @@ __global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const 
 
 // One CTA per long row: mark the row's columns in an n-bit bitmap, then
 // write the set bits in increasing order.
-__global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const uint32_t *pool,
-                                                     uint32_t n,
+__global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const uint32_t *tcnt,
+                                                     const uint32_t *pool,
+                                                     uint32_t n, const uint32_t *perm,
+                                                     const uint32_t *iperm,
                                                      const unsigned long long *row_out,
                                                      uint32_t *out_src, uint32_t *out_dst,
                                                      const uint32_t *big_rows,
@@ -985,11 +1371,23 @@ __global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const ui
     const uint32_t nb = *big_count;
     for (uint32_t r = blockIdx.x; r < nb; r += gridDim.x) {
         const uint32_t i = big_rows[r];
-        const uint4 d = desc[i];
+        const uint32_t sr = stored_row(perm, i);
+        const uint4 d = desc[sr];
+        const uint32_t nt = tcnt[sr];
+        const uint32_t *tl = pool + d.x - tile_words(nt);
         for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
         __syncthreads();
+        for (uint32_t q = threadIdx.x; q < nt; q += blockDim.x) {
+            const uint32_t w = tl[2 * q];
+            for (uint32_t rb = tl[2 * q + 1]; rb; rb &= rb - 1) {
+                uint32_t v = w * 32 + (__ffs(rb) - 1);
+                if (iperm) v = iperm[v];
+                atomicOr(&bm[v >> 5], 1u << (v & 31));
+            }
+        }
         for (uint32_t t = threadIdx.x; t < d.y; t += blockDim.x) {
-            const uint32_t v = pool[d.x + t];
+            uint32_t v = pool[d.x + t];
+            if (iperm) v = iperm[v];
             atomicOr(&bm[v >> 5], 1u << (v & 31));
         }
         __syncthreads();
@@ -1094,8 +1492,10 @@ static inline int grid_for(unsigned long long work, int per_block, int sms, int 
     return g < 1 ? 1 : (int)g;
 }
 
-constexpr size_t BIN1_SMEM = 8 * 2048 * 4;     // 8 warps x 2048 slots
-constexpr size_t BIN2_SMEM = 8192 * 4;
+// tables of words and bits: 2 x 4 bytes per slot
+constexpr size_t BIN0_SMEM = 8 * 2 * 256 * 4;    // 8 warps x 256 slots
+constexpr size_t BIN1_SMEM = 4 * 2 * 2048 * 4;   // 4 warps x 2048 slots
+constexpr size_t BIN2_SMEM = 2 * 8192 * 4;
 constexpr size_t SMEM_BITMAP_MAX = 200 * 1024;
 
 static void set_smem_attrs();
@@ -1105,13 +1505,15 @@ static void set_smem_attrs() {
     static bool done = false;
     if (done) return;
     done = true;
-    cudaFuncSetAttribute(k_spgemm_warp<11, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_spgemm_warp<11, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)BIN1_SMEM);
     cudaFuncSetAttribute(k_spgemm_cta<13>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)BIN2_SMEM);
     cudaFuncSetAttribute(k_spgemm_bitmap, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)SMEM_BITMAP_MAX);
     cudaFuncSetAttribute(k_extract_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SMEM_BITMAP_MAX);
+    cudaFuncSetAttribute(k_capacity_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)SMEM_BITMAP_MAX);
 }
 
@@ -1125,10 +1527,10 @@ void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &
     set_smem_attrs();
     switch (bin) {
     case 0:
-        k_spgemm_warp<8, 8><<<sms * T.ctas_per_sm[0], 256, 8 * 256 * 4, st>>>(S, P, W, 0);
+        k_spgemm_warp<8, 8><<<sms * T.ctas_per_sm[0], 256, BIN0_SMEM, st>>>(S, P, W, 0);
         break;
     case 1:
-        k_spgemm_warp<11, 8><<<sms * T.ctas_per_sm[1], 256, BIN1_SMEM, st>>>(S, P, W, 1);
+        k_spgemm_warp<11, 4><<<sms * T.ctas_per_sm[1], 128, BIN1_SMEM, st>>>(S, P, W, 1);
         break;
     case 2:
         k_spgemm_cta<13><<<sms * T.ctas_per_sm[2], 256, BIN2_SMEM, st>>>(S, P, W, 2);
@@ -1172,9 +1574,15 @@ void launch_count(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st)
     k_count<<<sms * 8, 256, 0, st>>>(S, W);
 }
 
-void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, int sms,
-                     cudaStream_t st) {
+void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t max_n,
+                     int sms, cudaStream_t st) {
+    set_smem_attrs();
     k_capacity<<<sms * 8, 256, 0, st>>>(S, I, W);
+    const size_t bm_bytes = (size_t)((max_n + 31) / 32) * 4;
+    const bool sm = bm_bytes <= SMEM_BITMAP_MAX;
+    int per_sm = sm ? (int)((220 * 1024) / (bm_bytes + 3072)) : 8;
+    per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+    k_capacity_big<<<sms * per_sm, 256, sm ? bm_bytes : 0, st>>>(S, I, W, sm ? 1 : 0);
 }
 
 void launch_scatter(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {
@@ -1227,25 +1635,34 @@ void launch_touched_split(const uint2 *in, unsigned long long n, const uint32_t 
                                                               cursor);
 }
 
-void launch_row_lengths(const uint4 *desc, uint32_t n, uint32_t *len, cudaStream_t st) {
-    if (!n) return;
-    k_row_lengths<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(desc, n, len);
+void launch_permute_ids(uint32_t *a, unsigned long long m, const uint32_t *perm, int sms,
+                        cudaStream_t st) {
+    if (!m) return;
+    k_permute_ids<<<grid_for(m, 256, sms, 8), 256, 0, st>>>(a, m, perm);
 }
 
-void launch_extract(const uint4 *desc, const uint32_t *pool, uint32_t n,
-                    const unsigned long long *row_out, uint32_t *out_src, uint32_t *out_dst,
-                    uint32_t *big_rows, uint32_t *big_count, uint32_t *bitmap, int sms,
-                    cudaStream_t st) {
+void launch_row_lengths(const uint4 *desc, const uint32_t *tcnt, const uint32_t *pool,
+                        uint32_t n, const uint32_t *perm, uint32_t *len, cudaStream_t st) {
+    if (!n) return;
+    k_row_lengths<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(desc, tcnt, pool, n, perm, len);
+}
+
+void launch_extract(const uint4 *desc, const uint32_t *tcnt, const uint32_t *pool, uint32_t n,
+                    const uint32_t *perm,
+                    const uint32_t *iperm, const unsigned long long *row_out, uint32_t *out_src,
+                    uint32_t *out_dst, uint32_t *big_rows, uint32_t *big_count,
+                    uint32_t *bitmap, int sms, cudaStream_t st) {
     if (!n) return;
     set_smem_attrs();
     cudaMemsetAsync(big_count, 0, sizeof(uint32_t), st);
-    k_extract_small<<<grid_for(n, 8, sms, 8), 256, 0, st>>>(desc, pool, n, row_out, out_src,
-                                                            out_dst, big_rows, big_count);
+    k_extract_small<<<grid_for(n, 8, sms, 8), 256, 0, st>>>(desc, tcnt, pool, n, perm, iperm,
+                                                            row_out, out_src, out_dst, big_rows,
+                                                            big_count);
     const size_t bm_bytes = (size_t)((n + 31) / 32) * 4;
     const bool sm = bm_bytes <= SMEM_BITMAP_MAX;
-    k_extract_big<<<sms * 4, 256, sm ? bm_bytes : 0, st>>>(desc, pool, n, row_out, out_src,
-                                                           out_dst, big_rows, big_count, bitmap,
-                                                           sm ? 1 : 0);
+    k_extract_big<<<sms * 4, 256, sm ? bm_bytes : 0, st>>>(desc, tcnt, pool, n, perm, iperm,
+                                                           row_out, out_src, out_dst, big_rows,
+                                                           big_count, bitmap, sm ? 1 : 0);
 }
 
 }  // namespace cflr

@@ -100,6 +100,7 @@ struct cflr_ctx {
     uint32_t n = 0;
     uint64_t ignored = 0;
     uint4 *desc = nullptr;              // n_nt * 2 * n descriptors
+    uint32_t *tcnt = nullptr;           // n_nt * 2 * n tile counts
     uint32_t *occ = nullptr;            // occupancy bits: 2 * n * occ_w words
     uint32_t occ_w = 0;
     uint32_t *pool = nullptr;
@@ -117,6 +118,9 @@ struct cflr_ctx {
     uint32_t *e_src = nullptr, *e_lab = nullptr, *e_dst = nullptr;
     uint32_t *t_off = nullptr, *t_slot = nullptr;
     size_t t_off_n = 0, t_slot_n = 0;
+    // vertex renumbering (null when the caller's order is kept):
+    // perm[caller id] = stored id, iperm[stored id] = caller id
+    uint32_t *perm = nullptr, *iperm = nullptr;
     std::vector<uint64_t> init_cnt;
     Runner *runner = nullptr;           // cached work buffers of solves led by this context
     // extraction scratch
@@ -192,6 +196,9 @@ struct cflr_ctx {
         if (e_dst) dfree(e_dst, m_edges * 4);
         if (t_off) dfree(t_off, t_off_n * 4);
         if (t_slot) dfree(t_slot, t_slot_n * 4);
+        if (perm) dfree(perm, (size_t)n * 4);
+        if (iperm) dfree(iperm, (size_t)n * 4);
+        perm = iperm = nullptr;
         e_src = e_lab = e_dst = t_off = t_slot = nullptr;
         m_edges = n_init = 0;
         t_off_n = t_slot_n = 0;
@@ -199,6 +206,8 @@ struct cflr_ctx {
         uint32_t nt = (uint32_t)g.nts.size();
         if (desc) dfree(desc, (size_t)nt * 2 * n * sizeof(uint4));
         desc = nullptr;
+        if (tcnt) dfree(tcnt, (size_t)nt * 2 * n * 4);
+        tcnt = nullptr;
         if (occ) dfree(occ, (size_t)2 * n * occ_w * 4);
         occ = nullptr;
         occ_w = 0;
@@ -309,6 +318,7 @@ struct Runner {
     std::vector<uint32_t> slot_ctx;    // slot -> context index
     // device tables
     DevArr<uint4 *> d_desc;
+    DevArr<uint32_t *> d_tcnt;
     DevArr<uint32_t *> d_pool;
     DevArr<uint32_t> d_n, d_inst, d_occw, d_local;
     DevArr<uint32_t *> d_occ;
@@ -405,6 +415,7 @@ struct Runner {
             max_n = std::max(max_n, cx[k]->n);
         }
         std::vector<uint4 *> hd(n_slots);
+        std::vector<uint32_t *> htc(n_slots);
         std::vector<uint32_t *> hoc(n_slots);
         std::vector<uint32_t> hn(n_slots), hi(n_slots), how(n_slots), hl(n_slots);
         std::vector<unsigned long long> hz(n_slots);
@@ -415,6 +426,7 @@ struct Runner {
             uint32_t nt = (uint32_t)c->g.nts.size(), b0 = base[k];
             for (uint32_t x = 0; x < nt; x++) {
                 hd[b0 + x] = c->desc + (size_t)x * 2 * c->n;
+                htc[b0 + x] = c->tcnt + (size_t)x * 2 * c->n;
                 hoc[b0 + x] = c->occ;
                 how[b0 + x] = c->occ_w;
                 hl[b0 + x] = x;
@@ -443,6 +455,7 @@ struct Runner {
         }
         const size_t ni = cx.size();
         d_desc.ensure(own, n_slots);
+        d_tcnt.ensure(own, n_slots);
         d_occ.ensure(own, n_slots);
         d_occw.ensure(own, n_slots);
         d_local.ensure(own, n_slots);
@@ -467,6 +480,7 @@ struct Runner {
         d_ctl.ensure(own, 1);
         d_parity.ensure(own, 1);
         ck(cudaMemcpyAsync(d_desc.p, hd.data(), n_slots * sizeof(uint4 *), cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_tcnt.p, htc.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_occ.p, hoc.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_occw.p, how.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_local.p, hl.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
@@ -544,7 +558,7 @@ struct Runner {
 
     SlotTab slots() {
         SlotTab S;
-        S.desc = d_desc.p; S.pool = d_pool.p; S.n = d_n.p; S.inst = d_inst.p;
+        S.desc = d_desc.p; S.tcnt = d_tcnt.p; S.pool = d_pool.p; S.n = d_n.p; S.inst = d_inst.p;
         S.htab = d_htab.p; S.hmask = d_hmask.p; S.cand = d_cand.p; S.delta = d_delta.p;
         S.nnz = d_nnz.p;
         S.occ = d_occ.p; S.occ_w = d_occw.p; S.local = d_local.p;
@@ -696,7 +710,7 @@ struct Runner {
             run(KID_RESET, [&] { launch_reset_dnew(S, W, sms, st); });
             run(KID_COUNT, [&] { launch_count(S, W, sms, st); });
         }
-        if (stage <= 1) run(KID_CAPACITY, [&] { launch_capacity(S, I, W, sms, st); });
+        if (stage <= 1) run(KID_CAPACITY, [&] { launch_capacity(S, I, W, max_n, sms, st); });
         run(KID_SCATTER, [&] { launch_scatter(S, W, sms, st); });
         launch_iter_end(S, I, W, d_ctl.p, n_slots, (uint32_t)cx.size(), count_iteration,
                         handle, in_graph, st);
@@ -917,6 +931,49 @@ Runner &runner_of(cflr_ctx *c) {
     return *c->runner;
 }
 
+// Breadth-first order of the vertices over the edges taken as undirected,
+// each unvisited vertex (in id order) starting a new search.  Vertices that
+// reach one another through few edges get nearby ids, so the rows of the
+// closure matrices fall into few 32-bit words.  Returns order[k] = the
+// caller id of stored vertex k.
+std::vector<uint32_t> locality_order(uint32_t n, uint64_t m, const uint32_t *src,
+                                     const uint32_t *dst) {
+    std::vector<uint64_t> off((size_t)n + 1, 0);
+    for (uint64_t e = 0; e < m; e++) {
+        off[(size_t)src[e] + 1]++;
+        off[(size_t)dst[e] + 1]++;
+    }
+    for (uint32_t v = 0; v < n; v++) off[v + 1] += off[v];
+    std::vector<uint32_t> adj(2 * m);
+    {
+        std::vector<uint64_t> cur(off.begin(), off.end() - 1);
+        for (uint64_t e = 0; e < m; e++) {
+            adj[cur[src[e]]++] = dst[e];
+            adj[cur[dst[e]]++] = src[e];
+        }
+    }
+    std::vector<uint32_t> order;
+    order.reserve(n);
+    std::vector<uint8_t> seen(n, 0);
+    for (uint32_t s = 0; s < n; s++) {
+        if (seen[s]) continue;
+        seen[s] = 1;
+        size_t head = order.size();
+        order.push_back(s);
+        while (head < order.size()) {
+            const uint32_t u = order[head++];
+            for (uint64_t q = off[u]; q < off[(size_t)u + 1]; q++) {
+                const uint32_t v = adj[q];
+                if (!seen[v]) {
+                    seen[v] = 1;
+                    order.push_back(v);
+                }
+            }
+        }
+    }
+    return order;
+}
+
 // Copy the graph to the device and size the matrices (cflr_load_graph).
 void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *lab,
                   const uint32_t *dst) {
@@ -947,6 +1004,21 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
         ck(cudaMemcpyAsync(c->e_lab, lab, m * 4, cudaMemcpyHostToDevice, st), "H2D edges");
         ck(cudaMemcpyAsync(c->e_dst, dst, m * 4, cudaMemcpyHostToDevice, st), "H2D edges");
     }
+    if (!c->cfg.keep_vertex_order && n > 0) {
+        const std::vector<uint32_t> order = locality_order(n, m, src, dst);
+        std::vector<uint32_t> perm(n);
+        for (uint32_t k = 0; k < n; k++) perm[order[k]] = k;
+        c->perm = (uint32_t *)c->dalloc((size_t)n * 4);
+        c->iperm = (uint32_t *)c->dalloc((size_t)n * 4);
+        ck(cudaMemcpyAsync(c->perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st),
+           "H2D order");
+        ck(cudaMemcpyAsync(c->iperm, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st),
+           "H2D order");
+        launch_permute_ids(c->e_src, m, c->perm, c->sms, st);
+        launch_permute_ids(c->e_dst, m, c->perm, c->sms, st);
+        // the host vectors die here: wait for the copies that read them
+        ck(cudaStreamSynchronize(st), "sync order");
+    }
     std::vector<uint32_t> toff(1, 0), tslot;
     for (uint32_t l = 0; l < nterm; l++) {
         tslot.insert(tslot.end(), g.term_nts[l].begin(), g.term_nts[l].end());
@@ -961,6 +1033,7 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
         ck(cudaMemcpyAsync(c->t_slot, tslot.data(), tslot.size() * 4, cudaMemcpyHostToDevice, st),
            "H2D");
     c->desc = (uint4 *)c->dalloc((size_t)nt * 2 * n * sizeof(uint4));
+    c->tcnt = (uint32_t *)c->dalloc((size_t)nt * 2 * n * 4);
     c->occ_w = (nt + 31) / 32;
     c->occ = (uint32_t *)c->dalloc((size_t)2 * n * c->occ_w * 4);
     c->pool_cap = std::min<uint64_t>(std::max<uint64_t>(16 * c->n_init, 1 << 16), 0xFFFFFFF0ull);
@@ -995,6 +1068,7 @@ void reset_matrices(cflr_ctx *c) {
     const uint32_t n = c->n;
     cudaStream_t st = c->stream;
     ck(cudaMemsetAsync(c->desc, 0, (size_t)nt * 2 * n * sizeof(uint4), st), "memset");
+    ck(cudaMemsetAsync(c->tcnt, 0, (size_t)nt * 2 * n * 4, st), "memset");
     ck(cudaMemsetAsync(c->occ, 0, (size_t)2 * n * c->occ_w * 4, st), "memset");
     for (uint32_t A = 0; A < nt; A++)
         ck(cudaMemsetAsync(c->htab[A], 0xFF, c->hcap[A] * 8, st), "memset");
@@ -1293,10 +1367,11 @@ void extract_device(cflr_ctx *c, uint32_t nt, uint32_t *out_src, uint32_t *out_d
         }
     }
     const uint4 *desc = c->desc + (size_t)nt * 2 * n;
-    launch_row_lengths(desc, n, c->x_len, st);
+    const uint32_t *tcnt = c->tcnt + (size_t)nt * 2 * n;
+    launch_row_lengths(desc, tcnt, c->pool, n, c->perm, c->x_len, st);
     launch_exclusive_scan(c->x_len, n, c->x_off, c->x_bsum, nullptr, st);
-    launch_extract(desc, c->pool, n, c->x_off, out_src, out_dst, c->x_big, c->x_big + n, c->x_bm,
-                   c->sms, st);
+    launch_extract(desc, tcnt, c->pool, n, c->perm, c->iperm, c->x_off, out_src, out_dst,
+                   c->x_big, c->x_big + n, c->x_bm, c->sms, st);
     ck(cudaGetLastError(), "extract");
 }
 
@@ -1615,12 +1690,14 @@ extern "C" int cflr_get_pairs_device_noalloc(const cflr_ctx *cc, uint32_t nonter
     uint32_t *big = (uint32_t *)(w + NA_OFF_WORDS + NA_BSUM_WORDS + NA_LEN_WORDS);
     const uint32_t n = c->n;
     const uint4 *desc = c->desc + (size_t)nonterminal * 2 * n;
+    const uint32_t *tcnt = c->tcnt + (size_t)nonterminal * 2 * n;
     cudaStream_t st = c->stream;
     // Every scratch word used below is written before it is read (lengths,
     // offsets, block sums) or cleared first (the long-row counter).
-    launch_row_lengths(desc, n, len, st);
+    launch_row_lengths(desc, tcnt, c->pool, n, c->perm, len, st);
     launch_exclusive_scan(len, n, off, bsum, nullptr, st);
-    launch_extract(desc, c->pool, n, off, d_src, d_dst, big, big + n, nullptr, c->sms, st);
+    launch_extract(desc, tcnt, c->pool, n, c->perm, c->iperm, off, d_src, d_dst, big, big + n,
+                   nullptr, c->sms, st);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(c, CudaError{e, "extract (no-alloc)"});

@@ -399,3 +399,31 @@ def test_size_hint_presizes_and_stays_exact():
     st_hint, _ = assert_parity(text, g, size_hint=100)
     st_none, _ = assert_parity(text, g)
     assert st_hint["regrows"] <= st_none["regrows"]
+
+
+@pytest.mark.parametrize("keep", [0, 1])
+@pytest.mark.parametrize("name", ["dyck1", "fica", "fsca2"])
+def test_vertex_order_kept_or_renumbered(keep, name):
+    """The internal breadth-first renumbering is invisible in the results."""
+    text, labels = GRAMMARS[name]
+    for seed, (n, m) in enumerate([(1, 1), (7, 12), (500, 1400)]):
+        g = gen.random_graph(n=n, n_edges=m, labels=labels, seed=50 + seed)
+        assert_parity(text, g, keep_vertex_order=keep)
+    g = gen.fica_like(n=6000, n_a=12_000, n_d=4500, seed=43)
+    assert_parity(gen.grammar_text("fica"), g, keep_vertex_order=keep)
+
+
+@pytest.mark.parametrize("keep", [0, 1])
+def test_rows_beyond_the_shared_memory_bitmap(keep):
+    """Over 1.6M vertices the row bitmaps (product bin 3, folding of large
+    rows) no longer fit shared memory and take their global-memory forms."""
+    n = 1_700_000
+    rng = np.random.default_rng(71)
+    ids = rng.choice(n, size=700, replace=False).astype(np.uint32)
+    # a path of 600 'a' edges over scattered ids (closure rows up to 600 long)
+    # and 100 'a' edges into the path (more rows that grow every iteration)
+    src = np.concatenate([ids[:600], ids[600:700]])
+    dst = np.concatenate([ids[1:601], ids[rng.integers(0, 600, size=100)]])
+    g = gen.Graph(n=n, labels=["a"], src=src, lab=np.zeros(src.size, np.uint32), dst=dst)
+    st, want = assert_parity("S -> a | S S\n", g, keep_vertex_order=keep)
+    assert want.pairs["S"].size > 150_000
