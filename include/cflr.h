@@ -97,7 +97,8 @@ typedef struct {
     double solve_ms;            /* device time of cflr_solve (CUDA events)          */
     uint64_t peak_device_bytes; /* high-water mark of this context's device memory  */
     uint64_t ignored_edges;     /* edges whose label no production uses             */
-    uint64_t flops;             /* boolean OR operations of all products            */
+    uint64_t flops;             /* product steps: every referenced 32-bit tile is one
+                                   step that ORs up to 32 pairs into an accumulator */
     uint64_t candidates;        /* pairs the products emitted after the mask        */
     uint64_t regrows;           /* buffer growths that re-ran a phase               */
     uint32_t converged;         /* 1 when the context has reached its fixpoint      */

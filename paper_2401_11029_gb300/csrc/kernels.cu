@@ -195,11 +195,11 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         uint32_t lg = 5;
         while (b < 3 && (1ull << lg) < 2 * need) lg++;
         grp = make_uint2(((code >> 2) << 8) | (lg << 3) | (probe ? MODE_PROBE : 0u) | part, idx);
-        // algorithmic bytes: the delta row (4 B per entry), the 20 bytes of
-        // descriptor and tile count of every referenced row, its tiles (8 B)
-        // and single entries (4 B), and the mask row when it is loaded
-        bytes[b] += 24ull * d + fbytes + (probe ? 0ull : mbytes + 20ull);
-        sym_bytes += 24ull * d + 40ull;
+        // algorithmic bytes: the delta entries (4 B each), the descriptor
+        // (16 B) and tiles (8 B each) of every referenced row, and the mask
+        // row's descriptor and tiles when it is loaded
+        bytes[b] += 20ull * d + fbytes + (probe ? 0ull : mbytes + 16ull);
+        sym_bytes += 20ull * d + 40ull;
         flops += f;
         return b;
     };
@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         const uint32_t xo = t.x, idx = t.y, slot = xo >> 1, o = xo & 1;
         const uint32_t n = S.n[slot];
         const uint4 dsc = S.desc[slot][(size_t)o * n + idx];
-        const uint32_t d = dsc.w, dstart = dsc.x + dsc.y - dsc.w;
+        const uint32_t d = S.dn[slot][(size_t)o * n + idx].x;
+        const uint32_t dstart = dsc.x + tile_words(dsc.z);
         const uint32_t *pool = S.pool[slot];
         const uint32_t u0 = P.use_off[xo], u1 = P.use_off[xo + 1];
         if (u1 - u0 >= 32 && d <= 16) {
@@ -223,8 +224,7 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                     if (prod_only < 0 || (code >> 2) == (uint32_t)prod_only) {
                         const uint32_t part = code & 3;
                         const uint4 pr = P.prod[code >> 2];
-                        const size_t mr = (size_t)o * n + idx;
-                        const uint32_t my = S.desc[pr.x][mr].y, mt = S.tcnt[pr.x][mr];
+                        const uint32_t mt = S.desc[pr.x][(size_t)o * n + idx].y;
                         unsigned long long f = 0, fb = 0;
                         if (part == PART_U) {
                             f = d;
@@ -232,24 +232,19 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                         } else {
                             const uint32_t xg = (part == PART_A) ? pr.z : pr.y;
                             const uint4 *dg = (part == PART_A) ? S.desc[xg] : S.desc[xg] + n;
-                            const uint32_t *tg = (part == PART_A) ? S.tcnt[xg] : S.tcnt[xg] + n;
                             const uint32_t *oc = S.occ[xg];
                             const uint32_t ow = S.occ_w[xg], lx = S.local[xg];
                             const uint32_t bit = 1u << (lx & 31);
                             for (uint32_t q = 0; q < d; q++) {
                                 const uint32_t k = pool[dstart + q];
                                 if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
-                                    const uint4 gd = dg[k];
-                                    const uint32_t nt = tg[k];
-                                    const uint32_t ne = (part == PART_A) ? gd.y : (gd.y - gd.w);
-                                    f += nt + ne;
-                                    fb += 8ull * nt + 4ull * ne;
+                                    const uint32_t nt = dg[k].y;
+                                    f += nt;
+                                    fb += 16ull + 8ull * nt;
                                 }
                             }
                         }
-                        if (f > 0)
-                            b = classify(code, part, idx, d, my + mt, 4ull * my + 8ull * mt, f,
-                                         fb, grp);
+                        if (f > 0) b = classify(code, part, idx, d, mt, 8ull * mt, f, fb, grp);
                     }
                 }
 #pragma unroll
@@ -274,8 +269,7 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
             if (prod_only >= 0 && (code >> 2) != (uint32_t)prod_only) continue;
             const uint32_t part = code & 3;
             const uint4 pr = P.prod[code >> 2];
-            const size_t mr = (size_t)o * n + idx;
-            const uint32_t my = S.desc[pr.x][mr].y, mt = S.tcnt[pr.x][mr];
+            const uint32_t mt = S.desc[pr.x][(size_t)o * n + idx].y;
             unsigned long long f = 0, fb = 0;
             if (part == PART_U) {
                 f = d;
@@ -286,18 +280,15 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                 // only when its occupancy bit says it is non-empty
                 const uint32_t xg = (part == PART_A) ? pr.z : pr.y;
                 const uint4 *dg = (part == PART_A) ? S.desc[xg] : S.desc[xg] + n;
-                const uint32_t *tg = (part == PART_A) ? S.tcnt[xg] : S.tcnt[xg] + n;
                 const uint32_t *oc = S.occ[xg];
                 const uint32_t ow = S.occ_w[xg], lx = S.local[xg];
                 const uint32_t bit = 1u << (lx & 31);
                 for (uint32_t q = lane; q < d; q += 32) {
                     const uint32_t k = pool[dstart + q];
                     if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
-                        const uint4 gd = dg[k];
-                        const uint32_t nt = tg[k];
-                        const uint32_t ne = (part == PART_A) ? gd.y : (gd.y - gd.w);
-                        f += nt + ne;
-                        fb += 8ull * nt + 4ull * ne;
+                        const uint32_t nt = dg[k].y;
+                        f += nt;
+                        fb += 16ull + 8ull * nt;
                     }
                 }
                 f = warp_sum64(f);
@@ -305,8 +296,7 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
             }
             if (lane == 0 && f > 0) {
                 uint2 grp;
-                const int b = classify(code, part, idx, d, my + mt, 4ull * my + 8ull * mt, f, fb,
-                                       grp);
+                const int b = classify(code, part, idx, d, mt, 8ull * mt, f, fb, grp);
                 stage[wib][b][fill[b]++] = grp;
                 if (fill[b] == SYM_BUF) flush(b);
             }
@@ -346,10 +336,13 @@ __device__ __forceinline__ GroupInfo decode_group(const ProdTab &P, const SlotTa
     return gi;
 }
 
-// The delta owner of a group: a's row form (PART_A, PART_U) or b's column form.
-__device__ __forceinline__ uint4 owner_desc(const SlotTab &S, const GroupInfo &gi) {
+// The delta of a group: the entries the last merge added to a's row form
+// (PART_A, PART_U) or b's column form; returns {pool offset, count}.
+__device__ __forceinline__ uint2 owner_delta(const SlotTab &S, const GroupInfo &gi) {
     const uint32_t x = (gi.part == PART_B) ? gi.b : gi.a;
-    return S.desc[x][(size_t)gi.o * gi.n + gi.idx];
+    const size_t r = (size_t)gi.o * gi.n + gi.idx;
+    const uint4 dsc = S.desc[x][r];
+    return make_uint2(dsc.x + tile_words(dsc.z), S.dn[x][r].x);
 }
 
 __device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uint32_t v) {
@@ -362,39 +355,27 @@ __device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uin
 // `acc` and emit the ones that are new (warp-collective).  Warp `warp_id` of
 // `nwarps` takes the entries warp_id + nwarps*l (lane l) of every block of
 // 32*nwarps entries, so all warps of a CTA get work even for short deltas.
-// A referenced row is its tiles, then its single entries.  A tile list of
-// 32 or more, or a run of 32 or more single entries, is walked by the whole
-// warp (coalesced 16-byte loads, two in flight per lane); shorter ones are
-// packed 32 per step with a per-lane search of the owning row.  Returns the
-// emitted count.
+// Each delta entry k gathers row k of the other operand as a list of tiles:
+// b's row form for dA . B, a's column form for A . dB (the whole of A: the
+// tiles hold A_old and dA together, and dA . dB is already in dA . B, so the
+// union of the two products is the one of optimisation 1).  A list of 32 or
+// more tiles is walked by the whole warp (coalesced 16-byte loads, two in
+// flight per lane); shorter ones are packed 32 tiles per step with a
+// per-lane search of the owning row.  Returns the emitted count.
 template <class Acc>
 __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs &W,
-                                                const GroupInfo &gi, uint4 own,
+                                                const GroupInfo &gi, uint2 own,
                                                 uint32_t warp_id, uint32_t nwarps, int lane,
                                                 const Acc &acc) {
-    const uint32_t d = own.w, dstart = own.x + own.y - own.w;
+    const uint32_t dstart = own.x, d = own.y;
     const uint32_t *pool = S.pool[gi.c];
-    const size_t oo = (gi.part == PART_B) ? gi.n : 0;
     const uint4 *dg = (gi.part == PART_A) ? S.desc[gi.b]
-                    : (gi.part == PART_B) ? S.desc[gi.a] + oo : nullptr;
-    const uint32_t *tg = (gi.part == PART_A) ? S.tcnt[gi.b]
-                       : (gi.part == PART_B) ? S.tcnt[gi.a] + oo : nullptr;
+                    : (gi.part == PART_B) ? S.desc[gi.a] + gi.n : nullptr;
     const unsigned long long *ht = S.htab[gi.c];
     const unsigned long long hm = S.hmask[gi.c];
     uint32_t emitted = 0;
-    // Nearly every product is already present, so the common path is one
-    // accumulator test and one vote; keys, probes and the append only run
-    // when some lane found a new element.
-    auto emit_one = [&](bool hit, uint32_t v) {
-        bool isnew = hit;
-        unsigned long long key = 0;
-        if (hit) {
-            key = group_key(gi, v);
-            if (gi.probe) isnew = !htab_contains(ht, hm, key);
-        }
-        emitted += emit_candidates(isnew, key, gi.c, W, lane);
-    };
-    // the new bits nb of word wd (any number per lane)
+    // the new bits nb of word wd (any number per lane); nearly every product
+    // is already present, so callers vote first and only then come here
     auto emit_bits = [&](uint32_t nb, uint32_t wd) {
         if (gi.probe) {
             uint32_t keep = 0;
@@ -421,26 +402,6 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
         if (lane == 0 && base + total > W.cand_cap) atomicOr(&W.cnt->overflow, OVF_CAND);
         emitted += total;
     };
-    auto ins1 = [&](uint32_t v) -> bool { return acc.ins(v >> 5, 1u << (v & 31)) != 0; };
-    auto consume = [&](bool valid, uint32_t v) {
-        const bool hit = valid && ins1(v);
-        if (__any_sync(FULL_MASK, hit)) emit_one(hit, v);
-    };
-    auto consume4 = [&](uint4 w, uint32_t nv) {
-        const bool h0 = nv > 0 && ins1(w.x);
-        const bool h1 = nv > 1 && ins1(w.y);
-        const bool h2 = nv > 2 && ins1(w.z);
-        const bool h3 = nv > 3 && ins1(w.w);
-        if (__any_sync(FULL_MASK, h0 || h1 || h2 || h3)) {
-            const uint32_t hits = (uint32_t)h0 | ((uint32_t)h1 << 1) | ((uint32_t)h2 << 2) |
-                                  ((uint32_t)h3 << 3);
-#pragma unroll 1
-            for (int u = 0; u < 4; u++) {
-                const uint32_t v = u == 0 ? w.x : u == 1 ? w.y : u == 2 ? w.z : w.w;
-                emit_one((hits >> u) & 1u, v);
-            }
-        }
-    };
     // two tiles (w.x, w.y) and (w.z, w.w), nv of them valid
     auto consume_tiles = [&](uint4 w, uint32_t nv) {
         const uint32_t n0 = nv > 0 ? acc.ins(w.x, w.y) : 0u;
@@ -450,20 +411,26 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
             emit_bits(n1, w.z);
         }
     };
+    if (gi.part == PART_U) {        // c -> a: the delta entries themselves
+        for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
+            const uint32_t e = cb + lane * nwarps;
+            uint32_t nb = 0, wd = 0;
+            if (e < d) {
+                const uint32_t v = pool[dstart + e];
+                wd = v >> 5;
+                nb = acc.ins(wd, 1u << (v & 31));
+            }
+            if (__any_sync(FULL_MASK, nb != 0)) emit_bits(nb, wd);
+        }
+        return emitted;
+    }
     for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
         const uint32_t e = cb + lane * nwarps;
-        uint32_t k = 0, off = 0, len = 0, toff = 0, tn = 0;
+        uint32_t toff = 0, tn = 0;
         if (e < d) {
-            k = pool[dstart + e];
-            if (gi.part == PART_U) {
-                len = 1;
-            } else {
-                const uint4 gd = dg[k];
-                tn = tg[k];
-                off = gd.x;
-                toff = gd.x - tile_words(tn);
-                len = (gi.part == PART_A) ? gd.y : gd.y - gd.w;   // B full, A_old prefix
-            }
+            const uint4 gd = dg[pool[dstart + e]];
+            toff = gd.x;
+            tn = gd.y;
         }
         // long tile lists: the warp strides over one list at a time
         unsigned lm = __ballot_sync(FULL_MASK, tn >= 32);
@@ -495,73 +462,11 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
             }
         }
         // short tile lists: packed, 32 tiles per step
-        {
-            const uint32_t stn = tn < 32 ? tn : 0;
-            const uint32_t incl = warp_incl_scan(stn, lane);
-            const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
-            for (uint32_t fb = 0; fb < total; fb += 32) {
-                const uint32_t f = fb + lane;
-                int lo = 0, hi = 31;
-#pragma unroll
-                for (int st = 0; st < 5; st++) {
-                    const int mid = (lo + hi) >> 1;
-                    const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
-                    if (f < v) hi = mid; else lo = mid + 1;
-                }
-                const int owner = lo > 31 ? 31 : lo;
-                const uint32_t o_toff = __shfl_sync(FULL_MASK, toff, owner);
-                const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
-                const uint32_t o_len = __shfl_sync(FULL_MASK, stn, owner);
-                uint4 w = make_uint4(0, 0, 0, 0);
-                uint32_t nv = 0;
-                if (f < total) {
-                    const uint2 t = *reinterpret_cast<const uint2 *>(
-                        pool + o_toff + 2 * (f - (o_incl - o_len)));
-                    w.x = t.x;
-                    w.y = t.y;
-                    nv = 1;
-                }
-                consume_tiles(w, nv);
-            }
-        }
-        // long runs of single entries: the warp strides over one row at a
-        // time, 16-byte loads (segments start at multiples of 4 entries)
-        lm = __ballot_sync(FULL_MASK, len >= 32);
-        while (lm) {
-            const int l = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const uint32_t *row = pool + __shfl_sync(FULL_MASK, off, l);
-            const uint32_t rlen = __shfl_sync(FULL_MASK, len, l);
-            for (uint32_t qb = 0; qb < rlen; qb += 256) {
-                // two 16-byte loads in flight per lane, then their products
-                uint4 w[2];
-                uint32_t nv[2];
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const uint32_t q = qb + 128 * h + 4 * lane;
-                    w[h] = make_uint4(0, 0, 0, 0);
-                    nv[h] = 0;
-                    if (q + 4 <= rlen) {
-                        w[h] = *reinterpret_cast<const uint4 *>(row + q);
-                        nv[h] = 4;
-                    } else if (q < rlen) {
-                        nv[h] = rlen - q;
-                        w[h].x = row[q];
-                        if (nv[h] > 1) w[h].y = row[q + 1];
-                        if (nv[h] > 2) w[h].z = row[q + 2];
-                    }
-                }
-                consume4(w[0], nv[0]);
-                if (qb + 128 < rlen) consume4(w[1], nv[1]);
-            }
-        }
-        // short runs: packed, 32 products per step
-        const uint32_t slen = len < 32 ? len : 0;
-        const uint32_t incl = warp_incl_scan(slen, lane);
+        const uint32_t stn = tn < 32 ? tn : 0;
+        const uint32_t incl = warp_incl_scan(stn, lane);
         const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
         for (uint32_t fb = 0; fb < total; fb += 32) {
             const uint32_t f = fb + lane;
-            const bool valid = f < total;
             int lo = 0, hi = 31;
 #pragma unroll
             for (int st = 0; st < 5; st++) {     // first lane whose inclusive sum > f
@@ -570,36 +475,34 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
                 if (f < v) hi = mid; else lo = mid + 1;
             }
             const int owner = lo > 31 ? 31 : lo;
-            const uint32_t o_off = __shfl_sync(FULL_MASK, off, owner);
+            const uint32_t o_toff = __shfl_sync(FULL_MASK, toff, owner);
             const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
-            const uint32_t o_len = __shfl_sync(FULL_MASK, slen, owner);
-            const uint32_t o_k = __shfl_sync(FULL_MASK, k, owner);
-            uint32_t v = 0;
-            if (valid)
-                v = (gi.part == PART_U) ? o_k : pool[o_off + (f - (o_incl - o_len))];
-            consume(valid, v);
+            const uint32_t o_len = __shfl_sync(FULL_MASK, stn, owner);
+            uint4 w = make_uint4(0, 0, 0, 0);
+            uint32_t nv = 0;
+            if (f < total) {
+                const uint2 t = *reinterpret_cast<const uint2 *>(
+                    pool + o_toff + 2 * (f - (o_incl - o_len)));
+                w.x = t.x;
+                w.y = t.y;
+                nv = 1;
+            }
+            consume_tiles(w, nv);
         }
     }
     return emitted;
 }
 
 // Load the mask row (the output row of c as it stands) into the accumulator:
-// thread tid of nth takes every nth tile and single entry.
+// thread tid of nth takes every nth tile.
 template <class Acc>
 __device__ __forceinline__ void preload_mask(const SlotTab &S, const GroupInfo &gi,
                                              const Acc &acc, uint32_t tid, uint32_t nth) {
-    const size_t r = (size_t)gi.o * gi.n + gi.idx;
-    const uint4 md = S.desc[gi.c][r];
-    const uint32_t nt = S.tcnt[gi.c][r];
-    const uint32_t *pool = S.pool[gi.c];
-    const uint32_t *tl = pool + md.x - tile_words(nt);
-    for (uint32_t q = tid; q < nt; q += nth) {
+    const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
+    const uint32_t *tl = S.pool[gi.c] + md.x;
+    for (uint32_t q = tid; q < md.y; q += nth) {
         const uint2 t = *reinterpret_cast<const uint2 *>(tl + 2 * q);
         acc.ins(t.x, t.y);
-    }
-    for (uint32_t q = tid; q < md.y; q += nth) {
-        const uint32_t v = pool[md.x + q];
-        acc.ins(v >> 5, 1u << (v & 31));
     }
 }
 
@@ -630,7 +533,7 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(
             preload_mask(S, gi, acc, lane, 32);
             __syncwarp();
         }
-        const uint4 own = owner_desc(S, gi);
+        const uint2 own = owner_delta(S, gi);
         const uint32_t e = expand_rows(S, W, gi, own, 0, 1, lane, acc);
         if (lane == 0 && e) {
             atomicAdd(&S.cand[gi.c], (unsigned long long)e);
@@ -662,7 +565,7 @@ __global__ void __launch_bounds__(256, 3) k_spgemm_cta(SlotTab S, ProdTab P, Wor
         const HashAcc acc{keys, bits, lg};
         if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
-        const uint4 own = owner_desc(S, gi);
+        const uint2 own = owner_delta(S, gi);
         const uint32_t e = expand_rows(S, W, gi, own, wib, blockDim.x >> 5, lane, acc);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
@@ -695,7 +598,7 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
         __syncthreads();
         if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
-        const uint4 own = owner_desc(S, gi);
+        const uint2 own = owner_delta(S, gi);
         const uint32_t e = expand_rows(S, W, gi, own, wib, blockDim.x >> 5, lane, acc);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
@@ -771,7 +674,7 @@ __global__ void k_reset_dnew(SlotTab S, WorkBufs W) {
          e < n_in; e += (unsigned long long)gridDim.x * blockDim.x) {
         const uint2 t = t_in[e];
         const uint32_t slot = t.x >> 1, o = t.x & 1;
-        S.desc[slot][(size_t)o * S.n[slot] + t.y].w = 0;
+        S.dn[slot][(size_t)o * S.n[slot] + t.y].x = 0;
     }
 }
 
@@ -795,10 +698,10 @@ __global__ void __launch_bounds__(256) k_count(SlotTab S, WorkBufs W) {
             slot = W.delta_slot[t];
             i = (uint32_t)(key >> 32);
             j = (uint32_t)key;
-            uint4 *dsc = S.desc[slot];
+            uint2 *dn = S.dn[slot];
             const uint32_t n = S.n[slot];
-            first_r = atomicAdd(&dsc[i].w, 1u) == 0;
-            first_c = atomicAdd(&dsc[(size_t)n + j].w, 1u) == 0;
+            first_r = atomicAdd(&dn[i].x, 1u) == 0;
+            first_c = atomicAdd(&dn[(size_t)n + j].x, 1u) == 0;
         }
 #pragma unroll
         for (int o = 0; o < 2; o++) {
@@ -817,26 +720,59 @@ __global__ void __launch_bounds__(256) k_count(SlotTab S, WorkBufs W) {
     }
 }
 
-constexpr uint32_t TILE_WARP_MAX = 256;   // tiles + entries one warp folds in k_capacity
+constexpr uint32_t TILE_WARP_MAX = 256;   // tiles one warp folds (k_capacity, k_pack)
 
-// Capacity for single entries after a move: room for this merge's entries
-// twice over, and for half the row's size, so a row that keeps growing
-// moves a logarithmic number of times.
-__device__ __forceinline__ uint32_t entry_cap_after_fold(uint32_t incoming, uint32_t units) {
-    const uint32_t c = max(incoming + 4u, units / 8);
-    return (c + 3) & ~3u;
+// Capacities of a moved row: its folded tiles plus room to append as many
+// tiles again (at least twice this merge's entries), and twice this merge's
+// entries; a row that keeps growing moves a logarithmic number of times.
+__device__ __forceinline__ uint32_t tile_cap_after_move(uint32_t tiles, uint32_t incoming) {
+    return tiles + max(max(2u * incoming, tiles), 8u);
 }
-__device__ __forceinline__ unsigned long long entry_cap_plain(uint32_t cap, unsigned long long need) {
-    unsigned long long c = max(2ull * cap, need);
-    return max((c + 3) & ~3ull, 4ull);
+__device__ __forceinline__ uint32_t entry_cap_after_move(uint32_t incoming) {
+    return (max(2u * incoming, 8u) + 3) & ~3u;
 }
 
-// Make room for every listed row.  A row that must grow moves to a new
-// segment: its tiles and single entries are folded into tiles when that
-// takes no more pool words than before (each distinct word once), else
-// copied as they are.  Rows with more than TILE_WARP_MAX tiles and entries
-// are left to k_capacity_big.  Idempotent: after a pool overflow the host
-// grows the pool and runs it again.
+// Deduplicate `cnt` tiles (word, bits), read through get(q), in a warp's
+// shared-memory table of 2^lg >= 2*cnt slots and write one tile per word to
+// out; returns the number written (warp-collective, all lanes).
+template <class Get>
+__device__ __forceinline__ uint32_t warp_fold_tiles(uint32_t *keys, uint32_t *bits, uint32_t cnt,
+                                                    Get get, uint32_t *out, int lane) {
+    uint32_t lg = 5;
+    while ((1u << lg) < 2 * cnt) lg++;
+    for (uint32_t s = lane; s < (1u << lg); s += 32) {
+        keys[s] = EMPTY32;
+        bits[s] = 0;
+    }
+    __syncwarp();
+    const HashAcc acc{keys, bits, (int)lg};
+    for (uint32_t q = lane; q < cnt; q += 32) {
+        const uint2 t = get(q);
+        acc.ins(t.x, t.y);
+    }
+    __syncwarp();
+    uint32_t base = 0;
+    for (uint32_t sb = 0; sb < (1u << lg); sb += 32) {
+        const uint32_t s = sb + lane;
+        const bool has = keys[s] != EMPTY32;
+        const unsigned m = __ballot_sync(FULL_MASK, has);
+        if (has) {
+            const uint32_t pos = base + __popc(m & ((1u << lane) - 1));
+            out[2 * pos] = keys[s];
+            out[2 * pos + 1] = bits[s];
+        }
+        base += __popc(m);
+    }
+    __syncwarp();
+    return base;
+}
+
+// Make room for every listed row: its new entries (dn.x) in the entry area
+// and as many tiles at the end of its tile list.  A row without that room
+// moves to a new segment with its tiles folded to one per word; rows of more
+// than TILE_WARP_MAX tiles are left to k_capacity_big.  Also sets the
+// occupancy bit of a row's first entries and clears the append cursors.
+// Idempotent: after a pool overflow the host grows the pool and runs it again.
 __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs W) {
     __shared__ uint32_t tab[8][4 * TILE_WARP_MAX];   // per warp: words, then bits
     if (W.cnt->overflow & OVF_PRE) return;
@@ -853,42 +789,36 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
         const size_t r = (size_t)o * S.n[slot] + t.y;
         uint4 *dp = &S.desc[slot][r];
         const uint4 dsc = *dp;
-        const uint32_t nt = S.tcnt[slot][r];
-        if (dsc.y == 0 && nt == 0 && lane == 0) {   // the row gets its first entries
-            const uint32_t lx = S.local[slot];
-            atomicOr(&S.occ[slot][r * S.occ_w[slot] + (lx >> 5)], 1u << (lx & 31));
+        const uint32_t w = S.dn[slot][r].x;
+        if (lane == 0) {
+            S.dn[slot][r].y = 0;
+            if (dsc.y == 0) {                 // the row gets its first entries
+                const uint32_t lx = S.local[slot];
+                atomicOr(&S.occ[slot][r * S.occ_w[slot] + (lx >> 5)], 1u << (lx & 31));
+            }
         }
-        const unsigned long long need = (unsigned long long)dsc.y + dsc.w;
-        if (need <= dsc.z) continue;
-        const uint32_t units = nt + dsc.y;
-        if (units > TILE_WARP_MAX) continue;
+        if ((unsigned long long)dsc.y + w <= dsc.z && w <= dsc.w) continue;
+        if (dsc.y > TILE_WARP_MAX) continue;
         uint32_t *pool = S.pool[slot];
-        const uint32_t toff = dsc.x - tile_words(nt);
+        // fold into the table first (the count sizes the new segment) ...
         uint32_t lg = 5;
-        while ((1u << lg) < 2 * units) lg++;
+        while ((1u << lg) < 2 * dsc.y) lg++;
         for (uint32_t s = lane; s < (1u << lg); s += 32) {
             keys[s] = EMPTY32;
             bits[s] = 0;
         }
         __syncwarp();
         const HashAcc acc{keys, bits, (int)lg};
-        for (uint32_t q = lane; q < nt; q += 32) {
-            const uint2 tl = *reinterpret_cast<const uint2 *>(pool + toff + 2 * q);
-            acc.ins(tl.x, tl.y);
-        }
         for (uint32_t q = lane; q < dsc.y; q += 32) {
-            const uint32_t v = pool[dsc.x + q];
-            acc.ins(v >> 5, 1u << (v & 31));
+            const uint2 tl = *reinterpret_cast<const uint2 *>(pool + dsc.x + 2 * q);
+            acc.ins(tl.x, tl.y);
         }
         __syncwarp();
         uint32_t D = 0;
         for (uint32_t s = lane; s < (1u << lg); s += 32) D += keys[s] != EMPTY32;
         for (int dd = 16; dd > 0; dd >>= 1) D += __shfl_xor_sync(FULL_MASK, D, dd);
-        const bool fold = 2 * D <= 2 * nt + dsc.y;
-        const unsigned long long cap = fold ? entry_cap_after_fold(dsc.w, units)
-                                            : entry_cap_plain(dsc.z, need);
-        const uint32_t ntn = fold ? D : nt;
-        const unsigned long long size = tile_words(ntn) + cap;
+        const uint32_t tcap = tile_cap_after_move(D, w), ecap = entry_cap_after_move(w);
+        const unsigned long long size = (unsigned long long)tile_words(tcap) + ecap;
         const uint32_t inst = S.inst[slot];
         unsigned long long off = 0;
         if (lane == 0) {
@@ -903,41 +833,31 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
             __syncwarp();
             continue;
         }
+        // ... then write the table's words as the new tile list
         uint32_t *np = pool + off;
-        if (fold) {
-            uint32_t base = 0;
-            for (uint32_t sb = 0; sb < (1u << lg); sb += 32) {
-                const uint32_t s = sb + lane;
-                const bool has = keys[s] != EMPTY32;
-                const unsigned m = __ballot_sync(FULL_MASK, has);
-                if (has) {
-                    const uint32_t pos = base + __popc(m & ((1u << lane) - 1));
-                    np[2 * pos] = keys[s];
-                    np[2 * pos + 1] = bits[s];
-                }
-                base += __popc(m);
+        uint32_t base = 0;
+        for (uint32_t sb = 0; sb < (1u << lg); sb += 32) {
+            const uint32_t s = sb + lane;
+            const bool has = keys[s] != EMPTY32;
+            const unsigned m = __ballot_sync(FULL_MASK, has);
+            if (has) {
+                const uint32_t pos = base + __popc(m & ((1u << lane) - 1));
+                np[2 * pos] = keys[s];
+                np[2 * pos + 1] = bits[s];
             }
-        } else {
-            for (uint32_t q = lane; q < 2 * nt; q += 32) np[q] = pool[toff + q];
-            const uint32_t tw = tile_words(nt);
-            for (uint32_t q = lane; q < dsc.y; q += 32) np[tw + q] = pool[dsc.x + q];
+            base += __popc(m);
         }
         __syncwarp();
-        if (lane == 0) {
-            dp->x = (uint32_t)off + tile_words(ntn);
-            dp->y = fold ? 0u : dsc.y;
-            dp->z = (uint32_t)cap;
-            S.tcnt[slot][r] = ntn;
-        }
+        if (lane == 0) *dp = make_uint4((uint32_t)off, D, tcap, ecap);
         __syncwarp();
     }
 }
 
-// The rows k_capacity leaves (more than TILE_WARP_MAX tiles and entries):
-// the CTA lists the large rows among 256 touched rows at a time, then folds
-// each through an n-bit bitmap in shared memory, so its tiles come out in
-// word order.  Without room for the bitmap (use_smem 0) the rows are copied
-// as they are.  Idempotent like k_capacity.
+// The rows k_capacity leaves (more than TILE_WARP_MAX tiles): the CTA lists
+// the large rows among 256 touched rows at a time, then folds each through
+// an n-bit bitmap in shared memory (its tiles come out in word order).
+// Without room for the bitmap (use_smem 0) the tiles are copied as they are.
+// Idempotent like k_capacity.
 __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, WorkBufs W,
                                                       int use_smem) {
     extern __shared__ uint32_t bm[];
@@ -959,8 +879,8 @@ __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, Work
             const uint32_t slot = t.x >> 1, o = t.x & 1;
             const size_t r = (size_t)o * S.n[slot] + t.y;
             const uint4 dsc = S.desc[slot][r];
-            const uint32_t nt = S.tcnt[slot][r];
-            if ((unsigned long long)dsc.y + dsc.w > dsc.z && nt + dsc.y > TILE_WARP_MAX)
+            const uint32_t w = S.dn[slot][r].x;
+            if (((unsigned long long)dsc.y + w > dsc.z || w > dsc.w) && dsc.y > TILE_WARP_MAX)
                 list[atomicAdd(&list_n, 1u)] = threadIdx.x;
         }
         __syncthreads();
@@ -972,36 +892,27 @@ __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, Work
             const size_t r = (size_t)o * n + t.y;
             uint4 *dp = &S.desc[slot][r];
             const uint4 dsc = *dp;
-            const uint32_t nt = S.tcnt[slot][r];
+            const uint32_t w = S.dn[slot][r].x;
             uint32_t *pool = S.pool[slot];
-            const uint32_t toff = dsc.x - tile_words(nt);
             const uint32_t words = (n + 31) >> 5;
             const uint32_t per = (words + blockDim.x - 1) / blockDim.x;
             const uint32_t w0 = min(words, threadIdx.x * per), w1 = min(words, w0 + per);
             uint32_t cnt = 0;
-            bool fold = false;
             if (use_smem) {
-                for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+                for (uint32_t q = threadIdx.x; q < words; q += blockDim.x) bm[q] = 0;
                 __syncthreads();
-                for (uint32_t q = threadIdx.x; q < nt; q += blockDim.x) {
-                    const uint2 tl = *reinterpret_cast<const uint2 *>(pool + toff + 2 * q);
+                for (uint32_t q = threadIdx.x; q < dsc.y; q += blockDim.x) {
+                    const uint2 tl = *reinterpret_cast<const uint2 *>(pool + dsc.x + 2 * q);
                     atomicOr(&bm[tl.x], tl.y);
                 }
-                for (uint32_t q = threadIdx.x; q < dsc.y; q += blockDim.x) {
-                    const uint32_t v = pool[dsc.x + q];
-                    atomicOr(&bm[v >> 5], 1u << (v & 31));
-                }
                 __syncthreads();
-                for (uint32_t w = w0; w < w1; w++) cnt += bm[w] != 0;
+                for (uint32_t q = w0; q < w1; q++) cnt += bm[q] != 0;
             }
             unsigned long long D = 0;
             const unsigned long long before = block_excl_scan256(cnt, sh, D);
-            if (use_smem) fold = 2 * D <= 2ull * nt + dsc.y;
-            const unsigned long long need = (unsigned long long)dsc.y + dsc.w;
-            const unsigned long long cap = fold ? entry_cap_after_fold(dsc.w, nt + dsc.y)
-                                                : entry_cap_plain(dsc.z, need);
-            const uint32_t ntn = fold ? (uint32_t)D : nt;
-            const unsigned long long size = tile_words(ntn) + cap;
+            const uint32_t ntn = use_smem ? (uint32_t)D : dsc.y;
+            const uint32_t tcap = tile_cap_after_move(ntn, w), ecap = entry_cap_after_move(w);
+            const unsigned long long size = (unsigned long long)tile_words(tcap) + ecap;
             if (threadIdx.x == 0) {
                 unsigned long long off = atomicAdd(&I.pool_top[S.inst[slot]], size);
                 if (off + size > I.pool_cap[S.inst[slot]]) {
@@ -1014,38 +925,30 @@ __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, Work
             const unsigned long long off = off_sh;
             if (off != ~0ull) {
                 uint32_t *np = pool + off;
-                if (fold) {
+                if (use_smem) {
                     unsigned long long pos = before;
-                    for (uint32_t w = w0; w < w1; w++) {
-                        const uint32_t b = bm[w];
+                    for (uint32_t q = w0; q < w1; q++) {
+                        const uint32_t b = bm[q];
                         if (b) {
-                            np[2 * pos] = w;
+                            np[2 * pos] = q;
                             np[2 * pos + 1] = b;
                             pos++;
                         }
                     }
                 } else {
-                    for (uint32_t q = threadIdx.x; q < 2 * nt; q += blockDim.x)
-                        np[q] = pool[toff + q];
-                    const uint32_t tw = tile_words(nt);
-                    for (uint32_t q = threadIdx.x; q < dsc.y; q += blockDim.x)
-                        np[tw + q] = pool[dsc.x + q];
+                    for (uint32_t q = threadIdx.x; q < 2 * dsc.y; q += blockDim.x)
+                        np[q] = pool[dsc.x + q];
                 }
                 __syncthreads();
-                if (threadIdx.x == 0) {
-                    dp->x = (uint32_t)off + tile_words(ntn);
-                    dp->y = fold ? 0u : dsc.y;
-                    dp->z = (uint32_t)cap;
-                    S.tcnt[slot][r] = ntn;
-                }
+                if (threadIdx.x == 0) *dp = make_uint4((uint32_t)off, ntn, tcap, ecap);
             }
             __syncthreads();
         }
     }
 }
 
-// Append the new pairs: (i, j) goes to row i of the row form and row j of
-// the column form.
+// Append the new pairs as single entries: (i, j) goes to the entry area of
+// row i of the row form and of row j of the column form.
 __global__ void __launch_bounds__(256) k_scatter(SlotTab S, WorkBufs W) {
     if (W.cnt->overflow & (OVF_PRE | OVF_POOL)) return;
     const unsigned long long nd = W.cnt->delta;
@@ -1054,13 +957,54 @@ __global__ void __launch_bounds__(256) k_scatter(SlotTab S, WorkBufs W) {
         const unsigned long long key = W.delta_key[t];
         const uint32_t slot = W.delta_slot[t];
         const uint32_t i = (uint32_t)(key >> 32), j = (uint32_t)key;
-        uint4 *dsc = S.desc[slot];
+        const uint4 *dsc = S.desc[slot];
+        uint2 *dn = S.dn[slot];
         uint32_t *pool = S.pool[slot];
         const uint32_t n = S.n[slot];
-        const uint32_t pr = atomicAdd(&dsc[i].y, 1u);
-        pool[(size_t)dsc[i].x + pr] = j;
-        const uint32_t pc = atomicAdd(&dsc[(size_t)n + j].y, 1u);
-        pool[(size_t)dsc[(size_t)n + j].x + pc] = i;
+        const uint4 dr = dsc[i];
+        const uint32_t pr = atomicAdd(&dn[i].y, 1u);
+        pool[(size_t)dr.x + tile_words(dr.z) + pr] = j;
+        const uint4 dc = dsc[(size_t)n + j];
+        const uint32_t pc = atomicAdd(&dn[(size_t)n + j].y, 1u);
+        pool[(size_t)dc.x + tile_words(dc.z) + pc] = i;
+    }
+}
+
+// Pack every appended row's new entries into tiles (one per word, 256
+// entries at a time) at the end of its tile list.  The new pairs are not in
+// the row yet, so the tiles of a row never share a set bit; a word may get a
+// second tile, until the row's next move folds them.
+__global__ void __launch_bounds__(256) k_pack(SlotTab S, WorkBufs W) {
+    __shared__ uint32_t tab[8][4 * TILE_WARP_MAX];
+    if (W.cnt->overflow & (OVF_PRE | OVF_POOL)) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *keys = tab[wib], *bits = tab[wib] + 2 * TILE_WARP_MAX;
+    const int par = *W.parity;
+    const uint2 *t_out = W.touched[par ^ 1];
+    const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
+    const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + wib;
+         e < n_t; e += nw) {
+        const uint2 t = t_out[e];
+        const uint32_t slot = t.x >> 1, o = t.x & 1;
+        const size_t r = (size_t)o * S.n[slot] + t.y;
+        uint4 *dp = &S.desc[slot][r];
+        const uint4 dsc = *dp;
+        const uint32_t w = S.dn[slot][r].x;
+        const uint32_t *ent = S.pool[slot] + dsc.x + tile_words(dsc.z);
+        uint32_t *tl = S.pool[slot] + dsc.x;
+        uint32_t nt = dsc.y;
+        for (uint32_t c0 = 0; c0 < w; c0 += TILE_WARP_MAX) {
+            const uint32_t cnt = min(TILE_WARP_MAX, w - c0);
+            nt += warp_fold_tiles(keys, bits, cnt,
+                                  [&](uint32_t q) {
+                                      const uint32_t v = ent[c0 + q];
+                                      return make_uint2(v >> 5, 1u << (v & 31));
+                                  },
+                                  tl + 2 * nt, lane);
+        }
+        if (lane == 0) dp->y = nt;
+        __syncwarp();
     }
 }
 
@@ -1254,16 +1198,14 @@ __device__ __forceinline__ uint32_t stored_row(const uint32_t *perm, uint32_t i)
     return perm ? perm[i] : i;
 }
 
-// Pairs in a row: its single entries plus the set bits of its tiles.
-__global__ void k_row_lengths(const uint4 *desc, const uint32_t *tcnt, const uint32_t *pool,
-                              uint32_t n, const uint32_t *perm, uint32_t *len) {
+// Pairs in a row: the set bits of its tiles (no two tiles share a bit).
+__global__ void k_row_lengths(const uint4 *desc, const uint32_t *pool, uint32_t n,
+                              const uint32_t *perm, uint32_t *len) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t r = stored_row(perm, i);
-        const uint4 d = desc[r];
-        const uint32_t nt = tcnt[r];
-        const uint32_t *tl = pool + d.x - tile_words(nt);
-        uint32_t c = d.y;
-        for (uint32_t q = 0; q < nt; q++) c += __popc(tl[2 * q + 1]);
+        const uint4 d = desc[stored_row(perm, i)];
+        const uint32_t *tl = pool + d.x;
+        uint32_t c = 0;
+        for (uint32_t q = 0; q < d.y; q++) c += __popc(tl[2 * q + 1]);
         len[i] = c;
     }
 }
@@ -1279,8 +1221,7 @@ constexpr int EXTRACT_WARP_MAX = 1024;
 
 // One warp per row: bitonic sort in shared memory for rows up to 1024
 // entries; longer rows are listed for k_extract_big.
-__global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const uint32_t *tcnt,
-                                                       const uint32_t *pool,
+__global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const uint32_t *pool,
                                                        uint32_t n, const uint32_t *perm,
                                                        const uint32_t *iperm,
                                                        const unsigned long long *row_out,
@@ -1291,14 +1232,12 @@ __global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *s = sbuf[wib];
     for (uint32_t i = blockIdx.x * 8 + wib; i < n; i += gridDim.x * 8) {
-        const uint32_t r = stored_row(perm, i);
-        const uint4 d = desc[r];
-        const uint32_t nt = tcnt[r];
-        const uint32_t *tl = pool + d.x - tile_words(nt);
-        uint32_t pc = 0;
-        for (uint32_t q = lane; q < nt; q += 32) pc += __popc(tl[2 * q + 1]);
-        for (int dd = 16; dd > 0; dd >>= 1) pc += __shfl_xor_sync(FULL_MASK, pc, dd);
-        const uint32_t len = d.y + pc;
+        const uint4 d = desc[stored_row(perm, i)];
+        const uint32_t nt = d.y;
+        const uint32_t *tl = pool + d.x;
+        uint32_t len = 0;
+        for (uint32_t q = lane; q < nt; q += 32) len += __popc(tl[2 * q + 1]);
+        for (int dd = 16; dd > 0; dd >>= 1) len += __shfl_xor_sync(FULL_MASK, len, dd);
         if (len == 0) continue;
         if (len > EXTRACT_WARP_MAX) {
             if (lane == 0) big_rows[atomicAdd(big_count, 1u)] = i;
@@ -1306,7 +1245,7 @@ __global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const 
         }
         uint32_t P = 32;
         while (P < len) P <<= 1;
-        // tiles first: each lane decodes one tile per round at its scan position
+        // each lane decodes one tile per round at its scan position
         uint32_t base = 0;
         for (uint32_t qb = 0; qb < nt; qb += 32) {
             const uint32_t q = qb + lane;
@@ -1321,14 +1260,7 @@ __global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const 
             }
             base += __shfl_sync(FULL_MASK, incl, 31);
         }
-        for (uint32_t t = pc + lane; t < P; t += 32) {
-            uint32_t v = EMPTY32;
-            if (t < len) {
-                v = pool[d.x + (t - pc)];
-                if (iperm) v = iperm[v];
-            }
-            s[t] = v;
-        }
+        for (uint32_t t = len + lane; t < P; t += 32) s[t] = EMPTY32;
         __syncwarp();
         for (uint32_t k = 2; k <= P; k <<= 1) {
             for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
@@ -1354,8 +1286,7 @@ __global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const 
 
 // One CTA per long row: mark the row's columns in an n-bit bitmap, then
 // write the set bits in increasing order.
-__global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const uint32_t *tcnt,
-                                                     const uint32_t *pool,
+__global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const uint32_t *pool,
                                                      uint32_t n, const uint32_t *perm,
                                                      const uint32_t *iperm,
                                                      const unsigned long long *row_out,
@@ -1371,24 +1302,17 @@ __global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const ui
     const uint32_t nb = *big_count;
     for (uint32_t r = blockIdx.x; r < nb; r += gridDim.x) {
         const uint32_t i = big_rows[r];
-        const uint32_t sr = stored_row(perm, i);
-        const uint4 d = desc[sr];
-        const uint32_t nt = tcnt[sr];
-        const uint32_t *tl = pool + d.x - tile_words(nt);
+        const uint4 d = desc[stored_row(perm, i)];
+        const uint32_t *tl = pool + d.x;
         for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
         __syncthreads();
-        for (uint32_t q = threadIdx.x; q < nt; q += blockDim.x) {
+        for (uint32_t q = threadIdx.x; q < d.y; q += blockDim.x) {
             const uint32_t w = tl[2 * q];
             for (uint32_t rb = tl[2 * q + 1]; rb; rb &= rb - 1) {
                 uint32_t v = w * 32 + (__ffs(rb) - 1);
                 if (iperm) v = iperm[v];
                 atomicOr(&bm[v >> 5], 1u << (v & 31));
             }
-        }
-        for (uint32_t t = threadIdx.x; t < d.y; t += blockDim.x) {
-            uint32_t v = pool[d.x + t];
-            if (iperm) v = iperm[v];
-            atomicOr(&bm[v >> 5], 1u << (v & 31));
         }
         __syncthreads();
         const uint32_t w0 = threadIdx.x * per, w1 = min(words, w0 + per);
@@ -1589,6 +1513,10 @@ void launch_scatter(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t s
     k_scatter<<<sms * 8, 256, 0, st>>>(S, W);
 }
 
+void launch_pack(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {
+    k_pack<<<sms * 8, 256, 0, st>>>(S, W);
+}
+
 void launch_init_edges(const uint32_t *src, const uint32_t *lab, const uint32_t *dst,
                        unsigned long long n_edges, const uint32_t *term_off,
                        const uint32_t *term_slot, uint32_t n_terms, const WorkBufs &W,
@@ -1641,26 +1569,25 @@ void launch_permute_ids(uint32_t *a, unsigned long long m, const uint32_t *perm,
     k_permute_ids<<<grid_for(m, 256, sms, 8), 256, 0, st>>>(a, m, perm);
 }
 
-void launch_row_lengths(const uint4 *desc, const uint32_t *tcnt, const uint32_t *pool,
-                        uint32_t n, const uint32_t *perm, uint32_t *len, cudaStream_t st) {
+void launch_row_lengths(const uint4 *desc, const uint32_t *pool, uint32_t n,
+                        const uint32_t *perm, uint32_t *len, cudaStream_t st) {
     if (!n) return;
-    k_row_lengths<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(desc, tcnt, pool, n, perm, len);
+    k_row_lengths<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(desc, pool, n, perm, len);
 }
 
-void launch_extract(const uint4 *desc, const uint32_t *tcnt, const uint32_t *pool, uint32_t n,
-                    const uint32_t *perm,
+void launch_extract(const uint4 *desc, const uint32_t *pool, uint32_t n, const uint32_t *perm,
                     const uint32_t *iperm, const unsigned long long *row_out, uint32_t *out_src,
                     uint32_t *out_dst, uint32_t *big_rows, uint32_t *big_count,
                     uint32_t *bitmap, int sms, cudaStream_t st) {
     if (!n) return;
     set_smem_attrs();
     cudaMemsetAsync(big_count, 0, sizeof(uint32_t), st);
-    k_extract_small<<<grid_for(n, 8, sms, 8), 256, 0, st>>>(desc, tcnt, pool, n, perm, iperm,
+    k_extract_small<<<grid_for(n, 8, sms, 8), 256, 0, st>>>(desc, pool, n, perm, iperm,
                                                             row_out, out_src, out_dst, big_rows,
                                                             big_count);
     const size_t bm_bytes = (size_t)((n + 31) / 32) * 4;
     const bool sm = bm_bytes <= SMEM_BITMAP_MAX;
-    k_extract_big<<<sms * 4, 256, sm ? bm_bytes : 0, st>>>(desc, tcnt, pool, n, perm, iperm,
+    k_extract_big<<<sms * 4, 256, sm ? bm_bytes : 0, st>>>(desc, pool, n, perm, iperm,
                                                            row_out, out_src, out_dst, big_rows,
                                                            big_count, bitmap, sm ? 1 : 0);
 }

@@ -4,19 +4,21 @@
 //   desc[s]     uint4 per row and orientation, 2*n entries per slot:
 //                 [0, n)  row form    (row i -> the j with M(i, j))
 //                 [n, 2n) column form (column j -> the i with M(i, j))
-//               .x = offset of the row's single entries in the instance pool
-//               .y = their count, .z = their capacity, .w = entries appended
-//               by the last merge ("dnew").  The row's last dnew entries are
-//               the delta of optimisation 1; everything before is M_old.
-//   tcnt[s]     uint32 per row and orientation: the row's tiles, stored just
-//               before its single entries at pool[.x - tile_words(tcnt)]:
-//               pairs (word w, bits b) meaning the columns 32w + i for each
-//               set bit i of b.  Tiles only ever hold M_old: when a row must
-//               grow, the merge folds its tiles and single entries into new
-//               tiles (bit-packed rows; with the breadth-first vertex order a
-//               closure row falls into few words) and the new pairs follow as
-//               single entries.
-//   pool        uint32 arena of row segments; rows grow by relocation.
+//               The row is a list of 32-bit tiles (word w, bits b: the
+//               columns 32w + i for every set bit i of b) at pool[.x ..],
+//               followed by an area of single entries:
+//               .x = offset of the row segment in the instance pool
+//                    (a multiple of 4 words, so loads of 16 bytes align)
+//               .y = tiles in use; they hold every pair of the row, and no
+//                    two tiles share a set bit
+//               .z = tile capacity; the entry area starts at
+//                    .x + tile_words(.z)
+//               .w = entry capacity
+//   dn[s]       uint2 per row and orientation: .x = pairs the last merge
+//               added to the row (its delta for optimisation 1, kept as
+//               single entries in the entry area), .y = append cursor
+//   pool        uint32 arena of row segments; rows grow by relocation,
+//               and a relocation folds the tiles (one tile per word).
 //   htab[s]     open-addressing set of 64-bit keys (i << 32 | j): every pair
 //               of M_s, used for the complement mask and for deduplication.
 // Work items refer to slots, so one launch covers many instances.
@@ -59,7 +61,7 @@ __host__ __device__ __forceinline__ uint32_t tile_words(uint32_t tiles) {
 
 struct SlotTab {              // per slot (device arrays, length n_slots)
     uint4 **desc;             // row descriptors (2*n per slot)
-    uint32_t **tcnt;          // tiles of every row (2*n per slot)
+    uint2 **dn;               // delta counts and append cursors (2*n per slot)
     uint32_t **pool;          // instance pool of the slot
     uint32_t *n;              // vertices of the slot's instance
     uint32_t *inst;           // instance index of the slot
@@ -160,13 +162,16 @@ void launch_iter_end(const SlotTab &S, const InstTab &I, const WorkBufs &W, Loop
                      cudaGraphConditionalHandle handle, bool in_graph, cudaStream_t st);
 void launch_reset_dnew(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
 void launch_count(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
-// Room for every row the merge appends to: rows that must grow move to a
-// new segment, their tiles and single entries folded into new tiles (one warp
-// per row up to TILE_WARP_MAX entries, then one CTA per row with an n-bit
-// shared-memory bitmap for max_n up to the shared-memory limit).
+// Room for every row the merge appends to (its new entries, and as many
+// tiles again): rows that must grow move to a new segment with their tiles
+// folded to one per word (one warp per row up to TILE_WARP_MAX tiles, then
+// one CTA per row with an n-bit shared-memory bitmap for max_n up to the
+// shared-memory limit, else copied as they are).
 void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t max_n,
                      int sms, cudaStream_t st);
 void launch_scatter(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
+// Pack every appended row's new entries into tiles at the end of its tile list.
+void launch_pack(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
 
 void launch_init_edges(const uint32_t *src, const uint32_t *lab, const uint32_t *dst,
                        unsigned long long n_edges, const uint32_t *term_off,
@@ -196,12 +201,11 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t n, unsigned long long *o
 // Extraction of one non-terminal's pairs, sorted by (src, dst), in the
 // caller's vertex ids: perm maps a caller id to its stored row, iperm a
 // stored id back (both null when the vertices kept their input order).
-void launch_row_lengths(const uint4 *desc, const uint32_t *tcnt, const uint32_t *pool,
-                        uint32_t n, const uint32_t *perm, uint32_t *len, cudaStream_t st);
+void launch_row_lengths(const uint4 *desc, const uint32_t *pool, uint32_t n,
+                        const uint32_t *perm, uint32_t *len, cudaStream_t st);
 // big_rows: scratch of n uint32 plus one counter; bitmap: scratch of
 // sms*4*ceil(n/32) words used when a row bitmap does not fit shared memory.
-void launch_extract(const uint4 *desc, const uint32_t *tcnt, const uint32_t *pool, uint32_t n,
-                    const uint32_t *perm,
+void launch_extract(const uint4 *desc, const uint32_t *pool, uint32_t n, const uint32_t *perm,
                     const uint32_t *iperm, const unsigned long long *row_out, uint32_t *out_src,
                     uint32_t *out_dst, uint32_t *big_rows, uint32_t *big_count,
                     uint32_t *bitmap, int sms, cudaStream_t st);

@@ -28,11 +28,12 @@ enum { ST_CREATED = 0, ST_GRAMMAR = 1, ST_GRAPH = 2, ST_SOLVED = 3 };
 
 enum KernelId {
     KID_SYMBOLIC = 0, KID_BIN0, KID_BIN1, KID_BIN2, KID_BIN3, KID_COMMIT, KID_RESET,
-    KID_COUNT, KID_CAPACITY, KID_SCATTER, KID_INIT, KID_REHASH, N_KID
+    KID_COUNT, KID_CAPACITY, KID_SCATTER, KID_PACK, KID_INIT, KID_REHASH, N_KID
 };
 const char *kKernelNames[N_KID] = {
     "k_symbolic", "k_spgemm_bin0", "k_spgemm_bin1", "k_spgemm_bin2", "k_spgemm_bin3",
-    "k_commit", "k_reset_dnew", "k_count", "k_capacity", "k_scatter", "k_init", "k_rehash"};
+    "k_commit", "k_reset_dnew", "k_count", "k_capacity", "k_scatter", "k_pack", "k_init",
+    "k_rehash"};
 
 struct CudaError {
     cudaError_t e;
@@ -100,7 +101,7 @@ struct cflr_ctx {
     uint32_t n = 0;
     uint64_t ignored = 0;
     uint4 *desc = nullptr;              // n_nt * 2 * n descriptors
-    uint32_t *tcnt = nullptr;           // n_nt * 2 * n tile counts
+    uint2 *dn = nullptr;                // n_nt * 2 * n delta counts / append cursors
     uint32_t *occ = nullptr;            // occupancy bits: 2 * n * occ_w words
     uint32_t occ_w = 0;
     uint32_t *pool = nullptr;
@@ -206,8 +207,8 @@ struct cflr_ctx {
         uint32_t nt = (uint32_t)g.nts.size();
         if (desc) dfree(desc, (size_t)nt * 2 * n * sizeof(uint4));
         desc = nullptr;
-        if (tcnt) dfree(tcnt, (size_t)nt * 2 * n * 4);
-        tcnt = nullptr;
+        if (dn) dfree(dn, (size_t)nt * 2 * n * sizeof(uint2));
+        dn = nullptr;
         if (occ) dfree(occ, (size_t)2 * n * occ_w * 4);
         occ = nullptr;
         occ_w = 0;
@@ -318,7 +319,7 @@ struct Runner {
     std::vector<uint32_t> slot_ctx;    // slot -> context index
     // device tables
     DevArr<uint4 *> d_desc;
-    DevArr<uint32_t *> d_tcnt;
+    DevArr<uint2 *> d_dn;
     DevArr<uint32_t *> d_pool;
     DevArr<uint32_t> d_n, d_inst, d_occw, d_local;
     DevArr<uint32_t *> d_occ;
@@ -415,7 +416,7 @@ struct Runner {
             max_n = std::max(max_n, cx[k]->n);
         }
         std::vector<uint4 *> hd(n_slots);
-        std::vector<uint32_t *> htc(n_slots);
+        std::vector<uint2 *> hdn(n_slots);
         std::vector<uint32_t *> hoc(n_slots);
         std::vector<uint32_t> hn(n_slots), hi(n_slots), how(n_slots), hl(n_slots);
         std::vector<unsigned long long> hz(n_slots);
@@ -426,7 +427,7 @@ struct Runner {
             uint32_t nt = (uint32_t)c->g.nts.size(), b0 = base[k];
             for (uint32_t x = 0; x < nt; x++) {
                 hd[b0 + x] = c->desc + (size_t)x * 2 * c->n;
-                htc[b0 + x] = c->tcnt + (size_t)x * 2 * c->n;
+                hdn[b0 + x] = c->dn + (size_t)x * 2 * c->n;
                 hoc[b0 + x] = c->occ;
                 how[b0 + x] = c->occ_w;
                 hl[b0 + x] = x;
@@ -455,7 +456,7 @@ struct Runner {
         }
         const size_t ni = cx.size();
         d_desc.ensure(own, n_slots);
-        d_tcnt.ensure(own, n_slots);
+        d_dn.ensure(own, n_slots);
         d_occ.ensure(own, n_slots);
         d_occw.ensure(own, n_slots);
         d_local.ensure(own, n_slots);
@@ -480,7 +481,7 @@ struct Runner {
         d_ctl.ensure(own, 1);
         d_parity.ensure(own, 1);
         ck(cudaMemcpyAsync(d_desc.p, hd.data(), n_slots * sizeof(uint4 *), cudaMemcpyHostToDevice, st), "H2D");
-        ck(cudaMemcpyAsync(d_tcnt.p, htc.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_dn.p, hdn.data(), n_slots * sizeof(uint2 *), cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_occ.p, hoc.data(), n_slots * sizeof(uint32_t *), cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_occw.p, how.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_local.p, hl.data(), n_slots * 4, cudaMemcpyHostToDevice, st), "H2D");
@@ -558,7 +559,7 @@ struct Runner {
 
     SlotTab slots() {
         SlotTab S;
-        S.desc = d_desc.p; S.tcnt = d_tcnt.p; S.pool = d_pool.p; S.n = d_n.p; S.inst = d_inst.p;
+        S.desc = d_desc.p; S.dn = d_dn.p; S.pool = d_pool.p; S.n = d_n.p; S.inst = d_inst.p;
         S.htab = d_htab.p; S.hmask = d_hmask.p; S.cand = d_cand.p; S.delta = d_delta.p;
         S.nnz = d_nnz.p;
         S.occ = d_occ.p; S.occ_w = d_occw.p; S.local = d_local.p;
@@ -712,6 +713,7 @@ struct Runner {
         }
         if (stage <= 1) run(KID_CAPACITY, [&] { launch_capacity(S, I, W, max_n, sms, st); });
         run(KID_SCATTER, [&] { launch_scatter(S, W, sms, st); });
+        run(KID_PACK, [&] { launch_pack(S, W, sms, st); });
         launch_iter_end(S, I, W, d_ctl.p, n_slots, (uint32_t)cx.size(), count_iteration,
                         handle, in_graph, st);
         ck(cudaGetLastError(), "k_iter_end");
@@ -921,7 +923,8 @@ struct Runner {
         own->k_bytes[KID_RESET] += 12 * h_ctl->total_touched_in;
         own->k_bytes[KID_COUNT] += 20 * h_ctl->total_delta + 8 * h_ctl->total_touched_out;
         own->k_bytes[KID_CAPACITY] += 24 * h_ctl->total_touched_out;
-        own->k_bytes[KID_SCATTER] += 52 * h_ctl->total_delta;
+        own->k_bytes[KID_SCATTER] += 60 * h_ctl->total_delta;
+        own->k_bytes[KID_PACK] += 24 * h_ctl->total_delta + 24 * h_ctl->total_touched_out;
     }
 };
 
@@ -1033,7 +1036,7 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
         ck(cudaMemcpyAsync(c->t_slot, tslot.data(), tslot.size() * 4, cudaMemcpyHostToDevice, st),
            "H2D");
     c->desc = (uint4 *)c->dalloc((size_t)nt * 2 * n * sizeof(uint4));
-    c->tcnt = (uint32_t *)c->dalloc((size_t)nt * 2 * n * 4);
+    c->dn = (uint2 *)c->dalloc((size_t)nt * 2 * n * sizeof(uint2));
     c->occ_w = (nt + 31) / 32;
     c->occ = (uint32_t *)c->dalloc((size_t)2 * n * c->occ_w * 4);
     c->pool_cap = std::min<uint64_t>(std::max<uint64_t>(16 * c->n_init, 1 << 16), 0xFFFFFFF0ull);
@@ -1068,7 +1071,7 @@ void reset_matrices(cflr_ctx *c) {
     const uint32_t n = c->n;
     cudaStream_t st = c->stream;
     ck(cudaMemsetAsync(c->desc, 0, (size_t)nt * 2 * n * sizeof(uint4), st), "memset");
-    ck(cudaMemsetAsync(c->tcnt, 0, (size_t)nt * 2 * n * 4, st), "memset");
+    ck(cudaMemsetAsync(c->dn, 0, (size_t)nt * 2 * n * sizeof(uint2), st), "memset");
     ck(cudaMemsetAsync(c->occ, 0, (size_t)2 * n * c->occ_w * 4, st), "memset");
     for (uint32_t A = 0; A < nt; A++)
         ck(cudaMemsetAsync(c->htab[A], 0xFF, c->hcap[A] * 8, st), "memset");
@@ -1367,11 +1370,10 @@ void extract_device(cflr_ctx *c, uint32_t nt, uint32_t *out_src, uint32_t *out_d
         }
     }
     const uint4 *desc = c->desc + (size_t)nt * 2 * n;
-    const uint32_t *tcnt = c->tcnt + (size_t)nt * 2 * n;
-    launch_row_lengths(desc, tcnt, c->pool, n, c->perm, c->x_len, st);
+    launch_row_lengths(desc, c->pool, n, c->perm, c->x_len, st);
     launch_exclusive_scan(c->x_len, n, c->x_off, c->x_bsum, nullptr, st);
-    launch_extract(desc, tcnt, c->pool, n, c->perm, c->iperm, c->x_off, out_src, out_dst,
-                   c->x_big, c->x_big + n, c->x_bm, c->sms, st);
+    launch_extract(desc, c->pool, n, c->perm, c->iperm, c->x_off, out_src, out_dst, c->x_big,
+                   c->x_big + n, c->x_bm, c->sms, st);
     ck(cudaGetLastError(), "extract");
 }
 
@@ -1690,14 +1692,13 @@ extern "C" int cflr_get_pairs_device_noalloc(const cflr_ctx *cc, uint32_t nonter
     uint32_t *big = (uint32_t *)(w + NA_OFF_WORDS + NA_BSUM_WORDS + NA_LEN_WORDS);
     const uint32_t n = c->n;
     const uint4 *desc = c->desc + (size_t)nonterminal * 2 * n;
-    const uint32_t *tcnt = c->tcnt + (size_t)nonterminal * 2 * n;
     cudaStream_t st = c->stream;
     // Every scratch word used below is written before it is read (lengths,
     // offsets, block sums) or cleared first (the long-row counter).
-    launch_row_lengths(desc, tcnt, c->pool, n, c->perm, len, st);
+    launch_row_lengths(desc, c->pool, n, c->perm, len, st);
     launch_exclusive_scan(len, n, off, bsum, nullptr, st);
-    launch_extract(desc, tcnt, c->pool, n, c->perm, c->iperm, off, d_src, d_dst, big, big + n,
-                   nullptr, c->sms, st);
+    launch_extract(desc, c->pool, n, c->perm, c->iperm, off, d_src, d_dst, big, big + n, nullptr,
+                   c->sms, st);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(c, CudaError{e, "extract (no-alloc)"});
