@@ -29,6 +29,8 @@ namespace {
 struct RawProd {
     int line;
     std::vector<std::string> toks;   // toks[0] = lhs
+    int32_t fam = -1;                // family of an expanded copy (see Grammar)
+    uint32_t member = 0;
 };
 
 std::vector<std::string> split_ws(const std::string &s) {
@@ -128,7 +130,9 @@ int parse_grammar(const char *text, size_t len, Grammar &g, std::string &err) {
     }
 
     // Expand indexed productions: one copy per assignment of their variables.
+    // The copies of a line with one variable form a family.
     std::vector<RawProd> prods;
+    std::vector<uint32_t> fam_size;
     for (const RawProd &rp : raw) {
         std::set<std::string> vars;
         for (const auto &t : rp.toks) index_vars(t, vars);
@@ -141,10 +145,19 @@ int parse_grammar(const char *text, size_t len, Grammar &g, std::string &err) {
             }
         std::map<std::string, long> cur;
         for (const auto &v : vs) cur[v] = ranges[v].first;
+        int32_t fam = -1;
+        if (vs.size() == 1 && ranges[vs[0]].second > ranges[vs[0]].first) {
+            fam = (int32_t)fam_size.size();
+            fam_size.push_back((uint32_t)(ranges[vs[0]].second - ranges[vs[0]].first + 1));
+        }
         for (;;) {
             RawProd e;
             e.line = rp.line;
             for (const auto &t : rp.toks) e.toks.push_back(substitute(t, cur));
+            if (fam >= 0) {
+                e.fam = fam;
+                e.member = (uint32_t)(cur[vs[0]] - ranges[vs[0]].first);
+            }
             prods.push_back(e);
             // odometer increment over the variables
             size_t k = 0;
@@ -193,6 +206,9 @@ int parse_grammar(const char *text, size_t len, Grammar &g, std::string &err) {
     };
 
     std::set<std::tuple<uint32_t, uint32_t, uint32_t>> bin;
+    // (c, a, b) -> (family, member); a production that two lines yield keeps
+    // no family (-2 marks the clash)
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t>, std::pair<int32_t, uint32_t>> famof;
     std::set<std::pair<uint32_t, uint32_t>> unit;
     std::set<uint32_t> eps;
     for (const RawProd &p : prods) {
@@ -211,7 +227,9 @@ int parse_grammar(const char *text, size_t len, Grammar &g, std::string &err) {
             }
             uint32_t a = operand(p.toks[1]);
             uint32_t b = operand(p.toks[2]);
-            bin.insert({c, a, b});
+            const auto key = std::make_tuple(c, a, b);
+            if (bin.insert(key).second) famof[key] = {p.fam, p.member};
+            else famof[key] = {-2, 0};
         } else {
             err = "line " + std::to_string(p.line) +
                   ": more than two right-hand symbols (not in WCNF)";
@@ -222,7 +240,11 @@ int parse_grammar(const char *text, size_t len, Grammar &g, std::string &err) {
         g.bin_c.push_back(std::get<0>(t));
         g.bin_a.push_back(std::get<1>(t));
         g.bin_b.push_back(std::get<2>(t));
+        const auto &fm = famof[t];
+        g.bin_fam.push_back(fm.first >= 0 ? fm.first : -1);
+        g.bin_member.push_back(fm.second);
     }
+    g.fam_size = fam_size;
     for (const auto &u : unit) {
         g.unit_c.push_back(u.first);
         g.unit_a.push_back(u.second);

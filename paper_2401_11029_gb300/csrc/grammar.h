@@ -19,6 +19,12 @@ struct Grammar {
     uint32_t n_named = 0;                // non-terminals named in the text
     std::vector<std::string> terms;      // terminal names (edge labels)
     std::vector<uint32_t> bin_c, bin_a, bin_b;   // c -> a b
+    // Indexed families (appendix B; optimisation 4): a production line with
+    // one index variable of range size F >= 2 expands to F members.  For each
+    // binary production: its family (-1: none) and member index 0..F-1.
+    std::vector<int32_t> bin_fam;
+    std::vector<uint32_t> bin_member;
+    std::vector<uint32_t> fam_size;              // family id -> F
     std::vector<uint32_t> unit_c, unit_a;        // c -> a
     std::vector<uint32_t> eps;                   // A -> eps
     std::vector<std::vector<uint32_t>> term_nts; // terminal id -> {A | A -> x}

@@ -29,6 +29,14 @@ namespace cflr {
 // ---------------------------------------------------------------------------
 
 // 64-bit mixer (the MurmurHash3 64-bit finaliser).
+__device__ __forceinline__ unsigned long long hmix(unsigned long long k);
+// Home slot of a pair key (i << 32 | j) in a pair set: the 32 columns of one
+// 32-bit word of a row share an aligned block of 32 slots, so the pairs one
+// tile emits land in one or two cache lines.
+__device__ __forceinline__ unsigned long long pair_home(unsigned long long key,
+                                                        unsigned long long m) {
+    return ((hmix(key >> 5) << 5) | (key & 31)) & m;
+}
 __device__ __forceinline__ unsigned long long hmix(unsigned long long k) {
     k ^= k >> 33;
     k *= 0xff51afd7ed558ccdull;
@@ -36,6 +44,21 @@ __device__ __forceinline__ unsigned long long hmix(unsigned long long k) {
     k *= 0xc4ceb9fe1a85ec53ull;
     k ^= k >> 33;
     return k;
+}
+
+// Position of the n-th (from 0) set bit of m; m has more than n set bits.
+__device__ __forceinline__ uint32_t select_bit(uint32_t m, uint32_t n) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const uint32_t c = __popc(m & ((1u << w) - 1));
+        if (n >= c) {
+            n -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
@@ -60,28 +83,37 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
 // present (masked or repeated), so a tile is tested with a plain
 // shared-memory read first and the atomic runs only when a bit is missing.
 
-// Open-addressing table of 2^lg words with their bits; the caller clears
-// keys to EMPTY32 and bits to 0 and keeps the load <= 1/2.
+// Open-addressing table of 2^lg slots (word, bits), interleaved so that
+// one 16-byte store clears two slots (clear_table); the caller keeps the
+// load <= 1/2.
 struct HashAcc {
-    uint32_t *keys, *bits;
+    uint32_t *tab;
     int lg;
     __device__ __forceinline__ uint32_t ins(uint32_t w, uint32_t b) const {
         const uint32_t m = (1u << lg) - 1;
         uint32_t s = (w * 2654435761u) >> (32 - lg);
         for (;;) {
-            const uint32_t cur = ((volatile uint32_t *)keys)[s];
+            const uint32_t cur = ((volatile uint32_t *)tab)[2 * s];
             if (cur == w) break;
             if (cur == EMPTY32) {
-                const uint32_t old = atomicCAS(&keys[s], EMPTY32, w);
+                const uint32_t old = atomicCAS(&tab[2 * s], EMPTY32, w);
                 if (old == EMPTY32 || old == w) break;
             }
             s = (s + 1) & m;
         }
-        const uint32_t ob = ((volatile uint32_t *)bits)[s];
+        const uint32_t ob = ((volatile uint32_t *)tab)[2 * s + 1];
         if ((ob & b) == b) return 0;
-        return b & ~atomicOr(&bits[s], b);
+        return b & ~atomicOr(&tab[2 * s + 1], b);
     }
 };
+
+// Empty all 2^lg slots of a table (16-byte aligned, lg >= 1); thread tid of nth.
+__device__ __forceinline__ void clear_table(uint32_t *tab, uint32_t lg, uint32_t tid,
+                                            uint32_t nth) {
+    uint4 *t4 = reinterpret_cast<uint4 *>(tab);
+    for (uint32_t s = tid; s < (1u << lg) / 2; s += nth)
+        t4[s] = make_uint4(EMPTY32, 0u, EMPTY32, 0u);
+}
 
 // n-bit bitmap of the row (bin 3).
 struct BitmapAcc {
@@ -95,7 +127,7 @@ struct BitmapAcc {
 
 __device__ __forceinline__ bool htab_contains(const unsigned long long *tab,
                                               unsigned long long m, unsigned long long key) {
-    unsigned long long h = hmix(key) & m;
+    unsigned long long h = pair_home(key, m);
     for (;;) {
         unsigned long long v = tab[h];
         if (v == key) return true;
@@ -161,6 +193,67 @@ __device__ __forceinline__ unsigned long long block_excl_scan256(unsigned long l
 
 constexpr int SYM_BUF = 16;   // per-warp staging of groups before one atomic
 
+// Product steps (referenced tiles) of one use and their bytes, over the
+// delta entries q0, q0 + qstep, ... (pool[dstart + q], q < d): each entry k
+// references row k of slot g in orientation o, counted only when the row's
+// occupancy bit says it is non-empty.
+struct Work {
+    unsigned long long f, fb;
+};
+
+__device__ __forceinline__ Work gathered_work(const SlotTab &S, uint32_t g, uint32_t o, uint32_t n,
+                                              const uint32_t *pool, uint32_t dstart, uint32_t d,
+                                              uint32_t q0, uint32_t qstep) {
+    const uint4 *dg = S.desc[g] + (size_t)o * n;
+    const uint32_t *oc = S.occ[g];
+    const uint32_t ow = S.occ_w[g], lx = S.local[g];
+    const uint32_t bit = 1u << (lx & 31);
+    Work w{0, 0};
+    for (uint32_t q = q0; q < d; q += qstep) {
+        const uint32_t k = pool[dstart + q];
+        if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
+            const uint32_t nt = dg[k].y;
+            w.f += nt;
+            w.fb += 16ull + 8ull * nt;
+        }
+    }
+    return w;
+}
+
+// The same for a family on its shared operand's delta (optimisation 4): the
+// members reference the consecutive slots g0 .. g0+F-1, whose occupancy bits
+// are consecutive, so a few words per entry say which members have a row.
+__device__ __forceinline__ Work family_work(const SlotTab &S, uint32_t g0, uint32_t F, uint32_t o,
+                                            uint32_t n, const uint32_t *pool, uint32_t dstart,
+                                            uint32_t d, uint32_t q0, uint32_t qstep) {
+    const uint32_t *oc = S.occ[g0];
+    const uint32_t ow = S.occ_w[g0], lx0 = S.local[g0];
+    Work w{0, 0};
+    for (uint32_t q = q0; q < d; q += qstep) {
+        const uint32_t k = pool[dstart + q];
+        const uint32_t *ok = oc + ((size_t)o * n + k) * ow;
+        for (uint32_t wi = lx0 >> 5; wi <= (lx0 + F - 1) >> 5; wi++) {
+            const uint32_t lo = wi * 32;
+            uint32_t m = ok[wi];
+            if (lx0 > lo) m &= ~0u << (lx0 - lo);
+            if (lx0 + F < lo + 32) m &= (1u << (lx0 + F - lo)) - 1;
+            for (; m; m &= m - 1) {
+                const uint32_t i = lo + (__ffs(m) - 1) - lx0;
+                const uint32_t nt = S.desc[g0 + i][(size_t)o * n + k].y;
+                w.f += nt;
+                w.fb += 16ull + 8ull * nt;
+            }
+        }
+    }
+    return w;
+}
+
+__device__ __forceinline__ Work warp_sum(Work w) {
+    w.f = warp_sum64(w.f);
+    w.fb = warp_sum64(w.fb);
+    return w;
+}
+
 // prod_only >= 0 restricts the work list to one production (the plain form).
 __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs W,
                                                   int prod_only, Tuning T) {
@@ -182,13 +275,22 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         if (pos + fill[b] > W.group_cap[b]) atomicOr(&W.cnt->overflow, OVF_GROUPS);
         fill[b] = 0;
     };
+    auto append = [&](int b, uint2 grp) {   // one group, any lane
+        const unsigned long long pos = atomicAdd(&W.cnt->groups[b], 1ull);
+        if (pos < W.group_cap[b]) W.groups[b][pos] = grp;
+        else atomicOr(&W.cnt->overflow, OVF_GROUPS);
+    };
 
-    // classify one (production, delta row) group of product count f: mode,
-    // bin and table size; returns the bin and fills the group record
+    // classify one group of f product steps: mode, bin and table size;
+    // returns the bin and fills the group record.  Groups of a family whose
+    // members write different non-terminals probe their pair sets (there is
+    // no single mask row) and stay in the hash bins (force_probe).
+    bool acct = true;   // whether this lane adds the group's work and bytes
     auto classify = [&](uint32_t code, uint32_t part, uint32_t idx, uint32_t d, uint32_t mlen,
                         unsigned long long mbytes, unsigned long long f,
-                        unsigned long long fbytes, uint2 &grp) -> int {
-        const bool probe = (unsigned long long)mlen > (unsigned long long)T.probe_ratio * f;
+                        unsigned long long fbytes, bool force_probe, uint2 &grp) -> int {
+        const bool probe =
+            force_probe || (unsigned long long)mlen > (unsigned long long)T.probe_ratio * f;
         const unsigned long long need = probe ? f : f + mlen;
         const int b = need <= T.limit[0] ? 0 : need <= T.limit[1] ? 1 : need <= T.limit[2] ? 2 : 3;
         // table of the smallest power of two >= 2*need slots (>= 32)
@@ -198,11 +300,62 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         // algorithmic bytes: the delta entries (4 B each), the descriptor
         // (16 B) and tiles (8 B each) of every referenced row, and the mask
         // row's descriptor and tiles when it is loaded
-        bytes[b] += 20ull * d + fbytes + (probe ? 0ull : mbytes + 16ull);
-        sym_bytes += 20ull * d + 40ull;
-        flops += f;
+        if (acct) {
+            bytes[b] += 4ull * d + fbytes + (probe ? 0ull : mbytes + 16ull);
+            sym_bytes += 20ull * d + 40ull;
+            flops += f;
+        }
         return b;
     };
+
+    // the groups of one use on delta row (o, idx); lanes q0 (step qstep)
+    // share the delta entries, `sum` reduces over them, and `emit` takes
+    // each group (called on every lane that shares the use)
+    auto use_groups = [&](uint32_t code, uint32_t o, uint32_t n, uint32_t idx,
+                          const uint32_t *pool, uint32_t dstart, uint32_t d, uint32_t q0,
+                          uint32_t qstep, auto sum, auto emit) {
+        const uint32_t part = code & 3;
+        const size_t r = (size_t)o * n + idx;
+        if (part == PART_F) {
+            const uint4 fm = P.fam[code >> 2];
+            const uint4 pr0 = P.prod[fm.x];
+            const uint32_t g0 = (fm.w == PART_A) ? pr0.z : pr0.y;
+            const Work wk = sum(family_work(S, g0, fm.y, o, n, pool, dstart, d, q0, qstep));
+            if (wk.f == 0) return;
+            uint2 grp;
+            if (fm.z) {            // every member writes c: one mask row
+                const uint32_t mt = S.desc[pr0.x][r].y;
+                emit(classify(code, PART_F, idx, d, mt, 8ull * mt, wk.f, wk.fb, false, grp), grp);
+            } else if (wk.f <= T.limit[2]) {
+                emit(classify(code, PART_F, idx, d, 0, 0, wk.f, wk.fb, true, grp), grp);
+            } else {               // too large for a hash bin: one group per member
+                for (uint32_t i = 0; i < fm.y; i++) {
+                    const Work wi = sum(gathered_work(S, g0 + i, o, n, pool, dstart, d, q0, qstep));
+                    if (wi.f == 0) continue;
+                    const uint32_t mt = S.desc[P.prod[fm.x + i].x][r].y;
+                    emit(classify(((fm.x + i) << 2) | fm.w, fm.w, idx, d, mt, 8ull * mt, wi.f,
+                                  wi.fb, false, grp),
+                         grp);
+                }
+            }
+            return;
+        }
+        const uint4 pr = P.prod[code >> 2];
+        const uint32_t mt = S.desc[pr.x][r].y;
+        Work wk{0, 0};
+        if (part == PART_U) {
+            wk.f = d;
+            wk.fb = 4ull * d;
+        } else {
+            // gathered rows: b's row form (PART_A) or a's column form (PART_B)
+            wk = sum(gathered_work(S, (part == PART_A) ? pr.z : pr.y, o, n, pool, dstart, d, q0,
+                                   qstep));
+        }
+        if (wk.f == 0) return;
+        uint2 grp;
+        emit(classify(code, part, idx, d, mt, 8ull * mt, wk.f, wk.fb, false, grp), grp);
+    };
+
     for (unsigned long long e = (unsigned long long)blockIdx.x * 8 + wib; e < n_in; e += nw) {
         const uint2 t = t_in[e];
         const uint32_t xo = t.x, idx = t.y, slot = xo >> 1, o = xo & 1;
@@ -214,7 +367,7 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         const uint32_t u0 = P.use_off[xo], u1 = P.use_off[xo + 1];
         if (u1 - u0 >= 32 && d <= 16) {
             // many productions read this row, each with few products: one
-            // lane per production, groups appended with one atomic per bin
+            // lane per use, groups appended with one atomic per bin
             for (uint32_t ub = u0; ub < u1; ub += 32) {
                 const uint32_t u = ub + lane;
                 int b = -1;
@@ -222,29 +375,21 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                 if (u < u1) {
                     const uint32_t code = P.use_code[u];
                     if (prod_only < 0 || (code >> 2) == (uint32_t)prod_only) {
-                        const uint32_t part = code & 3;
-                        const uint4 pr = P.prod[code >> 2];
-                        const uint32_t mt = S.desc[pr.x][(size_t)o * n + idx].y;
-                        unsigned long long f = 0, fb = 0;
-                        if (part == PART_U) {
-                            f = d;
-                            fb = 4ull * d;
-                        } else {
-                            const uint32_t xg = (part == PART_A) ? pr.z : pr.y;
-                            const uint4 *dg = (part == PART_A) ? S.desc[xg] : S.desc[xg] + n;
-                            const uint32_t *oc = S.occ[xg];
-                            const uint32_t ow = S.occ_w[xg], lx = S.local[xg];
-                            const uint32_t bit = 1u << (lx & 31);
-                            for (uint32_t q = 0; q < d; q++) {
-                                const uint32_t k = pool[dstart + q];
-                                if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
-                                    const uint32_t nt = dg[k].y;
-                                    f += nt;
-                                    fb += 16ull + 8ull * nt;
-                                }
-                            }
-                        }
-                        if (f > 0) b = classify(code, part, idx, d, mt, 8ull * mt, f, fb, grp);
+                        acct = true;
+                        // a use yields at most one group, except a split
+                        // family, whose member groups are appended at once
+                        bool one = true;
+                        use_groups(code, o, n, idx, pool, dstart, d, 0, 1,
+                                   [](Work w) { return w; },
+                                   [&](int bb, uint2 g) {
+                                       if (one && b < 0) {
+                                           b = bb;
+                                           grp = g;
+                                       } else {
+                                           append(bb, g);
+                                       }
+                                       one = false;
+                                   });
                     }
                 }
 #pragma unroll
@@ -267,42 +412,20 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         for (uint32_t u = u0; u < u1; u++) {
             const uint32_t code = P.use_code[u];
             if (prod_only >= 0 && (code >> 2) != (uint32_t)prod_only) continue;
-            const uint32_t part = code & 3;
-            const uint4 pr = P.prod[code >> 2];
-            const uint32_t mt = S.desc[pr.x][(size_t)o * n + idx].y;
-            unsigned long long f = 0, fb = 0;
-            if (part == PART_U) {
-                f = d;
-                fb = 4ull * d;
-            } else {
-                // gathered rows: b's row form (PART_A) or a's column form
-                // (PART_B), both in orientation o; a row's descriptor is read
-                // only when its occupancy bit says it is non-empty
-                const uint32_t xg = (part == PART_A) ? pr.z : pr.y;
-                const uint4 *dg = (part == PART_A) ? S.desc[xg] : S.desc[xg] + n;
-                const uint32_t *oc = S.occ[xg];
-                const uint32_t ow = S.occ_w[xg], lx = S.local[xg];
-                const uint32_t bit = 1u << (lx & 31);
-                for (uint32_t q = lane; q < d; q += 32) {
-                    const uint32_t k = pool[dstart + q];
-                    if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
-                        const uint32_t nt = dg[k].y;
-                        f += nt;
-                        fb += 16ull + 8ull * nt;
-                    }
-                }
-                f = warp_sum64(f);
-                fb = warp_sum64(fb);
-            }
-            if (lane == 0 && f > 0) {
-                uint2 grp;
-                const int b = classify(code, part, idx, d, mt, 8ull * mt, f, fb, grp);
-                stage[wib][b][fill[b]++] = grp;
-                if (fill[b] == SYM_BUF) flush(b);
-            }
+            // the warp shares the delta entries; lane 0 stages and counts
+            // the groups
+            acct = lane == 0;
+            use_groups(code, o, n, idx, pool, dstart, d, lane, 32,
+                       [](Work w) { return warp_sum(w); },
+                       [&](int bb, uint2 g) {
+                           if (lane == 0) {
+                               stage[wib][bb][fill[bb]++] = g;
+                               if (fill[bb] == SYM_BUF) flush(bb);
+                           }
+                       });
         }
     }
-    // every lane may hold byte and work counts (lane-per-production mode)
+    // every lane may hold byte and work counts (lane-per-use mode)
     for (int b = 0; b < N_BINS; b++) bytes[b] = warp_sum64(bytes[b]);
     flops = warp_sum64(flops);
     sym_bytes = warp_sum64(sym_bytes);
@@ -316,19 +439,37 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
     }
 }
 
-// Group code layout: prod << 8 | log2(table slots) << 3 | probe bit (MODE_PROBE) | part.
+// Group code layout: prod << 8 | log2(table slots) << 3 | probe bit (MODE_PROBE) | part,
+// or family << 8 | ... | PART_F for a family's block product.
 struct GroupInfo {
     uint32_t part, c, a, b, idx, n, o, lg;
     bool probe;
+    // family groups: members first .. first+F-1; `tagged` when the members
+    // write different non-terminals (accumulator keys carry the member)
+    bool fam, tagged;
+    uint32_t first, F;
 };
+
+constexpr uint32_t TAG_SHIFT = 21;   // member << TAG_SHIFT | word (words < 2^21)
 
 __device__ __forceinline__ GroupInfo decode_group(const ProdTab &P, const SlotTab &S,
                                                   uint2 g) {
     GroupInfo gi;
     gi.probe = (g.x & MODE_PROBE) != 0;
-    gi.part = g.x & 3;
     gi.lg = (g.x >> 3) & 31;
-    const uint4 pr = P.prod[g.x >> 8];
+    gi.part = g.x & 3;
+    gi.fam = gi.part == PART_F;
+    gi.tagged = false;
+    gi.first = g.x >> 8;
+    gi.F = 1;
+    if (gi.fam) {
+        const uint4 fm = P.fam[g.x >> 8];
+        gi.part = fm.w;
+        gi.first = fm.x;
+        gi.F = fm.y;
+        gi.tagged = fm.z == 0;
+    }
+    const uint4 pr = P.prod[gi.first];
     gi.c = pr.x; gi.a = pr.y; gi.b = pr.z;
     gi.idx = g.y;
     gi.n = S.n[gi.c];
@@ -337,7 +478,8 @@ __device__ __forceinline__ GroupInfo decode_group(const ProdTab &P, const SlotTa
 }
 
 // The delta of a group: the entries the last merge added to a's row form
-// (PART_A, PART_U) or b's column form; returns {pool offset, count}.
+// (PART_A, PART_U) or b's column form; returns {pool offset, count}.  A
+// family's shared operand is its members' a (PART_A) or b (PART_B).
 __device__ __forceinline__ uint2 owner_delta(const SlotTab &S, const GroupInfo &gi) {
     const uint32_t x = (gi.part == PART_B) ? gi.b : gi.a;
     const size_t r = (size_t)gi.o * gi.n + gi.idx;
@@ -352,32 +494,40 @@ __device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uin
 }
 
 // Expand the products of a group's delta entries into the accumulator
-// `acc` and emit the ones that are new (warp-collective).  Warp `warp_id` of
-// `nwarps` takes the entries warp_id + nwarps*l (lane l) of every block of
-// 32*nwarps entries, so all warps of a CTA get work even for short deltas.
-// Each delta entry k gathers row k of the other operand as a list of tiles:
-// b's row form for dA . B, a's column form for A . dB (the whole of A: the
-// tiles hold A_old and dA together, and dA . dB is already in dA . B, so the
-// union of the two products is the one of optimisation 1).  A list of 32 or
-// more tiles is walked by the whole warp (coalesced 16-byte loads, two in
-// flight per lane); shorter ones are packed 32 tiles per step with a
-// per-lane search of the owning row.  Returns the emitted count.
+// `acc` and emit the ones that are new (warp-collective).  Each delta entry
+// k gathers row k of the other operand as a list of tiles: b's row form for
+// dA . B, a's column form for A . dB (the whole of A: the tiles hold A_old
+// and dA together, and dA . dB is already in dA . B, so the union of the two
+// products is the one of optimisation 1).
+//   Plain groups: warp `warp_id` of `nwarps` takes the entries
+// warp_id + nwarps*l (lane l) of every block of 32*nwarps entries, so all
+// warps of a CTA get work even for short deltas.
+//   Family groups (optimisation 4): warp `warp_id` takes the entries
+// warp_id, warp_id + nwarps, ..., and for each its lanes take the members
+// (their gathered slots are consecutive); a member's row counts only when
+// its occupancy bit is set.  Tagged families key the accumulator by member
+// and word, and emit to each member's non-terminal.
+// A list of 32 or more tiles is walked by the whole warp (coalesced 16-byte
+// loads, two in flight per lane); shorter ones are packed 32 tiles per step
+// with a per-lane search of the owning row.  Returns the emitted count.
 template <class Acc>
-__device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs &W,
-                                                const GroupInfo &gi, uint2 own,
-                                                uint32_t warp_id, uint32_t nwarps, int lane,
-                                                const Acc &acc) {
+__device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab &P,
+                                                const WorkBufs &W, const GroupInfo &gi,
+                                                uint2 own, uint32_t warp_id, uint32_t nwarps,
+                                                int lane, const Acc &acc) {
     const uint32_t dstart = own.x, d = own.y;
     const uint32_t *pool = S.pool[gi.c];
-    const uint4 *dg = (gi.part == PART_A) ? S.desc[gi.b]
-                    : (gi.part == PART_B) ? S.desc[gi.a] + gi.n : nullptr;
-    const unsigned long long *ht = S.htab[gi.c];
-    const unsigned long long hm = S.hmask[gi.c];
+    const size_t oo = (size_t)gi.o * gi.n;
+    const uint32_t g0 = (gi.part == PART_A) ? gi.b : gi.a;   // gathered slot (member 0)
+    const uint4 *dg = (gi.part == PART_U) ? nullptr : S.desc[g0] + oo;
     uint32_t emitted = 0;
-    // the new bits nb of word wd (any number per lane); nearly every product
-    // is already present, so callers vote first and only then come here
-    auto emit_bits = [&](uint32_t nb, uint32_t wd) {
-        if (gi.probe) {
+    // the new bits nb of word wd of member tag (any number per lane); nearly
+    // every product is already present, so callers vote first
+    auto emit_bits = [&](uint32_t nb, uint32_t wd, uint32_t tag) {
+        const uint32_t slot = gi.tagged ? P.prod[gi.first + tag].x : gi.c;
+        if (gi.probe && nb) {
+            const unsigned long long *ht = S.htab[slot];
+            const unsigned long long hm = S.hmask[slot];
             uint32_t keep = 0;
             for (uint32_t r = nb; r; r &= r - 1) {
                 const uint32_t i = __ffs(r) - 1;
@@ -396,42 +546,28 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
         for (uint32_t r = nb; r; r &= r - 1, pos++) {
             if (pos < W.cand_cap) {
                 W.cand_key[pos] = group_key(gi, wd * 32 + (__ffs(r) - 1));
-                W.cand_slot[pos] = gi.c;
+                W.cand_slot[pos] = slot;
             }
         }
+        // the members' candidate counts (k_check sizes their pair sets)
+        if (gi.tagged && cnt) atomicAdd(&S.cand[slot], (unsigned long long)cnt);
         if (lane == 0 && base + total > W.cand_cap) atomicOr(&W.cnt->overflow, OVF_CAND);
         emitted += total;
     };
-    // two tiles (w.x, w.y) and (w.z, w.w), nv of them valid
-    auto consume_tiles = [&](uint4 w, uint32_t nv) {
-        const uint32_t n0 = nv > 0 ? acc.ins(w.x, w.y) : 0u;
-        const uint32_t n1 = nv > 1 ? acc.ins(w.z, w.w) : 0u;
+    auto key_of = [&](uint32_t wd, uint32_t tag) {
+        return gi.tagged ? (tag << TAG_SHIFT) | wd : wd;
+    };
+    // two tiles (w.x, w.y) and (w.z, w.w) of member tag, nv of them valid
+    auto consume_tiles = [&](uint4 w, uint32_t nv, uint32_t tag) {
+        const uint32_t n0 = nv > 0 ? acc.ins(key_of(w.x, tag), w.y) : 0u;
+        const uint32_t n1 = nv > 1 ? acc.ins(key_of(w.z, tag), w.w) : 0u;
         if (__any_sync(FULL_MASK, (n0 | n1) != 0)) {
-            emit_bits(n0, w.x);
-            emit_bits(n1, w.z);
+            emit_bits(n0, w.x, tag);
+            emit_bits(n1, w.z, tag);
         }
     };
-    if (gi.part == PART_U) {        // c -> a: the delta entries themselves
-        for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
-            const uint32_t e = cb + lane * nwarps;
-            uint32_t nb = 0, wd = 0;
-            if (e < d) {
-                const uint32_t v = pool[dstart + e];
-                wd = v >> 5;
-                nb = acc.ins(wd, 1u << (v & 31));
-            }
-            if (__any_sync(FULL_MASK, nb != 0)) emit_bits(nb, wd);
-        }
-        return emitted;
-    }
-    for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
-        const uint32_t e = cb + lane * nwarps;
-        uint32_t toff = 0, tn = 0;
-        if (e < d) {
-            const uint4 gd = dg[pool[dstart + e]];
-            toff = gd.x;
-            tn = gd.y;
-        }
+    // the tile lists held by the lanes (toff, tn; member tag)
+    auto walk = [&](uint32_t toff, uint32_t tn, uint32_t tag) {
         // long tile lists: the warp strides over one list at a time
         unsigned lm = __ballot_sync(FULL_MASK, tn >= 32);
         while (lm) {
@@ -439,6 +575,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
             lm &= lm - 1;
             const uint32_t *tl = pool + __shfl_sync(FULL_MASK, toff, l);
             const uint32_t T = __shfl_sync(FULL_MASK, tn, l);
+            const uint32_t ltag = __shfl_sync(FULL_MASK, tag, l);
             for (uint32_t qb = 0; qb < T; qb += 128) {
                 uint4 w[2];
                 uint32_t nv[2];
@@ -457,8 +594,8 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
                         nv[h] = 1;
                     }
                 }
-                consume_tiles(w[0], nv[0]);
-                if (qb + 64 < T) consume_tiles(w[1], nv[1]);
+                consume_tiles(w[0], nv[0], ltag);
+                if (qb + 64 < T) consume_tiles(w[1], nv[1], ltag);
             }
         }
         // short tile lists: packed, 32 tiles per step
@@ -478,6 +615,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
             const uint32_t o_toff = __shfl_sync(FULL_MASK, toff, owner);
             const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
             const uint32_t o_len = __shfl_sync(FULL_MASK, stn, owner);
+            const uint32_t o_tag = __shfl_sync(FULL_MASK, tag, owner);
             uint4 w = make_uint4(0, 0, 0, 0);
             uint32_t nv = 0;
             if (f < total) {
@@ -487,8 +625,104 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const WorkBufs
                 w.y = t.y;
                 nv = 1;
             }
-            consume_tiles(w, nv);
+            consume_tiles(w, nv, o_tag);
         }
+    };
+    if (gi.part == PART_U) {        // c -> a: the delta entries themselves
+        for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
+            const uint32_t e = cb + lane * nwarps;
+            uint32_t nb = 0, wd = 0;
+            if (e < d) {
+                const uint32_t v = pool[dstart + e];
+                wd = v >> 5;
+                nb = acc.ins(wd, 1u << (v & 31));
+            }
+            if (__any_sync(FULL_MASK, nb != 0)) emit_bits(nb, wd, 0);
+        }
+        return emitted;
+    }
+    if (gi.fam && gi.F <= 64) {
+        // the (entry, member) pairs whose member has a row, packed 32 per
+        // step: lane l takes entry l of a block of 32, its members' occupancy
+        // bits become a 64-bit mask, and a warp scan numbers the pairs
+        const uint32_t *oc = S.occ[g0];
+        const uint32_t ow = S.occ_w[g0], lx0 = S.local[g0];
+        const uint32_t w0 = lx0 >> 5, sh = lx0 & 31, wlast = (lx0 + gi.F - 1) >> 5;
+        const unsigned long long fmask = gi.F == 64 ? ~0ull : (1ull << gi.F) - 1;
+        for (uint32_t cb = warp_id * 32; cb < d; cb += nwarps * 32) {
+            const uint32_t e = cb + lane;
+            uint32_t k = 0, mlo = 0, mhi = 0;
+            if (e < d) {
+                k = pool[dstart + e];
+                const uint32_t *ok = oc + (oo + k) * ow + w0;
+                const uint32_t x0 = ok[0];
+                const uint32_t x1 = w0 + 1 <= wlast ? ok[1] : 0u;
+                const uint32_t x2 = w0 + 2 <= wlast ? ok[2] : 0u;
+                const unsigned long long lo64 = ((unsigned long long)x1 << 32) | x0;
+                const unsigned long long m64 =
+                    ((lo64 >> sh) | (sh ? (unsigned long long)x2 << (64 - sh) : 0ull)) & fmask;
+                mlo = (uint32_t)m64;
+                mhi = (uint32_t)(m64 >> 32);
+            }
+            const uint32_t cnt = __popc(mlo) + __popc(mhi);
+            const uint32_t incl = warp_incl_scan(cnt, lane);
+            const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+            for (uint32_t fb = 0; fb < total; fb += 32) {
+                const uint32_t f = fb + lane;
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int st = 0; st < 5; st++) {     // first lane whose inclusive sum > f
+                    const int mid = (lo + hi) >> 1;
+                    const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
+                    if (f < v) hi = mid; else lo = mid + 1;
+                }
+                const int owner = lo > 31 ? 31 : lo;
+                const uint32_t o_k = __shfl_sync(FULL_MASK, k, owner);
+                const uint32_t o_lo = __shfl_sync(FULL_MASK, mlo, owner);
+                const uint32_t o_hi = __shfl_sync(FULL_MASK, mhi, owner);
+                const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
+                const uint32_t o_cnt = __shfl_sync(FULL_MASK, cnt, owner);
+                uint32_t toff = 0, tn = 0, tag = 0;
+                if (f < total) {
+                    const uint32_t nth = f - (o_incl - o_cnt), plo = __popc(o_lo);
+                    tag = nth < plo ? select_bit(o_lo, nth) : 32 + select_bit(o_hi, nth - plo);
+                    const uint4 gd = S.desc[g0 + tag][oo + o_k];
+                    toff = gd.x;
+                    tn = gd.y;
+                }
+                walk(toff, tn, tag);
+            }
+        }
+        return emitted;
+    }
+    if (gi.fam) {
+        const uint32_t *oc = S.occ[g0];
+        const uint32_t ow = S.occ_w[g0], lx0 = S.local[g0];
+        for (uint32_t e = warp_id; e < d; e += nwarps) {
+            const uint32_t k = pool[dstart + e];
+            const uint32_t *ok = oc + (oo + k) * ow;
+            for (uint32_t ib = 0; ib < gi.F; ib += 32) {
+                const uint32_t i = ib + lane;
+                uint32_t toff = 0, tn = 0;
+                if (i < gi.F && ((ok[(lx0 + i) >> 5] >> ((lx0 + i) & 31)) & 1u)) {
+                    const uint4 gd = S.desc[g0 + i][oo + k];
+                    toff = gd.x;
+                    tn = gd.y;
+                }
+                if (__any_sync(FULL_MASK, tn != 0)) walk(toff, tn, i);
+            }
+        }
+        return emitted;
+    }
+    for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
+        const uint32_t e = cb + lane * nwarps;
+        uint32_t toff = 0, tn = 0;
+        if (e < d) {
+            const uint4 gd = dg[pool[dstart + e]];
+            toff = gd.x;
+            tn = gd.y;
+        }
+        walk(toff, tn, 0);
     }
     return emitted;
 }
@@ -511,10 +745,9 @@ __device__ __forceinline__ void preload_mask(const SlotTab &S, const GroupInfo &
 template <int LG, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(SlotTab S, ProdTab P, WorkBufs W,
                                                             int bin) {
-    extern __shared__ uint32_t smem[];
+    extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *keys = smem + (size_t)wib * (2u << LG);
-    uint32_t *bits = keys + (1u << LG);
+    uint32_t *tab = smem + (size_t)wib * (2u << LG);
     const unsigned long long n_groups =
         min(W.cnt->groups[bin], W.group_cap[bin]);
     const unsigned long long nw = (unsigned long long)gridDim.x * WARPS;
@@ -523,20 +756,17 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(
          g += nw) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
         const int lg = min((int)gi.lg, LG);
-        for (uint32_t s = lane; s < (1u << lg); s += 32) {
-            keys[s] = EMPTY32;
-            bits[s] = 0;
-        }
+        clear_table(tab, lg, lane, 32);
         __syncwarp();
-        const HashAcc acc{keys, bits, lg};
+        const HashAcc acc{tab, lg};
         if (!gi.probe) {
             preload_mask(S, gi, acc, lane, 32);
             __syncwarp();
         }
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows(S, W, gi, own, 0, 1, lane, acc);
+        const uint32_t e = expand_rows(S, P, W, gi, own, 0, 1, lane, acc);
         if (lane == 0 && e) {
-            atomicAdd(&S.cand[gi.c], (unsigned long long)e);
+            if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)e);
             bytes += 12ull * e;
         }
         __syncwarp();
@@ -546,31 +776,27 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(
 
 // Bin 2: one CTA per group sharing a 2^LG-word shared-memory table.
 template <int LG>
-__global__ void __launch_bounds__(256, 3) k_spgemm_cta(SlotTab S, ProdTab P, WorkBufs W, int bin) {
-    extern __shared__ uint32_t smem[];
+__global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S, ProdTab P, WorkBufs W, int bin) {
+    extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t emitted_sh;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned long long n_groups = min(W.cnt->groups[bin], W.group_cap[bin]);
-    uint32_t *keys = smem, *bits = smem + (1u << LG);
     unsigned long long bytes = 0;
     for (unsigned long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
         const int lg = min((int)gi.lg, LG);
-        for (uint32_t s = threadIdx.x; s < (1u << lg); s += blockDim.x) {
-            keys[s] = EMPTY32;
-            bits[s] = 0;
-        }
+        clear_table(smem, lg, threadIdx.x, blockDim.x);
         if (threadIdx.x == 0) emitted_sh = 0;
         __syncthreads();
-        const HashAcc acc{keys, bits, lg};
+        const HashAcc acc{smem, lg};
         if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows(S, W, gi, own, wib, blockDim.x >> 5, lane, acc);
+        const uint32_t e = expand_rows(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
-            atomicAdd(&S.cand[gi.c], (unsigned long long)emitted_sh);
+            if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)emitted_sh);
             bytes += 12ull * emitted_sh;
         }
     }
@@ -599,11 +825,11 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
         if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows(S, W, gi, own, wib, blockDim.x >> 5, lane, acc);
+        const uint32_t e = expand_rows(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
-            atomicAdd(&S.cand[gi.c], (unsigned long long)emitted_sh);
+            if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)emitted_sh);
             bytes += 12ull * emitted_sh;
         }
     }
@@ -631,7 +857,7 @@ __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
             slot = W.cand_slot[t];
             unsigned long long *tab = S.htab[slot];
             const unsigned long long m = S.hmask[slot];
-            unsigned long long h = hmix(key) & m;
+            unsigned long long h = pair_home(key, m);
             for (;;) {
                 unsigned long long v = tab[h];
                 if (v == key) break;
@@ -736,16 +962,13 @@ __device__ __forceinline__ uint32_t entry_cap_after_move(uint32_t incoming) {
 // shared-memory table of 2^lg >= 2*cnt slots and write one tile per word to
 // out; returns the number written (warp-collective, all lanes).
 template <class Get>
-__device__ __forceinline__ uint32_t warp_fold_tiles(uint32_t *keys, uint32_t *bits, uint32_t cnt,
-                                                    Get get, uint32_t *out, int lane) {
+__device__ __forceinline__ uint32_t warp_fold_tiles(uint32_t *tab, uint32_t cnt, Get get,
+                                                    uint32_t *out, int lane) {
     uint32_t lg = 5;
     while ((1u << lg) < 2 * cnt) lg++;
-    for (uint32_t s = lane; s < (1u << lg); s += 32) {
-        keys[s] = EMPTY32;
-        bits[s] = 0;
-    }
+    clear_table(tab, lg, lane, 32);
     __syncwarp();
-    const HashAcc acc{keys, bits, (int)lg};
+    const HashAcc acc{tab, (int)lg};
     for (uint32_t q = lane; q < cnt; q += 32) {
         const uint2 t = get(q);
         acc.ins(t.x, t.y);
@@ -754,13 +977,10 @@ __device__ __forceinline__ uint32_t warp_fold_tiles(uint32_t *keys, uint32_t *bi
     uint32_t base = 0;
     for (uint32_t sb = 0; sb < (1u << lg); sb += 32) {
         const uint32_t s = sb + lane;
-        const bool has = keys[s] != EMPTY32;
+        const uint2 sl = reinterpret_cast<const uint2 *>(tab)[s];
+        const bool has = sl.x != EMPTY32;
         const unsigned m = __ballot_sync(FULL_MASK, has);
-        if (has) {
-            const uint32_t pos = base + __popc(m & ((1u << lane) - 1));
-            out[2 * pos] = keys[s];
-            out[2 * pos + 1] = bits[s];
-        }
+        if (has) reinterpret_cast<uint2 *>(out)[base + __popc(m & ((1u << lane) - 1))] = sl;
         base += __popc(m);
     }
     __syncwarp();
@@ -774,10 +994,10 @@ __device__ __forceinline__ uint32_t warp_fold_tiles(uint32_t *keys, uint32_t *bi
 // occupancy bit of a row's first entries and clears the append cursors.
 // Idempotent: after a pool overflow the host grows the pool and runs it again.
 __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs W) {
-    __shared__ uint32_t tab[8][4 * TILE_WARP_MAX];   // per warp: words, then bits
+    __shared__ __align__(16) uint32_t tabs[8][4 * TILE_WARP_MAX];   // a table per warp
     if (W.cnt->overflow & OVF_PRE) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *keys = tab[wib], *bits = tab[wib] + 2 * TILE_WARP_MAX;
+    uint32_t *tab = tabs[wib];
     const int par = *W.parity;
     const uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
@@ -803,19 +1023,16 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
         // fold into the table first (the count sizes the new segment) ...
         uint32_t lg = 5;
         while ((1u << lg) < 2 * dsc.y) lg++;
-        for (uint32_t s = lane; s < (1u << lg); s += 32) {
-            keys[s] = EMPTY32;
-            bits[s] = 0;
-        }
+        clear_table(tab, lg, lane, 32);
         __syncwarp();
-        const HashAcc acc{keys, bits, (int)lg};
+        const HashAcc acc{tab, (int)lg};
         for (uint32_t q = lane; q < dsc.y; q += 32) {
             const uint2 tl = *reinterpret_cast<const uint2 *>(pool + dsc.x + 2 * q);
             acc.ins(tl.x, tl.y);
         }
         __syncwarp();
         uint32_t D = 0;
-        for (uint32_t s = lane; s < (1u << lg); s += 32) D += keys[s] != EMPTY32;
+        for (uint32_t s = lane; s < (1u << lg); s += 32) D += tab[2 * s] != EMPTY32;
         for (int dd = 16; dd > 0; dd >>= 1) D += __shfl_xor_sync(FULL_MASK, D, dd);
         const uint32_t tcap = tile_cap_after_move(D, w), ecap = entry_cap_after_move(w);
         const unsigned long long size = (unsigned long long)tile_words(tcap) + ecap;
@@ -837,14 +1054,10 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
         uint32_t *np = pool + off;
         uint32_t base = 0;
         for (uint32_t sb = 0; sb < (1u << lg); sb += 32) {
-            const uint32_t s = sb + lane;
-            const bool has = keys[s] != EMPTY32;
+            const uint2 sl = reinterpret_cast<const uint2 *>(tab)[sb + lane];
+            const bool has = sl.x != EMPTY32;
             const unsigned m = __ballot_sync(FULL_MASK, has);
-            if (has) {
-                const uint32_t pos = base + __popc(m & ((1u << lane) - 1));
-                np[2 * pos] = keys[s];
-                np[2 * pos + 1] = bits[s];
-            }
+            if (has) reinterpret_cast<uint2 *>(np)[base + __popc(m & ((1u << lane) - 1))] = sl;
             base += __popc(m);
         }
         __syncwarp();
@@ -975,10 +1188,10 @@ __global__ void __launch_bounds__(256) k_scatter(SlotTab S, WorkBufs W) {
 // the row yet, so the tiles of a row never share a set bit; a word may get a
 // second tile, until the row's next move folds them.
 __global__ void __launch_bounds__(256) k_pack(SlotTab S, WorkBufs W) {
-    __shared__ uint32_t tab[8][4 * TILE_WARP_MAX];
+    __shared__ __align__(16) uint32_t tabs[8][4 * TILE_WARP_MAX];
     if (W.cnt->overflow & (OVF_PRE | OVF_POOL)) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *keys = tab[wib], *bits = tab[wib] + 2 * TILE_WARP_MAX;
+    uint32_t *tab = tabs[wib];
     const int par = *W.parity;
     const uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
@@ -996,7 +1209,7 @@ __global__ void __launch_bounds__(256) k_pack(SlotTab S, WorkBufs W) {
         uint32_t nt = dsc.y;
         for (uint32_t c0 = 0; c0 < w; c0 += TILE_WARP_MAX) {
             const uint32_t cnt = min(TILE_WARP_MAX, w - c0);
-            nt += warp_fold_tiles(keys, bits, cnt,
+            nt += warp_fold_tiles(tab, cnt,
                                   [&](uint32_t q) {
                                       const uint32_t v = ent[c0 + q];
                                       return make_uint2(v >> 5, 1u << (v & 31));
@@ -1145,7 +1358,7 @@ __global__ void k_rehash(const unsigned long long *old_tab, unsigned long long o
          s < old_cap; s += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long key = old_tab[s];
         if (key == EMPTY_KEY) continue;
-        unsigned long long h = hmix(key) & m;
+        unsigned long long h = pair_home(key, m);
         while (atomicCAS(&new_tab[h], EMPTY_KEY, key) != EMPTY_KEY) h = (h + 1) & m;
     }
 }
@@ -1419,7 +1632,9 @@ static inline int grid_for(unsigned long long work, int per_block, int sms, int 
 // tables of words and bits: 2 x 4 bytes per slot
 constexpr size_t BIN0_SMEM = 8 * 2 * 256 * 4;    // 8 warps x 256 slots
 constexpr size_t BIN1_SMEM = 4 * 2 * 2048 * 4;   // 4 warps x 2048 slots
+constexpr size_t BIN1S_SMEM = 8 * 2 * 1024 * 4;  // 8 warps x 1024 slots (limit <= 512)
 constexpr size_t BIN2_SMEM = 2 * 8192 * 4;
+constexpr size_t BIN2S_SMEM = 2 * 4096 * 4;       // limit <= 2048
 constexpr size_t SMEM_BITMAP_MAX = 200 * 1024;
 
 static void set_smem_attrs();
@@ -1433,6 +1648,8 @@ static void set_smem_attrs() {
                          (int)BIN1_SMEM);
     cudaFuncSetAttribute(k_spgemm_cta<13>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)BIN2_SMEM);
+    cudaFuncSetAttribute(k_spgemm_warp<10, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)BIN1S_SMEM);
     cudaFuncSetAttribute(k_spgemm_bitmap, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)SMEM_BITMAP_MAX);
     cudaFuncSetAttribute(k_extract_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1453,11 +1670,17 @@ void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &
     case 0:
         k_spgemm_warp<8, 8><<<sms * T.ctas_per_sm[0], 256, BIN0_SMEM, st>>>(S, P, W, 0);
         break;
-    case 1:
-        k_spgemm_warp<11, 4><<<sms * T.ctas_per_sm[1], 128, BIN1_SMEM, st>>>(S, P, W, 1);
+    case 1:   // the smaller table when the limit allows it: more warps per SM
+        if (T.limit[1] <= 512)
+            k_spgemm_warp<10, 8><<<sms * T.ctas_per_sm[1], 256, BIN1S_SMEM, st>>>(S, P, W, 1);
+        else
+            k_spgemm_warp<11, 4><<<sms * T.ctas_per_sm[1], 128, BIN1_SMEM, st>>>(S, P, W, 1);
         break;
     case 2:
-        k_spgemm_cta<13><<<sms * T.ctas_per_sm[2], 256, BIN2_SMEM, st>>>(S, P, W, 2);
+        if (T.limit[2] <= 2048)
+            k_spgemm_cta<12><<<sms * T.ctas_per_sm[2], 256, BIN2S_SMEM, st>>>(S, P, W, 2);
+        else
+            k_spgemm_cta<13><<<sms * T.ctas_per_sm[2], 256, BIN2_SMEM, st>>>(S, P, W, 2);
         break;
     default: {
         const size_t bm_bytes = (size_t)((max_n + 31) / 32) * 4;

@@ -32,6 +32,8 @@ namespace cflr {
 constexpr uint32_t PART_A = 0;      // dA . B     : row groups of a's delta
 constexpr uint32_t PART_B = 1;      // A_old . dB : column groups of b's delta
 constexpr uint32_t PART_U = 2;      // c -> a     : row groups of a's delta
+constexpr uint32_t PART_F = 3;      // a family of productions on its shared
+                                    // operand's delta (optimisation 4)
 constexpr uint32_t MODE_PROBE = 4;  // group code bit: mask by probing htab[c]
                                     // group code: prod << 8 | lg << 3 | probe | part
 constexpr unsigned long long EMPTY_KEY = ~0ull;
@@ -104,7 +106,13 @@ struct LoopCtl {
 struct ProdTab {              // global production table of the batch
     const uint4 *prod;        // {c_slot, a_slot, b_slot, kind(0 binary, 1 unit)}
     const uint32_t *use_off;  // per slot*2+o: offsets into use_code
-    const uint32_t *use_code; // prod << 2 | part
+    const uint32_t *use_code; // prod << 2 | part, or family << 2 | PART_F
+    // families run as one block product (optimisation 4):
+    // {first production, members F, c shared by all members, part of the
+    // shared operand (PART_A: a shared, PART_B: b shared)}; the members are
+    // the productions first .. first+F-1, and the slots of their other
+    // operand are consecutive
+    const uint4 *fam;
 };
 
 struct Counters {

@@ -330,6 +330,7 @@ struct Runner {
     DevArr<unsigned long long> d_inst_cnt;
     DevArr<uint2 *> d_inst_out;
     DevArr<uint4> d_prod;
+    DevArr<uint4> d_fam;
     DevArr<uint32_t> d_use_off, d_use_code;
     // work buffers
     DevArr<uint2> d_touched[2];
@@ -420,7 +421,7 @@ struct Runner {
         std::vector<uint32_t *> hoc(n_slots);
         std::vector<uint32_t> hn(n_slots), hi(n_slots), how(n_slots), hl(n_slots);
         std::vector<unsigned long long> hz(n_slots);
-        std::vector<uint4> prods;
+        std::vector<uint4> prods, fams;
         std::vector<std::vector<uint32_t>> uses((size_t)n_slots * 2);
         for (size_t k = 0; k < cx.size(); k++) {
             cflr_ctx *c = cx[k];
@@ -436,7 +437,56 @@ struct Runner {
                 hz[b0 + x] = c->nnz[x];
             }
             const Grammar &g = c->g;
+            // Optimisation 4: an indexed family whose members share one
+            // operand runs as one block product on that operand's delta
+            // (one work-list use instead of F).  It needs every member, the
+            // other operand's members on consecutive slots (so their
+            // occupancy bits are consecutive), and, when the members write
+            // different non-terminals, vertex words below 2^21 so that a
+            // member tag fits beside the word in the accumulator.
+            std::vector<char> in_fam(g.bin_c.size(), 0);
+            if (own->cfg.form != CFLR_FORM_PLAIN) {
+                std::vector<std::vector<int>> members(g.fam_size.size());
+                for (size_t p = 0; p < g.bin_c.size(); p++) {
+                    if (g.bin_fam[p] < 0) continue;
+                    auto &m = members[g.bin_fam[p]];
+                    if (m.empty()) m.assign(g.fam_size[g.bin_fam[p]], -1);
+                    m[g.bin_member[p]] = (int)p;
+                }
+                for (const auto &m : members) {
+                    const uint32_t F = (uint32_t)m.size();
+                    if (F < 2 || F > 1024 || std::count(m.begin(), m.end(), -1)) continue;
+                    bool sa = true, sb = true, sc = true, consecutive = true;
+                    for (uint32_t i = 0; i < F; i++) {
+                        sa &= g.bin_a[m[i]] == g.bin_a[m[0]];
+                        sb &= g.bin_b[m[i]] == g.bin_b[m[0]];
+                        sc &= g.bin_c[m[i]] == g.bin_c[m[0]];
+                    }
+                    if (sa == sb || (!sc && c->n > (1u << 26))) continue;
+                    for (uint32_t i = 0; i < F; i++) {
+                        const uint32_t gi = sa ? g.bin_b[m[i]] : g.bin_a[m[i]];
+                        const uint32_t g0 = sa ? g.bin_b[m[0]] : g.bin_a[m[0]];
+                        consecutive &= gi == g0 + i;
+                    }
+                    if (!consecutive) continue;
+                    const uint32_t first = (uint32_t)prods.size();
+                    const uint32_t fid = (uint32_t)fams.size();
+                    fams.push_back(make_uint4(first, F, sc ? 1u : 0u, sa ? PART_A : PART_B));
+                    for (uint32_t i = 0; i < F; i++) {
+                        const int p = m[i];
+                        in_fam[p] = 1;
+                        const uint32_t id = (uint32_t)prods.size();
+                        prods.push_back(make_uint4(b0 + g.bin_c[p], b0 + g.bin_a[p],
+                                                   b0 + g.bin_b[p], 0));
+                        if (sa) uses[(size_t)(b0 + g.bin_b[p]) * 2 + 1].push_back(id << 2 | PART_B);
+                        else uses[(size_t)(b0 + g.bin_a[p]) * 2 + 0].push_back(id << 2 | PART_A);
+                    }
+                    if (sa) uses[(size_t)(b0 + g.bin_a[m[0]]) * 2 + 0].push_back(fid << 2 | PART_F);
+                    else uses[(size_t)(b0 + g.bin_b[m[0]]) * 2 + 1].push_back(fid << 2 | PART_F);
+                }
+            }
             for (size_t p = 0; p < g.bin_c.size(); p++) {
+                if (in_fam[p]) continue;
                 uint32_t id = (uint32_t)prods.size();
                 prods.push_back(make_uint4(b0 + g.bin_c[p], b0 + g.bin_a[p], b0 + g.bin_b[p], 0));
                 uses[(size_t)(b0 + g.bin_a[p]) * 2 + 0].push_back(id << 2 | PART_A);
@@ -469,6 +519,7 @@ struct Runner {
         d_delta.ensure(own, n_slots);
         d_nnz.ensure(own, n_slots);
         d_prod.ensure(own, prods.size());
+        d_fam.ensure(own, std::max<size_t>(fams.size(), 1));
         d_use_off.ensure(own, off.size());
         d_use_code.ensure(own, codes.size());
         d_pool_top.ensure(own, ni);
@@ -490,6 +541,8 @@ struct Runner {
         ck(cudaMemcpyAsync(d_nnz.p, hz.data(), n_slots * 8, cudaMemcpyHostToDevice, st), "H2D");
         if (!prods.empty())
             ck(cudaMemcpyAsync(d_prod.p, prods.data(), prods.size() * sizeof(uint4), cudaMemcpyHostToDevice, st), "H2D");
+        if (!fams.empty())
+            ck(cudaMemcpyAsync(d_fam.p, fams.data(), fams.size() * sizeof(uint4), cudaMemcpyHostToDevice, st), "H2D");
         ck(cudaMemcpyAsync(d_use_off.p, off.data(), off.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
         if (!codes.empty())
             ck(cudaMemcpyAsync(d_use_code.p, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
@@ -568,6 +621,7 @@ struct Runner {
     ProdTab prodtab() {
         ProdTab P;
         P.prod = d_prod.p; P.use_off = d_use_off.p; P.use_code = d_use_code.p;
+        P.fam = d_fam.p;
         return P;
     }
     InstTab insttab() {

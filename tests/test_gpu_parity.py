@@ -427,3 +427,24 @@ def test_rows_beyond_the_shared_memory_bitmap(keep):
     g = gen.Graph(n=n, labels=["a"], src=src, lab=np.zeros(src.size, np.uint32), dst=dst)
     st, want = assert_parity("S -> a | S S\n", g, keep_vertex_order=keep)
     assert want.pairs["S"].size > 150_000
+
+
+@pytest.mark.parametrize("form", [cflr.CFLR_FORM_PLAIN, cflr.CFLR_FORM_BATCHED,
+                                  cflr.CFLR_FORM_GRAPH])
+@pytest.mark.parametrize("tuning", [None, (1, [16, 64, 256], [1, 1, 1, 1])])
+def test_indexed_families_as_block_products(form, tuning):
+    """Optimisation 4: the 64-field points-to grammar runs its families as one
+    block product each (batched and graph forms; the plain form keeps one
+    product per member).  Small bin limits force the large families apart
+    into per-member groups."""
+    text = gen.grammar_text("fsjpt")
+    g = gen.fsjpt_like(n=6_000, n_edges=24_000, fields=64, seed=13)
+    want = oracle.solve(text, g)
+    with Solver(text, form=form) as s:
+        if tuning:
+            cflr.cflr_set_tuning(s.ctx, *tuning)
+        s.load(g)
+        st = s.solve()
+        assert st["total_pairs"] == want.total()
+        for x in want.grammar.nts[:want.grammar.n_user]:
+            assert np.array_equal(s.pairs(x), want.pairs[x]), x
