@@ -318,10 +318,13 @@ def run_cflr(args):
     for k in range(args.steps + 1):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        c2 = cflr.cflr_create(device=local, stream=stream.cuda_stream)
+        c2 = cflr.cflr_create(device=local, stream=stream.cuda_stream,
+                              form=cflr.CFLR_FORM_GRAPH, autotune_cache=TUNING_CACHE.encode())
         cflr.cflr_load_grammar(c2, text)
         cflr.cflr_load_graph(c2, g.n, h_src.numpy().view(np.uint32),
                              h_lab.numpy().view(np.uint32), h_dst.numpy().view(np.uint32))
+        if not args.no_autotune:
+            cflr.cflr_autotune(c2)          # the cached schedule of this workload
         cflr.cflr_solve(c2)
         tot = 0
         lib = cflr.load_library()

@@ -205,6 +205,7 @@ __device__ __forceinline__ Work gathered_work(const SlotTab &S, uint32_t g, uint
                                               const uint32_t *pool, uint32_t dstart, uint32_t d,
                                               uint32_t q0, uint32_t qstep) {
     const uint4 *dg = S.desc[g] + (size_t)o * n;
+    const uint2 *dd = S.dn[g] + (size_t)o * n;
     const uint32_t *oc = S.occ[g];
     const uint32_t ow = S.occ_w[g], lx = S.local[g];
     const uint32_t bit = 1u << (lx & 31);
@@ -212,7 +213,8 @@ __device__ __forceinline__ Work gathered_work(const SlotTab &S, uint32_t g, uint
     for (uint32_t q = q0; q < d; q += qstep) {
         const uint32_t k = pool[dstart + q];
         if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
-            const uint32_t nt = dg[k].y;
+            // column form (o = 1): A_old, the tiles before the last merge's
+            const uint32_t nt = dg[k].y - (o ? dd[k].y : 0u);
             w.f += nt;
             w.fb += 16ull + 8ull * nt;
         }
@@ -239,7 +241,8 @@ __device__ __forceinline__ Work family_work(const SlotTab &S, uint32_t g0, uint3
             if (lx0 + F < lo + 32) m &= (1u << (lx0 + F - lo)) - 1;
             for (; m; m &= m - 1) {
                 const uint32_t i = lo + (__ffs(m) - 1) - lx0;
-                const uint32_t nt = S.desc[g0 + i][(size_t)o * n + k].y;
+                const size_t rk = (size_t)o * n + k;
+                const uint32_t nt = S.desc[g0 + i][rk].y - (o ? S.dn[g0 + i][rk].y : 0u);
                 w.f += nt;
                 w.fb += 16ull + 8ull * nt;
             }
@@ -495,10 +498,9 @@ __device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uin
 
 // Expand the products of a group's delta entries into the accumulator
 // `acc` and emit the ones that are new (warp-collective).  Each delta entry
-// k gathers row k of the other operand as a list of tiles: b's row form for
-// dA . B, a's column form for A . dB (the whole of A: the tiles hold A_old
-// and dA together, and dA . dB is already in dA . B, so the union of the two
-// products is the one of optimisation 1).
+// k gathers row k of the other operand as a list of tiles: all of b's row k
+// for dA . B, and for A_old . dB the tiles of a's column k that precede the
+// last merge's (dn.y of them, at the end of the list).
 //   Plain groups: warp `warp_id` of `nwarps` takes the entries
 // warp_id + nwarps*l (lane l) of every block of 32*nwarps entries, so all
 // warps of a CTA get work even for short deltas.
@@ -688,7 +690,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                     tag = nth < plo ? select_bit(o_lo, nth) : 32 + select_bit(o_hi, nth - plo);
                     const uint4 gd = S.desc[g0 + tag][oo + o_k];
                     toff = gd.x;
-                    tn = gd.y;
+                    tn = gd.y - (gi.o ? S.dn[g0 + tag][oo + o_k].y : 0u);
                 }
                 walk(toff, tn, tag);
             }
@@ -707,7 +709,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                 if (i < gi.F && ((ok[(lx0 + i) >> 5] >> ((lx0 + i) & 31)) & 1u)) {
                     const uint4 gd = S.desc[g0 + i][oo + k];
                     toff = gd.x;
-                    tn = gd.y;
+                    tn = gd.y - (gi.o ? S.dn[g0 + i][oo + k].y : 0u);
                 }
                 if (__any_sync(FULL_MASK, tn != 0)) walk(toff, tn, i);
             }
@@ -718,9 +720,10 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
         const uint32_t e = cb + lane * nwarps;
         uint32_t toff = 0, tn = 0;
         if (e < d) {
-            const uint4 gd = dg[pool[dstart + e]];
+            const uint32_t k = pool[dstart + e];
+            const uint4 gd = dg[k];
             toff = gd.x;
-            tn = gd.y;
+            tn = gd.y - (gi.o ? S.dn[g0][oo + k].y : 0u);   // A_old for A . dB
         }
         walk(toff, tn, 0);
     }
@@ -900,7 +903,7 @@ __global__ void k_reset_dnew(SlotTab S, WorkBufs W) {
          e < n_in; e += (unsigned long long)gridDim.x * blockDim.x) {
         const uint2 t = t_in[e];
         const uint32_t slot = t.x >> 1, o = t.x & 1;
-        S.dn[slot][(size_t)o * S.n[slot] + t.y].x = 0;
+        S.dn[slot][(size_t)o * S.n[slot] + t.y] = make_uint2(0, 0);
     }
 }
 
@@ -1216,7 +1219,10 @@ __global__ void __launch_bounds__(256) k_pack(SlotTab S, WorkBufs W) {
                                   },
                                   tl + 2 * nt, lane);
         }
-        if (lane == 0) dp->y = nt;
+        if (lane == 0) {
+            dp->y = nt;
+            S.dn[slot][r].y = nt - dsc.y;   // the delta's tiles: A_old is the rest
+        }
         __syncwarp();
     }
 }

@@ -16,7 +16,10 @@
 //               .w = entry capacity
 //   dn[s]       uint2 per row and orientation: .x = pairs the last merge
 //               added to the row (its delta for optimisation 1, kept as
-//               single entries in the entry area), .y = append cursor
+//               single entries in the entry area); .y = the append cursor
+//               while a merge runs, then the number of tiles that merge
+//               appended at the end of the list (they hold the delta, and
+//               the tiles before them are M_old)
 //   pool        uint32 arena of row segments; rows grow by relocation,
 //               and a relocation folds the tiles (one tile per word).
 //   htab[s]     open-addressing set of 64-bit keys (i << 32 | j): every pair

@@ -875,8 +875,13 @@ struct Runner {
     // limit (false).
     bool run_loop() {
         const bool use_graph = own->cfg.form == CFLR_FORM_GRAPH && !prof.on;
+        // A buffer growth changes the pointers the graph was captured with,
+        // so after one the loop runs host-launched iterations until one of
+        // them needs no growth, and only then captures the graph again (a
+        // fresh context grows several buffers in its first iterations).
+        bool settled = graph_valid;
         for (;;) {
-            if (use_graph) {
+            if (use_graph && settled) {
                 ensure_graph();
                 ck(cudaGraphLaunch(gexec, st), "cudaGraphLaunch");
             } else {
@@ -884,6 +889,7 @@ struct Runner {
             }
             read_status();
             prof.collect();
+            settled = h_ctl->status == 0;
             if (h_ctl->status && !recover()) continue;
             if (h_ctl->last_delta == 0) return true;
             if (h_ctl->iter >= h_ctl->limit) return false;
@@ -1565,7 +1571,9 @@ int cflr_autotune(cflr_ctx *c, uint32_t max_trials, cflr_tuning *best) {
     if (cache && cache_lookup(cache, key, found)) {
         c->tuning = found;
         if (c->runner) c->runner->drop_graph();
-        int rc = cflr_reset(c);
+        // the schedule does not change the initial matrices: a context that
+        // has not run an iteration since its graph was loaded stays as it is
+        int rc = c->iterations == 0 ? CFLR_OK : cflr_reset(c);
         if (rc == CFLR_OK && best) cflr_get_tuning(c, best);
         return rc;
     }
