@@ -70,7 +70,8 @@ typedef struct {
     int form;                   /* CFLR_FORM_*                                      */
     int profile;                /* nonzero: time every kernel launch with CUDA events
                                    on the solve stream (see cflr_kernel_stats)      */
-    const char *autotune_cache; /* reserved; may be NULL                            */
+    const char *autotune_cache; /* path of the cflr_autotune cache file, or NULL;
+                                   cflr_create copies the string                    */
     uint32_t initial_capacity;  /* entries of the first work buffers; 0 = sized from
                                    the input.  Small values exercise the growth
                                    paths (every phase re-runs after a growth).      */

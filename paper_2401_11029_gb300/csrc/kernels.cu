@@ -321,23 +321,40 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         const size_t r = (size_t)o * n + idx;
         if (part == PART_F) {
             const uint4 fm = P.fam[code >> 2];
-            const uint4 pr0 = P.prod[fm.x];
+            const uint32_t *mp = P.fam_prod + fm.x;
+            const uint4 pr0 = P.prod[mp[0]];
             const uint32_t g0 = (fm.w == PART_A) ? pr0.z : pr0.y;
-            const Work wk = sum(family_work(S, g0, fm.y, o, n, pool, dstart, d, q0, qstep));
+            auto member_slot = [&](uint32_t i) {
+                const uint4 pr = P.prod[mp[i]];
+                return (fm.w == PART_A) ? pr.z : pr.y;
+            };
+            Work wk{0, 0};
+            if (fm.z & FAM_CONSEC) {
+                wk = family_work(S, g0, fm.y, o, n, pool, dstart, d, q0, qstep);
+            } else {
+                for (uint32_t i = 0; i < fm.y; i++) {
+                    const Work wi = gathered_work(S, member_slot(i), o, n, pool, dstart, d, q0,
+                                                  qstep);
+                    wk.f += wi.f;
+                    wk.fb += wi.fb;
+                }
+            }
+            wk = sum(wk);
             if (wk.f == 0) return;
             uint2 grp;
-            if (fm.z) {            // every member writes c: one mask row
+            if (fm.z & FAM_CSHARED) {   // every member writes c: one mask row
                 const uint32_t mt = S.desc[pr0.x][r].y;
                 emit(classify(code, PART_F, idx, d, mt, 8ull * mt, wk.f, wk.fb, false, grp), grp);
             } else if (wk.f <= T.limit[2]) {
                 emit(classify(code, PART_F, idx, d, 0, 0, wk.f, wk.fb, true, grp), grp);
             } else {               // too large for a hash bin: one group per member
                 for (uint32_t i = 0; i < fm.y; i++) {
-                    const Work wi = sum(gathered_work(S, g0 + i, o, n, pool, dstart, d, q0, qstep));
+                    const Work wi =
+                        sum(gathered_work(S, member_slot(i), o, n, pool, dstart, d, q0, qstep));
                     if (wi.f == 0) continue;
-                    const uint32_t mt = S.desc[P.prod[fm.x + i].x][r].y;
-                    emit(classify(((fm.x + i) << 2) | fm.w, fm.w, idx, d, mt, 8ull * mt, wi.f,
-                                  wi.fb, false, grp),
+                    const uint32_t mt = S.desc[P.prod[mp[i]].x][r].y;
+                    emit(classify((mp[i] << 2) | fm.w, fm.w, idx, d, mt, 8ull * mt, wi.f, wi.fb,
+                                  false, grp),
                          grp);
                 }
             }
@@ -447,9 +464,11 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
 struct GroupInfo {
     uint32_t part, c, a, b, idx, n, o, lg;
     bool probe;
-    // family groups: members first .. first+F-1; `tagged` when the members
-    // write different non-terminals (accumulator keys carry the member)
-    bool fam, tagged;
+    // family groups: member i is production P.fam_prod[first + i]; `tagged`
+    // when the members write different non-terminals (accumulator keys
+    // carry the member); `consec` when the slots of their other operand are
+    // consecutive.  A plain group has first = its production.
+    bool fam, tagged, consec;
     uint32_t first, F;
 };
 
@@ -463,16 +482,20 @@ __device__ __forceinline__ GroupInfo decode_group(const ProdTab &P, const SlotTa
     gi.part = g.x & 3;
     gi.fam = gi.part == PART_F;
     gi.tagged = false;
+    gi.consec = false;
     gi.first = g.x >> 8;
     gi.F = 1;
+    uint32_t p0 = gi.first;
     if (gi.fam) {
         const uint4 fm = P.fam[g.x >> 8];
         gi.part = fm.w;
         gi.first = fm.x;
         gi.F = fm.y;
-        gi.tagged = fm.z == 0;
+        gi.tagged = (fm.z & FAM_CSHARED) == 0;
+        gi.consec = (fm.z & FAM_CONSEC) != 0;
+        p0 = P.fam_prod[fm.x];
     }
-    const uint4 pr = P.prod[gi.first];
+    const uint4 pr = P.prod[p0];
     gi.c = pr.x; gi.a = pr.y; gi.b = pr.z;
     gi.idx = g.y;
     gi.n = S.n[gi.c];
@@ -526,7 +549,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
     // the new bits nb of word wd of member tag (any number per lane); nearly
     // every product is already present, so callers vote first
     auto emit_bits = [&](uint32_t nb, uint32_t wd, uint32_t tag) {
-        const uint32_t slot = gi.tagged ? P.prod[gi.first + tag].x : gi.c;
+        const uint32_t slot = gi.tagged ? P.prod[P.fam_prod[gi.first + tag]].x : gi.c;
         if (gi.probe && nb) {
             const unsigned long long *ht = S.htab[slot];
             const unsigned long long hm = S.hmask[slot];
@@ -643,7 +666,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
         }
         return emitted;
     }
-    if (gi.fam && gi.F <= 64) {
+    if (gi.fam && gi.consec && gi.F <= 64) {
         // the (entry, member) pairs whose member has a row, packed 32 per
         // step: lane l takes entry l of a block of 32, its members' occupancy
         // bits become a 64-bit mask, and a warp scan numbers the pairs
@@ -698,21 +721,27 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
         return emitted;
     }
     if (gi.fam) {
-        const uint32_t *oc = S.occ[g0];
-        const uint32_t ow = S.occ_w[g0], lx0 = S.local[g0];
-        for (uint32_t e = warp_id; e < d; e += nwarps) {
-            const uint32_t k = pool[dstart + e];
-            const uint32_t *ok = oc + (oo + k) * ow;
-            for (uint32_t ib = 0; ib < gi.F; ib += 32) {
-                const uint32_t i = ib + lane;
-                uint32_t toff = 0, tn = 0;
-                if (i < gi.F && ((ok[(lx0 + i) >> 5] >> ((lx0 + i) & 31)) & 1u)) {
-                    const uint4 gd = S.desc[g0 + i][oo + k];
+        // any family: the (entry, member) pairs numbered entry * F + member,
+        // 32 per warp step; a member's row counts when its occupancy bit is set
+        const unsigned long long items = (unsigned long long)d * gi.F;
+        for (unsigned long long ib = (unsigned long long)warp_id * 32; ib < items;
+             ib += (unsigned long long)nwarps * 32) {
+            const unsigned long long it = ib + lane;
+            uint32_t toff = 0, tn = 0, tag = 0;
+            if (it < items) {
+                const uint32_t e = (uint32_t)(it / gi.F), i = (uint32_t)(it - (unsigned long long)e * gi.F);
+                const uint32_t k = pool[dstart + e];
+                const uint4 pr = P.prod[P.fam_prod[gi.first + i]];
+                const uint32_t gs = (gi.part == PART_A) ? pr.z : pr.y;
+                const uint32_t lx = S.local[gs];
+                if ((S.occ[gs][(oo + k) * S.occ_w[gs] + (lx >> 5)] >> (lx & 31)) & 1u) {
+                    const uint4 gd = S.desc[gs][oo + k];
                     toff = gd.x;
-                    tn = gd.y - (gi.o ? S.dn[g0 + i][oo + k].y : 0u);
+                    tn = gd.y - (gi.o ? S.dn[gs][oo + k].y : 0u);
+                    tag = i;
                 }
-                if (__any_sync(FULL_MASK, tn != 0)) walk(toff, tn, i);
             }
+            walk(toff, tn, tag);
         }
         return emitted;
     }

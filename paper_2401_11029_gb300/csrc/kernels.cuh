@@ -111,12 +111,15 @@ struct ProdTab {              // global production table of the batch
     const uint32_t *use_off;  // per slot*2+o: offsets into use_code
     const uint32_t *use_code; // prod << 2 | part, or family << 2 | PART_F
     // families run as one block product (optimisation 4):
-    // {first production, members F, c shared by all members, part of the
-    // shared operand (PART_A: a shared, PART_B: b shared)}; the members are
-    // the productions first .. first+F-1, and the slots of their other
-    // operand are consecutive
+    // {offset into fam_prod, members F, flags, part of the shared operand
+    // (PART_A: a shared, PART_B: b shared)}; member i is production
+    // fam_prod[offset + i].  Flags: FAM_CSHARED when every member writes the
+    // same c, FAM_CONSEC when the slots of the members' other operand are
+    // consecutive (so are their occupancy bits)
     const uint4 *fam;
+    const uint32_t *fam_prod;
 };
+constexpr uint32_t FAM_CSHARED = 1, FAM_CONSEC = 2;
 
 struct Counters {
     unsigned long long groups[N_BINS];

@@ -13,6 +13,7 @@
 #include "kernels.cuh"
 
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -135,6 +136,7 @@ struct cflr_ctx {
     cflr_stats last{};
     Tuning tuning;                      // product-kernel schedule (cflr_autotune)
     std::string grammar_text;           // as loaded (key of the autotune cache)
+    std::string cache_path;             // copy of cfg.autotune_cache (cfg points here)
     // profiling (per kernel)
     uint64_t k_launches[N_KID] = {};
     double k_ms[N_KID] = {};
@@ -331,6 +333,7 @@ struct Runner {
     DevArr<uint2 *> d_inst_out;
     DevArr<uint4> d_prod;
     DevArr<uint4> d_fam;
+    DevArr<uint32_t> d_fam_prod;
     DevArr<uint32_t> d_use_off, d_use_code;
     // work buffers
     DevArr<uint2> d_touched[2];
@@ -422,6 +425,7 @@ struct Runner {
         std::vector<uint32_t> hn(n_slots), hi(n_slots), how(n_slots), hl(n_slots);
         std::vector<unsigned long long> hz(n_slots);
         std::vector<uint4> prods, fams;
+        std::vector<uint32_t> fam_prod;
         std::vector<std::vector<uint32_t>> uses((size_t)n_slots * 2);
         for (size_t k = 0; k < cx.size(); k++) {
             cflr_ctx *c = cx[k];
@@ -437,15 +441,41 @@ struct Runner {
                 hz[b0 + x] = c->nnz[x];
             }
             const Grammar &g = c->g;
-            // Optimisation 4: an indexed family whose members share one
-            // operand runs as one block product on that operand's delta
-            // (one work-list use instead of F).  It needs every member, the
-            // other operand's members on consecutive slots (so their
-            // occupancy bits are consecutive), and, when the members write
-            // different non-terminals, vertex words below 2^21 so that a
-            // member tag fits beside the word in the accumulator.
-            std::vector<char> in_fam(g.bin_c.size(), 0);
+            std::vector<uint32_t> pid(g.bin_c.size());
+            for (size_t p = 0; p < g.bin_c.size(); p++) {
+                pid[p] = (uint32_t)prods.size();
+                prods.push_back(make_uint4(b0 + g.bin_c[p], b0 + g.bin_a[p], b0 + g.bin_b[p], 0));
+            }
+            // covered[p][side]: the use of production p on its a (side 0,
+            // dA . B) or its b (side 1, A_old . dB) belongs to a family use
+            std::vector<std::array<char, 2>> covered(g.bin_c.size(), {0, 0});
+            // A family runs as one block product on the delta of the operand
+            // its members share (one work-list use instead of F):
+            // {offset into fam_prod, F, 1 if every member writes one c | 2
+            // if the other operand's slots are consecutive, part}.
+            auto add_family = [&](const std::vector<int> &m, int side, bool sc) {
+                const uint32_t F = (uint32_t)m.size(), off = (uint32_t)fam_prod.size();
+                bool consecutive = true;
+                for (uint32_t i = 0; i < F; i++) {
+                    fam_prod.push_back(pid[m[i]]);
+                    covered[m[i]][side] = 1;
+                    const uint32_t gi = side == 0 ? g.bin_b[m[i]] : g.bin_a[m[i]];
+                    const uint32_t g0 = side == 0 ? g.bin_b[m[0]] : g.bin_a[m[0]];
+                    consecutive &= gi == g0 + i;
+                }
+                const uint32_t fid = (uint32_t)fams.size();
+                fams.push_back(make_uint4(off, F, (sc ? 1u : 0u) | (consecutive ? 2u : 0u),
+                                          side == 0 ? PART_A : PART_B));
+                const uint32_t x = side == 0 ? g.bin_a[m[0]] : g.bin_b[m[0]];
+                uses[(size_t)(b0 + x) * 2 + side].push_back(fid << 2 | PART_F);
+            };
             if (own->cfg.form != CFLR_FORM_PLAIN) {
+                // Optimisation 4: an indexed family whose members share one
+                // operand.  It needs every member and the other operand's
+                // members on consecutive slots (their occupancy bits are then
+                // consecutive); when the members write different
+                // non-terminals, vertex words below 2^21, so that a member tag
+                // fits beside the word in the accumulator.
                 std::vector<std::vector<int>> members(g.fam_size.size());
                 for (size_t p = 0; p < g.bin_c.size(); p++) {
                     if (g.bin_fam[p] < 0) continue;
@@ -461,36 +491,23 @@ struct Runner {
                         sa &= g.bin_a[m[i]] == g.bin_a[m[0]];
                         sb &= g.bin_b[m[i]] == g.bin_b[m[0]];
                         sc &= g.bin_c[m[i]] == g.bin_c[m[0]];
-                    }
-                    if (sa == sb || (!sc && c->n > (1u << 26))) continue;
-                    for (uint32_t i = 0; i < F; i++) {
                         const uint32_t gi = sa ? g.bin_b[m[i]] : g.bin_a[m[i]];
                         const uint32_t g0 = sa ? g.bin_b[m[0]] : g.bin_a[m[0]];
                         consecutive &= gi == g0 + i;
                     }
-                    if (!consecutive) continue;
-                    const uint32_t first = (uint32_t)prods.size();
-                    const uint32_t fid = (uint32_t)fams.size();
-                    fams.push_back(make_uint4(first, F, sc ? 1u : 0u, sa ? PART_A : PART_B));
-                    for (uint32_t i = 0; i < F; i++) {
-                        const int p = m[i];
-                        in_fam[p] = 1;
-                        const uint32_t id = (uint32_t)prods.size();
-                        prods.push_back(make_uint4(b0 + g.bin_c[p], b0 + g.bin_a[p],
-                                                   b0 + g.bin_b[p], 0));
-                        if (sa) uses[(size_t)(b0 + g.bin_b[p]) * 2 + 1].push_back(id << 2 | PART_B);
-                        else uses[(size_t)(b0 + g.bin_a[p]) * 2 + 0].push_back(id << 2 | PART_A);
-                    }
-                    if (sa) uses[(size_t)(b0 + g.bin_a[m[0]]) * 2 + 0].push_back(fid << 2 | PART_F);
-                    else uses[(size_t)(b0 + g.bin_b[m[0]]) * 2 + 1].push_back(fid << 2 | PART_F);
+                    if (sa == sb || !consecutive || (!sc && c->n > (1u << 26))) continue;
+                    add_family(m, sa ? 0 : 1, sc);
                 }
+                // (Grouping the other productions that share the operand, the
+                // side and the output non-terminal the same way, as in
+                // M -> N1 N3 | N2 N3, was measured slower: 3 % fewer
+                // candidates did not pay for the per-member lookups.)
             }
             for (size_t p = 0; p < g.bin_c.size(); p++) {
-                if (in_fam[p]) continue;
-                uint32_t id = (uint32_t)prods.size();
-                prods.push_back(make_uint4(b0 + g.bin_c[p], b0 + g.bin_a[p], b0 + g.bin_b[p], 0));
-                uses[(size_t)(b0 + g.bin_a[p]) * 2 + 0].push_back(id << 2 | PART_A);
-                uses[(size_t)(b0 + g.bin_b[p]) * 2 + 1].push_back(id << 2 | PART_B);
+                if (!covered[p][0])
+                    uses[(size_t)(b0 + g.bin_a[p]) * 2 + 0].push_back(pid[p] << 2 | PART_A);
+                if (!covered[p][1])
+                    uses[(size_t)(b0 + g.bin_b[p]) * 2 + 1].push_back(pid[p] << 2 | PART_B);
             }
             for (size_t p = 0; p < g.unit_c.size(); p++) {
                 uint32_t id = (uint32_t)prods.size();
@@ -520,6 +537,7 @@ struct Runner {
         d_nnz.ensure(own, n_slots);
         d_prod.ensure(own, prods.size());
         d_fam.ensure(own, std::max<size_t>(fams.size(), 1));
+        d_fam_prod.ensure(own, std::max<size_t>(fam_prod.size(), 1));
         d_use_off.ensure(own, off.size());
         d_use_code.ensure(own, codes.size());
         d_pool_top.ensure(own, ni);
@@ -541,8 +559,10 @@ struct Runner {
         ck(cudaMemcpyAsync(d_nnz.p, hz.data(), n_slots * 8, cudaMemcpyHostToDevice, st), "H2D");
         if (!prods.empty())
             ck(cudaMemcpyAsync(d_prod.p, prods.data(), prods.size() * sizeof(uint4), cudaMemcpyHostToDevice, st), "H2D");
-        if (!fams.empty())
+        if (!fams.empty()) {
             ck(cudaMemcpyAsync(d_fam.p, fams.data(), fams.size() * sizeof(uint4), cudaMemcpyHostToDevice, st), "H2D");
+            ck(cudaMemcpyAsync(d_fam_prod.p, fam_prod.data(), fam_prod.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
+        }
         ck(cudaMemcpyAsync(d_use_off.p, off.data(), off.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
         if (!codes.empty())
             ck(cudaMemcpyAsync(d_use_code.p, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
@@ -622,6 +642,7 @@ struct Runner {
         ProdTab P;
         P.prod = d_prod.p; P.use_off = d_use_off.p; P.use_code = d_use_code.p;
         P.fam = d_fam.p;
+        P.fam_prod = d_fam_prod.p;
         return P;
     }
     InstTab insttab() {
@@ -1253,6 +1274,11 @@ int cflr_create(cflr_ctx **out, const cflr_config *cfg) {
     if (c.form < CFLR_FORM_PLAIN || c.form > CFLR_FORM_GRAPH) return CFLR_EINVAL;
     std::unique_ptr<cflr_ctx> x(new cflr_ctx());
     x->cfg = c;
+    // the caller's string need not outlive this call
+    if (c.autotune_cache) {
+        x->cache_path = c.autotune_cache;
+        x->cfg.autotune_cache = x->cache_path.c_str();
+    }
     x->device = c.device;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {

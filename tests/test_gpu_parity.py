@@ -448,3 +448,25 @@ def test_indexed_families_as_block_products(form, tuning):
         assert st["total_pairs"] == want.total()
         for x in want.grammar.nts[:want.grammar.n_user]:
             assert np.array_equal(s.pairs(x), want.pairs[x]), x
+
+
+def test_autotune_cache_path_is_copied_at_create(tmp_path):
+    """The context keeps its own copy of cfg.autotune_cache: the caller's
+    buffer may be reused right after cflr_create."""
+    import ctypes
+    text = gen.grammar_text("fica")
+    g = gen.fica_like(n=5000, n_a=10_000, n_d=3750, seed=7)
+    cache = str(tmp_path / "t.txt")
+    buf = ctypes.create_string_buffer(cache.encode(), 4096)
+    cfg = cflr.cflr_default_config()
+    cfg.autotune_cache = ctypes.cast(buf, ctypes.c_char_p)
+    s = Solver.__new__(Solver)
+    s.ctx = cflr.cflr_create(cfg)
+    try:
+        cflr.cflr_load_grammar(s.ctx, text)
+        ctypes.memset(buf, ord("x"), 4095)          # the caller's buffer changes
+        s.load(g)
+        cflr.cflr_autotune(s.ctx, 3)
+    finally:
+        cflr.cflr_destroy(s.ctx)
+    assert open(cache).read().count("\n") == 1
