@@ -4,17 +4,20 @@
 // production c -> a b,  T_c = (dA . B) u (A_old . dB),  dC = T_c \ M_c,
 // M_c <- M_c u dC  (paper Sec. 3, optimisations 1 and 2).  The kernels below
 // split it into:
-//   k_symbolic   work list: one group per (production, delta row) with its
-//                product count, binned by the shared memory it needs
+//   k_symbolic   work list: one group per (production or indexed family,
+//                delta row) with its product steps (referenced tiles),
+//                binned by the shared memory its accumulator needs
 //   k_spgemm_*   the boolean products of a group with the mask fused:
 //                a shared-memory set of the mask row plus the products;
 //                a product is emitted only when the set did not hold it
 //   k_commit     dedupe across groups into the per-non-terminal hash set;
-//                the winners are the new pairs dC
-//   k_reset_dnew / k_count / k_capacity / k_scatter
-//                the union M_c u dC: append dC to the row and column forms
-//                (rows keep slack and move when full, so a union touches
-//                only the rows that grow - the role optimisation 3 plays)
+//                the winners are the new pairs dC, counted per row
+//   k_reset_dnew / k_capacity / k_capacity_big / k_scatter / k_pack
+//                the union M_c u dC in the row and column forms: rows are
+//                lists of 32-bit tiles with slack; a row that lacks room
+//                moves (folding its tiles), the new pairs are appended and
+//                packed into tiles, so a union touches only the rows that
+//                grow (the role optimisation 3 plays)
 // All work is integer; the result does not depend on thread timing.
 #include "kernels.cuh"
 
@@ -205,7 +208,6 @@ __device__ __forceinline__ Work gathered_work(const SlotTab &S, uint32_t g, uint
                                               const uint32_t *pool, uint32_t dstart, uint32_t d,
                                               uint32_t q0, uint32_t qstep) {
     const uint4 *dg = S.desc[g] + (size_t)o * n;
-    const uint2 *dd = S.dn[g] + (size_t)o * n;
     const uint32_t *oc = S.occ[g];
     const uint32_t ow = S.occ_w[g], lx = S.local[g];
     const uint32_t bit = 1u << (lx & 31);
@@ -214,7 +216,8 @@ __device__ __forceinline__ Work gathered_work(const SlotTab &S, uint32_t g, uint
         const uint32_t k = pool[dstart + q];
         if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
             // column form (o = 1): A_old, the tiles before the last merge's
-            const uint32_t nt = dg[k].y - (o ? dd[k].y : 0u);
+            const uint4 gd = dg[k];
+            const uint32_t nt = gd.y - (o ? (gd.w & DLAST_MASK) : 0u);
             w.f += nt;
             w.fb += 16ull + 8ull * nt;
         }
@@ -241,8 +244,8 @@ __device__ __forceinline__ Work family_work(const SlotTab &S, uint32_t g0, uint3
             if (lx0 + F < lo + 32) m &= (1u << (lx0 + F - lo)) - 1;
             for (; m; m &= m - 1) {
                 const uint32_t i = lo + (__ffs(m) - 1) - lx0;
-                const size_t rk = (size_t)o * n + k;
-                const uint32_t nt = S.desc[g0 + i][rk].y - (o ? S.dn[g0 + i][rk].y : 0u);
+                const uint4 gd = S.desc[g0 + i][(size_t)o * n + k];
+                const uint32_t nt = gd.y - (o ? (gd.w & DLAST_MASK) : 0u);
                 w.f += nt;
                 w.fb += 16ull + 8ull * nt;
             }
@@ -713,7 +716,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                     tag = nth < plo ? select_bit(o_lo, nth) : 32 + select_bit(o_hi, nth - plo);
                     const uint4 gd = S.desc[g0 + tag][oo + o_k];
                     toff = gd.x;
-                    tn = gd.y - (gi.o ? S.dn[g0 + tag][oo + o_k].y : 0u);
+                    tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);
                 }
                 walk(toff, tn, tag);
             }
@@ -737,7 +740,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                 if ((S.occ[gs][(oo + k) * S.occ_w[gs] + (lx >> 5)] >> (lx & 31)) & 1u) {
                     const uint4 gd = S.desc[gs][oo + k];
                     toff = gd.x;
-                    tn = gd.y - (gi.o ? S.dn[gs][oo + k].y : 0u);
+                    tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);
                     tag = i;
                 }
             }
@@ -752,7 +755,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
             const uint32_t k = pool[dstart + e];
             const uint4 gd = dg[k];
             toff = gd.x;
-            tn = gd.y - (gi.o ? S.dn[g0][oo + k].y : 0u);   // A_old for A . dB
+            tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);   // A_old for A . dB
         }
         walk(toff, tn, 0);
     }
@@ -875,6 +878,9 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
 __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
     if (W.cnt->overflow & OVF_PRE) return;     // the iteration is re-run after a growth
     const int lane = threadIdx.x & 31;
+    const int par = *W.parity;
+    unsigned long long *out_n = &W.touched_n[par ^ 1];
+    uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long nc = min(W.cnt->cand, W.cand_cap);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x +
@@ -914,6 +920,29 @@ __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
             const unsigned same = __match_any_sync(FULL_MASK, isnew ? slot : EMPTY32);
             if (isnew && lane == __ffs(same & m) - 1)
                 atomicAdd(&S.delta[slot], (unsigned long long)__popc(same & m));
+            // count the new pair in its row of each form, and list a row the
+            // first time it gets one (the rows the merge appends to)
+            bool first_r = false, first_c = false;
+            const uint32_t i = (uint32_t)(key >> 32), j = (uint32_t)key;
+            if (isnew) {
+                uint2 *dn = S.dn[slot];
+                first_r = atomicAdd(&dn[i].x, 1u) == 0;
+                first_c = atomicAdd(&dn[(size_t)S.n[slot] + j].x, 1u) == 0;
+            }
+#pragma unroll
+            for (int o = 0; o < 2; o++) {
+                const bool f = o ? first_c : first_r;
+                const unsigned fm = __ballot_sync(FULL_MASK, f);
+                if (!fm) continue;
+                unsigned long long tp = 0;
+                if (lane == 0) tp = atomicAdd(out_n, (unsigned long long)__popc(fm));
+                tp = __shfl_sync(FULL_MASK, tp, 0);
+                if (f) {
+                    tp += __popc(fm & ((1u << lane) - 1));
+                    if (tp < W.touched_cap) t_out[tp] = make_uint2(slot * 2 + o, o ? j : i);
+                    else atomicOr(&W.cnt->overflow, OVF_TOUCHED);
+                }
+            }
         }
     }
 }
@@ -932,62 +961,25 @@ __global__ void k_reset_dnew(SlotTab S, WorkBufs W) {
          e < n_in; e += (unsigned long long)gridDim.x * blockDim.x) {
         const uint2 t = t_in[e];
         const uint32_t slot = t.x >> 1, o = t.x & 1;
-        S.dn[slot][(size_t)o * S.n[slot] + t.y] = make_uint2(0, 0);
-    }
-}
-
-// Count the new entries of every row; list each row the first time.
-__global__ void __launch_bounds__(256) k_count(SlotTab S, WorkBufs W) {
-    if (W.cnt->overflow & OVF_PRE) return;
-    const int lane = threadIdx.x & 31;
-    const int par = *W.parity;
-    unsigned long long *out_n = &W.touched_n[par ^ 1];
-    uint2 *t_out = W.touched[par ^ 1];
-    const unsigned long long nd = W.cnt->delta;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x +
-                                   (threadIdx.x & ~31u);
-         base < nd; base += stride) {
-        const unsigned long long t = base + lane;
-        bool first_r = false, first_c = false;
-        uint32_t slot = 0, i = 0, j = 0;
-        if (t < nd) {
-            const unsigned long long key = W.delta_key[t];
-            slot = W.delta_slot[t];
-            i = (uint32_t)(key >> 32);
-            j = (uint32_t)key;
-            uint2 *dn = S.dn[slot];
-            const uint32_t n = S.n[slot];
-            first_r = atomicAdd(&dn[i].x, 1u) == 0;
-            first_c = atomicAdd(&dn[(size_t)n + j].x, 1u) == 0;
-        }
-#pragma unroll
-        for (int o = 0; o < 2; o++) {
-            const bool f = o ? first_c : first_r;
-            const unsigned m = __ballot_sync(FULL_MASK, f);
-            if (!m) continue;
-            unsigned long long pos = 0;
-            if (lane == 0) pos = atomicAdd(out_n, (unsigned long long)__popc(m));
-            pos = __shfl_sync(FULL_MASK, pos, 0);
-            if (f) {
-                pos += __popc(m & ((1u << lane) - 1));
-                if (pos < W.touched_cap) t_out[pos] = make_uint2(slot * 2 + o, o ? j : i);
-                else atomicOr(&W.cnt->overflow, OVF_TOUCHED);
-            }
-        }
+        const size_t r = (size_t)o * S.n[slot] + t.y;
+        S.dn[slot][r] = make_uint2(0, 0);
+        S.desc[slot][r].w &= ~DLAST_MASK;
     }
 }
 
 constexpr uint32_t TILE_WARP_MAX = 256;   // tiles one warp folds (k_capacity, k_pack)
 
 // Capacities of a moved row: its folded tiles plus room to append as many
-// tiles again (at least twice this merge's entries), and twice this merge's
-// entries; a row that keeps growing moves a logarithmic number of times.
+// tiles again (at least twice this merge's entries), and a power of two of
+// at least twice this merge's entries (desc.w keeps its log2); a row that
+// keeps growing moves a logarithmic number of times.
 __device__ __forceinline__ uint32_t tile_cap_after_move(uint32_t tiles, uint32_t incoming) {
     return tiles + max(max(2u * incoming, tiles), 8u);
 }
-__device__ __forceinline__ uint32_t entry_cap_after_move(uint32_t incoming) {
-    return (max(2u * incoming, 8u) + 3) & ~3u;
+__device__ __forceinline__ uint32_t entry_log_after_move(uint32_t incoming) {
+    uint32_t lg = 3;
+    while ((1u << lg) < 2u * incoming) lg++;
+    return lg;
 }
 
 // Deduplicate `cnt` tiles (word, bits), read through get(q), in a warp's
@@ -1049,7 +1041,7 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
                 atomicOr(&S.occ[slot][r * S.occ_w[slot] + (lx >> 5)], 1u << (lx & 31));
             }
         }
-        if ((unsigned long long)dsc.y + w <= dsc.z && w <= dsc.w) continue;
+        if ((unsigned long long)dsc.y + w <= dsc.z && w <= entry_cap(dsc)) continue;
         if (dsc.y > TILE_WARP_MAX) continue;
         uint32_t *pool = S.pool[slot];
         // fold into the table first (the count sizes the new segment) ...
@@ -1066,8 +1058,8 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
         uint32_t D = 0;
         for (uint32_t s = lane; s < (1u << lg); s += 32) D += tab[2 * s] != EMPTY32;
         for (int dd = 16; dd > 0; dd >>= 1) D += __shfl_xor_sync(FULL_MASK, D, dd);
-        const uint32_t tcap = tile_cap_after_move(D, w), ecap = entry_cap_after_move(w);
-        const unsigned long long size = (unsigned long long)tile_words(tcap) + ecap;
+        const uint32_t tcap = tile_cap_after_move(D, w), elog = entry_log_after_move(w);
+        const unsigned long long size = (unsigned long long)tile_words(tcap) + (1ull << elog);
         const uint32_t inst = S.inst[slot];
         unsigned long long off = 0;
         if (lane == 0) {
@@ -1093,7 +1085,7 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
             base += __popc(m);
         }
         __syncwarp();
-        if (lane == 0) *dp = make_uint4((uint32_t)off, D, tcap, ecap);
+        if (lane == 0) *dp = make_uint4((uint32_t)off, D, tcap, elog << ELOG_SHIFT);
         __syncwarp();
     }
 }
@@ -1125,7 +1117,8 @@ __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, Work
             const size_t r = (size_t)o * S.n[slot] + t.y;
             const uint4 dsc = S.desc[slot][r];
             const uint32_t w = S.dn[slot][r].x;
-            if (((unsigned long long)dsc.y + w > dsc.z || w > dsc.w) && dsc.y > TILE_WARP_MAX)
+            if (((unsigned long long)dsc.y + w > dsc.z || w > entry_cap(dsc)) &&
+                dsc.y > TILE_WARP_MAX)
                 list[atomicAdd(&list_n, 1u)] = threadIdx.x;
         }
         __syncthreads();
@@ -1156,8 +1149,8 @@ __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, Work
             unsigned long long D = 0;
             const unsigned long long before = block_excl_scan256(cnt, sh, D);
             const uint32_t ntn = use_smem ? (uint32_t)D : dsc.y;
-            const uint32_t tcap = tile_cap_after_move(ntn, w), ecap = entry_cap_after_move(w);
-            const unsigned long long size = (unsigned long long)tile_words(tcap) + ecap;
+            const uint32_t tcap = tile_cap_after_move(ntn, w), elog = entry_log_after_move(w);
+            const unsigned long long size = (unsigned long long)tile_words(tcap) + (1ull << elog);
             if (threadIdx.x == 0) {
                 unsigned long long off = atomicAdd(&I.pool_top[S.inst[slot]], size);
                 if (off + size > I.pool_cap[S.inst[slot]]) {
@@ -1185,7 +1178,7 @@ __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, Work
                         np[q] = pool[dsc.x + q];
                 }
                 __syncthreads();
-                if (threadIdx.x == 0) *dp = make_uint4((uint32_t)off, ntn, tcap, ecap);
+                if (threadIdx.x == 0) *dp = make_uint4((uint32_t)off, ntn, tcap, elog << ELOG_SHIFT);
             }
             __syncthreads();
         }
@@ -1250,7 +1243,10 @@ __global__ void __launch_bounds__(256) k_pack(SlotTab S, WorkBufs W) {
         }
         if (lane == 0) {
             dp->y = nt;
-            S.dn[slot][r].y = nt - dsc.y;   // the delta's tiles: A_old is the rest
+            // the delta's tiles (a count beyond the field falls back to
+            // gathering all of A, a superset of A_old with the same union)
+            const uint32_t dl = nt - dsc.y;
+            dp->w = (dsc.w & ~DLAST_MASK) | (dl <= DLAST_MASK ? dl : 0u);
         }
         __syncwarp();
     }
@@ -1752,9 +1748,6 @@ void launch_reset_dnew(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_
     k_reset_dnew<<<sms * 4, 256, 0, st>>>(S, W);
 }
 
-void launch_count(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {
-    k_count<<<sms * 8, 256, 0, st>>>(S, W);
-}
 
 void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t max_n,
                      int sms, cudaStream_t st) {

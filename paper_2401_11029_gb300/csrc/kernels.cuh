@@ -13,13 +13,12 @@
 //                    two tiles share a set bit
 //               .z = tile capacity; the entry area starts at
 //                    .x + tile_words(.z)
-//               .w = entry capacity
+//               .w = log2 of the entry capacity << ELOG_SHIFT | the tiles
+//                    the last merge appended (they hold the delta; the tiles
+//                    before them are M_old)
 //   dn[s]       uint2 per row and orientation: .x = pairs the last merge
 //               added to the row (its delta for optimisation 1, kept as
-//               single entries in the entry area); .y = the append cursor
-//               while a merge runs, then the number of tiles that merge
-//               appended at the end of the list (they hold the delta, and
-//               the tiles before them are M_old)
+//               single entries in the entry area), .y = append cursor
 //   pool        uint32 arena of row segments; rows grow by relocation,
 //               and a relocation folds the tiles (one tile per word).
 //   htab[s]     open-addressing set of 64-bit keys (i << 32 | j): every pair
@@ -57,6 +56,14 @@ struct Tuning {
     uint32_t limit[3] = {BIN0_LIMIT, BIN1_LIMIT, BIN2_LIMIT};   // need bounds of bins 0-2
     uint32_t ctas_per_sm[4] = {8, 3, 3, 8};      // grids (bin 3: upper bound)
 };
+
+// desc.w: log2 of the entry capacity << ELOG_SHIFT | the number of tiles the
+// last merge appended (DLAST_MASK)
+constexpr uint32_t ELOG_SHIFT = 27;
+constexpr uint32_t DLAST_MASK = (1u << ELOG_SHIFT) - 1;
+__host__ __device__ __forceinline__ uint32_t entry_cap(uint4 desc) {
+    return 1u << (desc.w >> ELOG_SHIFT);
+}
 
 // pool words of a row's tile section (a multiple of 4, so both the tiles and
 // the single entries after them start on 16-byte boundaries)
@@ -175,7 +182,6 @@ void launch_iter_end(const SlotTab &S, const InstTab &I, const WorkBufs &W, Loop
                      uint32_t n_slots, uint32_t n_inst, bool count_iteration,
                      cudaGraphConditionalHandle handle, bool in_graph, cudaStream_t st);
 void launch_reset_dnew(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
-void launch_count(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
 // Room for every row the merge appends to (its new entries, and as many
 // tiles again): rows that must grow move to a new segment with their tiles
 // folded to one per word (one warp per row up to TILE_WARP_MAX tiles, then

@@ -29,11 +29,11 @@ enum { ST_CREATED = 0, ST_GRAMMAR = 1, ST_GRAPH = 2, ST_SOLVED = 3 };
 
 enum KernelId {
     KID_SYMBOLIC = 0, KID_BIN0, KID_BIN1, KID_BIN2, KID_BIN3, KID_COMMIT, KID_RESET,
-    KID_COUNT, KID_CAPACITY, KID_SCATTER, KID_PACK, KID_INIT, KID_REHASH, N_KID
+    KID_CAPACITY, KID_SCATTER, KID_PACK, KID_INIT, KID_REHASH, N_KID
 };
 const char *kKernelNames[N_KID] = {
     "k_symbolic", "k_spgemm_bin0", "k_spgemm_bin1", "k_spgemm_bin2", "k_spgemm_bin3",
-    "k_commit", "k_reset_dnew", "k_count", "k_capacity", "k_scatter", "k_pack", "k_init",
+    "k_commit", "k_reset_dnew", "k_capacity", "k_scatter", "k_pack", "k_init",
     "k_rehash"};
 
 struct CudaError {
@@ -782,9 +782,9 @@ struct Runner {
                       bool count_iteration, bool in_graph, bool timed) {
         auto run = [&](int kid, auto f) { if (timed) prof.run(kid, f); else f(); };
         if (stage <= 0) {
-            run(KID_COMMIT, [&] { launch_commit(S, W, sms, st); });
+            // the previous deltas end before the commit counts the new ones
             run(KID_RESET, [&] { launch_reset_dnew(S, W, sms, st); });
-            run(KID_COUNT, [&] { launch_count(S, W, sms, st); });
+            run(KID_COMMIT, [&] { launch_commit(S, W, sms, st); });
         }
         if (stage <= 1) run(KID_CAPACITY, [&] { launch_capacity(S, I, W, max_n, sms, st); });
         run(KID_SCATTER, [&] { launch_scatter(S, W, sms, st); });
@@ -1000,9 +1000,9 @@ struct Runner {
         read_status();
         own->k_bytes[KID_SYMBOLIC] += h_ctl->bytes_sym;
         for (int b = 0; b < N_BINS; b++) own->k_bytes[KID_BIN0 + b] += h_ctl->bytes_bin[b];
-        own->k_bytes[KID_COMMIT] += 20 * h_ctl->total_cand + 12 * h_ctl->total_delta;
+        own->k_bytes[KID_COMMIT] += 20 * h_ctl->total_cand + 20 * h_ctl->total_delta +
+                                    8 * h_ctl->total_touched_out;
         own->k_bytes[KID_RESET] += 12 * h_ctl->total_touched_in;
-        own->k_bytes[KID_COUNT] += 20 * h_ctl->total_delta + 8 * h_ctl->total_touched_out;
         own->k_bytes[KID_CAPACITY] += 24 * h_ctl->total_touched_out;
         own->k_bytes[KID_SCATTER] += 60 * h_ctl->total_delta;
         own->k_bytes[KID_PACK] += 24 * h_ctl->total_delta + 24 * h_ctl->total_touched_out;
