@@ -89,6 +89,11 @@ typedef struct {
                                    so a row's entries fall into few 32-bit words (the
                                    bit-packed tiles of the row storage); results
                                    always use the caller's ids                      */
+    int witness;                /* nonzero: keep one derivation step for every pair
+                                   (single-path semantics, see cflr_get_witness);
+                                   costs 8 more bytes per pair-set slot and per
+                                   candidate, and needs at most 32768
+                                   non-terminals                                    */
 } cflr_config;
 
 typedef struct {
@@ -189,6 +194,28 @@ int cflr_get_pairs(const cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint3
  * returns after the copy has finished on the context's stream. */
 int cflr_get_pairs_device(const cflr_ctx *c, uint32_t nonterminal, uint32_t *d_src,
                           uint32_t *d_dst, uint64_t capacity, uint64_t *n_pairs);
+
+/* Kinds of a derivation step (cflr_get_witness). */
+enum {
+    CFLR_WIT_BINARY = 0,  /* nonterminal -> A B: (src, mid) in A, (mid, dst) in B    */
+    CFLR_WIT_EDGE = 1,    /* nonterminal -> x: an edge src --x--> dst (id = label)   */
+    CFLR_WIT_UNIT = 2,    /* nonterminal -> A: (src, dst) in A (id = A)              */
+    CFLR_WIT_EPS = 3      /* nonterminal -> eps: src == dst                          */
+};
+
+/* Single-path semantics (the paper's closing remarks: its optimisations carry
+ * over by changing the semiring).  With cfg.witness set, every pair keeps the
+ * first derivation step the closure found for it: *kind is a CFLR_WIT_*
+ * value, *id and *id2 the non-terminal ids A and B (CFLR_WIT_BINARY), A
+ * (CFLR_WIT_UNIT) or the label (CFLR_WIT_EDGE), and *mid the middle vertex
+ * of a binary step.  The steps of a pair refer only to pairs found in
+ * earlier iterations, so following them down to edges always ends, and
+ * gives a path from src to dst whose label word the non-terminal derives.
+ * Pointers other than kind may be NULL.  Errors: CFLR_ESTATE (no graph, or
+ * the context was created without cfg.witness), CFLR_EINVAL (a bad id, or
+ * (src, dst) not in the relation), CFLR_ECUDA. */
+int cflr_get_witness(const cflr_ctx *c, uint32_t nonterminal, uint32_t src, uint32_t dst,
+                     int *kind, uint32_t *id, uint32_t *id2, uint32_t *mid);
 
 /* Largest graph (vertices) cflr_get_pairs_device_noalloc accepts. */
 #define CFLR_NOALLOC_MAX_VERTICES 1048576u

@@ -38,7 +38,10 @@ EXPORTS = ["cflr_default_config", "cflr_create", "cflr_load_grammar", "cflr_symb
            "cflr_grammar_sizes", "cflr_load_graph", "cflr_solve", "cflr_get_pairs",
            "cflr_get_pairs_device", "cflr_get_pairs_device_noalloc", "cflr_reset",
            "cflr_solve_batch", "cflr_kernel_stats", "cflr_get_tuning", "cflr_set_tuning",
-           "cflr_autotune", "cflr_last_error", "cflr_destroy"]
+           "cflr_autotune", "cflr_get_witness", "cflr_last_error", "cflr_destroy"]
+
+# Kinds of a derivation step (cflr_get_witness).
+CFLR_WIT_BINARY, CFLR_WIT_EDGE, CFLR_WIT_UNIT, CFLR_WIT_EPS = 0, 1, 2, 3
 
 # Largest graph the allocation-free extraction accepts (CFLR_NOALLOC_MAX_VERTICES).
 CFLR_NOALLOC_MAX_VERTICES = 1048576
@@ -57,7 +60,7 @@ class cflr_config(ctypes.Structure):
                 ("form", ctypes.c_int), ("profile", ctypes.c_int),
                 ("autotune_cache", ctypes.c_char_p), ("initial_capacity", ctypes.c_uint32),
                 ("size_hint", ctypes.c_uint32), ("stop_on_first_converged", ctypes.c_int),
-                ("keep_vertex_order", ctypes.c_int)]
+                ("keep_vertex_order", ctypes.c_int), ("witness", ctypes.c_int)]
 
 
 class cflr_tuning(ctypes.Structure):
@@ -117,6 +120,8 @@ def load_library(path: str = LIB_PATH):
     lib.cflr_get_pairs_device.restype = i32
     lib.cflr_get_pairs_device_noalloc.argtypes = [vp, u32, vp, vp, u64, ctypes.POINTER(u64)]
     lib.cflr_get_pairs_device_noalloc.restype = i32
+    lib.cflr_get_witness.argtypes = [vp, u32, u32, u32, ctypes.POINTER(i32), u32p, u32p, u32p]
+    lib.cflr_get_witness.restype = i32
     lib.cflr_reset.argtypes = [vp]
     lib.cflr_reset.restype = i32
     lib.cflr_solve_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(cflr_stats)]
@@ -242,6 +247,17 @@ def cflr_get_pairs_device(ctx, nonterminal: int, d_src: int, d_dst: int, capacit
     return int(n.value)
 
 
+def cflr_get_witness(ctx, nonterminal: int, src: int, dst: int):
+    """The derivation step recorded for (src, dst) in `nonterminal` (the
+    context must have been created with witness=1): (kind, id, id2, mid)."""
+    k = ctypes.c_int()
+    a, b, m = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(ctx, load_library().cflr_get_witness(ctx, int(nonterminal), int(src), int(dst),
+                                                ctypes.byref(k), ctypes.byref(a),
+                                                ctypes.byref(b), ctypes.byref(m)))
+    return k.value, a.value, b.value, m.value
+
+
 def cflr_get_pairs_device_noalloc(ctx, nonterminal: int, d_src: int, d_dst: int,
                                   capacity: int) -> int:
     """As cflr_get_pairs_device, for callers that may not allocate device
@@ -362,3 +378,21 @@ class Solver:
 
     def count(self, name: str) -> int:
         return cflr_get_pairs(self.ctx, self.nt_id(name), count_only=True)
+
+    def path(self, name: str, src: int, dst: int, labels: list) -> list:
+        """A path src -> dst whose label word `name` derives, rebuilt from
+        the recorded derivation steps (needs witness=1): a list of edges
+        (u, label name, v).  `labels` maps terminal ids to names."""
+        out = []
+        stack = [(self.nt_id(name), src, dst)]
+        while stack:                   # depth first, left operand first
+            x, u, v = stack.pop()
+            kind, a, b, m = cflr_get_witness(self.ctx, x, u, v)
+            if kind == CFLR_WIT_EDGE:
+                out.append((u, labels[a], v))
+            elif kind == CFLR_WIT_UNIT:
+                stack.append((a, u, v))
+            elif kind == CFLR_WIT_BINARY:
+                stack.append((b, m, v))
+                stack.append((a, u, m))
+        return out

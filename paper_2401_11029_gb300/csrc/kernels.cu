@@ -143,7 +143,7 @@ __device__ __forceinline__ bool htab_contains(const unsigned long long *tab,
 // lanes must call it.  Returns (in every lane) the number appended.
 __device__ __forceinline__ uint32_t emit_candidates(bool flag, unsigned long long key,
                                                     uint32_t slot, const WorkBufs &W,
-                                                    int lane) {
+                                                    int lane, uint2 wit) {
     const unsigned m = __ballot_sync(FULL_MASK, flag);
     if (!m) return 0;
     const uint32_t cnt = __popc(m);
@@ -155,6 +155,7 @@ __device__ __forceinline__ uint32_t emit_candidates(bool flag, unsigned long lon
         if (pos < W.cand_cap) {
             W.cand_key[pos] = key;
             W.cand_slot[pos] = slot;
+            if (W.cand_wit) W.cand_wit[pos] = wit;
         }
     }
     if (lane == 0 && base + cnt > W.cand_cap) atomicOr(&W.cnt->overflow, OVF_CAND);
@@ -538,7 +539,7 @@ __device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uin
 // A list of 32 or more tiles is walked by the whole warp (coalesced 16-byte
 // loads, two in flight per lane); shorter ones are packed 32 tiles per step
 // with a per-lane search of the owning row.  Returns the emitted count.
-template <class Acc>
+template <bool WIT, class Acc>
 __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab &P,
                                                 const WorkBufs &W, const GroupInfo &gi,
                                                 uint2 own, uint32_t warp_id, uint32_t nwarps,
@@ -551,7 +552,15 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
     uint32_t emitted = 0;
     // the new bits nb of word wd of member tag (any number per lane); nearly
     // every product is already present, so callers vote first
-    auto emit_bits = [&](uint32_t nb, uint32_t wd, uint32_t tag) {
+    // the derivation step new pairs record (single-path semantics): the
+    // production's operands, or the unit production's one, and the middle
+    // vertex k (the delta entry whose gathered row gave the pair)
+    auto witness = [&](uint32_t tag, uint32_t k) -> uint2 {
+        if (gi.part == PART_U) return make_uint2(WIT_UNIT | S.local[gi.a], 0);
+        const uint4 pr = gi.fam ? P.prod[P.fam_prod[gi.first + tag]] : make_uint4(0, gi.a, gi.b, 0);
+        return make_uint2(WIT_BINARY | (S.local[pr.y] << 15) | S.local[pr.z], k);
+    };
+    auto emit_bits = [&](uint32_t nb, uint32_t wd, uint32_t tag, uint32_t k) {
         const uint32_t slot = gi.tagged ? P.prod[P.fam_prod[gi.first + tag]].x : gi.c;
         if (gi.probe && nb) {
             const unsigned long long *ht = S.htab[slot];
@@ -571,10 +580,15 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
         if (lane == 0) base = atomicAdd(&W.cnt->cand, (unsigned long long)total);
         base = __shfl_sync(FULL_MASK, base, 0);
         unsigned long long pos = base + incl - cnt;
+        uint2 wit = make_uint2(0, 0);
+        if constexpr (WIT) {
+            if (nb) wit = witness(tag, k);
+        }
         for (uint32_t r = nb; r; r &= r - 1, pos++) {
             if (pos < W.cand_cap) {
                 W.cand_key[pos] = group_key(gi, wd * 32 + (__ffs(r) - 1));
                 W.cand_slot[pos] = slot;
+                if constexpr (WIT) W.cand_wit[pos] = wit;
             }
         }
         // the members' candidate counts (k_check sizes their pair sets)
@@ -585,17 +599,18 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
     auto key_of = [&](uint32_t wd, uint32_t tag) {
         return gi.tagged ? (tag << TAG_SHIFT) | wd : wd;
     };
-    // two tiles (w.x, w.y) and (w.z, w.w) of member tag, nv of them valid
-    auto consume_tiles = [&](uint4 w, uint32_t nv, uint32_t tag) {
+    // two tiles (w.x, w.y) and (w.z, w.w) of member tag, gathered through
+    // delta entry k, nv of them valid
+    auto consume_tiles = [&](uint4 w, uint32_t nv, uint32_t tag, uint32_t k) {
         const uint32_t n0 = nv > 0 ? acc.ins(key_of(w.x, tag), w.y) : 0u;
         const uint32_t n1 = nv > 1 ? acc.ins(key_of(w.z, tag), w.w) : 0u;
         if (__any_sync(FULL_MASK, (n0 | n1) != 0)) {
-            emit_bits(n0, w.x, tag);
-            emit_bits(n1, w.z, tag);
+            emit_bits(n0, w.x, tag, k);
+            emit_bits(n1, w.z, tag, k);
         }
     };
-    // the tile lists held by the lanes (toff, tn; member tag)
-    auto walk = [&](uint32_t toff, uint32_t tn, uint32_t tag) {
+    // the tile lists held by the lanes (toff, tn; member tag; delta entry k)
+    auto walk = [&](uint32_t toff, uint32_t tn, uint32_t tag, uint32_t k) {
         // long tile lists: the warp strides over one list at a time
         unsigned lm = __ballot_sync(FULL_MASK, tn >= 32);
         while (lm) {
@@ -604,6 +619,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
             const uint32_t *tl = pool + __shfl_sync(FULL_MASK, toff, l);
             const uint32_t T = __shfl_sync(FULL_MASK, tn, l);
             const uint32_t ltag = __shfl_sync(FULL_MASK, tag, l);
+            const uint32_t lk = WIT ? __shfl_sync(FULL_MASK, k, l) : 0u;
             for (uint32_t qb = 0; qb < T; qb += 128) {
                 uint4 w[2];
                 uint32_t nv[2];
@@ -622,8 +638,8 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                         nv[h] = 1;
                     }
                 }
-                consume_tiles(w[0], nv[0], ltag);
-                if (qb + 64 < T) consume_tiles(w[1], nv[1], ltag);
+                consume_tiles(w[0], nv[0], ltag, lk);
+                if (qb + 64 < T) consume_tiles(w[1], nv[1], ltag, lk);
             }
         }
         // short tile lists: packed, 32 tiles per step
@@ -644,6 +660,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
             const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
             const uint32_t o_len = __shfl_sync(FULL_MASK, stn, owner);
             const uint32_t o_tag = __shfl_sync(FULL_MASK, tag, owner);
+            const uint32_t o_kk = WIT ? __shfl_sync(FULL_MASK, k, owner) : 0u;
             uint4 w = make_uint4(0, 0, 0, 0);
             uint32_t nv = 0;
             if (f < total) {
@@ -653,7 +670,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                 w.y = t.y;
                 nv = 1;
             }
-            consume_tiles(w, nv, o_tag);
+            consume_tiles(w, nv, o_tag, o_kk);
         }
     };
     if (gi.part == PART_U) {        // c -> a: the delta entries themselves
@@ -665,7 +682,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                 wd = v >> 5;
                 nb = acc.ins(wd, 1u << (v & 31));
             }
-            if (__any_sync(FULL_MASK, nb != 0)) emit_bits(nb, wd, 0);
+            if (__any_sync(FULL_MASK, nb != 0)) emit_bits(nb, wd, 0, 0);
         }
         return emitted;
     }
@@ -718,7 +735,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                     toff = gd.x;
                     tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);
                 }
-                walk(toff, tn, tag);
+                walk(toff, tn, tag, o_k);
             }
         }
         return emitted;
@@ -730,10 +747,10 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
         for (unsigned long long ib = (unsigned long long)warp_id * 32; ib < items;
              ib += (unsigned long long)nwarps * 32) {
             const unsigned long long it = ib + lane;
-            uint32_t toff = 0, tn = 0, tag = 0;
+            uint32_t toff = 0, tn = 0, tag = 0, k = 0;
             if (it < items) {
                 const uint32_t e = (uint32_t)(it / gi.F), i = (uint32_t)(it - (unsigned long long)e * gi.F);
-                const uint32_t k = pool[dstart + e];
+                k = pool[dstart + e];
                 const uint4 pr = P.prod[P.fam_prod[gi.first + i]];
                 const uint32_t gs = (gi.part == PART_A) ? pr.z : pr.y;
                 const uint32_t lx = S.local[gs];
@@ -744,20 +761,20 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                     tag = i;
                 }
             }
-            walk(toff, tn, tag);
+            walk(toff, tn, tag, k);
         }
         return emitted;
     }
     for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
         const uint32_t e = cb + lane * nwarps;
-        uint32_t toff = 0, tn = 0;
+        uint32_t toff = 0, tn = 0, k = 0;
         if (e < d) {
-            const uint32_t k = pool[dstart + e];
+            k = pool[dstart + e];
             const uint4 gd = dg[k];
             toff = gd.x;
             tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);   // A_old for A . dB
         }
-        walk(toff, tn, 0);
+        walk(toff, tn, 0, k);
     }
     return emitted;
 }
@@ -777,7 +794,7 @@ __device__ __forceinline__ void preload_mask(const SlotTab &S, const GroupInfo &
 
 // Bins 0 and 1: one warp per group, a private shared-memory table per warp
 // (2^LG words and their bits).
-template <int LG, int WARPS>
+template <int LG, int WARPS, bool WIT>
 __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(SlotTab S, ProdTab P, WorkBufs W,
                                                             int bin) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -799,7 +816,7 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(
             __syncwarp();
         }
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows(S, P, W, gi, own, 0, 1, lane, acc);
+        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, 0, 1, lane, acc);
         if (lane == 0 && e) {
             if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)e);
             bytes += 12ull * e;
@@ -810,7 +827,7 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(
 }
 
 // Bin 2: one CTA per group sharing a 2^LG-word shared-memory table.
-template <int LG>
+template <int LG, bool WIT>
 __global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S, ProdTab P, WorkBufs W, int bin) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t emitted_sh;
@@ -827,7 +844,7 @@ __global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S,
         if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc);
+        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
@@ -842,6 +859,7 @@ __global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S,
 // memory when it fits, else a per-CTA slice of global scratch).  In mask mode
 // the mask row's bits are set first; in probe mode new bits are checked
 // against the non-terminal's hash set instead.
+template <bool WIT>
 __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, WorkBufs W,
                                                           int bin, int use_smem) {
     extern __shared__ uint32_t smem[];
@@ -860,7 +878,7 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
         if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc);
+        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
@@ -901,7 +919,11 @@ __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
                 if (v == key) break;
                 if (v == EMPTY_KEY) {
                     v = atomicCAS(&tab[h], EMPTY_KEY, key);
-                    if (v == EMPTY_KEY) { isnew = true; break; }
+                    if (v == EMPTY_KEY) {
+                        isnew = true;
+                        if (W.cand_wit && S.hval[slot]) S.hval[slot][h] = W.cand_wit[t];
+                        break;
+                    }
                     if (v == key) break;
                 }
                 h = (h + 1) & m;
@@ -1353,10 +1375,10 @@ __global__ void __launch_bounds__(256) k_init_edges(const uint32_t *src, const u
                                    (threadIdx.x & ~31u);
          base < n_edges; base += stride) {
         const unsigned long long e = base + lane;
-        uint32_t q0 = 0, q1 = 0;
+        uint32_t q0 = 0, q1 = 0, l = 0;
         unsigned long long key = 0;
         if (e < n_edges) {
-            const uint32_t l = lab[e];
+            l = lab[e];
             if (l < n_terms) { q0 = term_off[l]; q1 = term_off[l + 1]; }
             key = ((unsigned long long)src[e] << 32) | dst[e];
         }
@@ -1366,7 +1388,7 @@ __global__ void __launch_bounds__(256) k_init_edges(const uint32_t *src, const u
         for (uint32_t r = 0; r < rounds; r++) {
             const bool f = q0 + r < q1;
             const uint32_t slot = f ? term_slot[q0 + r] : 0;
-            emit_candidates(f, key, slot, W, lane);
+            emit_candidates(f, key, slot, W, lane, make_uint2(WIT_EDGE | (l & WIT_PAYLOAD), 0));
         }
     }
 }
@@ -1378,12 +1400,13 @@ __global__ void k_init_eps(uint32_t slot, uint32_t n, WorkBufs W) {
                                    (threadIdx.x & ~31u);
          base < n; base += stride) {
         const unsigned long long i = base + lane;
-        emit_candidates(i < n, (i << 32) | i, slot, W, lane);
+        emit_candidates(i < n, (i << 32) | i, slot, W, lane, make_uint2(WIT_EPS, 0));
     }
 }
 
-__global__ void k_rehash(const unsigned long long *old_tab, unsigned long long old_cap,
-                         unsigned long long *new_tab, unsigned long long new_cap) {
+__global__ void k_rehash(const unsigned long long *old_tab, const uint2 *old_val,
+                         unsigned long long old_cap, unsigned long long *new_tab,
+                         uint2 *new_val, unsigned long long new_cap) {
     const unsigned long long m = new_cap - 1;
     for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
          s < old_cap; s += (unsigned long long)gridDim.x * blockDim.x) {
@@ -1391,7 +1414,25 @@ __global__ void k_rehash(const unsigned long long *old_tab, unsigned long long o
         if (key == EMPTY_KEY) continue;
         unsigned long long h = pair_home(key, m);
         while (atomicCAS(&new_tab[h], EMPTY_KEY, key) != EMPTY_KEY) h = (h + 1) & m;
+        if (new_val) new_val[h] = old_val[s];
     }
+}
+
+// The recorded derivation step of one pair (single thread): {~0, ~0} when
+// the pair is not in the set.
+__global__ void k_witness_lookup(const unsigned long long *tab, const uint2 *val,
+                                 unsigned long long m, unsigned long long key, uint2 *out) {
+    unsigned long long h = pair_home(key, m);
+    for (unsigned long long probes = 0; probes <= m; probes++) {
+        const unsigned long long v = tab[h];
+        if (v == key) {
+            *out = val[h];
+            return;
+        }
+        if (v == EMPTY_KEY) break;
+        h = (h + 1) & m;
+    }
+    *out = make_uint2(EMPTY32, EMPTY32);
 }
 
 __global__ void k_fill_u64(unsigned long long *p, unsigned long long count,
@@ -1671,18 +1712,24 @@ constexpr size_t SMEM_BITMAP_MAX = 200 * 1024;
 static void set_smem_attrs();
 void prepare_launch_attributes() { set_smem_attrs(); }
 
+template <bool WIT>
+static void set_bin_smem_attrs() {
+    cudaFuncSetAttribute(k_spgemm_warp<11, 4, WIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)BIN1_SMEM);
+    cudaFuncSetAttribute(k_spgemm_cta<13, WIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)BIN2_SMEM);
+    cudaFuncSetAttribute(k_spgemm_warp<10, 8, WIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)BIN1S_SMEM);
+    cudaFuncSetAttribute(k_spgemm_bitmap<WIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SMEM_BITMAP_MAX);
+}
+
 static void set_smem_attrs() {
     static bool done = false;
     if (done) return;
     done = true;
-    cudaFuncSetAttribute(k_spgemm_warp<11, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)BIN1_SMEM);
-    cudaFuncSetAttribute(k_spgemm_cta<13>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)BIN2_SMEM);
-    cudaFuncSetAttribute(k_spgemm_warp<10, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)BIN1S_SMEM);
-    cudaFuncSetAttribute(k_spgemm_bitmap, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)SMEM_BITMAP_MAX);
+    set_bin_smem_attrs<false>();
+    set_bin_smem_attrs<true>();
     cudaFuncSetAttribute(k_extract_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)SMEM_BITMAP_MAX);
     cudaFuncSetAttribute(k_capacity_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1694,34 +1741,44 @@ void launch_symbolic(const SlotTab &S, const ProdTab &P, const WorkBufs &W, int 
     k_symbolic<<<sms * 8, 256, 0, st>>>(S, P, W, prod_only, T);
 }
 
-void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &W,
-                   uint32_t max_n, const Tuning &T, int sms, cudaStream_t st) {
-    set_smem_attrs();
+// The product bins, with the witness plumbing compiled in only when the
+// batch records witnesses (it costs registers).
+template <bool WIT>
+static void launch_bin(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &W,
+                       uint32_t max_n, const Tuning &T, int sms, cudaStream_t st) {
     switch (bin) {
     case 0:
-        k_spgemm_warp<8, 8><<<sms * T.ctas_per_sm[0], 256, BIN0_SMEM, st>>>(S, P, W, 0);
+        k_spgemm_warp<8, 8, WIT><<<sms * T.ctas_per_sm[0], 256, BIN0_SMEM, st>>>(S, P, W, 0);
         break;
     case 1:   // the smaller table when the limit allows it: more warps per SM
         if (T.limit[1] <= 512)
-            k_spgemm_warp<10, 8><<<sms * T.ctas_per_sm[1], 256, BIN1S_SMEM, st>>>(S, P, W, 1);
+            k_spgemm_warp<10, 8, WIT><<<sms * T.ctas_per_sm[1], 256, BIN1S_SMEM, st>>>(S, P, W, 1);
         else
-            k_spgemm_warp<11, 4><<<sms * T.ctas_per_sm[1], 128, BIN1_SMEM, st>>>(S, P, W, 1);
+            k_spgemm_warp<11, 4, WIT><<<sms * T.ctas_per_sm[1], 128, BIN1_SMEM, st>>>(S, P, W, 1);
         break;
     case 2:
         if (T.limit[2] <= 2048)
-            k_spgemm_cta<12><<<sms * T.ctas_per_sm[2], 256, BIN2S_SMEM, st>>>(S, P, W, 2);
+            k_spgemm_cta<12, WIT><<<sms * T.ctas_per_sm[2], 256, BIN2S_SMEM, st>>>(S, P, W, 2);
         else
-            k_spgemm_cta<13><<<sms * T.ctas_per_sm[2], 256, BIN2_SMEM, st>>>(S, P, W, 2);
+            k_spgemm_cta<13, WIT><<<sms * T.ctas_per_sm[2], 256, BIN2_SMEM, st>>>(S, P, W, 2);
         break;
     default: {
         const size_t bm_bytes = (size_t)((max_n + 31) / 32) * 4;
         const bool sm = bm_bytes <= SMEM_BITMAP_MAX;
         int per_sm = sm ? (int)((220 * 1024) / (bm_bytes + 1024)) : 4;
         per_sm = per_sm < 1 ? 1 : (per_sm > (int)T.ctas_per_sm[3] ? (int)T.ctas_per_sm[3] : per_sm);
-        k_spgemm_bitmap<<<sms * per_sm, 256, sm ? bm_bytes : 0, st>>>(S, P, W, 3, sm ? 1 : 0);
+        k_spgemm_bitmap<WIT><<<sms * per_sm, 256, sm ? bm_bytes : 0, st>>>(S, P, W, 3,
+                                                                          sm ? 1 : 0);
         break;
     }
     }
+}
+
+void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &W,
+                   uint32_t max_n, const Tuning &T, int sms, cudaStream_t st) {
+    set_smem_attrs();
+    if (W.cand_wit) launch_bin<true>(bin, S, P, W, max_n, T, sms, st);
+    else launch_bin<false>(bin, S, P, W, max_n, T, sms, st);
 }
 
 void launch_commit(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {
@@ -1782,10 +1839,17 @@ void launch_init_eps(uint32_t slot, uint32_t n, const WorkBufs &W, int sms, cuda
     k_init_eps<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(slot, n, W);
 }
 
-void launch_rehash(const unsigned long long *old_tab, unsigned long long old_cap,
-                   unsigned long long *new_tab, unsigned long long new_cap, int sms,
-                   cudaStream_t st) {
-    k_rehash<<<grid_for(old_cap, 256, sms, 8), 256, 0, st>>>(old_tab, old_cap, new_tab, new_cap);
+void launch_rehash(const unsigned long long *old_tab, const uint2 *old_val,
+                   unsigned long long old_cap, unsigned long long *new_tab, uint2 *new_val,
+                   unsigned long long new_cap, int sms, cudaStream_t st) {
+    k_rehash<<<grid_for(old_cap, 256, sms, 8), 256, 0, st>>>(old_tab, old_val, old_cap, new_tab,
+                                                              new_val, new_cap);
+}
+
+void launch_witness_lookup(const unsigned long long *tab, const uint2 *val,
+                           unsigned long long mask, unsigned long long key, uint2 *out,
+                           cudaStream_t st) {
+    k_witness_lookup<<<1, 1, 0, st>>>(tab, val, mask, key, out);
 }
 
 void launch_fill_u64(unsigned long long *p, unsigned long long count, unsigned long long v,

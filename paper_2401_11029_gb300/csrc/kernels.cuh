@@ -71,6 +71,13 @@ __host__ __device__ __forceinline__ uint32_t tile_words(uint32_t tiles) {
     return (2 * tiles + 3) & ~3u;
 }
 
+// Derivation step of a pair (single-path semantics), kept beside its key in
+// the pair set when witnesses are on: .x = kind | payload, .y = the middle
+// vertex (stored id) of a binary step.  Payloads: local ids a << 15 | b
+// (binary), a (unit), the label (edge).
+constexpr uint32_t WIT_BINARY = 0u << 30, WIT_EDGE = 1u << 30, WIT_UNIT = 2u << 30,
+                   WIT_EPS = 3u << 30, WIT_PAYLOAD = (1u << 30) - 1;
+
 struct SlotTab {              // per slot (device arrays, length n_slots)
     uint4 **desc;             // row descriptors (2*n per slot)
     uint2 **dn;               // delta counts and append cursors (2*n per slot)
@@ -78,6 +85,7 @@ struct SlotTab {              // per slot (device arrays, length n_slots)
     uint32_t *n;              // vertices of the slot's instance
     uint32_t *inst;           // instance index of the slot
     unsigned long long **htab;
+    uint2 **hval;                   // witnesses beside htab's keys (null: off)
     unsigned long long *hmask;      // capacity - 1
     unsigned long long *cand;       // candidates emitted for the slot (iteration)
     unsigned long long *delta;      // new pairs of the slot (iteration)
@@ -158,6 +166,7 @@ struct WorkBufs {
     unsigned long long touched_cap;
     uint2 *groups[N_BINS]; unsigned long long group_cap[N_BINS];   // {code, idx}
     unsigned long long *cand_key; uint32_t *cand_slot; unsigned long long cand_cap;
+    uint2 *cand_wit;                   // witness of each candidate (null: off)
     unsigned long long *delta_key; uint32_t *delta_slot;
     uint32_t *bitmap_scratch; unsigned long long bitmap_words;  // per CTA, global
     Counters *cnt;
@@ -198,9 +207,16 @@ void launch_init_edges(const uint32_t *src, const uint32_t *lab, const uint32_t 
                        const uint32_t *term_slot, uint32_t n_terms, const WorkBufs &W,
                        int sms, cudaStream_t st);
 void launch_init_eps(uint32_t slot, uint32_t n, const WorkBufs &W, int sms, cudaStream_t st);
-void launch_rehash(const unsigned long long *old_tab, unsigned long long old_cap,
-                   unsigned long long *new_tab, unsigned long long new_cap, int sms,
-                   cudaStream_t st);
+// Move a pair set (and its witnesses, when val pointers are non-null) into
+// a larger table.
+void launch_rehash(const unsigned long long *old_tab, const uint2 *old_val,
+                   unsigned long long old_cap, unsigned long long *new_tab, uint2 *new_val,
+                   unsigned long long new_cap, int sms, cudaStream_t st);
+// The witness of pair `key` in a pair set of capacity mask + 1, written to
+// *out ({~0, ~0} when the pair is absent).
+void launch_witness_lookup(const unsigned long long *tab, const uint2 *val,
+                           unsigned long long mask, unsigned long long key, uint2 *out,
+                           cudaStream_t st);
 void launch_fill_u64(unsigned long long *p, unsigned long long count, unsigned long long v,
                      int sms, cudaStream_t st);
 void launch_remap_touched(const uint2 *in, unsigned long long n, uint32_t slot_base,

@@ -109,6 +109,7 @@ struct cflr_ctx {
     uint64_t pool_cap = 0;
     uint64_t pool_top = 0;              // host mirror between solves
     std::vector<unsigned long long *> htab;
+    std::vector<uint2 *> hval;          // witnesses beside htab (cfg.witness only)
     std::vector<uint64_t> hcap;
     std::vector<uint64_t> nnz;
     uint2 *touched = nullptr;           // rows with dnew > 0 (local slot ids)
@@ -217,9 +218,12 @@ struct cflr_ctx {
         if (pool) dfree(pool, pool_cap * 4);
         pool = nullptr;
         pool_cap = pool_top = 0;
-        for (size_t s = 0; s < htab.size(); s++)
+        for (size_t s = 0; s < htab.size(); s++) {
             if (htab[s]) dfree(htab[s], hcap[s] * 8);
+            if (s < hval.size() && hval[s]) dfree(hval[s], hcap[s] * 8);
+        }
         htab.clear();
+        hval.clear();
         hcap.clear();
         nnz.clear();
         if (touched) dfree(touched, touched_cap * sizeof(uint2));
@@ -326,6 +330,9 @@ struct Runner {
     DevArr<uint32_t> d_n, d_inst, d_occw, d_local;
     DevArr<uint32_t *> d_occ;
     DevArr<unsigned long long *> d_htab;
+    DevArr<uint2 *> d_hval;
+    DevArr<uint2> d_cand_wit;
+    bool wit = false;                  // some context of the batch records witnesses
     DevArr<unsigned long long> d_hmask, d_cand, d_delta, d_nnz;
     DevArr<unsigned long long> d_pool_top, d_pool_cap, d_inst_delta;
     DevArr<uint32_t> d_inst_active, d_inst_iters, d_inst_base;
@@ -408,6 +415,9 @@ struct Runner {
         cx = std::move(ctxs);
         regrows = 0;
         drop_graph();
+        wit = false;
+        for (auto *c : cx) wit |= c->cfg.witness != 0;
+        if (wit && cand_cap && d_cand_wit.n < cand_cap) d_cand_wit.alloc(own, cand_cap);
         base.clear();
         slot_ctx.clear();
         n_slots = 0;
@@ -531,6 +541,7 @@ struct Runner {
         d_n.ensure(own, n_slots);
         d_inst.ensure(own, n_slots);
         d_htab.ensure(own, n_slots);
+        d_hval.ensure(own, n_slots);
         d_hmask.ensure(own, n_slots);
         d_cand.ensure(own, n_slots);
         d_delta.ensure(own, n_slots);
@@ -585,14 +596,18 @@ struct Runner {
 
     void upload_htabs() {
         std::vector<unsigned long long *> ht(n_slots);
+        std::vector<uint2 *> hv(n_slots);
         std::vector<unsigned long long> hm(n_slots);
         for (uint32_t s = 0; s < n_slots; s++) {
             cflr_ctx *c = cx[slot_ctx[s]];
             uint32_t x = s - base[slot_ctx[s]];
             ht[s] = c->htab[x];
+            hv[s] = x < c->hval.size() ? c->hval[x] : nullptr;
             hm[s] = c->hcap[x] - 1;
         }
         ck(cudaMemcpyAsync(d_htab.p, ht.data(), n_slots * 8, cudaMemcpyHostToDevice, st), "H2D");
+        ck(cudaMemcpyAsync(d_hval.p, hv.data(), n_slots * sizeof(uint2 *), cudaMemcpyHostToDevice,
+                           st), "H2D");
         ck(cudaMemcpyAsync(d_hmask.p, hm.data(), n_slots * 8, cudaMemcpyHostToDevice, st), "H2D");
         sync("upload htabs");
     }
@@ -633,7 +648,7 @@ struct Runner {
     SlotTab slots() {
         SlotTab S;
         S.desc = d_desc.p; S.dn = d_dn.p; S.pool = d_pool.p; S.n = d_n.p; S.inst = d_inst.p;
-        S.htab = d_htab.p; S.hmask = d_hmask.p; S.cand = d_cand.p; S.delta = d_delta.p;
+        S.htab = d_htab.p; S.hval = d_hval.p; S.hmask = d_hmask.p; S.cand = d_cand.p; S.delta = d_delta.p;
         S.nnz = d_nnz.p;
         S.occ = d_occ.p; S.occ_w = d_occw.p; S.local = d_local.p;
         return S;
@@ -663,6 +678,7 @@ struct Runner {
             W.group_cap[b] = group_cap[b];
         }
         W.cand_key = d_cand_key.p; W.cand_slot = d_cand_slot.p; W.cand_cap = cand_cap;
+        W.cand_wit = wit ? d_cand_wit.p : nullptr;
         W.delta_key = d_delta_key.p; W.delta_slot = d_delta_slot.p;
         W.bitmap_scratch = d_bitmap.p;
         W.bitmap_words = (max_n + 31) / 32;
@@ -682,6 +698,7 @@ struct Runner {
         cand_cap = cap;
         d_cand_key.alloc(own, cap);
         d_cand_slot.alloc(own, cap);
+        if (wit) d_cand_wit.alloc(own, cap);
         d_delta_key.alloc(own, cap);
         d_delta_slot.alloc(own, cap);
         graph_valid = false;
@@ -732,11 +749,16 @@ struct Runner {
         uint64_t cap = next_pow2(std::max<uint64_t>(4 * need, 1024));
         unsigned long long *nt = (unsigned long long *)alloc_for(c, cap * 8);
         ck(cudaMemsetAsync(nt, 0xFF, cap * 8, st), "memset");
-        prof.run(KID_REHASH, [&] { launch_rehash(c->htab[x], c->hcap[x], nt, cap, sms, st); });
+        uint2 *nv = c->hval[x] ? (uint2 *)alloc_for(c, cap * 8) : nullptr;
+        prof.run(KID_REHASH, [&] {
+            launch_rehash(c->htab[x], c->hval[x], c->hcap[x], nt, nv, cap, sms, st);
+        });
         own->k_bytes[KID_REHASH] += c->hcap[x] * 8 + need * 8;
         sync("rehash");
         c->dfree(c->htab[x], c->hcap[x] * 8);
+        if (c->hval[x]) c->dfree(c->hval[x], c->hcap[x] * 8);
         c->htab[x] = nt;
+        c->hval[x] = nv;
         c->hcap[x] = cap;
         regrows++;
     }
@@ -1131,7 +1153,10 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
         c->pool_cap = std::min<uint64_t>(std::max<uint64_t>(c->pool_cap, 3 * expect),
                                          0xFFFFFFF0ull);
     c->pool = (uint32_t *)c->dalloc(c->pool_cap * 4);
+    if (c->cfg.witness && nt > 32768)
+        throw Status{CFLR_EINVAL, "witnesses need at most 32768 non-terminals"};
     c->htab.assign(nt, nullptr);
+    c->hval.assign(nt, nullptr);
     c->hcap.assign(nt, 0);
     c->nnz.assign(nt, 0);
     for (uint32_t A = 0; A < nt; A++) {
@@ -1139,6 +1164,7 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
         if (A < g.n_named) want = std::max<uint64_t>(want, 2 * share);
         c->hcap[A] = next_pow2(want);
         c->htab[A] = (unsigned long long *)c->dalloc(c->hcap[A] * 8);
+        if (c->cfg.witness) c->hval[A] = (uint2 *)c->dalloc(c->hcap[A] * 8);
     }
 }
 
@@ -1514,6 +1540,65 @@ int cflr_get_pairs_device(const cflr_ctx *cc, uint32_t nonterminal, uint32_t *d_
                           uint32_t *d_dst, uint64_t capacity, uint64_t *n_pairs) {
     return get_pairs_common(const_cast<cflr_ctx *>(cc), nonterminal, d_src, d_dst, capacity,
                             n_pairs, true);
+}
+
+int cflr_get_witness(const cflr_ctx *cc, uint32_t nonterminal, uint32_t src, uint32_t dst,
+                     int *kind, uint32_t *id, uint32_t *id2, uint32_t *mid) {
+    cflr_ctx *c = const_cast<cflr_ctx *>(cc);
+    if (!c || !kind) return CFLR_EINVAL;
+    if (c->state < ST_GRAPH) return c->fail(CFLR_ESTATE, "no graph loaded");
+    if (!c->cfg.witness) return c->fail(CFLR_ESTATE, "the context records no witnesses");
+    if (nonterminal >= c->g.nts.size()) return c->fail(CFLR_EINVAL, "bad non-terminal id");
+    if (src >= c->n || dst >= c->n) return c->fail(CFLR_EINVAL, "vertex id out of range");
+    try {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        cudaStream_t st = c->stream;
+        uint32_t s = src, d = dst;
+        if (c->perm) {      // stored ids
+            ck(cudaMemcpyAsync(&s, c->perm + src, 4, cudaMemcpyDeviceToHost, st), "D2H");
+            ck(cudaMemcpyAsync(&d, c->perm + dst, 4, cudaMemcpyDeviceToHost, st), "D2H");
+            ck(cudaStreamSynchronize(st), "sync");
+        }
+        uint2 *out = (uint2 *)c->dalloc(sizeof(uint2));
+        launch_witness_lookup(c->htab[nonterminal], c->hval[nonterminal],
+                              c->hcap[nonterminal] - 1, ((unsigned long long)s << 32) | d, out,
+                              st);
+        uint2 w;
+        ck(cudaMemcpyAsync(&w, out, sizeof(uint2), cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaStreamSynchronize(st), "sync witness");
+        c->dfree(out, sizeof(uint2));
+        if (w.x == EMPTY32 && w.y == EMPTY32)
+            return c->fail(CFLR_EINVAL, "the pair is not in the relation");
+        const uint32_t k = w.x >> 30, pay = w.x & WIT_PAYLOAD;
+        *kind = (int)k;
+        uint32_t a = 0, b = 0, m = 0;
+        if (w.x >= WIT_EPS) {
+            *kind = CFLR_WIT_EPS;
+        } else if (k == 0) {
+            *kind = CFLR_WIT_BINARY;
+            a = pay >> 15;
+            b = pay & 0x7FFF;
+            m = w.y;
+            if (c->iperm) {
+                ck(cudaMemcpyAsync(&m, c->iperm + w.y, 4, cudaMemcpyDeviceToHost, st), "D2H");
+                ck(cudaStreamSynchronize(st), "sync");
+            }
+        } else if (k == 1) {
+            *kind = CFLR_WIT_EDGE;
+            a = pay;
+        } else {
+            *kind = CFLR_WIT_UNIT;
+            a = pay;
+        }
+        if (id) *id = a;
+        if (id2) *id2 = b;
+        if (mid) *mid = m;
+        return CFLR_OK;
+    } catch (const Status &e) {
+        return finish_status(c, e);
+    } catch (const CudaError &e) {
+        return cuda_status(c, e);
+    }
 }
 
 int cflr_get_tuning(const cflr_ctx *c, cflr_tuning *t) {

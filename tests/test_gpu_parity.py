@@ -470,3 +470,66 @@ def test_autotune_cache_path_is_copied_at_create(tmp_path):
     finally:
         cflr.cflr_destroy(s.ctx)
     assert open(cache).read().count("\n") == 1
+
+
+@pytest.mark.parametrize("name", ["dyck1", "fica", "fsca2", "cscvf2", "fsjpt2"])
+def test_witness_steps_rebuild_valid_paths(name):
+    """Single-path semantics (cfg.witness): the pair sets are unchanged, every
+    recorded step of a sampled pair is a production whose operand pairs the
+    oracle holds (or an edge of the graph), and the path those steps rebuild
+    joins the pair over the graph's edges; short paths' label words are
+    checked with CYK too."""
+    from pins import CYK
+    text, labels = GRAMMARS[name]
+    g = gen.random_graph(n=50, n_edges=140, labels=labels, seed=61)
+    want = oracle.solve(text, g)
+    pg = want.grammar
+    binary = set(pg.binary)
+    unit = set(pg.unit)
+    eps = set(pg.eps)
+    term = {(A, x) for x, As in pg.term.items() for A in As}
+    edges = {(int(a), g.labels[l], int(b)) for a, l, b in zip(g.src, g.lab, g.dst)}
+    pairs = {pg.nt_id(x): set(map(int, want.pairs[x])) for x in pg.nts}
+    cyk = CYK(text)
+    rng = np.random.default_rng(5)
+    with Solver(text, witness=1) as s:
+        s.load(g)
+        s.solve()
+        lib_of = {s.nt_id(x): pg.nt_id(x) for x in pg.nts}     # library id -> oracle id
+        ids = s.label_ids(g.labels)
+        label_name = {int(i): lab for i, lab in zip(ids, g.labels) if i != 0xFFFFFFFF}
+        for x in pg.nts[:pg.n_user]:
+            keys = want.pairs[x]
+            assert np.array_equal(s.pairs(x), keys), x
+            if keys.size == 0:
+                continue
+            for key in rng.choice(keys, size=min(12, keys.size), replace=False):
+                u, v = int(key >> 32), int(key & 0xFFFFFFFF)
+                # every step of the derivation, checked against the oracle
+                stack = [(s.nt_id(x), u, v)]
+                while stack:
+                    X, a, b = stack.pop()
+                    kind, i1, i2, m = cflr.cflr_get_witness(s.ctx, X, a, b)
+                    ox = lib_of[X]
+                    if kind == cflr.CFLR_WIT_EDGE:
+                        assert (ox, label_name[i1]) in term and (a, label_name[i1], b) in edges
+                    elif kind == cflr.CFLR_WIT_EPS:
+                        assert a == b and ox in eps
+                    elif kind == cflr.CFLR_WIT_UNIT:
+                        assert (ox, lib_of[i1]) in unit
+                        assert (a << 32) | b in pairs[lib_of[i1]]
+                        stack.append((i1, a, b))
+                    else:
+                        assert (ox, lib_of[i1], lib_of[i2]) in binary
+                        assert (a << 32) | m in pairs[lib_of[i1]]
+                        assert (m << 32) | b in pairs[lib_of[i2]]
+                        stack.append((i2, m, b))
+                        stack.append((i1, a, m))
+                path = s.path(x, u, v, label_name)
+                cur = u
+                for a, lab, b in path:
+                    assert a == cur and (a, lab, b) in edges
+                    cur = b
+                assert cur == v
+                if len(path) <= 12:
+                    assert x in cyk.derives(tuple(lab for _, lab, _ in path))
