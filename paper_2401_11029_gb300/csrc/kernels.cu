@@ -108,6 +108,7 @@ struct HashAcc {
         if ((ob & b) == b) return 0;
         return b & ~atomicOr(&tab[2 * s + 1], b);
     }
+    __device__ __forceinline__ void set(uint32_t w, uint32_t b) const { ins(w, b); }
 };
 
 // Empty all 2^lg slots of a table (16-byte aligned, lg >= 1); thread tid of nth.
@@ -126,6 +127,8 @@ struct BitmapAcc {
         if ((ob & b) == b) return 0;
         return b & ~atomicOr(&bm[w], b);
     }
+    // bits whose newness nobody asks (the mask row): one atomic, no read
+    __device__ __forceinline__ void set(uint32_t w, uint32_t b) const { atomicOr(&bm[w], b); }
 };
 
 __device__ __forceinline__ bool htab_contains(const unsigned long long *tab,
@@ -788,7 +791,7 @@ __device__ __forceinline__ void preload_mask(const SlotTab &S, const GroupInfo &
     const uint32_t *tl = S.pool[gi.c] + md.x;
     for (uint32_t q = tid; q < md.y; q += nth) {
         const uint2 t = *reinterpret_cast<const uint2 *>(tl + 2 * q);
-        acc.ins(t.x, t.y);
+        acc.set(t.x, t.y);
     }
 }
 
@@ -1253,6 +1256,16 @@ __global__ void __launch_bounds__(256) k_pack(SlotTab S, WorkBufs W) {
         const uint32_t w = S.dn[slot][r].x;
         const uint32_t *ent = S.pool[slot] + dsc.x + tile_words(dsc.z);
         uint32_t *tl = S.pool[slot] + dsc.x;
+        if (w == 1) {                  // one new pair: one tile, no table
+            if (lane == 0) {
+                const uint32_t v = ent[0];
+                reinterpret_cast<uint2 *>(tl)[dsc.y] = make_uint2(v >> 5, 1u << (v & 31));
+                dp->y = dsc.y + 1;
+                dp->w = (dsc.w & ~DLAST_MASK) | 1u;
+            }
+            __syncwarp();
+            continue;
+        }
         uint32_t nt = dsc.y;
         for (uint32_t c0 = 0; c0 < w; c0 += TILE_WARP_MAX) {
             const uint32_t cnt = min(TILE_WARP_MAX, w - c0);
