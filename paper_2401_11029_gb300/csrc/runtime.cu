@@ -1711,7 +1711,8 @@ int cflr_autotune(cflr_ctx *c, uint32_t max_trials, cflr_tuning *best) {
     const std::vector<std::pair<int, std::vector<uint32_t>>> fields = {
         {0, {1, 2, 8, 16, 64}},             // probe_ratio
         {5, {4, 6, 8}},                     // ctas_per_sm[3] (bitmap bin)
-        {3, {1024, 2048, 3072}},            // limit[2]
+        {3, {0, 1024, 2048, 3072}},         // limit[2]; 0: limit[1] + 1, bin 2 off
+                                            // (the bitmap bin takes those groups)
         {2, {256, 512}},                    // limit[1]
         {4, {2, 4}},                        // ctas_per_sm[2]
         {6, {2, 4, 6}},                     // ctas_per_sm[1]
@@ -1720,7 +1721,7 @@ int cflr_autotune(cflr_ctx *c, uint32_t max_trials, cflr_tuning *best) {
         switch (field) {
         case 0: t.probe_ratio = v; break;
         case 2: t.limit[1] = v; break;
-        case 3: t.limit[2] = v; break;
+        case 3: t.limit[2] = v ? v : t.limit[1] + 1; break;
         case 4: t.ctas_per_sm[2] = v; break;
         case 5: t.ctas_per_sm[3] = v; break;
         case 6: t.ctas_per_sm[1] = v; break;
