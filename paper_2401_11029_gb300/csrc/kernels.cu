@@ -862,34 +862,46 @@ __global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S,
 // memory when it fits, else a per-CTA slice of global scratch).  In mask mode
 // the mask row's bits are set first; in probe mode new bits are checked
 // against the non-terminal's hash set instead.
-template <bool WIT>
+template <bool WIT, int GPC>
 __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, WorkBufs W,
-                                                          int bin, int use_smem) {
-    extern __shared__ uint32_t smem[];
-    __shared__ uint32_t emitted_sh;
+                                                          int bin, int use_smem,
+                                                          uint32_t bm_stride) {
+    // GPC groups at a time: each half (quarter, ...) of the CTA has its own
+    // bitmap and its own named barrier, so a short group does not hold the
+    // others up and twice the groups are in flight per SM
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ uint32_t emitted_sh[GPC];
+    constexpr int TPG = 256 / GPC;                    // threads per group
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int part = threadIdx.x / TPG, ptid = threadIdx.x % TPG;
+    auto psync = [&]() {
+        if (GPC == 1) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(part + 1), "r"(TPG) : "memory");
+    };
     const unsigned long long n_groups = min(W.cnt->groups[bin], W.group_cap[bin]);
-    uint32_t *bm = use_smem ? smem : W.bitmap_scratch + (size_t)blockIdx.x * W.bitmap_words;
+    uint32_t *bm = use_smem ? smem + (size_t)part * bm_stride
+                            : W.bitmap_scratch + ((size_t)blockIdx.x * GPC + part) * W.bitmap_words;
     const BitmapAcc acc{bm};
     unsigned long long bytes = 0;
-    for (unsigned long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
+    for (unsigned long long g = (unsigned long long)blockIdx.x * GPC + part; g < n_groups;
+         g += (unsigned long long)gridDim.x * GPC) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
         const uint32_t words = (gi.n + 31) >> 5;
-        for (uint32_t s = threadIdx.x; s < words; s += blockDim.x) bm[s] = 0;
-        if (threadIdx.x == 0) emitted_sh = 0;
-        __syncthreads();
-        if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
-        __syncthreads();
+        for (uint32_t s = ptid; s < words; s += TPG) bm[s] = 0;
+        if (ptid == 0) emitted_sh[part] = 0;
+        psync();
+        if (!gi.probe) preload_mask(S, gi, acc, ptid, TPG);
+        psync();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc);
-        if (lane == 0 && e) atomicAdd(&emitted_sh, e);
-        __syncthreads();
-        if (threadIdx.x == 0 && emitted_sh) {
-            if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)emitted_sh);
-            bytes += 12ull * emitted_sh;
+        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, wib % (8 / GPC), 8 / GPC, lane, acc);
+        if (lane == 0 && e) atomicAdd(&emitted_sh[part], e);
+        psync();
+        if (ptid == 0 && emitted_sh[part]) {
+            if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)emitted_sh[part]);
+            bytes += 12ull * emitted_sh[part];
         }
     }
-    if (threadIdx.x == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
+    if (ptid == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
 }
 
 // ---------------------------------------------------------------------------
@@ -1733,7 +1745,9 @@ static void set_bin_smem_attrs() {
                          (int)BIN2_SMEM);
     cudaFuncSetAttribute(k_spgemm_warp<10, 8, WIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)BIN1S_SMEM);
-    cudaFuncSetAttribute(k_spgemm_bitmap<WIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_spgemm_bitmap<WIT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SMEM_BITMAP_MAX);
+    cudaFuncSetAttribute(k_spgemm_bitmap<WIT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)SMEM_BITMAP_MAX);
 }
 
@@ -1776,12 +1790,20 @@ static void launch_bin(int bin, const SlotTab &S, const ProdTab &P, const WorkBu
             k_spgemm_cta<13, WIT><<<sms * T.ctas_per_sm[2], 256, BIN2_SMEM, st>>>(S, P, W, 2);
         break;
     default: {
-        const size_t bm_bytes = (size_t)((max_n + 31) / 32) * 4;
+        // bitmap words rounded to 16 bytes; two groups per CTA when four CTAs
+        // of two bitmaps fit the shared memory (then registers, not shared
+        // memory, bound the CTAs per SM either way)
+        const uint32_t words = ((max_n + 31) / 32 + 3) & ~3u;
+        const size_t bm_bytes = (size_t)words * 4;
         const bool sm = bm_bytes <= SMEM_BITMAP_MAX;
-        int per_sm = sm ? (int)((220 * 1024) / (bm_bytes + 1024)) : 4;
+        const bool two = sm && 8 * (bm_bytes + 512) <= 220 * 1024;
+        int per_sm = sm ? (int)((220 * 1024) / ((two ? 2 : 1) * bm_bytes + 1024)) : 4;
         per_sm = per_sm < 1 ? 1 : (per_sm > (int)T.ctas_per_sm[3] ? (int)T.ctas_per_sm[3] : per_sm);
-        k_spgemm_bitmap<WIT><<<sms * per_sm, 256, sm ? bm_bytes : 0, st>>>(S, P, W, 3,
-                                                                          sm ? 1 : 0);
+        if (two)
+            k_spgemm_bitmap<WIT, 2><<<sms * per_sm, 256, 2 * bm_bytes, st>>>(S, P, W, 3, 1, words);
+        else
+            k_spgemm_bitmap<WIT, 1><<<sms * per_sm, 256, sm ? bm_bytes : 0, st>>>(S, P, W, 3,
+                                                                                 sm ? 1 : 0, words);
         break;
     }
     }
