@@ -395,7 +395,8 @@ def run_cflr(args):
 
 
 def run_dyck3_batch(args):
-    """Config 4: 256 independent Dyck-3 instances.  Times the solve of all of
+    """The batched workload: 256 independent Dyck-3 instances (1k-50k vertices
+    each, log-uniform).  Times the solve of all of
     them as one batch (every production of every instance in one launch
     sequence per iteration, the iterations looping inside one CUDA graph)
     against solving each alone in the plain per-production form; both after
@@ -479,7 +480,7 @@ def _gen_request(args):
 
 
 def run_serving(args):
-    """Config 5: a Poisson stream of alias-analysis solves (sizes log-uniform
+    """The serving workload: a Poisson stream of alias-analysis solves (sizes log-uniform
     in [5k, 300k] vertices) served with continuous batching; p50/p99 latency
     from arrival to result on the host, after a warm-up window."""
     import multiprocessing as mp

@@ -1044,23 +1044,55 @@ Runner &runner_of(cflr_ctx *c) {
 // caller id of stored vertex k.
 std::vector<uint32_t> locality_order(uint32_t n, uint64_t m, const uint32_t *src,
                                      const uint32_t *dst) {
-    std::vector<uint64_t> off((size_t)n + 1, 0);
+    // Scratch kept per host thread: a server loads many graphs, and fresh
+    // buffers would page-fault on every load.
+    thread_local std::vector<uint64_t> boff, half, off;
+    thread_local std::vector<uint32_t> adj, cnt;
+    thread_local std::vector<uint8_t> seen;
+    // undirected adjacency (CSR) in two cache-friendly passes: the 2m
+    // half-edges go to buckets of 4096 consecutive sources (sequential
+    // writes), then each bucket is counting-sorted by source; the order of
+    // each vertex's neighbours is the edge order, as a direct fill gives
+    const uint32_t SH = 12;
+    const uint32_t nb = (n >> SH) + 1;
+    boff.assign((size_t)nb + 1, 0);
     for (uint64_t e = 0; e < m; e++) {
-        off[(size_t)src[e] + 1]++;
-        off[(size_t)dst[e] + 1]++;
+        boff[(src[e] >> SH) + 1]++;
+        boff[(dst[e] >> SH) + 1]++;
     }
-    for (uint32_t v = 0; v < n; v++) off[v + 1] += off[v];
-    std::vector<uint32_t> adj(2 * m);
+    for (uint32_t b = 0; b < nb; b++) boff[b + 1] += boff[b];
+    if (half.size() < 2 * m) half.resize(2 * m);
     {
-        std::vector<uint64_t> cur(off.begin(), off.end() - 1);
+        std::vector<uint64_t> cur(boff.begin(), boff.end() - 1);
         for (uint64_t e = 0; e < m; e++) {
-            adj[cur[src[e]]++] = dst[e];
-            adj[cur[dst[e]]++] = src[e];
+            half[cur[src[e] >> SH]++] = ((uint64_t)src[e] << 32) | dst[e];
+            half[cur[dst[e] >> SH]++] = ((uint64_t)dst[e] << 32) | src[e];
         }
     }
+    off.assign((size_t)n + 1, 0);
+    if (adj.size() < 2 * m) adj.resize(2 * m);
+    cnt.assign((size_t)1 << SH, 0);
+    for (uint32_t b = 0; b < nb; b++) {
+        const uint32_t v0 = b << SH;
+        const uint32_t vn = std::min<uint32_t>(n - std::min(n, v0), 1u << SH);
+        std::fill(cnt.begin(), cnt.begin() + vn, 0);
+        for (uint64_t q = boff[b]; q < boff[b + 1]; q++) cnt[(uint32_t)(half[q] >> 32) - v0]++;
+        uint64_t acc = boff[b];
+        for (uint32_t i = 0; i < vn; i++) {
+            off[v0 + i] = acc;
+            const uint32_t c = cnt[i];
+            cnt[i] = (uint32_t)(acc - boff[b]);
+            acc += c;
+        }
+        for (uint64_t q = boff[b]; q < boff[b + 1]; q++) {
+            const uint32_t s = (uint32_t)(half[q] >> 32) - v0;
+            adj[boff[b] + cnt[s]++] = (uint32_t)half[q];
+        }
+    }
+    off[n] = 2 * m;
     std::vector<uint32_t> order;
     order.reserve(n);
-    std::vector<uint8_t> seen(n, 0);
+    seen.assign(n, 0);
     for (uint32_t s = 0; s < n; s++) {
         if (seen[s]) continue;
         seen[s] = 1;
