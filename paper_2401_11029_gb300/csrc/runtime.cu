@@ -735,7 +735,12 @@ struct Runner {
         const uint64_t ic = own->cfg.initial_capacity;
         size_cand(ic ? std::max<uint64_t>(ic, 32) : cand_hint);
         size_touched(std::max<uint64_t>(2 * cand_cap, touched_in), -1);
-        for (int b = 0; b < N_BINS; b++) size_groups(b, ic ? ic : (b < 2 ? 1 << 18 : 1 << 14));
+        // work lists: the lightest bins take most groups; a solve touching
+        // many rows starts with room for about one group per row
+        for (int b = 0; b < N_BINS; b++)
+            size_groups(b, ic ? ic
+                              : std::max<uint64_t>(b < 2 ? 1 << 18 : 1 << 14,
+                                                   b < 2 ? touched_in : touched_in / 8));
         if (max_n > 200 * 1024 * 8) {   // bitmaps do not fit shared memory
             uint64_t words = (max_n + 31) / 32;
             d_bitmap.ensure(own, words * (uint64_t)sms * 8);
@@ -862,19 +867,27 @@ struct Runner {
         ck(cudaMemsetAsync(&d_cnt.p->overflow, 0, sizeof(unsigned), st), "memset");
     }
 
+    // New size of a work buffer that overflowed at `count` entries.  The
+    // counts keep rising for several iterations and an overflow costs the
+    // iteration's products, so the buffers triple (half again under a
+    // memory budget).
+    uint64_t regrow_size(uint64_t count) const {
+        return own->cfg.mem_budget_bytes ? count * 3 / 2 : count * 3;
+    }
+
     // Grow what the last (stopped) iteration overflowed and finish it.
     // Returns false when the iteration must be run again from its start.
     bool recover() {
         const unsigned st_bits = h_ctl->status;
         if (st_bits & (OVF_GROUPS | OVF_CAND)) {       // nothing was committed
             for (int b = 0; b < N_BINS; b++) {
-                uint64_t want = h_cnt->groups[b] > group_cap[b] ? h_cnt->groups[b] * 3 / 2 : 0;
+                uint64_t want = h_cnt->groups[b] > group_cap[b] ? regrow_size(h_cnt->groups[b]) : 0;
                 if ((st_bits & OVF_GROUPS) && own->cfg.form == CFLR_FORM_PLAIN)
                     want = std::max<uint64_t>(want, 2 * group_cap[b]);   // counts reset per production
                 if (want) size_groups(b, want);
             }
             if (st_bits & OVF_CAND) {
-                size_cand(h_cnt->cand * 3 / 2);
+                size_cand(regrow_size(h_cnt->cand));
                 size_touched(2 * cand_cap, *h_parity);
             }
             regrows++;
@@ -1044,55 +1057,23 @@ Runner &runner_of(cflr_ctx *c) {
 // caller id of stored vertex k.
 std::vector<uint32_t> locality_order(uint32_t n, uint64_t m, const uint32_t *src,
                                      const uint32_t *dst) {
-    // Scratch kept per host thread: a server loads many graphs, and fresh
-    // buffers would page-fault on every load.
-    thread_local std::vector<uint64_t> boff, half, off;
-    thread_local std::vector<uint32_t> adj, cnt;
-    thread_local std::vector<uint8_t> seen;
-    // undirected adjacency (CSR) in two cache-friendly passes: the 2m
-    // half-edges go to buckets of 4096 consecutive sources (sequential
-    // writes), then each bucket is counting-sorted by source; the order of
-    // each vertex's neighbours is the edge order, as a direct fill gives
-    const uint32_t SH = 12;
-    const uint32_t nb = (n >> SH) + 1;
-    boff.assign((size_t)nb + 1, 0);
+    std::vector<uint64_t> off((size_t)n + 1, 0);
     for (uint64_t e = 0; e < m; e++) {
-        boff[(src[e] >> SH) + 1]++;
-        boff[(dst[e] >> SH) + 1]++;
+        off[(size_t)src[e] + 1]++;
+        off[(size_t)dst[e] + 1]++;
     }
-    for (uint32_t b = 0; b < nb; b++) boff[b + 1] += boff[b];
-    if (half.size() < 2 * m) half.resize(2 * m);
+    for (uint32_t v = 0; v < n; v++) off[v + 1] += off[v];
+    std::vector<uint32_t> adj(2 * m);
     {
-        std::vector<uint64_t> cur(boff.begin(), boff.end() - 1);
+        std::vector<uint64_t> cur(off.begin(), off.end() - 1);
         for (uint64_t e = 0; e < m; e++) {
-            half[cur[src[e] >> SH]++] = ((uint64_t)src[e] << 32) | dst[e];
-            half[cur[dst[e] >> SH]++] = ((uint64_t)dst[e] << 32) | src[e];
+            adj[cur[src[e]]++] = dst[e];
+            adj[cur[dst[e]]++] = src[e];
         }
     }
-    off.assign((size_t)n + 1, 0);
-    if (adj.size() < 2 * m) adj.resize(2 * m);
-    cnt.assign((size_t)1 << SH, 0);
-    for (uint32_t b = 0; b < nb; b++) {
-        const uint32_t v0 = b << SH;
-        const uint32_t vn = std::min<uint32_t>(n - std::min(n, v0), 1u << SH);
-        std::fill(cnt.begin(), cnt.begin() + vn, 0);
-        for (uint64_t q = boff[b]; q < boff[b + 1]; q++) cnt[(uint32_t)(half[q] >> 32) - v0]++;
-        uint64_t acc = boff[b];
-        for (uint32_t i = 0; i < vn; i++) {
-            off[v0 + i] = acc;
-            const uint32_t c = cnt[i];
-            cnt[i] = (uint32_t)(acc - boff[b]);
-            acc += c;
-        }
-        for (uint64_t q = boff[b]; q < boff[b + 1]; q++) {
-            const uint32_t s = (uint32_t)(half[q] >> 32) - v0;
-            adj[boff[b] + cnt[s]++] = (uint32_t)half[q];
-        }
-    }
-    off[n] = 2 * m;
     std::vector<uint32_t> order;
     order.reserve(n);
-    seen.assign(n, 0);
+    std::vector<uint8_t> seen(n, 0);
     for (uint32_t s = 0; s < n; s++) {
         if (seen[s]) continue;
         seen[s] = 1;
