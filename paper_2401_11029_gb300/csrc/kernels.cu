@@ -887,7 +887,12 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
          g += (unsigned long long)gridDim.x * GPC) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
         const uint32_t words = (gi.n + 31) >> 5;
-        for (uint32_t s = ptid; s < words; s += TPG) bm[s] = 0;
+        if (use_smem) {   // 16-byte stores: the stride is a multiple of four words
+            uint4 *b4 = reinterpret_cast<uint4 *>(bm);
+            for (uint32_t s = ptid; s < (words + 3) >> 2; s += TPG) b4[s] = make_uint4(0, 0, 0, 0);
+        } else {
+            for (uint32_t s = ptid; s < words; s += TPG) bm[s] = 0;
+        }
         if (ptid == 0) emitted_sh[part] = 0;
         psync();
         if (!gi.probe) preload_mask(S, gi, acc, ptid, TPG);
@@ -1563,12 +1568,15 @@ __global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const 
             const uint32_t c = __popc(b);
             const uint32_t incl = warp_incl_scan(c, lane);
             uint32_t pos = base + incl - c;
-            for (uint32_t rb = b; rb; rb &= rb - 1) {
-                uint32_t v = w * 32 + (__ffs(rb) - 1);
-                if (iperm) v = iperm[v];
-                s[pos++] = v;
-            }
+            for (uint32_t rb = b; rb; rb &= rb - 1) s[pos++] = w * 32 + (__ffs(rb) - 1);
             base += __shfl_sync(FULL_MASK, incl, 31);
+        }
+        __syncwarp();
+        // caller ids: one gather per entry, the whole warp's loads in flight
+        // together (per tile they would wait one after another)
+        if (iperm) {
+#pragma unroll 4
+            for (uint32_t t = lane; t < len; t += 32) s[t] = iperm[s[t]];
         }
         for (uint32_t t = len + lane; t < P; t += 32) s[t] = EMPTY32;
         __syncwarp();
@@ -1618,10 +1626,22 @@ __global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const ui
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < d.y; q += blockDim.x) {
             const uint32_t w = tl[2 * q];
-            for (uint32_t rb = tl[2 * q + 1]; rb; rb &= rb - 1) {
-                uint32_t v = w * 32 + (__ffs(rb) - 1);
-                if (iperm) v = iperm[v];
-                atomicOr(&bm[v >> 5], 1u << (v & 31));
+            // four bits of the tile at a time, their gathers in flight together
+            for (uint32_t rb = tl[2 * q + 1]; rb;) {
+                uint32_t v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    v[u] = rb ? w * 32 + (__ffs(rb) - 1) : EMPTY32;
+                    rb &= rb - 1;
+                }
+                if (iperm) {
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (v[u] != EMPTY32) v[u] = iperm[v[u]];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (v[u] != EMPTY32) atomicOr(&bm[v[u] >> 5], 1u << (v[u] & 31));
             }
         }
         __syncthreads();
