@@ -165,6 +165,23 @@ __device__ __forceinline__ uint32_t emit_candidates(bool flag, unsigned long lon
     return cnt;
 }
 
+// A warp's reservation in the candidate buffer: entries [pos, end) are its
+// own.  The product kernels reserve CAND_CHUNK entries (or more) at a time,
+// so most emits take no atomic on the shared count; what a warp leaves
+// unused when it ends is marked empty (slot EMPTY32) for the commit.
+struct CandChunk {
+    unsigned long long pos, end;
+};
+constexpr unsigned long long CAND_CHUNK = 64;
+
+// Warp-collective: mark the rest of the warp's reservation empty.
+__device__ __forceinline__ void release_chunk(const WorkBufs &W, const CandChunk &ck, int lane) {
+    if (ck.pos >= ck.end) return;
+    for (unsigned long long q = ck.pos + lane; q < ck.end; q += 32)
+        if (q < W.cand_cap) W.cand_slot[q] = EMPTY32;
+    if (lane == 0) atomicAdd(&W.cnt->holes, ck.end - ck.pos);
+}
+
 // Exclusive scan over the 256 threads of a block; `total` gets the block sum.
 __device__ __forceinline__ unsigned long long block_excl_scan256(unsigned long long v,
                                                                  unsigned long long *sh,
@@ -546,15 +563,13 @@ template <bool WIT, class Acc>
 __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab &P,
                                                 const WorkBufs &W, const GroupInfo &gi,
                                                 uint2 own, uint32_t warp_id, uint32_t nwarps,
-                                                int lane, const Acc &acc) {
+                                                int lane, const Acc &acc, CandChunk &ck) {
     const uint32_t dstart = own.x, d = own.y;
     const uint32_t *pool = S.pool[gi.c];
     const size_t oo = (size_t)gi.o * gi.n;
     const uint32_t g0 = (gi.part == PART_A) ? gi.b : gi.a;   // gathered slot (member 0)
     const uint4 *dg = (gi.part == PART_U) ? nullptr : S.desc[g0] + oo;
     uint32_t emitted = 0;
-    // the new bits nb of word wd of member tag (any number per lane); nearly
-    // every product is already present, so callers vote first
     // the derivation step new pairs record (single-path semantics): the
     // production's operands, or the unit production's one, and the middle
     // vertex k (the delta entry whose gathered row gave the pair)
@@ -563,40 +578,68 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
         const uint4 pr = gi.fam ? P.prod[P.fam_prod[gi.first + tag]] : make_uint4(0, gi.a, gi.b, 0);
         return make_uint2(WIT_BINARY | (S.local[pr.y] << 15) | S.local[pr.z], k);
     };
-    auto emit_bits = [&](uint32_t nb, uint32_t wd, uint32_t tag, uint32_t k) {
+    // the new bits n[i] of word wd[i] (i < 4) of member tag (any number per
+    // lane), one reservation in the candidate buffer for all of them; nearly
+    // every product is already present, so callers vote first
+    auto emit_bits = [&](uint32_t n0, uint32_t wd0, uint32_t n1, uint32_t wd1, uint32_t n2,
+                         uint32_t wd2, uint32_t n3, uint32_t wd3, uint32_t tag, uint32_t k) {
         const uint32_t slot = gi.tagged ? P.prod[P.fam_prod[gi.first + tag]].x : gi.c;
-        if (gi.probe && nb) {
+        if (gi.probe && (n0 | n1 | n2 | n3)) {
             const unsigned long long *ht = S.htab[slot];
             const unsigned long long hm = S.hmask[slot];
-            uint32_t keep = 0;
-            for (uint32_t r = nb; r; r &= r - 1) {
-                const uint32_t i = __ffs(r) - 1;
-                if (!htab_contains(ht, hm, group_key(gi, wd * 32 + i))) keep |= 1u << i;
-            }
-            nb = keep;
+            auto absent = [&](uint32_t nb, uint32_t wd) {
+                uint32_t keep = 0;
+                for (uint32_t r = nb; r; r &= r - 1) {
+                    const uint32_t i = __ffs(r) - 1;
+                    if (!htab_contains(ht, hm, group_key(gi, wd * 32 + i))) keep |= 1u << i;
+                }
+                return keep;
+            };
+            n0 = absent(n0, wd0);
+            n1 = absent(n1, wd1);
+            n2 = absent(n2, wd2);
+            n3 = absent(n3, wd3);
         }
-        const uint32_t cnt = __popc(nb);
+        const uint32_t cnt = __popc(n0) + __popc(n1) + __popc(n2) + __popc(n3);
         const uint32_t incl = warp_incl_scan(cnt, lane);
         const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
         if (!total) return;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&W.cnt->cand, (unsigned long long)total);
-        base = __shfl_sync(FULL_MASK, base, 0);
-        unsigned long long pos = base + incl - cnt;
+        // the warp's q-th new entry goes to the rest of its reservation,
+        // then to a new one of at least CAND_CHUNK entries
+        const unsigned long long rem = ck.end - ck.pos;
+        unsigned long long nbase = 0;
+        if (total > rem) {
+            const unsigned long long take = max((unsigned long long)total - rem, CAND_CHUNK);
+            if (lane == 0) {
+                nbase = atomicAdd(&W.cnt->cand, take);
+                if (nbase + take > W.cand_cap) atomicOr(&W.cnt->overflow, OVF_CAND);
+            }
+            nbase = __shfl_sync(FULL_MASK, nbase, 0);
+            ck.end = nbase + take;
+        }
+        unsigned long long q = incl - cnt;
+        const unsigned long long cpos = ck.pos;
+        ck.pos = total > rem ? nbase + (total - rem) : ck.pos + total;
         uint2 wit = make_uint2(0, 0);
         if constexpr (WIT) {
-            if (nb) wit = witness(tag, k);
+            if (cnt) wit = witness(tag, k);
         }
-        for (uint32_t r = nb; r; r &= r - 1, pos++) {
-            if (pos < W.cand_cap) {
-                W.cand_key[pos] = group_key(gi, wd * 32 + (__ffs(r) - 1));
-                W.cand_slot[pos] = slot;
-                if constexpr (WIT) W.cand_wit[pos] = wit;
+        auto put = [&](uint32_t nb, uint32_t wd) {
+            for (uint32_t r = nb; r; r &= r - 1, q++) {
+                const unsigned long long pos = q < rem ? cpos + q : nbase + (q - rem);
+                if (pos < W.cand_cap) {
+                    W.cand_key[pos] = group_key(gi, wd * 32 + (__ffs(r) - 1));
+                    W.cand_slot[pos] = slot;
+                    if constexpr (WIT) W.cand_wit[pos] = wit;
+                }
             }
-        }
+        };
+        put(n0, wd0);
+        put(n1, wd1);
+        put(n2, wd2);
+        put(n3, wd3);
         // the members' candidate counts (k_check sizes their pair sets)
         if (gi.tagged && cnt) atomicAdd(&S.cand[slot], (unsigned long long)cnt);
-        if (lane == 0 && base + total > W.cand_cap) atomicOr(&W.cnt->overflow, OVF_CAND);
         emitted += total;
     };
     auto key_of = [&](uint32_t wd, uint32_t tag) {
@@ -607,10 +650,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
     auto consume_tiles = [&](uint4 w, uint32_t nv, uint32_t tag, uint32_t k) {
         const uint32_t n0 = nv > 0 ? acc.ins(key_of(w.x, tag), w.y) : 0u;
         const uint32_t n1 = nv > 1 ? acc.ins(key_of(w.z, tag), w.w) : 0u;
-        if (__any_sync(FULL_MASK, (n0 | n1) != 0)) {
-            emit_bits(n0, w.x, tag, k);
-            emit_bits(n1, w.z, tag, k);
-        }
+        if (__any_sync(FULL_MASK, (n0 | n1) != 0)) emit_bits(n0, w.x, n1, w.z, 0u, 0u, 0u, 0u, tag, k);
     };
     // the tile lists held by the lanes (toff, tn; member tag; delta entry k)
     auto walk = [&](uint32_t toff, uint32_t tn, uint32_t tag, uint32_t k) {
@@ -641,8 +681,13 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                         nv[h] = 1;
                     }
                 }
-                consume_tiles(w[0], nv[0], ltag, lk);
-                if (qb + 64 < T) consume_tiles(w[1], nv[1], ltag, lk);
+                // four tiles per lane, one vote and one reservation
+                const uint32_t n0 = nv[0] > 0 ? acc.ins(key_of(w[0].x, ltag), w[0].y) : 0u;
+                const uint32_t n1 = nv[0] > 1 ? acc.ins(key_of(w[0].z, ltag), w[0].w) : 0u;
+                const uint32_t n2 = nv[1] > 0 ? acc.ins(key_of(w[1].x, ltag), w[1].y) : 0u;
+                const uint32_t n3 = nv[1] > 1 ? acc.ins(key_of(w[1].z, ltag), w[1].w) : 0u;
+                if (__any_sync(FULL_MASK, (n0 | n1 | n2 | n3) != 0))
+                    emit_bits(n0, w[0].x, n1, w[0].z, n2, w[1].x, n3, w[1].z, ltag, lk);
             }
         }
         // short tile lists: packed, 32 tiles per step
@@ -685,7 +730,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                 wd = v >> 5;
                 nb = acc.ins(wd, 1u << (v & 31));
             }
-            if (__any_sync(FULL_MASK, nb != 0)) emit_bits(nb, wd, 0, 0);
+            if (__any_sync(FULL_MASK, nb != 0)) emit_bits(nb, wd, 0u, 0u, 0u, 0u, 0u, 0u, 0, 0);
         }
         return emitted;
     }
@@ -806,6 +851,7 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(
     const unsigned long long n_groups =
         min(W.cnt->groups[bin], W.group_cap[bin]);
     const unsigned long long nw = (unsigned long long)gridDim.x * WARPS;
+    CandChunk ck{0, 0};
     unsigned long long bytes = 0;
     for (unsigned long long g = (unsigned long long)blockIdx.x * WARPS + wib; g < n_groups;
          g += nw) {
@@ -819,13 +865,14 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(
             __syncwarp();
         }
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, 0, 1, lane, acc);
+        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, 0, 1, lane, acc, ck);
         if (lane == 0 && e) {
             if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)e);
             bytes += 12ull * e;
         }
         __syncwarp();
     }
+    release_chunk(W, ck, lane);
     if (lane == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
 }
 
@@ -836,6 +883,7 @@ __global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S,
     __shared__ uint32_t emitted_sh;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned long long n_groups = min(W.cnt->groups[bin], W.group_cap[bin]);
+    CandChunk ck{0, 0};
     unsigned long long bytes = 0;
     for (unsigned long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
@@ -847,7 +895,7 @@ __global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S,
         if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc);
+        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc, ck);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
@@ -855,6 +903,7 @@ __global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S,
             bytes += 12ull * emitted_sh;
         }
     }
+    release_chunk(W, ck, lane);
     if (threadIdx.x == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
 }
 
@@ -882,6 +931,7 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
     uint32_t *bm = use_smem ? smem + (size_t)part * bm_stride
                             : W.bitmap_scratch + ((size_t)blockIdx.x * GPC + part) * W.bitmap_words;
     const BitmapAcc acc{bm};
+    CandChunk ck{0, 0};
     unsigned long long bytes = 0;
     for (unsigned long long g = (unsigned long long)blockIdx.x * GPC + part; g < n_groups;
          g += (unsigned long long)gridDim.x * GPC) {
@@ -898,7 +948,7 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
         if (!gi.probe) preload_mask(S, gi, acc, ptid, TPG);
         psync();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, wib % (8 / GPC), 8 / GPC, lane, acc);
+        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, wib % (8 / GPC), 8 / GPC, lane, acc, ck);
         if (lane == 0 && e) atomicAdd(&emitted_sh[part], e);
         psync();
         if (ptid == 0 && emitted_sh[part]) {
@@ -906,6 +956,7 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
             bytes += 12ull * emitted_sh[part];
         }
     }
+    release_chunk(W, ck, lane);
     if (ptid == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
 }
 
@@ -928,9 +979,9 @@ __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
         bool isnew = false;
         unsigned long long key = 0;
         uint32_t slot = EMPTY32;
-        if (t < nc) {
+        if (t < nc) slot = W.cand_slot[t];
+        if (slot != EMPTY32) {            // not an unused reserved entry
             key = W.cand_key[t];
-            slot = W.cand_slot[t];
             unsigned long long *tab = S.htab[slot];
             const unsigned long long m = S.hmask[slot];
             unsigned long long h = pair_home(key, m);
@@ -1369,7 +1420,7 @@ __global__ void __launch_bounds__(256) k_iter_end(SlotTab S, InstTab I, WorkBufs
         const int par = *W.parity;
         if (count_iteration) {
             ctl->total_flops += W.cnt->flops;
-            ctl->total_cand += W.cnt->cand;
+            ctl->total_cand += W.cnt->cand - W.cnt->holes;
             ctl->total_delta += total;
             ctl->total_touched_in += W.touched_n[par];
             ctl->total_touched_out += W.touched_n[par ^ 1];

@@ -143,6 +143,7 @@ struct Counters {
     unsigned long long flops;
     unsigned long long bytes_bin[N_BINS];
     unsigned long long bytes_sym;
+    unsigned long long holes;       // reserved candidate entries left unused
     unsigned int overflow;          // OVF_* bits
     unsigned int pad;
 };
