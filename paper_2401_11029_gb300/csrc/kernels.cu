@@ -1584,72 +1584,108 @@ __global__ void k_permute_ids(uint32_t *a, unsigned long long m, const uint32_t 
 }
 
 constexpr int EXTRACT_WARP_MAX = 1024;
+constexpr uint32_t EXTRACT_BATCH = 4;   // rows a warp takes per claim
 
-// One warp per row: bitonic sort in shared memory for rows up to 1024
-// entries; longer rows are listed for k_extract_big.
+// One warp per row: rows up to 32 entries are sorted in registers (one entry
+// per lane), longer ones up to 1024 entries by a bitonic sort in shared
+// memory; longer rows are listed for k_extract_big.  Warps claim rows
+// EXTRACT_BATCH at a time from cursor[1] (zeroed by the launcher), so a few
+// long rows do not leave one warp running after the others; cursor[0]
+// counts the listed long rows.
 __global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const uint32_t *pool,
                                                        uint32_t n, const uint32_t *perm,
                                                        const uint32_t *iperm,
                                                        const unsigned long long *row_out,
                                                        uint32_t *out_src, uint32_t *out_dst,
                                                        uint32_t *big_rows,
-                                                       uint32_t *big_count) {
+                                                       uint32_t *cursor) {
     __shared__ uint32_t sbuf[8][EXTRACT_WARP_MAX];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *s = sbuf[wib];
-    for (uint32_t i = blockIdx.x * 8 + wib; i < n; i += gridDim.x * 8) {
-        const uint4 d = desc[stored_row(perm, i)];
-        const uint32_t nt = d.y;
-        const uint32_t *tl = pool + d.x;
-        uint32_t len = 0;
-        for (uint32_t q = lane; q < nt; q += 32) len += __popc(tl[2 * q + 1]);
-        for (int dd = 16; dd > 0; dd >>= 1) len += __shfl_xor_sync(FULL_MASK, len, dd);
-        if (len == 0) continue;
-        if (len > EXTRACT_WARP_MAX) {
-            if (lane == 0) big_rows[atomicAdd(big_count, 1u)] = i;
-            continue;
-        }
-        uint32_t P = 32;
-        while (P < len) P <<= 1;
-        // each lane decodes one tile per round at its scan position
-        uint32_t base = 0;
-        for (uint32_t qb = 0; qb < nt; qb += 32) {
-            const uint32_t q = qb + lane;
-            const uint32_t w = q < nt ? tl[2 * q] : 0, b = q < nt ? tl[2 * q + 1] : 0;
-            const uint32_t c = __popc(b);
-            const uint32_t incl = warp_incl_scan(c, lane);
-            uint32_t pos = base + incl - c;
-            for (uint32_t rb = b; rb; rb &= rb - 1) s[pos++] = w * 32 + (__ffs(rb) - 1);
-            base += __shfl_sync(FULL_MASK, incl, 31);
-        }
-        __syncwarp();
-        // caller ids: one gather per entry, the whole warp's loads in flight
-        // together (per tile they would wait one after another)
-        if (iperm) {
+    for (;;) {
+        uint32_t i0 = 0;
+        if (lane == 0) i0 = atomicAdd(&cursor[1], EXTRACT_BATCH);
+        i0 = __shfl_sync(FULL_MASK, i0, 0);
+        if (i0 >= n) break;
+        for (uint32_t i = i0; i < min(n, i0 + EXTRACT_BATCH); i++) {
+            const uint4 d = desc[stored_row(perm, i)];
+            const uint32_t nt = d.y;
+            const uint32_t *tl = pool + d.x;
+            uint32_t len = 0;
+            for (uint32_t q = lane; q < nt; q += 32) len += __popc(tl[2 * q + 1]);
+            for (int dd = 16; dd > 0; dd >>= 1) len += __shfl_xor_sync(FULL_MASK, len, dd);
+            if (len == 0) continue;
+            if (len > EXTRACT_WARP_MAX) {
+                if (lane == 0) big_rows[atomicAdd(&cursor[0], 1u)] = i;
+                continue;
+            }
+            // each lane decodes one tile per round at its scan position
+            uint32_t base = 0;
+            for (uint32_t qb = 0; qb < nt; qb += 32) {
+                const uint32_t q = qb + lane;
+                const uint32_t w = q < nt ? tl[2 * q] : 0, b = q < nt ? tl[2 * q + 1] : 0;
+                const uint32_t c = __popc(b);
+                const uint32_t incl = warp_incl_scan(c, lane);
+                uint32_t pos = base + incl - c;
+                for (uint32_t rb = b; rb; rb &= rb - 1) s[pos++] = w * 32 + (__ffs(rb) - 1);
+                base += __shfl_sync(FULL_MASK, incl, 31);
+            }
+            __syncwarp();
+            // caller ids: one gather per entry, the whole warp's loads in
+            // flight together (per tile they would wait one after another)
+            if (iperm) {
 #pragma unroll 4
-            for (uint32_t t = lane; t < len; t += 32) s[t] = iperm[s[t]];
-        }
-        for (uint32_t t = len + lane; t < P; t += 32) s[t] = EMPTY32;
-        __syncwarp();
-        for (uint32_t k = 2; k <= P; k <<= 1) {
-            for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
-                for (uint32_t t = lane; t < P; t += 32) {
-                    const uint32_t ixj = t ^ jj;
-                    if (ixj > t) {
-                        const uint32_t a = s[t], b = s[ixj];
-                        const bool up = (t & k) == 0;
-                        if ((a > b) == up) { s[t] = b; s[ixj] = a; }
+                for (uint32_t t = lane; t < len; t += 32) s[t] = iperm[s[t]];
+            }
+            __syncwarp();
+            const unsigned long long o = row_out[i];
+            if (len <= 32) {
+                // bitonic network over the lanes: in each block of k lanes
+                // (ascending when lane & k is clear) the lower lane of every
+                // pair j apart keeps the minimum
+                uint32_t v = (uint32_t)lane < len ? s[lane] : EMPTY32;
+#pragma unroll
+                for (uint32_t k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                        const uint32_t u = __shfl_xor_sync(FULL_MASK, v, j);
+                        const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+                        v = (lower == up) ? min(v, u) : max(v, u);
                     }
                 }
+                if ((uint32_t)lane < len) {
+                    out_src[o + lane] = i;
+                    out_dst[o + lane] = v;
+                }
                 __syncwarp();
+                continue;
             }
+            uint32_t P = 64;
+            while (P < len) P <<= 1;
+            for (uint32_t t = len + lane; t < P; t += 32) s[t] = EMPTY32;
+            __syncwarp();
+            // bitonic sort of P entries: every lane takes whole pairs (t, t + jj),
+            // t the q-th index with bit jj clear
+            for (uint32_t k = 2; k <= P; k <<= 1) {
+                for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+                    for (uint32_t q = lane; q < P / 2; q += 32) {
+                        const uint32_t t = ((q & ~(jj - 1)) << 1) | (q & (jj - 1));
+                        const uint32_t a = s[t], b = s[t | jj];
+                        const bool up = (t & k) == 0;
+                        if ((a > b) == up) {
+                            s[t] = b;
+                            s[t | jj] = a;
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            for (uint32_t t = lane; t < len; t += 32) {
+                out_src[o + t] = i;
+                out_dst[o + t] = s[t];
+            }
+            __syncwarp();
         }
-        const unsigned long long o = row_out[i];
-        for (uint32_t t = lane; t < len; t += 32) {
-            out_src[o + t] = i;
-            out_dst[o + t] = s[t];
-        }
-        __syncwarp();
     }
 }
 
@@ -2002,7 +2038,7 @@ void launch_extract(const uint4 *desc, const uint32_t *pool, uint32_t n, const u
                     uint32_t *bitmap, int sms, cudaStream_t st) {
     if (!n) return;
     set_smem_attrs();
-    cudaMemsetAsync(big_count, 0, sizeof(uint32_t), st);
+    cudaMemsetAsync(big_count, 0, 2 * sizeof(uint32_t), st);   // long-row count, row cursor
     k_extract_small<<<grid_for(n, 8, sms, 8), 256, 0, st>>>(desc, pool, n, perm, iperm,
                                                             row_out, out_src, out_dst, big_rows,
                                                             big_count);

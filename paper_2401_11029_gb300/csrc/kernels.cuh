@@ -240,7 +240,8 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t n, unsigned long long *o
 // stored id back (both null when the vertices kept their input order).
 void launch_row_lengths(const uint4 *desc, const uint32_t *pool, uint32_t n,
                         const uint32_t *perm, uint32_t *len, cudaStream_t st);
-// big_rows: scratch of n uint32 plus one counter; bitmap: scratch of
+// big_rows: scratch of n uint32 followed by two counters (big_count points
+// at the first: the long-row count, then the row cursor); bitmap: scratch of
 // sms*4*ceil(n/32) words used when a row bitmap does not fit shared memory.
 void launch_extract(const uint4 *desc, const uint32_t *pool, uint32_t n, const uint32_t *perm,
                     const uint32_t *iperm, const unsigned long long *row_out, uint32_t *out_src,

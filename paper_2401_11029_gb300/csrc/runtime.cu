@@ -176,7 +176,7 @@ struct cflr_ctx {
     // extraction scratch (row lengths, offsets, long-row list, bitmaps)
     void free_extract_scratch() {
         if (x_len) dfree(x_len, x_n * 4);
-        if (x_big) dfree(x_big, (x_n + 1) * 4);
+        if (x_big) dfree(x_big, (x_n + 2) * 4);
         if (x_off) dfree(x_off, x_n * 8);
         if (x_bsum) dfree(x_bsum, (x_n / 1024 + 2) * 8);
         if (x_bm) dfree(x_bm, x_bm_n * 4);
@@ -1485,7 +1485,7 @@ void extract_device(cflr_ctx *c, uint32_t nt, uint32_t *out_src, uint32_t *out_d
         c->free_extract_scratch();
         c->x_n = n;
         c->x_len = (uint32_t *)c->dalloc((size_t)n * 4);
-        c->x_big = (uint32_t *)c->dalloc(((size_t)n + 1) * 4);
+        c->x_big = (uint32_t *)c->dalloc(((size_t)n + 2) * 4);
         c->x_off = (unsigned long long *)c->dalloc((size_t)n * 8);
         c->x_bsum = (unsigned long long *)c->dalloc(((size_t)n / 1024 + 2) * 8);
         const size_t words = ((size_t)n + 31) / 32;
