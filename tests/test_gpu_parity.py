@@ -429,6 +429,31 @@ def test_rows_beyond_the_shared_memory_bitmap(keep):
     assert want.pairs["S"].size > 150_000
 
 
+@pytest.mark.parametrize("keep", [0, 1])
+def test_extraction_across_row_lengths(keep):
+    """Rows of every length class of the extraction: up to 32 entries (sorted
+    in registers), up to 1024 (sorted in shared memory, around each power of
+    two) and longer (the per-row bitmap), each ending sorted in caller ids."""
+    n = 9000
+    rng = np.random.default_rng(73)
+    lengths = [1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513,
+               1000, 1023, 1024, 1025, 1500, 4000]
+    srcs, dsts = [], []
+    for r, L in enumerate(lengths):     # sources 0..22 point into 100..n-1 only
+        srcs.append(np.full(L, r, np.uint32))
+        dsts.append((100 + rng.choice(n - 100, size=L, replace=False)).astype(np.uint32))
+    # links among the targets scramble the breadth-first renumbering
+    extra = rng.integers(100, n, size=(3000, 2)).astype(np.uint32)
+    src = np.concatenate(srcs + [extra[:, 0]])
+    dst = np.concatenate(dsts + [extra[:, 1]])
+    g = gen.Graph(n=n, labels=["a", "b"], src=src,
+                  lab=np.concatenate([np.zeros(src.size - 3000, np.uint32),
+                                      np.ones(3000, np.uint32)]), dst=dst)
+    st, want = assert_parity("S -> a | S S\nT -> b\n", g, keep_vertex_order=keep)
+    rows = np.bincount((want.pairs["S"] >> 32).astype(np.int64), minlength=len(lengths))
+    assert list(rows[:len(lengths)]) == lengths
+
+
 @pytest.mark.parametrize("form", [cflr.CFLR_FORM_PLAIN, cflr.CFLR_FORM_BATCHED,
                                   cflr.CFLR_FORM_GRAPH])
 @pytest.mark.parametrize("tuning", [None, (1, [16, 64, 256], [1, 1, 1, 1])])
