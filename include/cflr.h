@@ -65,7 +65,9 @@ typedef struct cflr_ctx cflr_ctx;
 typedef struct {
     int device;                 /* CUDA device ordinal                              */
     void *stream;               /* cudaStream_t to run on; NULL = a private stream  */
-    uint64_t mem_budget_bytes;  /* cap on device bytes this context may hold; 0 = none */
+    uint64_t mem_budget_bytes;  /* cap on device bytes this context may hold; 0 = none.
+                                   A work buffer that overflows triples without a
+                                   budget and grows by half under one              */
     uint32_t max_iterations;    /* stop with CFLR_ELIMIT after this many; 0 = none  */
     int form;                   /* CFLR_FORM_*                                      */
     int profile;                /* nonzero: time every kernel launch with CUDA events
