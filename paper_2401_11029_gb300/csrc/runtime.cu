@@ -19,6 +19,8 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 using namespace cflr;
@@ -1057,20 +1059,44 @@ Runner &runner_of(cflr_ctx *c) {
 // caller id of stored vertex k.
 std::vector<uint32_t> locality_order(uint32_t n, uint64_t m, const uint32_t *src,
                                      const uint32_t *dst) {
+    // Undirected adjacency (CSR).  Degree counting and the fill run on up to
+    // eight host threads, each owning a range of vertices: a thread scans
+    // every edge in order and touches only its own vertices, so each list
+    // keeps the edge order (the order a one-thread fill gives).
+    unsigned T = std::min(std::max(1u, std::thread::hardware_concurrency()), 8u);
+    if (m < (1u << 18)) T = 1;
     std::vector<uint64_t> off((size_t)n + 1, 0);
-    for (uint64_t e = 0; e < m; e++) {
-        off[(size_t)src[e] + 1]++;
-        off[(size_t)dst[e] + 1]++;
-    }
-    for (uint32_t v = 0; v < n; v++) off[v + 1] += off[v];
     std::vector<uint32_t> adj(2 * m);
-    {
-        std::vector<uint64_t> cur(off.begin(), off.end() - 1);
-        for (uint64_t e = 0; e < m; e++) {
-            adj[cur[src[e]]++] = dst[e];
-            adj[cur[dst[e]]++] = src[e];
+    auto on_threads = [&](auto &&work) {
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < T; t++) {
+            const uint32_t v0 = (uint32_t)((uint64_t)n * t / T);
+            const uint32_t v1 = (uint32_t)((uint64_t)n * (t + 1) / T);
+            try {
+                th.emplace_back(work, v0, v1);
+            } catch (const std::system_error &) {
+                work(v0, v1);      // no thread to be had: do that range here
+            }
         }
-    }
+        for (auto &x : th) x.join();
+    };
+    on_threads([&](uint32_t v0, uint32_t v1) {
+        uint64_t *o = off.data() + 1;
+        for (uint64_t e = 0; e < m; e++) {
+            if (src[e] - v0 < v1 - v0) o[src[e]]++;
+            if (dst[e] - v0 < v1 - v0) o[dst[e]]++;
+        }
+    });
+    for (uint32_t v = 0; v < n; v++) off[v + 1] += off[v];
+    on_threads([&](uint32_t v0, uint32_t v1) {
+        std::vector<uint64_t> cur(off.begin() + v0, off.begin() + v1);
+        uint64_t *c = cur.data() - v0;     // indexed by vertex, v0 <= v < v1
+        for (uint64_t e = 0; e < m; e++) {
+            const uint32_t s = src[e], d = dst[e];
+            if (s - v0 < v1 - v0) adj[c[s]++] = d;
+            if (d - v0 < v1 - v0) adj[c[d]++] = s;
+        }
+    });
     std::vector<uint32_t> order;
     order.reserve(n);
     std::vector<uint8_t> seen(n, 0);
