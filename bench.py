@@ -10,8 +10,16 @@ One step is one pass of the whole hot path on the alias-analysis workload
 value = pairs of all named non-terminals / step time (CUDA events on the
 solve stream, L2 flushed between steps).  e2e repeats the step through the
 host-buffer API: grammar text and host edges in, host pair arrays out.
+After the timed steps the extracted pairs of every named non-terminal are
+fingerprinted and compared with the oracle's stored fingerprints.
+
+The default line also carries the other workloads, each with its own step
+time: the 64-field points-to solve (500 000 vertices), the 256 batched Dyck-3
+instances (one batched CUDA-graph solve against each instance alone in the
+per-production form) and a short served Poisson stream of alias solves.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cflr|reference]
+                  [--workload all|fica|fsjpt|dyck3_batch|serving]
 
 Under torchrun (N > 1) every rank solves its own replica (different seed):
 the single-instance fixpoint has no exchange step that would let it shard,
@@ -42,8 +50,12 @@ METRIC = "CFL-r solve throughput (pairs of all non-terminals / solve time)"
 UNIT = "pairs/s"
 WORKLOAD = {"workload": "fica_like alias analysis (Fig. wcnf:fica)", "n_vertices": 200_000,
             "a_edges": 400_000, "d_edges": 150_000, "reverse_edges": True, "seed": 2}
+FSJPT = {"workload": "fsjpt_like field-sensitive points-to (Fig. wcnf:fsjpt, 64 fields)",
+         "n_vertices": 500_000, "forward_edges": 2_000_000, "reverse_edges": True, "seed": 3,
+         "productions": 514}
 SAMPLE_N = 20_000     # oracle sample: same generator and ratios, 1/10 of the vertices
 TUNING_CACHE = os.path.join(ROOT, "paper_2401_11029_gb300", "tuning", "gb300.txt")
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def peaks() -> dict:
@@ -53,11 +65,6 @@ def peaks() -> dict:
         return {"hbm_gbs": float(p["hbm_gbs"]), "src": "measured"}
     except Exception:
         return {"hbm_gbs": 6800.0, "src": "fallback"}
-
-
-FSJPT = {"workload": "fsjpt_like field-sensitive points-to (Fig. wcnf:fsjpt, 64 fields)",
-         "n_vertices": 500_000, "forward_edges": 2_000_000, "reverse_edges": True, "seed": 3,
-         "productions": 514}
 
 
 def workload_graph(seed: int, n: int = None, kind: str = "fica"):
@@ -73,6 +80,24 @@ def workload_graph(seed: int, n: int = None, kind: str = "fica"):
 
 def grammar_of(kind: str) -> str:
     return gen.grammar_text("fsjpt" if kind == "fsjpt" else "fica")
+
+
+def golden_of(name: str, g) -> dict | None:
+    """The oracle's stored fingerprints of workload `name`, when they exist
+    and were made from this very edge list."""
+    path = os.path.join(GOLDEN, name + ".json")
+    try:
+        with open(path) as f:
+            gold = json.load(f)
+    except OSError:
+        return None
+    if g is not None and gold.get("edge_digest") != g.edge_digest():
+        return None
+    return gold
+
+
+def golden_name(kind: str, n: int) -> str:
+    return {"fica": f"fica_like_{n // 1000}k", "fsjpt": f"fsjpt_like_{n // 1000}k"}[kind]
 
 
 class ClockSampler:
@@ -130,10 +155,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_from_profile(kernel: str):
+def traffic_from_profile(kernel: str, workload: str = "fica_like"):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if
     the kernel source has not changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_fica_like.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -148,18 +173,35 @@ def traffic_from_profile(kernel: str):
     return int(t.group(1))
 
 
-def cpu_oracle_sample(seed: int, kind: str = "fica") -> dict:
-    """The oracle, as it stands, on a bounded sample of the workload."""
+def oracle_sample_graph(kind: str = "fica"):
+    return workload_graph(WORKLOAD["seed"] if kind == "fica" else FSJPT["seed"], SAMPLE_N, kind)
+
+
+def cpu_oracle_sample(kind: str = "fica") -> dict:
+    """The oracle, as it stands, on a bounded sample of the workload: the same
+    generator and ratios at SAMPLE_N vertices."""
     import oracle
-    g = workload_graph(seed, SAMPLE_N, kind)
+    g = oracle_sample_graph(kind)
     text = grammar_of(kind)
     res = oracle.solve(text, g)
     pairs = res.total()
     name = "fsjpt_like" if kind == "fsjpt" else "fica_like"
-    return {"value": pairs / res.seconds, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{name} n={SAMPLE_N} (same generator and ratios as the workload, "
-                      f"{g.n_edges} edges, {pairs} pairs), one worklist solve, "
-                      f"{res.seconds:.1f} s on 1 host core", "seconds": res.seconds}
+    out = {"value": pairs / res.seconds, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{name} n={SAMPLE_N} (same generator and ratios as the workload, "
+                     f"{g.n_edges} edges, {pairs} pairs), one worklist solve, "
+                     f"{res.seconds:.1f} s on 1 host core", "seconds": res.seconds,
+           "sample_edges": g.n_edges, "sample_pairs": pairs}
+    full = golden_of(golden_name(kind, (WORKLOAD if kind == "fica" else FSJPT)["n_vertices"]),
+                     None)
+    if full and full.get("oracle_seconds"):
+        # context only: the same oracle at the full size, recorded when the
+        # stored fingerprints were written (one core of the x86 build host)
+        out["full_size_oracle"] = {
+            "value": full["total_pairs"] / full["oracle_seconds"], "unit": UNIT,
+            "seconds": full["oracle_seconds"], "pairs": full["total_pairs"],
+            "where": "1 core of the x86-64 build host, recorded with tests/golden/"
+                     f"{full['workload']}.json"}
+    return out
 
 
 def dist_setup():
@@ -189,51 +231,47 @@ def aggregate(dist, device, ms: float, pairs: int, e2e_s: float):
 
 
 def run_reference(args):
+    """The reference arm: the oracle, as it stands, on the host cores, on a
+    bounded sample of the headline workload (rank 0 only)."""
     world, rank, local, dist = dist_setup()
     if rank != 0:
         return
     vals, secs = [], []
     info = None
     for _ in range(args.warmup):
-        cpu_oracle_sample(WORKLOAD["seed"])
+        cpu_oracle_sample()
     for _ in range(args.steps):
-        info = cpu_oracle_sample(WORKLOAD["seed"])
+        info = cpu_oracle_sample()
         vals.append(info["value"])
         secs.append(info.pop("seconds"))
     v = statistics.mean(vals)
     info["value"] = v
+    scale = SAMPLE_N / WORKLOAD["n_vertices"]
+    # the configuration actually solved: the sample, not the full workload
+    config = dict(WORKLOAD, n_vertices=SAMPLE_N, a_edges=int(WORKLOAD["a_edges"] * scale),
+                  d_edges=int(WORKLOAD["d_edges"] * scale), edges=info["sample_edges"],
+                  pairs=info["sample_pairs"],
+                  sample_of=f"fica_like at {WORKLOAD['n_vertices']} vertices (same generator "
+                            "and ratios, 1/10 of the vertices)",
+                  parallelism=f"replicas{args.gpus}")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             # one step is one oracle solve of the bounded sample
             "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": dict(WORKLOAD, parallelism=f"replicas{args.gpus}"),
-            "cpu_baseline": info,
+            "config": config, "cpu_baseline": info,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_cflr(args):
-    import torch
+# ---------------------------------------------------------------------------
+# the timed launch configuration (shared with the full-size parity tests)
+# ---------------------------------------------------------------------------
+
+def label_array(ctx, g) -> np.ndarray:
+    """Terminal id of every edge (0xFFFFFFFF for labels the grammar lacks)."""
     from paper_2401_11029_gb300 import cflr
-
-    world, rank, local, dist = dist_setup()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    kind = args.workload
-    wl = FSJPT if kind == "fsjpt" else WORKLOAD
-    seed = wl["seed"] + 1000 * rank
-    g = workload_graph(seed, args.vertices, kind)
-    text = grammar_of(kind)
-
-    # timed context: the device-driven loop (one CUDA graph per solve), with
-    # the product schedule picked by cflr_autotune (cached per grammar and size)
-    ctx = cflr.cflr_create(device=local, stream=stream.cuda_stream, form=cflr.CFLR_FORM_GRAPH,
-                           autotune_cache=TUNING_CACHE.encode())
-    cflr.cflr_load_grammar(ctx, text)
-    n_nt, n_named, _ = cflr.cflr_grammar_sizes(ctx)
     term = {}
     for name in g.labels:
         try:
@@ -241,82 +279,182 @@ def run_cflr(args):
             term[name] = i if is_t else 0xFFFFFFFF
         except cflr.CflrError:
             term[name] = 0xFFFFFFFF
-    lab = np.asarray([term[x] for x in g.labels], np.uint32)[g.lab]
-    # pinned host copies of the inputs for the end-to-end leg
-    h_src = torch.from_numpy(g.src.astype(np.uint32).view(np.int32)).pin_memory()
-    h_lab = torch.from_numpy(lab.view(np.int32)).pin_memory()
-    h_dst = torch.from_numpy(g.dst.astype(np.uint32).view(np.int32)).pin_memory()
-    cflr.cflr_load_graph(ctx, g.n, h_src.numpy().view(np.uint32), h_lab.numpy().view(np.uint32),
-                         h_dst.numpy().view(np.uint32))
-    tuning = cflr.cflr_autotune(ctx) if not args.no_autotune else cflr.cflr_get_tuning(ctx)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    # profiled context: the same iterations launched one by one from the host
-    # with CUDA events around every kernel (events cannot sit inside the
-    # graph's loop body); it supplies the per-kernel times of the roofline
-    pctx = cflr.cflr_create(device=local, stream=stream.cuda_stream,
-                            form=cflr.CFLR_FORM_BATCHED, profile=1)
+    return np.asarray([term[x] for x in g.labels], np.uint32)[g.lab]
+
+
+def timed_context(g, text, device: int, stream, autotune: bool = True, **cfg):
+    """The context the bench times: the device-driven loop (one CUDA graph per
+    solve) with the product schedule cflr_autotune picks from the tuning
+    cache.  Returns (ctx, tuning)."""
+    from paper_2401_11029_gb300 import cflr
+    ctx = cflr.cflr_create(device=device, stream=stream, form=cflr.CFLR_FORM_GRAPH,
+                           autotune_cache=TUNING_CACHE.encode(), **cfg)
+    cflr.cflr_load_grammar(ctx, text)
+    cflr.cflr_load_graph(ctx, g.n, g.src, label_array(ctx, g), g.dst)
+    tuning = cflr.cflr_autotune(ctx) if autotune else cflr.cflr_get_tuning(ctx)
+    return ctx, tuning
+
+
+def device_step(ctx, n_named: int, out=None, last: dict | None = None) -> int:
+    """One step: reset, solve, and extract every named non-terminal's pairs
+    into the device buffers `out` (src, dst); returns the pair count."""
+    from paper_2401_11029_gb300 import cflr
+    cflr.cflr_reset(ctx)
+    st = cflr.cflr_solve(ctx)
+    if last is not None:
+        last.update(st)
+    total = 0
+    for x in range(n_named):
+        cnt = cflr.cflr_get_pairs(ctx, x, count_only=True)
+        if cnt and out is not None:
+            cflr.cflr_get_pairs_device(ctx, x, out[0].data_ptr(), out[1].data_ptr(), cnt)
+        total += cnt
+    return total
+
+
+def device_fingerprints(ctx, names, out) -> dict:
+    """Fingerprint of each named non-terminal's pairs as the device extraction
+    writes them (out: device buffers large enough for the largest)."""
+    from paper_2401_11029_gb300 import cflr
+    fps = {}
+    for name in names:
+        x, _ = cflr.cflr_symbol_id(ctx, name)
+        cnt = cflr.cflr_get_pairs(ctx, x, count_only=True)
+        if cnt:
+            cflr.cflr_get_pairs_device(ctx, x, out[0].data_ptr(), out[1].data_ptr(), cnt)
+        s = out[0][:cnt].cpu().numpy().view(np.uint32)
+        d = out[1][:cnt].cpu().numpy().view(np.uint32)
+        keys = gen.pair_keys(s, d)
+        if keys.size > 1 and not np.all(keys[1:] > keys[:-1]):
+            fps[name] = "unsorted"
+        else:
+            fps[name] = gen.pair_fingerprint(keys)
+    return fps
+
+
+def parity_record(ctx, gold: dict | None, out) -> dict:
+    if not gold:
+        return {"checked": False, "why": "no stored oracle fingerprints for this graph"}
+    fps = device_fingerprints(ctx, list(gold["pairs"]), out)
+    bad = [x for x, fp in gold["pairs"].items() if fps.get(x) != fp]
+    return {"checked": True, "match": not bad, "mismatched": bad[:8],
+            "nonterminals": len(gold["pairs"]),
+            "against": f"oracle fingerprints tests/golden/{gold['workload']}.json"}
+
+
+def kernel_rows(before: dict, after: dict) -> list:
+    rows = []
+    for name, a in after.items():
+        b = before.get(name, {"launches": 0, "ms": 0.0, "alg_bytes": 0})
+        rows.append((a["ms"] - b["ms"], a["launches"] - b["launches"],
+                     a["alg_bytes"] - b["alg_bytes"], name))
+    rows.sort(reverse=True)
+    return rows
+
+
+def roofline_of(rows: list, workload: str) -> dict:
+    kms, kl, kb, kname = rows[0]
+    pk = peaks()
+    achieved = (kb / 1e9) / (kms / 1e3) if kms > 0 else 0.0
+    return {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic_from_profile(kname, workload),
+            "kernel": kname, "launches": kl, "avg_launch_ms": kms / max(kl, 1),
+            "peak_src": pk["src"]}
+
+
+def profiled_kernels(g, text, tuning, device, stream, n_named, out, flush, steps, warmup,
+                     expect):
+    """Per-kernel event times of the same steps: a context with the same
+    schedule whose iterations are launched one by one from the host with
+    CUDA events around every kernel (events cannot sit inside the graph's
+    loop body)."""
+    from paper_2401_11029_gb300 import cflr
+    pctx = cflr.cflr_create(device=device, stream=stream, form=cflr.CFLR_FORM_BATCHED, profile=1)
     cflr.cflr_load_grammar(pctx, text)
     cflr.cflr_set_tuning(pctx, tuning["probe_ratio"], tuning["bin_limit"], tuning["ctas_per_sm"])
-    cflr.cflr_load_graph(pctx, g.n, h_src.numpy().view(np.uint32), h_lab.numpy().view(np.uint32),
-                         h_dst.numpy().view(np.uint32))
+    cflr.cflr_load_graph(pctx, g.n, g.src, label_array(pctx, g), g.dst)
+    for _ in range(warmup):
+        device_step(pctx, n_named, out)
+    before = {k["name"]: k for k in cflr.cflr_kernel_stats(pctx)}
+    for _ in range(steps):
+        flush.fill_(1)
+        assert device_step(pctx, n_named, out) == expect
+    import torch
+    torch.cuda.synchronize()
+    after = {k["name"]: k for k in cflr.cflr_kernel_stats(pctx)}
+    cflr.cflr_destroy(pctx)
+    return kernel_rows(before, after)
 
+
+def timed_steps(ctx, n_named, out, flush, stream, steps, fill=1, expect=None, last=None):
+    import torch
+    step_ms = []
+    for _ in range(steps):
+        flush.fill_(fill)                          # evict L2 between steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p = device_step(ctx, n_named, out, last)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        if expect is not None:
+            assert p == expect, "pair count changed between steps"
+    return step_ms
+
+
+def run_cflr(args, kind: str = "fica", extras: bool = False):
+    import torch
+    from paper_2401_11029_gb300 import cflr
+
+    world, rank, local, dist = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    wl = FSJPT if kind == "fsjpt" else WORKLOAD
+    seed = wl["seed"] + 1000 * rank
+    g = workload_graph(seed, args.vertices, kind)
+    text = grammar_of(kind)
+
+    ctx, tuning = timed_context(g, text, local, stream.cuda_stream,
+                                autotune=not args.no_autotune)
+    n_nt, n_named, _ = cflr.cflr_grammar_sizes(ctx)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     last = {}
-
-    def device_step(out=None, c=None):
-        c = c or ctx
-        cflr.cflr_reset(c)
-        last.update(cflr.cflr_solve(c))
-        total = 0
-        for x in range(n_named):
-            cnt = cflr.cflr_get_pairs(c, x, count_only=True)
-            if cnt and out is not None:
-                cflr.cflr_get_pairs_device(c, x, out[0].data_ptr(), out[1].data_ptr(), cnt)
-            total += cnt
-        return total
-
-    pairs = device_step()
+    pairs = device_step(ctx, n_named, None, last)
     cap = max(cflr.cflr_get_pairs(ctx, x, count_only=True) for x in range(n_named))
-    out = (torch.empty(cap, dtype=torch.int32, device=dev),
-           torch.empty(cap, dtype=torch.int32, device=dev))
+    out = (torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
+           torch.empty(max(cap, 1), dtype=torch.int32, device=dev))
     for _ in range(max(0, args.warmup - 1)):
-        device_step(out)
+        device_step(ctx, n_named, out)
 
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    step_ms = []
-    for _ in range(args.steps):
-        flush.fill_(rank + 1)                      # evict L2 between steps
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        p = device_step(out)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        assert p == pairs, "pair count changed between steps"
+    step_ms = timed_steps(ctx, n_named, out, flush, stream, args.steps, rank + 1, pairs, last)
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
     clk = clocks.stop()
     solve_stats = dict(last)
+    # the result of the timed configuration against the oracle's fingerprints
+    gold = golden_of(golden_name(kind, g.n), g) if rank == 0 else None
+    parity = parity_record(ctx, gold, out) if rank == 0 else None
 
-    # per-kernel event times: the same steps on the profiled context
-    for _ in range(args.warmup):
-        device_step(out, pctx)
-    before = {k["name"]: k for k in cflr.cflr_kernel_stats(pctx)}
-    for _ in range(args.steps):
-        flush.fill_(rank + 1)
-        assert device_step(out, pctx) == pairs
-    torch.cuda.synchronize(dev)
-    after = {k["name"]: k for k in cflr.cflr_kernel_stats(pctx)}
-    cflr.cflr_destroy(pctx)
+    rows = profiled_kernels(g, text, tuning, local, stream.cuda_stream, n_named, out, flush,
+                            args.steps, args.warmup, pairs)
 
     # end-to-end through the host-buffer API
+    h_src = torch.from_numpy(g.src.astype(np.uint32).view(np.int32)).pin_memory()
+    h_dst = torch.from_numpy(g.dst.astype(np.uint32).view(np.int32)).pin_memory()
     h_out_s = torch.empty(cap, dtype=torch.int32).pin_memory()
     h_out_d = torch.empty(cap, dtype=torch.int32).pin_memory()
+    lab_ids = label_array(ctx, g)
+    h_lab = torch.from_numpy(lab_ids.view(np.int32)).pin_memory()
+    lib = cflr.load_library()
+    import ctypes
     e2e_s = []
     for k in range(args.steps + 1):
         torch.cuda.synchronize(dev)
@@ -324,14 +462,13 @@ def run_cflr(args):
         c2 = cflr.cflr_create(device=local, stream=stream.cuda_stream,
                               form=cflr.CFLR_FORM_GRAPH, autotune_cache=TUNING_CACHE.encode())
         cflr.cflr_load_grammar(c2, text)
-        cflr.cflr_load_graph(c2, g.n, h_src.numpy().view(np.uint32),
-                             h_lab.numpy().view(np.uint32), h_dst.numpy().view(np.uint32))
+        rc = lib.cflr_load_graph(c2, g.n, g.n_edges, h_src.data_ptr(), h_lab.data_ptr(),
+                                 h_dst.data_ptr())
+        assert rc == 0
         if not args.no_autotune:
             cflr.cflr_autotune(c2)          # the cached schedule of this workload
         cflr.cflr_solve(c2)
         tot = 0
-        lib = cflr.load_library()
-        import ctypes
         for x in range(n_named):
             n_p = ctypes.c_uint64()
             rc = lib.cflr_get_pairs(c2, x, h_out_s.data_ptr(), h_out_d.data_ptr(), cap,
@@ -347,20 +484,9 @@ def run_cflr(args):
 
     ms = statistics.mean(step_ms)
     ms_all, pairs_all, e2e_all = aggregate(dist, dev, ms, pairs, statistics.mean(e2e_s))
-
-    # roofline of the dominant kernel over the timed steps
-    rows = []
-    for name, a in after.items():
-        b = before.get(name, {"launches": 0, "ms": 0.0, "alg_bytes": 0})
-        rows.append((a["ms"] - b["ms"], a["launches"] - b["launches"],
-                     a["alg_bytes"] - b["alg_bytes"], name))
-    rows.sort(reverse=True)
-    kms, kl, kb, kname = rows[0]
-    pk = peaks()
-    achieved = (kb / 1e9) / (kms / 1e3) if kms > 0 else 0.0
-    traffic = traffic_from_profile(kname)
     launches = sum(r[1] for r in rows) + args.steps * n_named * 6   # + extraction kernels
     if rank != 0:
+        cflr.cflr_destroy(ctx)
         return
     line = {
         "metric": METRIC, "value": pairs_all / (ms_all / 1e3), "unit": UNIT,
@@ -374,16 +500,13 @@ def run_cflr(args):
                 "h2d_bytes_per_step": int(12 * g.n_edges),
                 "d2h_bytes_per_step": int(8 * pairs)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                     "traffic": traffic, "kernel": kname,
-                     "launches": kl, "avg_launch_ms": kms / max(kl, 1),
-                     "peak_src": pk["src"]},
+        "roofline": roofline_of(rows, "fsjpt_like" if kind == "fsjpt" else "fica_like"),
         "kernels": [{"name": r[3], "ms": round(r[0], 4), "launches": r[1],
                      "gbs": round((r[2] / 1e9) / (r[0] / 1e3), 1) if r[0] > 0 else None}
                     for r in rows if r[1]],
         "clocks": clk,
         "tuning": tuning,
+        "parity": parity,
         "solve": {"form": "graph", "iterations": solve_stats["iterations"],
                   "groups_per_bin": solve_stats["groups"],
                   "flops": solve_stats["flops"], "candidates": solve_stats["candidates"],
@@ -391,14 +514,70 @@ def run_cflr(args):
         "roofline_note": "kernel times from the same steps replayed with per-kernel CUDA "
                          "events (host-launched iterations) right after the timed region",
     }
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(wl["seed"], kind)
-        line["cpu_baseline"].pop("seconds")
-    print(json.dumps(line), flush=True)
     cflr.cflr_destroy(ctx)
+    del out, flush
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(kind)
+        line["cpu_baseline"].pop("seconds")
+    if extras and world == 1:
+        # the other workloads, each with its own steps (fewer of them)
+        sub = argparse.Namespace(**vars(args))
+        sub.steps = max(1, min(args.steps, 5))
+        sub.warmup = max(3, min(args.warmup, 3))
+        sub.vertices = None
+        line["fsjpt_like_500k"] = run_fsjpt_sub(sub)
+        line["dyck3_batch_256"] = run_dyck3_batch(sub, print_line=False)
+        sub.requests = args.extra_requests
+        sub.serve_warmup = 1.0
+        line["serving"] = run_serving(sub, print_line=False)
+    print(json.dumps(line), flush=True)
 
 
-def run_dyck3_batch(args):
+def run_fsjpt_sub(args) -> dict:
+    """The field-sensitive points-to workload in the timed configuration:
+    step time, pairs/s, the roofline of its dominant kernel and parity."""
+    import torch
+    from paper_2401_11029_gb300 import cflr
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    g = workload_graph(FSJPT["seed"], None, "fsjpt")
+    text = grammar_of("fsjpt")
+    ctx, tuning = timed_context(g, text, 0, stream.cuda_stream)
+    n_nt, n_named, _ = cflr.cflr_grammar_sizes(ctx)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    last = {}
+    pairs = device_step(ctx, n_named, None, last)
+    cap = max(cflr.cflr_get_pairs(ctx, x, count_only=True) for x in range(n_named))
+    out = (torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
+           torch.empty(max(cap, 1), dtype=torch.int32, device=dev))
+    for _ in range(max(0, args.warmup - 1)):
+        device_step(ctx, n_named, out)
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    step_ms = timed_steps(ctx, n_named, out, flush, stream, args.steps, 1, pairs, last)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    parity = parity_record(ctx, golden_of("fsjpt_like_500k", g), out)
+    rows = profiled_kernels(g, text, tuning, 0, stream.cuda_stream, n_named, out, flush,
+                            args.steps, args.warmup, pairs)
+    cflr.cflr_destroy(ctx)
+    ms = statistics.mean(step_ms)
+    return {"metric": METRIC, "value": pairs / (ms / 1e3), "unit": UNIT, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms,
+            "config": dict(FSJPT, edges=int(g.n_edges), pairs=int(pairs),
+                           l2="flushed between steps (256 MiB write)"),
+            "roofline": roofline_of(rows, "fsjpt_like"),
+            "kernels": [{"name": r[3], "ms": round(r[0], 4), "launches": r[1],
+                         "gbs": round((r[2] / 1e9) / (r[0] / 1e3), 1) if r[0] > 0 else None}
+                        for r in rows if r[1]][:6],
+            "clocks": clk, "tuning": tuning, "parity": parity,
+            "solve": {"form": "graph", "iterations": last["iterations"],
+                      "groups_per_bin": last["groups"]}}
+
+
+def run_dyck3_batch(args, print_line: bool = True):
     """The batched workload: 256 independent Dyck-3 instances (1k-50k vertices
     each, log-uniform).  Times the solve of all of
     them as one batch (every production of every instance in one launch
@@ -408,7 +587,7 @@ def run_dyck3_batch(args):
     import torch
     from paper_2401_11029_gb300 import cflr
 
-    world, rank, local, dist = dist_setup()
+    world, rank, local, dist = (1, 0, 0, None) if not print_line else dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
@@ -420,12 +599,7 @@ def run_dyck3_batch(args):
         for g in graphs:
             c = cflr.cflr_create(device=local, stream=stream.cuda_stream, form=form)
             cflr.cflr_load_grammar(c, text)
-            ids = {}
-            for name in g.labels:
-                i, _ = cflr.cflr_symbol_id(c, name)
-                ids[name] = i
-            lab = np.asarray([ids[x] for x in g.labels], np.uint32)[g.lab]
-            cflr.cflr_load_graph(c, g.n, g.src, lab, g.dst)
+            cflr.cflr_load_graph(c, g.n, g.src, label_array(c, g), g.dst)
             out.append(c)
         return out
 
@@ -448,9 +622,11 @@ def run_dyck3_batch(args):
                 ts.append(e0.elapsed_time(e1))
         return statistics.mean(ts)
 
+    clocks = ClockSampler(local)
+    clocks.start()
     ms_b = timed(lambda cs: cflr.cflr_solve_batch(cs), batched)
     ms_p = timed(lambda cs: [cflr.cflr_solve(c) for c in cs], plain)
-    named = None
+    clk = clocks.stop()
     pairs = 0
     for c in batched:
         n_nt, n_named, _ = cflr.cflr_grammar_sizes(c)
@@ -460,22 +636,42 @@ def run_dyck3_batch(args):
         n_nt, n_named, _ = cflr.cflr_grammar_sizes(c)
         pairs_p += sum(cflr.cflr_get_pairs(c, x, count_only=True) for x in range(n_named))
     assert pairs == pairs_p
-    if rank == 0:
-        line = {"metric": "batched CFL-r solve throughput (pairs / solve time)",
-                "value": pairs / (ms_b / 1e3), "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "u32", "data": "synthetic",
-                "config": {"workload": f"dyck3 x{args.instances} (seeds 4000..)",
-                           "vertices": int(sum(g.n for g in graphs)),
-                           "edges": int(sum(g.n_edges for g in graphs)), "pairs": pairs},
-                "plain_form": {"ms_per_step": ms_p, "value": pairs / (ms_p / 1e3),
-                               "form": "each instance alone, one launch sequence per "
-                                       "production"},
-                "batched_over_plain": ms_p / ms_b}
-        print(json.dumps(line), flush=True)
+    # the batched result against the oracle's per-instance fingerprints
+    parity = {"checked": False, "why": "no stored oracle fingerprints for these instances"}
+    gold = golden_of("dyck3_batch_256", None) if rank == 0 and args.instances == 256 else None
+    if gold:
+        bad = []
+        for c, g, gi in zip(batched, graphs, gold["instances"]):
+            if g.edge_digest() != gi["edge_digest"]:
+                bad.append((gi["seed"], "graph"))
+                continue
+            for x, fp in gi["pairs"].items():
+                i, _ = cflr.cflr_symbol_id(c, x)
+                s, d = cflr.cflr_get_pairs(c, i)
+                if gen.pair_fingerprint(gen.pair_keys(s, d)) != fp:
+                    bad.append((gi["seed"], x))
+        parity = {"checked": True, "match": not bad, "mismatched": bad[:8],
+                  "instances": len(gold["instances"]),
+                  "against": "oracle fingerprints tests/golden/dyck3_batch_256.json"}
     for c in batched + plain:
         cflr.cflr_destroy(c)
+    line = {"metric": "batched CFL-r solve throughput (pairs / solve time)",
+            "value": pairs / (ms_b / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"dyck3 x{args.instances} (seeds 4000..)",
+                       "vertices": int(sum(g.n for g in graphs)),
+                       "edges": int(sum(g.n_edges for g in graphs)), "pairs": pairs,
+                       "step": "cflr_solve_batch of all instances (graph form) after "
+                               "cflr_reset; extraction not timed"},
+            "plain_form": {"ms_per_step": ms_p, "value": pairs / (ms_p / 1e3),
+                           "form": "each instance alone, one launch sequence per "
+                                   "production"},
+            "batched_over_plain": ms_p / ms_b, "parity": parity, "clocks": clk}
+    if print_line and rank == 0:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def _gen_request(args):
@@ -483,17 +679,17 @@ def _gen_request(args):
     return gen.fica_like(n=n, n_a=2 * n, n_d=(3 * n) // 4, seed=seed)
 
 
-def run_serving(args):
+def run_serving(args, print_line: bool = True):
     """The serving workload: a Poisson stream of alias-analysis solves (sizes log-uniform
     in [5k, 300k] vertices) served with continuous batching; p50/p99 latency
     from arrival to result on the host, after a warm-up window."""
     import multiprocessing as mp
     reqs = gen.serving_stream(n_req=args.requests, rate=args.rate, seed=5)
-    # graphs are made before the first GPU call, in spawned workers
+    # graphs are made in spawned workers (a forked worker would inherit the
+    # parent's CUDA state)
     with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
         graphs = pool.map(_gen_request, [(r.n, r.seed) for r in reqs], chunksize=4)
     import torch
-    from paper_2401_11029_gb300 import cflr
     from paper_2401_11029_gb300.serve import Server, summarize
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
@@ -529,7 +725,9 @@ def run_serving(args):
                        "mem_budget_gb": args.serve_budget_gb, "max_active": args.max_active},
             "serving": dict(summ, wall_s=wall, warmup_s=args.serve_warmup, host_time=srv_time),
             "clocks": clk}
-    print(json.dumps(line), flush=True)
+    if print_line:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -538,10 +736,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cflr", choices=["cflr", "reference"])
-    ap.add_argument("--workload", default="fica",
-                    choices=["fica", "fsjpt", "dyck3_batch", "serving"])
+    ap.add_argument("--workload", default="all",
+                    choices=["all", "fica", "fsjpt", "dyck3_batch", "serving"],
+                    help="all: the alias workload's line with the other workloads as "
+                         "extra keys")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--extra-requests", type=int, default=200,
+                    help="requests of the serving run inside the default line")
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--serve-warmup", type=float, default=5.0)
     ap.add_argument("--serve-budget-gb", type=int, default=96)
@@ -559,8 +761,10 @@ def main():
         run_dyck3_batch(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "fsjpt":
+        run_cflr(args, "fsjpt")
     else:
-        run_cflr(args)
+        run_cflr(args, "fica", extras=args.workload == "all" and args.vertices is None)
 
 
 if __name__ == "__main__":

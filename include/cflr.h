@@ -234,7 +234,10 @@ int cflr_get_witness(const cflr_ctx *c, uint32_t nonterminal, uint32_t src, uint
  *     with CFLR_EINVAL; nothing is launched.
  *   - The first call for a device looks up the array's device address on
  *     that device (cudaGetSymbolAddress); make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the life of the process: a
+ *     cudaDeviceReset destroys the array (and every context of this library
+ *     on that device), and this entry point must not be called for that
+ *     device afterwards.
  *   - All calls share the one array per device: calls whose work overlaps
  *     on the GPU (other host threads, or contexts on other streams) race and
  *     may return wrong pairs.  Serialise them.

@@ -22,6 +22,7 @@
 #include "kernels.cuh"
 
 #include <cstdio>
+#include <mutex>
 
 namespace cflr {
 
@@ -1858,10 +1859,17 @@ static void set_bin_smem_attrs() {
                          (int)SMEM_BITMAP_MAX);
 }
 
+// cudaFuncSetAttribute applies to the device current at the call, so the
+// limits are set once per device (under a lock: contexts on several host
+// threads may launch at the same time).
 static void set_smem_attrs() {
-    static bool done = false;
-    if (done) return;
-    done = true;
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 64 && done[dev]) return;
+    if (dev < 64) done[dev] = true;
     set_bin_smem_attrs<false>();
     set_bin_smem_attrs<true>();
     cudaFuncSetAttribute(k_extract_big, cudaFuncAttributeMaxDynamicSharedMemorySize,

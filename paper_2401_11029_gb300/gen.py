@@ -80,6 +80,28 @@ class Graph:
             np.sum(h, dtype=np.uint64) if h.size else 0)
 
 
+def pair_keys(src, dst) -> np.ndarray:
+    """Pairs (src[i], dst[i]) as 64-bit keys src << 32 | dst."""
+    return (np.asarray(src).astype(np.uint32).astype(np.uint64) << np.uint64(32)) | \
+        np.asarray(dst).astype(np.uint32).astype(np.uint64)
+
+
+def pair_fingerprint(keys: np.ndarray) -> str:
+    """Order-independent digest of a set of 64-bit pair keys: the count, and
+    the xor and the sum of a 64-bit mix of every key.  Stored fingerprints of
+    the oracle's full-size results are compared against it."""
+    x = np.asarray(keys).astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        x ^= x >> np.uint64(31)
+        x *= np.uint64(0x7FB5D329728EA185)
+        x ^= x >> np.uint64(27)
+        x *= np.uint64(0x81DADEF4BC2DD44D)
+        x ^= x >> np.uint64(33)
+    xr = int(np.bitwise_xor.reduce(x)) if x.size else 0
+    sm = int(np.sum(x, dtype=np.uint64)) if x.size else 0
+    return "%d:%016x:%016x" % (x.size, xr, sm)
+
+
 def _mix64(x: np.ndarray) -> np.ndarray:
     """splitmix64 finaliser on a uint64 array (wrapping arithmetic)."""
     x = x.astype(np.uint64, copy=True)

@@ -31,19 +31,9 @@ RANDOM_GRAMMARS = [
 
 
 def keys_of(src, dst) -> np.ndarray:
-    return (np.asarray(src, np.uint64) << np.uint64(32)) | np.asarray(dst, np.uint64)
+    return gen.pair_keys(src, dst)
 
 
-def fingerprint(keys: np.ndarray) -> str:
-    """Order-independent digest of a set of uint64 keys: count, xor and sum of
-    a 64-bit mix of every key."""
-    x = keys.astype(np.uint64, copy=True)
-    with np.errstate(over="ignore"):
-        x ^= x >> np.uint64(31)
-        x *= np.uint64(0x7FB5D329728EA185)
-        x ^= x >> np.uint64(27)
-        x *= np.uint64(0x81DADEF4BC2DD44D)
-        x ^= x >> np.uint64(33)
-    xr = int(np.bitwise_xor.reduce(x)) if x.size else 0
-    sm = int(np.sum(x, dtype=np.uint64)) if x.size else 0
-    return "%d:%016x:%016x" % (keys.size, xr, sm)
+# order-independent digest of a set of uint64 keys (count, xor and sum of a
+# 64-bit mix of every key)
+fingerprint = gen.pair_fingerprint

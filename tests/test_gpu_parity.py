@@ -236,29 +236,68 @@ def test_full_size_fica_200k():
     _check_full("fica_like_200k", "fica", gen.fica_like())
 
 
-def test_full_size_fica_200k_launch_config_of_bench():
-    """The bench's call sequence: reset from device-resident edges, solve,
-    extract to device buffers, read back and compare."""
+def _check_timed_configuration(kind, n_vertices):
+    """The exact launch configuration bench.py times (graph form, the cached
+    tuned schedule through cflr_autotune, reset + solve + extraction to
+    device buffers, twice on the same context) against the oracle's stored
+    fingerprints of every named non-terminal."""
     import torch
-    gold = _golden("fica_like_200k")
-    g = gen.fica_like()
+    import bench
+    g = bench.workload_graph(bench.WORKLOAD["seed"] if kind == "fica" else bench.FSJPT["seed"],
+                             n_vertices, kind)
+    gold = _golden(bench.golden_name(kind, g.n))
     if g.edge_digest() != gold["edge_digest"]:
         pytest.skip("the generator made a different graph on this machine")
-    with Solver(gen.grammar_text("fica"), profile=1) as s:
-        s.load(g)
+    stream = torch.cuda.current_stream()
+    ctx, tuning = bench.timed_context(g, bench.grammar_of(kind), 0, stream.cuda_stream)
+    try:
+        # the schedule is the cached one the bench line reports
+        assert open(bench.TUNING_CACHE).read().count(f"_{g.n}_{g.n_edges} ") >= 1
+        n_nt, n_named, _ = cflr.cflr_grammar_sizes(ctx)
+        cap = max(int(v.split(":")[0]) for v in gold["pairs"].values())
+        out = (torch.empty(cap, dtype=torch.int32, device="cuda"),
+               torch.empty(cap, dtype=torch.int32, device="cuda"))
         for _ in range(2):                       # second pass runs on reused buffers
-            cflr.cflr_reset(s.ctx)
-            s.solve()
-        for x, fp in gold["pairs"].items():
-            i = s.nt_id(x)
-            cnt = cflr.cflr_get_pairs(s.ctx, i, count_only=True)
-            d_s = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
-            d_d = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
-            cflr.cflr_get_pairs_device(s.ctx, i, d_s.data_ptr(), d_d.data_ptr(), cnt)
-            keys = keys_of(d_s[:cnt].cpu().numpy().view(np.uint32),
-                           d_d[:cnt].cpu().numpy().view(np.uint32))
-            assert np.all(keys[1:] > keys[:-1]), "pairs not sorted by (src, dst)"
-            assert fingerprint(keys) == fp, x
+            total = bench.device_step(ctx, n_named, out)
+            assert total == gold["total_pairs"]
+            fps = bench.device_fingerprints(ctx, list(gold["pairs"]), out)
+            for x, fp in gold["pairs"].items():
+                assert fps[x] == fp, x
+    finally:
+        cflr.cflr_destroy(ctx)
+    return tuning
+
+
+def test_full_size_fica_200k_launch_config_of_bench():
+    t = _check_timed_configuration("fica", 200_000)
+    assert t["bin_limit"][2] == t["bin_limit"][1] + 1      # bin 2 routed to the bitmap bin
+
+
+def test_full_size_fsjpt_500k_launch_config_of_bench():
+    _check_timed_configuration("fsjpt", 500_000)
+
+
+def test_full_size_dyck3_batch_256_graph_form():
+    """The 256 Dyck-3 instances as bench.py times them: graph-form contexts
+    solved together by cflr_solve_batch after cflr_reset, twice."""
+    gold = _golden("dyck3_batch_256")
+    text = gen.grammar_text("dyck3")
+    graphs = gen.dyck3_batch(count=256, seed0=4000)
+    solvers = [Solver(text, form=cflr.CFLR_FORM_GRAPH) for _ in graphs]
+    try:
+        for s, g, gi in zip(solvers, graphs, gold["instances"]):
+            assert g.edge_digest() == gi["edge_digest"]
+            s.load(g)
+        for _ in range(2):
+            for s in solvers:
+                cflr.cflr_reset(s.ctx)
+            cflr.cflr_solve_batch([s.ctx for s in solvers])
+            for s, gi in zip(solvers, gold["instances"]):
+                for x, fp in gi["pairs"].items():
+                    assert fingerprint(s.pairs(x)) == fp, (gi["seed"], x)
+    finally:
+        for s in solvers:
+            s.close()
 
 
 def test_full_size_fsjpt_500k():

@@ -57,3 +57,36 @@ def test_noalloc_extraction_rejects_graphs_over_the_limit():
         # the allocating entry point still serves this graph
         src, dst = cflr.cflr_get_pairs(s.ctx, 0)
         assert list(zip(src.tolist(), dst.tolist())) == [(0, 1), (0, n - 1), (1, n - 1)]
+
+
+def test_noalloc_extraction_at_the_vertex_limit_with_long_rows():
+    """A graph of exactly CFLR_NOALLOC_MAX_VERTICES vertices: the long-row list
+    fills its last slots' region and rows of more than 1024 pairs take the
+    per-row bitmap (128 KiB of shared memory at this size); both entry points
+    must agree, on two calls in a row."""
+    torch = pytest.importorskip("torch")
+    n = cflr.CFLR_NOALLOC_MAX_VERTICES
+    rng = np.random.default_rng(91)
+    ids = rng.choice(n, size=4000, replace=False).astype(np.uint32)
+    # 'a': vertex ids[0] reaches 1500 scattered vertices directly and a path
+    # of 400 more through them; 'b': a second relation with a 2000-pair row
+    hub, fan, path = ids[0], ids[1:1501], ids[1501:1901]
+    src_a = np.concatenate([np.full(fan.size, hub, np.uint32), path[:-1], [fan[0]]])
+    dst_a = np.concatenate([fan, path[1:], [path[0]]])
+    src_b = np.full(2000, ids[1901], np.uint32)
+    dst_b = ids[1902:3902]
+    g = gen.Graph(n=n, labels=["a", "b"], src=np.concatenate([src_a, src_b]),
+                  lab=np.concatenate([np.zeros(src_a.size, np.uint32),
+                                      np.ones(src_b.size, np.uint32)]),
+                  dst=np.concatenate([dst_a, dst_b]))
+    with Solver("S -> S S | a\nT -> b\n") as s:
+        s.load(g)
+        s.solve()
+        for name in ("S", "T"):
+            nt = s.nt_id(name)
+            cnt = cflr.cflr_get_pairs(s.ctx, nt, count_only=True)
+            row_len = np.bincount((s.pairs(name) >> np.uint64(32)).astype(np.int64)).max()
+            assert row_len > 1024, (name, row_len)
+            ref = _device_pairs(cflr.cflr_get_pairs_device, s.ctx, nt, cnt, torch)
+            got = _device_pairs(cflr.cflr_get_pairs_device_noalloc, s.ctx, nt, cnt, torch)
+            assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1]), name
