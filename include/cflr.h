@@ -96,6 +96,12 @@ typedef struct {
                                    costs 8 more bytes per pair-set slot and per
                                    candidate, and needs at most 32768
                                    non-terminals                                    */
+    int test_fixed_pair_sets;   /* testing only: nonzero keeps every pair set at its
+                                   first size.  A set that fills up then stops the
+                                   solve: its hash probes are capped at one pass over
+                                   the table and report the full set, cflr_solve
+                                   returns CFLR_ECUDA and the context needs a new
+                                   graph (it stays usable)                          */
 } cflr_config;
 
 typedef struct {

@@ -60,7 +60,8 @@ class cflr_config(ctypes.Structure):
                 ("form", ctypes.c_int), ("profile", ctypes.c_int),
                 ("autotune_cache", ctypes.c_char_p), ("initial_capacity", ctypes.c_uint32),
                 ("size_hint", ctypes.c_uint32), ("stop_on_first_converged", ctypes.c_int),
-                ("keep_vertex_order", ctypes.c_int), ("witness", ctypes.c_int)]
+                ("keep_vertex_order", ctypes.c_int), ("witness", ctypes.c_int),
+                ("test_fixed_pair_sets", ctypes.c_int)]
 
 
 class cflr_tuning(ctypes.Structure):

@@ -93,10 +93,17 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
 struct HashAcc {
     uint32_t *tab;
     int lg;
+    unsigned *err;     // gets OVF_FULL if a probe sequence finds the table full
     __device__ __forceinline__ uint32_t ins(uint32_t w, uint32_t b) const {
         const uint32_t m = (1u << lg) - 1;
         uint32_t s = (w * 2654435761u) >> (32 - lg);
-        for (;;) {
+        // at most one pass over the table (the callers keep it at most half
+        // full, so the pass always ends early)
+        for (uint32_t p = 0;; p++) {
+            if (p > m) {
+                atomicOr(err, OVF_FULL);
+                return 0;
+            }
             const uint32_t cur = ((volatile uint32_t *)tab)[2 * s];
             if (cur == w) break;
             if (cur == EMPTY32) {
@@ -132,15 +139,21 @@ struct BitmapAcc {
     __device__ __forceinline__ void set(uint32_t w, uint32_t b) const { atomicOr(&bm[w], b); }
 };
 
+// Whether a pair set holds `key`; a probe sequence that passes over the
+// whole table (a full set: k_check keeps every set at most half full) ends
+// with OVF_FULL in *err.
 __device__ __forceinline__ bool htab_contains(const unsigned long long *tab,
-                                              unsigned long long m, unsigned long long key) {
+                                              unsigned long long m, unsigned long long key,
+                                              unsigned *err) {
     unsigned long long h = pair_home(key, m);
-    for (;;) {
+    for (unsigned long long p = 0; p <= m; p++) {
         unsigned long long v = tab[h];
         if (v == key) return true;
         if (v == EMPTY_KEY) return false;
         h = (h + 1) & m;
     }
+    atomicOr(err, OVF_FULL);
+    return false;
 }
 
 // Warp-collective append of flagged keys to the candidate buffer.  All 32
@@ -549,18 +562,22 @@ __device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uin
 // k gathers row k of the other operand as a list of tiles: all of b's row k
 // for dA . B, and for A_old . dB the tiles of a's column k that precede the
 // last merge's (dn.y of them, at the end of the list).
-//   Plain groups: warp `warp_id` of `nwarps` takes the entries
-// warp_id + nwarps*l (lane l) of every block of 32*nwarps entries, so all
-// warps of a CTA get work even for short deltas.
-//   Family groups (optimisation 4): warp `warp_id` takes the entries
-// warp_id, warp_id + nwarps, ..., and for each its lanes take the members
-// (their gathered slots are consecutive); a member's row counts only when
-// its occupancy bit is set.  Tagged families key the accumulator by member
-// and word, and emit to each member's non-terminal.
-// A list of 32 or more tiles is walked by the whole warp (coalesced 16-byte
-// loads, two in flight per lane); shorter ones are packed 32 tiles per step
-// with a per-lane search of the owning row.  Returns the emitted count.
-template <bool WIT, class Acc>
+//   Plain groups: warp `warp_id` of `nwarps` takes an even share of the
+// entries, 32 consecutive ones at a time (lane l the l-th).
+//   Family groups (optimisation 4): when the members' gathered slots are
+// consecutive, the same shares of the entries, each entry's members found
+// from its occupancy bits; otherwise warp `warp_id` takes the (entry, member)
+// items warp_id*32 + l of every block of nwarps*32.  A member's row counts
+// only when its occupancy bit is set.  Tagged families key the accumulator
+// by member and word, and emit to each member's non-terminal.
+// The 32 tile lists the lanes hold are walked together as one packed
+// sequence of 16-byte tile pairs (see `walk`).  Returns the emitted count.
+
+// TAGS false: the caller never gets a tagged family group (the bitmap bin:
+// a tagged family stays within bin 2's limit or splits into its members), so
+// the member tags are not carried through the walk.  WALK_U: 16-byte
+// tile-pair loads each lane of a walking warp has in flight.
+template <bool WIT, bool TAGS, int WALK_U, class Acc>
 __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab &P,
                                                 const WorkBufs &W, const GroupInfo &gi,
                                                 uint2 own, uint32_t warp_id, uint32_t nwarps,
@@ -584,7 +601,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
     // every product is already present, so callers vote first
     auto emit_bits = [&](uint32_t n0, uint32_t wd0, uint32_t n1, uint32_t wd1, uint32_t n2,
                          uint32_t wd2, uint32_t n3, uint32_t wd3, uint32_t tag, uint32_t k) {
-        const uint32_t slot = gi.tagged ? P.prod[P.fam_prod[gi.first + tag]].x : gi.c;
+        const uint32_t slot = TAGS && gi.tagged ? P.prod[P.fam_prod[gi.first + tag]].x : gi.c;
         if (gi.probe && (n0 | n1 | n2 | n3)) {
             const unsigned long long *ht = S.htab[slot];
             const unsigned long long hm = S.hmask[slot];
@@ -592,7 +609,8 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                 uint32_t keep = 0;
                 for (uint32_t r = nb; r; r &= r - 1) {
                     const uint32_t i = __ffs(r) - 1;
-                    if (!htab_contains(ht, hm, group_key(gi, wd * 32 + i))) keep |= 1u << i;
+                    if (!htab_contains(ht, hm, group_key(gi, wd * 32 + i), &W.cnt->overflow))
+                        keep |= 1u << i;
                 }
                 return keep;
             };
@@ -640,86 +658,85 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
         put(n2, wd2);
         put(n3, wd3);
         // the members' candidate counts (k_check sizes their pair sets)
-        if (gi.tagged && cnt) atomicAdd(&S.cand[slot], (unsigned long long)cnt);
+        if (TAGS && gi.tagged && cnt) atomicAdd(&S.cand[slot], (unsigned long long)cnt);
         emitted += total;
     };
     auto key_of = [&](uint32_t wd, uint32_t tag) {
-        return gi.tagged ? (tag << TAG_SHIFT) | wd : wd;
+        return TAGS && gi.tagged ? (tag << TAG_SHIFT) | wd : wd;
     };
-    // two tiles (w.x, w.y) and (w.z, w.w) of member tag, gathered through
-    // delta entry k, nv of them valid
-    auto consume_tiles = [&](uint4 w, uint32_t nv, uint32_t tag, uint32_t k) {
-        const uint32_t n0 = nv > 0 ? acc.ins(key_of(w.x, tag), w.y) : 0u;
-        const uint32_t n1 = nv > 1 ? acc.ins(key_of(w.z, tag), w.w) : 0u;
-        if (__any_sync(FULL_MASK, (n0 | n1) != 0)) emit_bits(n0, w.x, n1, w.z, 0u, 0u, 0u, 0u, tag, k);
-    };
-    // the tile lists held by the lanes (toff, tn; member tag; delta entry k)
+    // The tile lists held by the lanes (toff, tn; member tag; delta entry k),
+    // walked as one sequence of 16-byte tile pairs: the lists with tiles are
+    // moved to the front lanes, list l owns the pairs [excl_l, incl_l) of the
+    // sequence, and each lane loads the pair at its position in WALK_U
+    // windows of 32 positions at a time (all loads in flight before any is
+    // used).  The owner of position p is the number of lists that end at or
+    // before p: the lists that end before the window (a ballot) plus those
+    // that end inside it (one bit each, OR-reduced over the warp).  Segments
+    // start on 16-byte boundaries and a tile section holds an even number of
+    // tiles, so a pair never leaves its segment; the second tile of a list's
+    // last pair is ignored when the list has an odd count.
     auto walk = [&](uint32_t toff, uint32_t tn, uint32_t tag, uint32_t k) {
-        // long tile lists: the warp strides over one list at a time
-        unsigned lm = __ballot_sync(FULL_MASK, tn >= 32);
-        while (lm) {
-            const int l = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const uint32_t *tl = pool + __shfl_sync(FULL_MASK, toff, l);
-            const uint32_t T = __shfl_sync(FULL_MASK, tn, l);
-            const uint32_t ltag = __shfl_sync(FULL_MASK, tag, l);
-            const uint32_t lk = WIT ? __shfl_sync(FULL_MASK, k, l) : 0u;
-            for (uint32_t qb = 0; qb < T; qb += 128) {
-                uint4 w[2];
-                uint32_t nv[2];
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const uint32_t q = qb + 64 * h + 2 * lane;
-                    w[h] = make_uint4(0, 0, 0, 0);
-                    nv[h] = 0;
-                    if (q + 2 <= T) {
-                        w[h] = *reinterpret_cast<const uint4 *>(tl + 2 * q);
-                        nv[h] = 2;
-                    } else if (q < T) {
-                        const uint2 t = *reinterpret_cast<const uint2 *>(tl + 2 * q);
-                        w[h].x = t.x;
-                        w[h].y = t.y;
-                        nv[h] = 1;
-                    }
-                }
-                // four tiles per lane, one vote and one reservation
-                const uint32_t n0 = nv[0] > 0 ? acc.ins(key_of(w[0].x, ltag), w[0].y) : 0u;
-                const uint32_t n1 = nv[0] > 1 ? acc.ins(key_of(w[0].z, ltag), w[0].w) : 0u;
-                const uint32_t n2 = nv[1] > 0 ? acc.ins(key_of(w[1].x, ltag), w[1].y) : 0u;
-                const uint32_t n3 = nv[1] > 1 ? acc.ins(key_of(w[1].z, ltag), w[1].w) : 0u;
-                if (__any_sync(FULL_MASK, (n0 | n1 | n2 | n3) != 0))
-                    emit_bits(n0, w[0].x, n1, w[0].z, n2, w[1].x, n3, w[1].z, ltag, lk);
-            }
-        }
-        // short tile lists: packed, 32 tiles per step
-        const uint32_t stn = tn < 32 ? tn : 0;
-        const uint32_t incl = warp_incl_scan(stn, lane);
+        const unsigned nz = __ballot_sync(FULL_MASK, tn != 0);
+        if (!nz) return;
+        const uint32_t cnt = __popc(nz);
+        const uint32_t src = (uint32_t)lane < cnt ? select_bit(nz, (uint32_t)lane) : 0u;
+        toff = __shfl_sync(FULL_MASK, toff, src);
+        tn = __shfl_sync(FULL_MASK, tn, src);
+        if (TAGS || WIT) tag = __shfl_sync(FULL_MASK, tag, src);
+        if (WIT) k = __shfl_sync(FULL_MASK, k, src);
+        if ((uint32_t)lane >= cnt) tn = 0;
+        const uint32_t np = (tn + 1) >> 1;
+        const uint32_t incl = warp_incl_scan(np, lane);
+        const uint32_t excl = incl - np;
         const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
-        for (uint32_t fb = 0; fb < total; fb += 32) {
-            const uint32_t f = fb + lane;
-            int lo = 0, hi = 31;
+        const uint32_t le = FULL_MASK >> (31 - lane);
+        for (uint32_t b = 0; b < total; b += 32 * WALK_U) {
+            uint4 w[WALK_U];
+            uint32_t nv[WALK_U], tg[WALK_U], kk[WALK_U];
 #pragma unroll
-            for (int st = 0; st < 5; st++) {     // first lane whose inclusive sum > f
-                const int mid = (lo + hi) >> 1;
-                const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
-                if (f < v) hi = mid; else lo = mid + 1;
+            for (int u = 0; u < WALK_U; u++) {
+                w[u] = make_uint4(0, 0, 0, 0);
+                nv[u] = tg[u] = kk[u] = 0;
+                const uint32_t bu = b + 32 * u, p = bu + lane;
+                if (bu >= total) continue;          // uniform: the last windows may be empty
+                const uint32_t first = __popc(__ballot_sync(FULL_MASK, incl <= bu));
+                const uint32_t ends =
+                    __reduce_or_sync(FULL_MASK, (incl > bu && incl - bu < 32) ? 1u << (incl - bu) : 0u);
+                const uint32_t own = min(first + __popc(ends & le), 31u);
+                const uint32_t o_toff = __shfl_sync(FULL_MASK, toff, own);
+                const uint32_t o_excl = __shfl_sync(FULL_MASK, excl, own);
+                const uint32_t o_tn = __shfl_sync(FULL_MASK, tn, own);
+                tg[u] = (TAGS || WIT) ? __shfl_sync(FULL_MASK, tag, own) : 0u;
+                kk[u] = WIT ? __shfl_sync(FULL_MASK, k, own) : 0u;
+                if (p < total) {
+                    const uint32_t rel = p - o_excl;
+                    nv[u] = min(2u, o_tn - 2 * rel);
+                    w[u] = *reinterpret_cast<const uint4 *>(pool + o_toff + 4 * rel);
+                }
             }
-            const int owner = lo > 31 ? 31 : lo;
-            const uint32_t o_toff = __shfl_sync(FULL_MASK, toff, owner);
-            const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
-            const uint32_t o_len = __shfl_sync(FULL_MASK, stn, owner);
-            const uint32_t o_tag = __shfl_sync(FULL_MASK, tag, owner);
-            const uint32_t o_kk = WIT ? __shfl_sync(FULL_MASK, k, owner) : 0u;
-            uint4 w = make_uint4(0, 0, 0, 0);
-            uint32_t nv = 0;
-            if (f < total) {
-                const uint2 t = *reinterpret_cast<const uint2 *>(
-                    pool + o_toff + 2 * (f - (o_incl - o_len)));
-                w.x = t.x;
-                w.y = t.y;
-                nv = 1;
+            uint32_t nb[2 * WALK_U], any = 0;
+#pragma unroll
+            for (int u = 0; u < WALK_U; u++) {
+                nb[2 * u] = nv[u] > 0 ? acc.ins(key_of(w[u].x, tg[u]), w[u].y) : 0u;
+                nb[2 * u + 1] = nv[u] > 1 ? acc.ins(key_of(w[u].z, tg[u]), w[u].w) : 0u;
+                any |= nb[2 * u] | nb[2 * u + 1];
             }
-            consume_tiles(w, nv, o_tag, o_kk);
+            // nearly every product is already present: one vote, then the
+            // new bits go out four tiles per reservation (with tags or
+            // witnesses, one window's pair at a time)
+            if (__any_sync(FULL_MASK, any != 0)) {
+                if constexpr (!TAGS && !WIT) {
+#pragma unroll
+                    for (int u = 0; u < WALK_U; u += 2)
+                        emit_bits(nb[2 * u], w[u].x, nb[2 * u + 1], w[u].z, nb[2 * u + 2],
+                                  w[u + 1].x, nb[2 * u + 3], w[u + 1].z, 0u, 0u);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < WALK_U; u++)
+                        emit_bits(nb[2 * u], w[u].x, nb[2 * u + 1], w[u].z, 0u, 0u, 0u, 0u, tg[u],
+                                  kk[u]);
+                }
+            }
         }
     };
     if (gi.part == PART_U) {        // c -> a: the delta entries themselves
@@ -743,10 +760,12 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
         const uint32_t ow = S.occ_w[g0], lx0 = S.local[g0];
         const uint32_t w0 = lx0 >> 5, sh = lx0 & 31, wlast = (lx0 + gi.F - 1) >> 5;
         const unsigned long long fmask = gi.F == 64 ? ~0ull : (1ull << gi.F) - 1;
-        for (uint32_t cb = warp_id * 32; cb < d; cb += nwarps * 32) {
+        const uint32_t lo_e = (uint32_t)((unsigned long long)d * warp_id / nwarps);
+        const uint32_t hi_e = (uint32_t)((unsigned long long)d * (warp_id + 1) / nwarps);
+        for (uint32_t cb = lo_e; cb < hi_e; cb += 32) {
             const uint32_t e = cb + lane;
             uint32_t k = 0, mlo = 0, mhi = 0;
-            if (e < d) {
+            if (e < hi_e) {
                 k = pool[dstart + e];
                 const uint32_t *ok = oc + (oo + k) * ow + w0;
                 const uint32_t x0 = ok[0];
@@ -814,10 +833,13 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
         }
         return emitted;
     }
-    for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
-        const uint32_t e = cb + lane * nwarps;
+    // an even share of the entries per warp, in runs of 32 (coalesced)
+    const uint32_t lo_e = (uint32_t)((unsigned long long)d * warp_id / nwarps);
+    const uint32_t hi_e = (uint32_t)((unsigned long long)d * (warp_id + 1) / nwarps);
+    for (uint32_t cb = lo_e; cb < hi_e; cb += 32) {
+        const uint32_t e = cb + lane;
         uint32_t toff = 0, tn = 0, k = 0;
-        if (e < d) {
+        if (e < hi_e) {
             k = pool[dstart + e];
             const uint4 gd = dg[k];
             toff = gd.x;
@@ -835,9 +857,11 @@ __device__ __forceinline__ void preload_mask(const SlotTab &S, const GroupInfo &
                                              const Acc &acc, uint32_t tid, uint32_t nth) {
     const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
     const uint32_t *tl = S.pool[gi.c] + md.x;
-    for (uint32_t q = tid; q < md.y; q += nth) {
-        const uint2 t = *reinterpret_cast<const uint2 *>(tl + 2 * q);
+    // tile pairs (a tile section holds an even number of tiles)
+    for (uint32_t q = tid; 2 * q < md.y; q += nth) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(tl + 4 * q);
         acc.set(t.x, t.y);
+        if (2 * q + 1 < md.y) acc.set(t.z, t.w);
     }
 }
 
@@ -860,13 +884,13 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(
         const int lg = min((int)gi.lg, LG);
         clear_table(tab, lg, lane, 32);
         __syncwarp();
-        const HashAcc acc{tab, lg};
+        const HashAcc acc{tab, lg, &W.cnt->overflow};
         if (!gi.probe) {
             preload_mask(S, gi, acc, lane, 32);
             __syncwarp();
         }
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, 0, 1, lane, acc, ck);
+        const uint32_t e = expand_rows<WIT, true, 2>(S, P, W, gi, own, 0, 1, lane, acc, ck);
         if (lane == 0 && e) {
             if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)e);
             bytes += 12ull * e;
@@ -883,26 +907,36 @@ __global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S,
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint32_t emitted_sh;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __shared__ unsigned long long next_sh[2];
     const unsigned long long n_groups = min(W.cnt->groups[bin], W.group_cap[bin]);
     CandChunk ck{0, 0};
     unsigned long long bytes = 0;
-    for (unsigned long long g = blockIdx.x; g < n_groups; g += gridDim.x) {
+    // groups are claimed one at a time from a cursor (their sizes vary a
+    // lot), the next one while the current one starts
+    if (threadIdx.x == 0) next_sh[0] = atomicAdd(&W.cnt->claim[bin], 1ull);
+    __syncthreads();
+    unsigned long long g = next_sh[0];
+    for (uint32_t q = 1; g < n_groups; q ^= 1) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
         const int lg = min((int)gi.lg, LG);
         clear_table(smem, lg, threadIdx.x, blockDim.x);
-        if (threadIdx.x == 0) emitted_sh = 0;
+        if (threadIdx.x == 0) {
+            emitted_sh = 0;
+            next_sh[q] = atomicAdd(&W.cnt->claim[bin], 1ull);
+        }
         __syncthreads();
-        const HashAcc acc{smem, lg};
+        const HashAcc acc{smem, lg, &W.cnt->overflow};
         if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc, ck);
+        const uint32_t e = expand_rows<WIT, true, 2>(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc, ck);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
             if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)emitted_sh);
             bytes += 12ull * emitted_sh;
         }
+        g = next_sh[q];
     }
     release_chunk(W, ck, lane);
     if (threadIdx.x == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
@@ -934,8 +968,13 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
     const BitmapAcc acc{bm};
     CandChunk ck{0, 0};
     unsigned long long bytes = 0;
-    for (unsigned long long g = (unsigned long long)blockIdx.x * GPC + part; g < n_groups;
-         g += (unsigned long long)gridDim.x * GPC) {
+    // each part claims groups one at a time from a cursor (their sizes vary
+    // a lot), the next one while the current one starts
+    __shared__ unsigned long long next_sh[GPC][2];
+    if (ptid == 0) next_sh[part][0] = atomicAdd(&W.cnt->claim[bin], 1ull);
+    psync();
+    unsigned long long g = next_sh[part][0];
+    for (uint32_t q = 1; g < n_groups; q ^= 1) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
         const uint32_t words = (gi.n + 31) >> 5;
         if (use_smem) {   // 16-byte stores: the stride is a multiple of four words
@@ -944,18 +983,23 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
         } else {
             for (uint32_t s = ptid; s < words; s += TPG) bm[s] = 0;
         }
-        if (ptid == 0) emitted_sh[part] = 0;
+        if (ptid == 0) {
+            emitted_sh[part] = 0;
+            next_sh[part][q] = atomicAdd(&W.cnt->claim[bin], 1ull);
+        }
         psync();
         if (!gi.probe) preload_mask(S, gi, acc, ptid, TPG);
         psync();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows<WIT>(S, P, W, gi, own, wib % (8 / GPC), 8 / GPC, lane, acc, ck);
+        const uint32_t e = expand_rows<WIT, false, 4>(S, P, W, gi, own, wib % (8 / GPC), 8 / GPC,
+                                                     lane, acc, ck);
         if (lane == 0 && e) atomicAdd(&emitted_sh[part], e);
         psync();
         if (ptid == 0 && emitted_sh[part]) {
             if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)emitted_sh[part]);
             bytes += 12ull * emitted_sh[part];
         }
+        g = next_sh[part][q];
     }
     release_chunk(W, ck, lane);
     if (ptid == 0 && bytes) atomicAdd(&W.cnt->bytes_bin[bin], bytes);
@@ -965,55 +1009,67 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
 // k_commit: global dedupe of candidates into the per-slot pair sets
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
-    if (W.cnt->overflow & OVF_PRE) return;     // the iteration is re-run after a growth
+// The commit stages a CTA's new pairs and touched rows in shared memory and
+// reserves their room in the global lists with one atomic per list per
+// round: per-warp atomics on those few counters serialise at the L2 (every
+// warp of the grid hits the same addresses).
+constexpr uint32_t COMMIT_ROUND = 512;    // candidates a CTA takes per round
+constexpr uint32_t COMMIT_SLOTS = 1024;   // per-slot counts kept in shared memory
+
+__global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W, uint32_t n_slots) {
+    __shared__ unsigned long long st_key[COMMIT_ROUND];
+    __shared__ uint32_t st_slot[COMMIT_ROUND];
+    __shared__ uint2 st_touch[2 * COMMIT_ROUND];
+    __shared__ uint32_t slot_new[COMMIT_SLOTS];
+    __shared__ uint32_t n_new, n_touch;
+    __shared__ unsigned long long base_new, base_touch;
+    if (W.cnt->overflow & OVF_STOP) return;    // the iteration is re-run after a growth
     const int lane = threadIdx.x & 31;
     const int par = *W.parity;
     unsigned long long *out_n = &W.touched_n[par ^ 1];
     uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long nc = min(W.cnt->cand, W.cand_cap);
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x +
-                                   (threadIdx.x & ~31u);
-         base < nc; base += stride) {
-        const unsigned long long t = base + lane;
-        bool isnew = false;
-        unsigned long long key = 0;
-        uint32_t slot = EMPTY32;
-        if (t < nc) slot = W.cand_slot[t];
-        if (slot != EMPTY32) {            // not an unused reserved entry
-            key = W.cand_key[t];
-            unsigned long long *tab = S.htab[slot];
-            const unsigned long long m = S.hmask[slot];
-            unsigned long long h = pair_home(key, m);
-            for (;;) {
-                unsigned long long v = tab[h];
-                if (v == key) break;
-                if (v == EMPTY_KEY) {
-                    v = atomicCAS(&tab[h], EMPTY_KEY, key);
-                    if (v == EMPTY_KEY) {
-                        isnew = true;
-                        if (W.cand_wit && S.hval[slot]) S.hval[slot][h] = W.cand_wit[t];
+    const bool hist = n_slots <= COMMIT_SLOTS;
+    for (uint32_t s = threadIdx.x; s < COMMIT_SLOTS; s += blockDim.x) slot_new[s] = 0;
+    if (threadIdx.x == 0) n_new = n_touch = 0;
+    __syncthreads();
+    for (unsigned long long r0 = (unsigned long long)blockIdx.x * COMMIT_ROUND; r0 < nc;
+         r0 += (unsigned long long)gridDim.x * COMMIT_ROUND) {
+        for (uint32_t q = 0; q < COMMIT_ROUND; q += blockDim.x) {
+            const unsigned long long t = r0 + q + threadIdx.x;
+            bool isnew = false;
+            unsigned long long key = 0;
+            uint32_t slot = EMPTY32;
+            if (t < nc) slot = W.cand_slot[t];
+            if (slot != EMPTY32) {            // not an unused reserved entry
+                key = W.cand_key[t];
+                unsigned long long *tab = S.htab[slot];
+                const unsigned long long m = S.hmask[slot];
+                unsigned long long h = pair_home(key, m);
+                bool placed = false;
+                // at most one pass over the set (k_check keeps it half full)
+                for (unsigned long long p = 0; p <= m; p++) {
+                    unsigned long long v = tab[h];
+                    if (v == key) {
+                        placed = true;
                         break;
                     }
-                    if (v == key) break;
+                    if (v == EMPTY_KEY) {
+                        v = atomicCAS(&tab[h], EMPTY_KEY, key);
+                        if (v == EMPTY_KEY) {
+                            isnew = placed = true;
+                            if (W.cand_wit && S.hval[slot]) S.hval[slot][h] = W.cand_wit[t];
+                            break;
+                        }
+                        if (v == key) {
+                            placed = true;
+                            break;
+                        }
+                    }
+                    h = (h + 1) & m;
                 }
-                h = (h + 1) & m;
+                if (!placed) atomicOr(&W.cnt->overflow, OVF_FULL);
             }
-        }
-        const unsigned m = __ballot_sync(FULL_MASK, isnew);
-        if (m) {
-            unsigned long long pos = 0;
-            if (lane == 0) pos = atomicAdd(&W.cnt->delta, (unsigned long long)__popc(m));
-            pos = __shfl_sync(FULL_MASK, pos, 0);
-            if (isnew) {
-                pos += __popc(m & ((1u << lane) - 1));
-                W.delta_key[pos] = key;       // delta count <= candidate count <= cap
-                W.delta_slot[pos] = slot;
-            }
-            const unsigned same = __match_any_sync(FULL_MASK, isnew ? slot : EMPTY32);
-            if (isnew && lane == __ffs(same & m) - 1)
-                atomicAdd(&S.delta[slot], (unsigned long long)__popc(same & m));
             // count the new pair in its row of each form, and list a row the
             // first time it gets one (the rows the merge appends to)
             bool first_r = false, first_c = false;
@@ -1022,22 +1078,58 @@ __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
                 uint2 *dn = S.dn[slot];
                 first_r = atomicAdd(&dn[i].x, 1u) == 0;
                 first_c = atomicAdd(&dn[(size_t)S.n[slot] + j].x, 1u) == 0;
+                if (hist) atomicAdd(&slot_new[slot], 1u);
+                else atomicAdd(&S.delta[slot], 1ull);
             }
-#pragma unroll
-            for (int o = 0; o < 2; o++) {
-                const bool f = o ? first_c : first_r;
-                const unsigned fm = __ballot_sync(FULL_MASK, f);
-                if (!fm) continue;
-                unsigned long long tp = 0;
-                if (lane == 0) tp = atomicAdd(out_n, (unsigned long long)__popc(fm));
-                tp = __shfl_sync(FULL_MASK, tp, 0);
-                if (f) {
-                    tp += __popc(fm & ((1u << lane) - 1));
-                    if (tp < W.touched_cap) t_out[tp] = make_uint2(slot * 2 + o, o ? j : i);
-                    else atomicOr(&W.cnt->overflow, OVF_TOUCHED);
+            // stage the warp's new pairs and first-touched rows (one shared
+            // atomic per warp and list)
+            const unsigned m = __ballot_sync(FULL_MASK, isnew);
+            if (m) {
+                uint32_t p0 = 0;
+                if (lane == 0) p0 = atomicAdd(&n_new, (uint32_t)__popc(m));
+                p0 = __shfl_sync(FULL_MASK, p0, 0);
+                if (isnew) {
+                    const uint32_t p = p0 + __popc(m & ((1u << lane) - 1));
+                    st_key[p] = key;
+                    st_slot[p] = slot;
+                }
+                const unsigned fr = __ballot_sync(FULL_MASK, first_r);
+                const unsigned fc = __ballot_sync(FULL_MASK, first_c);
+                if (fr | fc) {
+                    uint32_t q0 = 0;
+                    if (lane == 0) q0 = atomicAdd(&n_touch, (uint32_t)(__popc(fr) + __popc(fc)));
+                    q0 = __shfl_sync(FULL_MASK, q0, 0);
+                    const unsigned below = (1u << lane) - 1;
+                    if (first_r) st_touch[q0 + __popc(fr & below)] = make_uint2(slot * 2, i);
+                    if (first_c)
+                        st_touch[q0 + __popc(fr) + __popc(fc & below)] = make_uint2(slot * 2 + 1, j);
                 }
             }
         }
+        __syncthreads();
+        const uint32_t nn = n_new, nt = n_touch;
+        if (threadIdx.x == 0) {
+            base_new = nn ? atomicAdd(&W.cnt->delta, (unsigned long long)nn) : 0;
+            base_touch = nt ? atomicAdd(out_n, (unsigned long long)nt) : 0;
+        }
+        __syncthreads();
+        // new pairs <= candidates <= the delta buffer's capacity
+        for (uint32_t q = threadIdx.x; q < nn; q += blockDim.x) {
+            W.delta_key[base_new + q] = st_key[q];
+            W.delta_slot[base_new + q] = st_slot[q];
+        }
+        for (uint32_t q = threadIdx.x; q < nt; q += blockDim.x) {
+            const unsigned long long tp = base_touch + q;
+            if (tp < W.touched_cap) t_out[tp] = st_touch[q];
+            else atomicOr(&W.cnt->overflow, OVF_TOUCHED);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) n_new = n_touch = 0;
+        __syncthreads();
+    }
+    if (hist) {
+        for (uint32_t s = threadIdx.x; s < n_slots; s += blockDim.x)
+            if (slot_new[s]) atomicAdd(&S.delta[s], (unsigned long long)slot_new[s]);
     }
 }
 
@@ -1047,7 +1139,7 @@ __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W) {
 
 // Rows that received entries in the previous merge stop being "new".
 __global__ void k_reset_dnew(SlotTab S, WorkBufs W) {
-    if (W.cnt->overflow & OVF_PRE) return;
+    if (W.cnt->overflow & OVF_STOP) return;
     const int par = *W.parity;
     const unsigned long long n_in = W.touched_n[par];
     const uint2 *t_in = W.touched[par];
@@ -1081,12 +1173,12 @@ __device__ __forceinline__ uint32_t entry_log_after_move(uint32_t incoming) {
 // out; returns the number written (warp-collective, all lanes).
 template <class Get>
 __device__ __forceinline__ uint32_t warp_fold_tiles(uint32_t *tab, uint32_t cnt, Get get,
-                                                    uint32_t *out, int lane) {
+                                                    uint32_t *out, int lane, unsigned *err) {
     uint32_t lg = 5;
     while ((1u << lg) < 2 * cnt) lg++;
     clear_table(tab, lg, lane, 32);
     __syncwarp();
-    const HashAcc acc{tab, (int)lg};
+    const HashAcc acc{tab, (int)lg, err};
     for (uint32_t q = lane; q < cnt; q += 32) {
         const uint2 t = get(q);
         acc.ins(t.x, t.y);
@@ -1113,7 +1205,7 @@ __device__ __forceinline__ uint32_t warp_fold_tiles(uint32_t *tab, uint32_t cnt,
 // Idempotent: after a pool overflow the host grows the pool and runs it again.
 __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs W) {
     __shared__ __align__(16) uint32_t tabs[8][4 * TILE_WARP_MAX];   // a table per warp
-    if (W.cnt->overflow & OVF_PRE) return;
+    if (W.cnt->overflow & OVF_STOP) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *tab = tabs[wib];
     const int par = *W.parity;
@@ -1143,7 +1235,7 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
         while ((1u << lg) < 2 * dsc.y) lg++;
         clear_table(tab, lg, lane, 32);
         __syncwarp();
-        const HashAcc acc{tab, (int)lg};
+        const HashAcc acc{tab, (int)lg, &W.cnt->overflow};
         for (uint32_t q = lane; q < dsc.y; q += 32) {
             const uint2 tl = *reinterpret_cast<const uint2 *>(pool + dsc.x + 2 * q);
             acc.ins(tl.x, tl.y);
@@ -1196,7 +1288,7 @@ __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, Work
     __shared__ uint32_t list_n;
     __shared__ unsigned long long sh[16];
     __shared__ unsigned long long off_sh;
-    if (W.cnt->overflow & OVF_PRE) return;
+    if (W.cnt->overflow & OVF_STOP) return;
     const int par = *W.parity;
     const uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
@@ -1282,7 +1374,7 @@ __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, Work
 // Append the new pairs as single entries: (i, j) goes to the entry area of
 // row i of the row form and of row j of the column form.
 __global__ void __launch_bounds__(256) k_scatter(SlotTab S, WorkBufs W) {
-    if (W.cnt->overflow & (OVF_PRE | OVF_POOL)) return;
+    if (W.cnt->overflow & (OVF_STOP | OVF_POOL)) return;
     const unsigned long long nd = W.cnt->delta;
     for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
          t < nd; t += (unsigned long long)gridDim.x * blockDim.x) {
@@ -1308,7 +1400,7 @@ __global__ void __launch_bounds__(256) k_scatter(SlotTab S, WorkBufs W) {
 // second tile, until the row's next move folds them.
 __global__ void __launch_bounds__(256) k_pack(SlotTab S, WorkBufs W) {
     __shared__ __align__(16) uint32_t tabs[8][4 * TILE_WARP_MAX];
-    if (W.cnt->overflow & (OVF_PRE | OVF_POOL)) return;
+    if (W.cnt->overflow & (OVF_STOP | OVF_POOL)) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *tab = tabs[wib];
     const int par = *W.parity;
@@ -1343,7 +1435,7 @@ __global__ void __launch_bounds__(256) k_pack(SlotTab S, WorkBufs W) {
                                       const uint32_t v = ent[c0 + q];
                                       return make_uint2(v >> 5, 1u << (v & 31));
                                   },
-                                  tl + 2 * nt, lane);
+                                  tl + 2 * nt, lane, &W.cnt->overflow);
         }
         if (lane == 0) {
             dp->y = nt;
@@ -1376,7 +1468,9 @@ __global__ void __launch_bounds__(256) k_iter_begin(SlotTab S, InstTab I, WorkBu
 
 // Before the commit: stop the iteration if a buffer overflowed or if some
 // pair set could pass half full with this iteration's candidates.
-__global__ void __launch_bounds__(256) k_check(SlotTab S, WorkBufs W, uint32_t n_slots) {
+__global__ void __launch_bounds__(256) k_check(SlotTab S, WorkBufs W, uint32_t n_slots,
+                                               int growth) {
+    if (!growth) return;               // sets kept at their size (a test setting)
     bool grow = false;
     for (uint32_t s = threadIdx.x; s < n_slots; s += blockDim.x)
         grow |= 2 * (S.nnz[s] + S.cand[s]) > S.hmask[s] + 1;
@@ -1391,7 +1485,7 @@ __global__ void __launch_bounds__(256) k_iter_end(SlotTab S, InstTab I, WorkBufs
                                                   int count_iteration,
                                                   cudaGraphConditionalHandle handle,
                                                   int in_graph) {
-    const unsigned flags = W.cnt->overflow & (OVF_PRE | OVF_POOL);
+    const unsigned flags = W.cnt->overflow & (OVF_STOP | OVF_POOL);
     if (flags) {                        // the host grows a buffer and finishes the iteration
         if (threadIdx.x == 0) {
             ctl->status = flags;
@@ -1488,14 +1582,19 @@ __global__ void k_init_eps(uint32_t slot, uint32_t n, WorkBufs W) {
 
 __global__ void k_rehash(const unsigned long long *old_tab, const uint2 *old_val,
                          unsigned long long old_cap, unsigned long long *new_tab,
-                         uint2 *new_val, unsigned long long new_cap) {
+                         uint2 *new_val, unsigned long long new_cap, unsigned *err) {
     const unsigned long long m = new_cap - 1;
     for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
          s < old_cap; s += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long key = old_tab[s];
         if (key == EMPTY_KEY) continue;
         unsigned long long h = pair_home(key, m);
-        while (atomicCAS(&new_tab[h], EMPTY_KEY, key) != EMPTY_KEY) h = (h + 1) & m;
+        unsigned long long p = 0;     // one pass at most (the new set is at most 1/4 full)
+        while (atomicCAS(&new_tab[h], EMPTY_KEY, key) != EMPTY_KEY && ++p <= m) h = (h + 1) & m;
+        if (p > m) {
+            atomicOr(err, OVF_FULL);
+            continue;
+        }
         if (new_val) new_val[h] = old_val[s];
     }
 }
@@ -1931,8 +2030,9 @@ void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &
     else launch_bin<false>(bin, S, P, W, max_n, T, sms, st);
 }
 
-void launch_commit(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st) {
-    k_commit<<<sms * 8, 256, 0, st>>>(S, W);
+void launch_commit(const SlotTab &S, const WorkBufs &W, uint32_t n_slots, int sms,
+                   cudaStream_t st) {
+    k_commit<<<sms * 8, 256, 0, st>>>(S, W, n_slots);
 }
 
 void launch_iter_begin(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t n_slots,
@@ -1940,8 +2040,9 @@ void launch_iter_begin(const SlotTab &S, const InstTab &I, const WorkBufs &W, ui
     k_iter_begin<<<1, 256, 0, st>>>(S, I, W, n_slots, n_inst);
 }
 
-void launch_check(const SlotTab &S, const WorkBufs &W, uint32_t n_slots, cudaStream_t st) {
-    k_check<<<1, 256, 0, st>>>(S, W, n_slots);
+void launch_check(const SlotTab &S, const WorkBufs &W, uint32_t n_slots, bool growth,
+                  cudaStream_t st) {
+    k_check<<<1, 256, 0, st>>>(S, W, n_slots, growth ? 1 : 0);
 }
 
 void launch_iter_end(const SlotTab &S, const InstTab &I, const WorkBufs &W, LoopCtl *ctl,
@@ -1991,9 +2092,9 @@ void launch_init_eps(uint32_t slot, uint32_t n, const WorkBufs &W, int sms, cuda
 
 void launch_rehash(const unsigned long long *old_tab, const uint2 *old_val,
                    unsigned long long old_cap, unsigned long long *new_tab, uint2 *new_val,
-                   unsigned long long new_cap, int sms, cudaStream_t st) {
+                   unsigned long long new_cap, unsigned *err, int sms, cudaStream_t st) {
     k_rehash<<<grid_for(old_cap, 256, sms, 8), 256, 0, st>>>(old_tab, old_val, old_cap, new_tab,
-                                                              new_val, new_cap);
+                                                              new_val, new_cap, err);
 }
 
 void launch_witness_lookup(const unsigned long long *tab, const uint2 *val,

@@ -138,6 +138,7 @@ constexpr uint32_t FAM_CSHARED = 1, FAM_CONSEC = 2;
 
 struct Counters {
     unsigned long long groups[N_BINS];
+    unsigned long long claim[N_BINS];   // next group of the bin to take (CTA-level bins)
     unsigned long long cand;
     unsigned long long delta;
     unsigned long long flops;
@@ -153,7 +154,10 @@ constexpr unsigned OVF_CAND = 2u;      // candidate buffer overflow (before the 
 constexpr unsigned OVF_POOL = 4u;      // row pool exhausted        (inside the merge)
 constexpr unsigned OVF_TOUCHED = 8u;   // touched list overflow (cannot happen: sized 2x)
 constexpr unsigned OVF_HASH = 16u;     // a pair set would pass half full (before the commit)
+constexpr unsigned OVF_FULL = 32u;     // a probe sequence passed over a whole hash table
+                                       // (cannot happen while sets stay half full): fatal
 constexpr unsigned OVF_PRE = OVF_GROUPS | OVF_CAND | OVF_HASH;   // iteration not committed
+constexpr unsigned OVF_STOP = OVF_PRE | OVF_FULL;   // the merge kernels do nothing
 
 struct WorkBufs {
     // touched rows {slot*2+o, idx}: touched[*parity] lists the rows whose
@@ -181,13 +185,17 @@ void launch_symbolic(const SlotTab &S, const ProdTab &P, const WorkBufs &W, int 
                      const Tuning &T, int sms, cudaStream_t st);
 void launch_spgemm(int bin, const SlotTab &S, const ProdTab &P, const WorkBufs &W,
                    uint32_t max_n, const Tuning &T, int sms, cudaStream_t st);
-void launch_commit(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
+void launch_commit(const SlotTab &S, const WorkBufs &W, uint32_t n_slots, int sms,
+                   cudaStream_t st);
 // Iteration frame: zero the per-iteration counters; check the pre-commit
 // conditions (buffer overflow, pair-set load); finish the iteration (pair
 // counts, per-instance iteration counts, parity flip, loop condition).
 void launch_iter_begin(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t n_slots,
                        uint32_t n_inst, cudaStream_t st);
-void launch_check(const SlotTab &S, const WorkBufs &W, uint32_t n_slots, cudaStream_t st);
+// growth false (a test setting): never stop for a pair set's load, so a set
+// may fill up (the capped probes then report OVF_FULL)
+void launch_check(const SlotTab &S, const WorkBufs &W, uint32_t n_slots, bool growth,
+                  cudaStream_t st);
 void launch_iter_end(const SlotTab &S, const InstTab &I, const WorkBufs &W, LoopCtl *ctl,
                      uint32_t n_slots, uint32_t n_inst, bool count_iteration,
                      cudaGraphConditionalHandle handle, bool in_graph, cudaStream_t st);
@@ -209,10 +217,11 @@ void launch_init_edges(const uint32_t *src, const uint32_t *lab, const uint32_t 
                        int sms, cudaStream_t st);
 void launch_init_eps(uint32_t slot, uint32_t n, const WorkBufs &W, int sms, cudaStream_t st);
 // Move a pair set (and its witnesses, when val pointers are non-null) into
-// a larger table.
+// a larger table; a key that finds no free slot in one pass sets OVF_FULL in
+// *err.
 void launch_rehash(const unsigned long long *old_tab, const uint2 *old_val,
                    unsigned long long old_cap, unsigned long long *new_tab, uint2 *new_val,
-                   unsigned long long new_cap, int sms, cudaStream_t st);
+                   unsigned long long new_cap, unsigned *err, int sms, cudaStream_t st);
 // The witness of pair `key` in a pair set of capacity mask + 1, written to
 // *out ({~0, ~0} when the pair is absent).
 void launch_witness_lookup(const unsigned long long *tab, const uint2 *val,

@@ -758,7 +758,8 @@ struct Runner {
         ck(cudaMemsetAsync(nt, 0xFF, cap * 8, st), "memset");
         uint2 *nv = c->hval[x] ? (uint2 *)alloc_for(c, cap * 8) : nullptr;
         prof.run(KID_REHASH, [&] {
-            launch_rehash(c->htab[x], c->hval[x], c->hcap[x], nt, nv, cap, sms, st);
+            launch_rehash(c->htab[x], c->hval[x], c->hcap[x], nt, nv, cap,
+                          &d_cnt.p->overflow, sms, st);
         });
         own->k_bytes[KID_REHASH] += c->hcap[x] * 8 + need * 8;
         sync("rehash");
@@ -797,7 +798,10 @@ struct Runner {
                 for (int b = 0; b < N_BINS; b++)
                     run(KID_BIN0 + b,
                         [&] { launch_spgemm(b, S, P, W, max_n, tuning(), sms, st); });
-                ck(cudaMemsetAsync(d_cnt.p->groups, 0, sizeof(d_cnt.p->groups), st), "memset");
+                // group counts and claim cursors (adjacent) start again
+                ck(cudaMemsetAsync(d_cnt.p->groups, 0,
+                                   sizeof(d_cnt.p->groups) + sizeof(d_cnt.p->claim), st),
+                   "memset");
             }
         } else {
             run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, -1, tuning(), sms, st); });
@@ -813,7 +817,7 @@ struct Runner {
         if (stage <= 0) {
             // the previous deltas end before the commit counts the new ones
             run(KID_RESET, [&] { launch_reset_dnew(S, W, sms, st); });
-            run(KID_COMMIT, [&] { launch_commit(S, W, sms, st); });
+            run(KID_COMMIT, [&] { launch_commit(S, W, n_slots, sms, st); });
         }
         if (stage <= 1) run(KID_CAPACITY, [&] { launch_capacity(S, I, W, max_n, sms, st); });
         run(KID_SCATTER, [&] { launch_scatter(S, W, sms, st); });
@@ -830,7 +834,9 @@ struct Runner {
         const WorkBufs W = work();
         launch_iter_begin(S, I, W, n_slots, (uint32_t)cx.size(), st);
         launch_products(S, P, W, timed);
-        launch_check(S, W, n_slots, st);
+        bool growth = true;
+        for (auto *c : cx) growth &= c->cfg.test_fixed_pair_sets == 0;
+        launch_check(S, W, n_slots, growth, st);
         launch_merge(S, I, W, 0, true, in_graph, timed);
     }
 
@@ -881,6 +887,9 @@ struct Runner {
     // Returns false when the iteration must be run again from its start.
     bool recover() {
         const unsigned st_bits = h_ctl->status;
+        if (st_bits & OVF_FULL)
+            throw Status{CFLR_ECUDA, "a pair set filled up: a hash probe passed over the "
+                                     "whole table (the pair sets were kept at their size)"};
         if (st_bits & (OVF_GROUPS | OVF_CAND)) {       // nothing was committed
             for (int b = 0; b < N_BINS; b++) {
                 uint64_t want = h_cnt->groups[b] > group_cap[b] ? regrow_size(h_cnt->groups[b]) : 0;
@@ -925,6 +934,9 @@ struct Runner {
             launch_merge(S, I, W, 1, true, false, true);
             read_status();
         }
+        if (h_ctl->status & OVF_FULL)
+            throw Status{CFLR_ECUDA, "a pair set filled up: a hash probe passed over the "
+                                     "whole table"};
         if (h_ctl->status) throw Status{CFLR_ECUDA, "internal: unexpected loop status"};
         return true;
     }

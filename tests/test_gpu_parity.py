@@ -597,3 +597,28 @@ def test_witness_steps_rebuild_valid_paths(name):
                 assert cur == v
                 if len(path) <= 12:
                     assert x in cyk.derives(tuple(lab for _, lab, _ in path))
+
+
+def test_full_pair_set_stops_the_solve_and_context_stays_usable():
+    """Every hash probe is capped at one pass over its table.  With the pair
+    sets kept at their first size (a test-only setting) a set fills up: the
+    capped probes report it, the solve returns CFLR_ECUDA instead of spinning,
+    and the same context then solves a new graph correctly."""
+    text = gen.grammar_text("fica")
+    big = gen.fica_like(n=5000, n_a=10_000, n_d=3750, seed=11)
+    small = gen.random_graph(n=20, n_edges=30, labels=["a", "d", "a_r", "d_r"], seed=1)
+    for form in (cflr.CFLR_FORM_BATCHED, cflr.CFLR_FORM_GRAPH):
+        with Solver(text, form=form, test_fixed_pair_sets=1) as s:
+            s.load(big)
+            with pytest.raises(CflrError) as e:
+                s.solve()
+            assert e.value.code == cflr.CFLR_ECUDA
+            assert "filled up" in e.value.message
+            with pytest.raises(CflrError) as e:      # the matrices were dropped
+                s.solve()
+            assert e.value.code == cflr.CFLR_ESTATE
+            s.load(small)
+            s.solve()
+            want = oracle.solve(text, small)
+            for x in want.grammar.nts:
+                assert np.array_equal(s.pairs(x), want.pairs[x]), x
