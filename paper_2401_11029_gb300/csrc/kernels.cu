@@ -269,6 +269,25 @@ __device__ __forceinline__ Work family_work(const SlotTab &S, uint32_t g0, uint3
     const uint32_t *oc = S.occ[g0];
     const uint32_t ow = S.occ_w[g0], lx0 = S.local[g0];
     Work w{0, 0};
+    if (qstep == 32 && F >= 16 && d <= 32) {
+        // a whole warp on a short delta (lane q0 of 32): the lanes take the
+        // members of each entry in turn, so the members' descriptors load
+        // together instead of one after another on the entry's lane
+        for (uint32_t q = 0; q < d; q++) {
+            const uint32_t k = pool[dstart + q];
+            const uint32_t *ok = oc + ((size_t)o * n + k) * ow;
+            for (uint32_t i = q0; i < F; i += 32) {
+                const uint32_t x = lx0 + i;
+                if ((ok[x >> 5] >> (x & 31)) & 1u) {
+                    const uint4 gd = S.desc[g0 + i][(size_t)o * n + k];
+                    const uint32_t nt = gd.y - (o ? (gd.w & DLAST_MASK) : 0u);
+                    w.f += nt;
+                    w.fb += 16ull + 8ull * nt;
+                }
+            }
+        }
+        return w;
+    }
     for (uint32_t q = q0; q < d; q += qstep) {
         const uint32_t k = pool[dstart + q];
         const uint32_t *ok = oc + ((size_t)o * n + k) * ow;
@@ -277,12 +296,27 @@ __device__ __forceinline__ Work family_work(const SlotTab &S, uint32_t g0, uint3
             uint32_t m = ok[wi];
             if (lx0 > lo) m &= ~0u << (lx0 - lo);
             if (lx0 + F < lo + 32) m &= (1u << (lx0 + F - lo)) - 1;
-            for (; m; m &= m - 1) {
-                const uint32_t i = lo + (__ffs(m) - 1) - lx0;
-                const uint4 gd = S.desc[g0 + i][(size_t)o * n + k];
-                const uint32_t nt = gd.y - (o ? (gd.w & DLAST_MASK) : 0u);
-                w.f += nt;
-                w.fb += 16ull + 8ull * nt;
+            while (m) {
+                // up to four members' descriptors in flight together
+                uint4 gd[4];
+                uint32_t cnt = 0;
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    gd[t] = make_uint4(0, 0, 0, 0);
+                    if (m) {
+                        const uint32_t i = lo + (__ffs(m) - 1) - lx0;
+                        m &= m - 1;
+                        gd[t] = S.desc[g0 + i][(size_t)o * n + k];
+                        cnt++;
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    const uint32_t nt = gd[t].y - (o ? (gd[t].w & DLAST_MASK) : 0u);
+                    w.f += nt;
+                    w.fb += 8ull * nt;
+                }
+                w.fb += 16ull * cnt;
             }
         }
     }
@@ -575,9 +609,11 @@ __device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uin
 
 // TAGS false: the caller never gets a tagged family group (the bitmap bin:
 // a tagged family stays within bin 2's limit or splits into its members), so
-// the member tags are not carried through the walk.  WALK_U: 16-byte
-// tile-pair loads each lane of a walking warp has in flight.
-template <bool WIT, bool TAGS, int WALK_U, class Acc>
+// the member tags are not carried through the walk.  PACKED: walk the lanes'
+// tile lists as one packed sequence (walk_packed) rather than list by list
+// (walk_lists); WALK_U: 16-byte tile-pair loads each lane of the packed walk
+// has in flight.
+template <bool WIT, bool TAGS, bool PACKED, int WALK_U, class Acc>
 __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab &P,
                                                 const WorkBufs &W, const GroupInfo &gi,
                                                 uint2 own, uint32_t warp_id, uint32_t nwarps,
@@ -664,6 +700,87 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
     auto key_of = [&](uint32_t wd, uint32_t tag) {
         return TAGS && gi.tagged ? (tag << TAG_SHIFT) | wd : wd;
     };
+    // two tiles (w.x, w.y) and (w.z, w.w) of member tag, gathered through
+    // delta entry k, nv of them valid
+    auto consume_tiles = [&](uint4 w, uint32_t nv, uint32_t tag, uint32_t k) {
+        const uint32_t n0 = nv > 0 ? acc.ins(key_of(w.x, tag), w.y) : 0u;
+        const uint32_t n1 = nv > 1 ? acc.ins(key_of(w.z, tag), w.w) : 0u;
+        if (__any_sync(FULL_MASK, (n0 | n1) != 0)) emit_bits(n0, w.x, n1, w.z, 0u, 0u, 0u, 0u, tag, k);
+    };
+    // The tile lists held by the lanes (toff, tn; member tag; delta entry k),
+    // one at a time: a list of 32 or more tiles is walked by the whole warp
+    // (16-byte loads, two in flight per lane), shorter ones are packed 32
+    // tiles per step with a per-lane search of the owning list.  Cheaper
+    // than the packed walk below when a group has few, short lists (its
+    // fixed cost per call is lower): the warp bins use it.
+    auto walk_lists = [&](uint32_t toff, uint32_t tn, uint32_t tag, uint32_t k) {
+        // long tile lists: the warp strides over one list at a time
+        unsigned lm = __ballot_sync(FULL_MASK, tn >= 32);
+        while (lm) {
+            const int l = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const uint32_t *tl = pool + __shfl_sync(FULL_MASK, toff, l);
+            const uint32_t T = __shfl_sync(FULL_MASK, tn, l);
+            const uint32_t ltag = __shfl_sync(FULL_MASK, tag, l);
+            const uint32_t lk = WIT ? __shfl_sync(FULL_MASK, k, l) : 0u;
+            for (uint32_t qb = 0; qb < T; qb += 128) {
+                uint4 w[2];
+                uint32_t nv[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t q = qb + 64 * h + 2 * lane;
+                    w[h] = make_uint4(0, 0, 0, 0);
+                    nv[h] = 0;
+                    if (q + 2 <= T) {
+                        w[h] = *reinterpret_cast<const uint4 *>(tl + 2 * q);
+                        nv[h] = 2;
+                    } else if (q < T) {
+                        const uint2 t = *reinterpret_cast<const uint2 *>(tl + 2 * q);
+                        w[h].x = t.x;
+                        w[h].y = t.y;
+                        nv[h] = 1;
+                    }
+                }
+                // four tiles per lane, one vote and one reservation
+                const uint32_t n0 = nv[0] > 0 ? acc.ins(key_of(w[0].x, ltag), w[0].y) : 0u;
+                const uint32_t n1 = nv[0] > 1 ? acc.ins(key_of(w[0].z, ltag), w[0].w) : 0u;
+                const uint32_t n2 = nv[1] > 0 ? acc.ins(key_of(w[1].x, ltag), w[1].y) : 0u;
+                const uint32_t n3 = nv[1] > 1 ? acc.ins(key_of(w[1].z, ltag), w[1].w) : 0u;
+                if (__any_sync(FULL_MASK, (n0 | n1 | n2 | n3) != 0))
+                    emit_bits(n0, w[0].x, n1, w[0].z, n2, w[1].x, n3, w[1].z, ltag, lk);
+            }
+        }
+        // short tile lists: packed, 32 tiles per step
+        const uint32_t stn = tn < 32 ? tn : 0;
+        const uint32_t incl = warp_incl_scan(stn, lane);
+        const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+        for (uint32_t fb = 0; fb < total; fb += 32) {
+            const uint32_t f = fb + lane;
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int st = 0; st < 5; st++) {     // first lane whose inclusive sum > f
+                const int mid = (lo + hi) >> 1;
+                const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
+                if (f < v) hi = mid; else lo = mid + 1;
+            }
+            const int owner = lo > 31 ? 31 : lo;
+            const uint32_t o_toff = __shfl_sync(FULL_MASK, toff, owner);
+            const uint32_t o_incl = __shfl_sync(FULL_MASK, incl, owner);
+            const uint32_t o_len = __shfl_sync(FULL_MASK, stn, owner);
+            const uint32_t o_tag = __shfl_sync(FULL_MASK, tag, owner);
+            const uint32_t o_kk = WIT ? __shfl_sync(FULL_MASK, k, owner) : 0u;
+            uint4 w = make_uint4(0, 0, 0, 0);
+            uint32_t nv = 0;
+            if (f < total) {
+                const uint2 t = *reinterpret_cast<const uint2 *>(
+                    pool + o_toff + 2 * (f - (o_incl - o_len)));
+                w.x = t.x;
+                w.y = t.y;
+                nv = 1;
+            }
+            consume_tiles(w, nv, o_tag, o_kk);
+        }
+    };
     // The tile lists held by the lanes (toff, tn; member tag; delta entry k),
     // walked as one sequence of 16-byte tile pairs: the lists with tiles are
     // moved to the front lanes, list l owns the pairs [excl_l, incl_l) of the
@@ -675,7 +792,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
     // start on 16-byte boundaries and a tile section holds an even number of
     // tiles, so a pair never leaves its segment; the second tile of a list's
     // last pair is ignored when the list has an odd count.
-    auto walk = [&](uint32_t toff, uint32_t tn, uint32_t tag, uint32_t k) {
+    auto walk_packed = [&](uint32_t toff, uint32_t tn, uint32_t tag, uint32_t k) {
         const unsigned nz = __ballot_sync(FULL_MASK, tn != 0);
         if (!nz) return;
         const uint32_t cnt = __popc(nz);
@@ -738,6 +855,10 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                 }
             }
         }
+    };
+    auto walk = [&](uint32_t toff, uint32_t tn, uint32_t tag, uint32_t k) {
+        if constexpr (PACKED) walk_packed(toff, tn, tag, k);
+        else walk_lists(toff, tn, tag, k);
     };
     if (gi.part == PART_U) {        // c -> a: the delta entries themselves
         for (uint32_t cb = warp_id; cb < d; cb += nwarps * 32) {
@@ -890,7 +1011,8 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(
             __syncwarp();
         }
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows<WIT, true, 2>(S, P, W, gi, own, 0, 1, lane, acc, ck);
+        const uint32_t e =
+            expand_rows<WIT, true, false, 2>(S, P, W, gi, own, 0, 1, lane, acc, ck);
         if (lane == 0 && e) {
             if (!gi.tagged) atomicAdd(&S.cand[gi.c], (unsigned long long)e);
             bytes += 12ull * e;
@@ -929,7 +1051,8 @@ __global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S,
         if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
         __syncthreads();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows<WIT, true, 2>(S, P, W, gi, own, wib, blockDim.x >> 5, lane, acc, ck);
+        const uint32_t e = expand_rows<WIT, true, true, 2>(S, P, W, gi, own, wib,
+                                                            blockDim.x >> 5, lane, acc, ck);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
         __syncthreads();
         if (threadIdx.x == 0 && emitted_sh) {
@@ -991,7 +1114,7 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
         if (!gi.probe) preload_mask(S, gi, acc, ptid, TPG);
         psync();
         const uint2 own = owner_delta(S, gi);
-        const uint32_t e = expand_rows<WIT, false, 4>(S, P, W, gi, own, wib % (8 / GPC), 8 / GPC,
+        const uint32_t e = expand_rows<WIT, false, true, 4>(S, P, W, gi, own, wib % (8 / GPC), 8 / GPC,
                                                      lane, acc, ck);
         if (lane == 0 && e) atomicAdd(&emitted_sh[part], e);
         psync();
@@ -2057,10 +2180,14 @@ void launch_reset_dnew(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_
 }
 
 
-void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t max_n,
-                     int sms, cudaStream_t st) {
-    set_smem_attrs();
+void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, int sms,
+                     cudaStream_t st) {
     k_capacity<<<sms * 8, 256, 0, st>>>(S, I, W);
+}
+
+void launch_capacity_big(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t max_n,
+                         int sms, cudaStream_t st) {
+    set_smem_attrs();
     const size_t bm_bytes = (size_t)((max_n + 31) / 32) * 4;
     const bool sm = bm_bytes <= SMEM_BITMAP_MAX;
     int per_sm = sm ? (int)((220 * 1024) / (bm_bytes + 3072)) : 8;

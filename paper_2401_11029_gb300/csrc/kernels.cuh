@@ -205,8 +205,10 @@ void launch_reset_dnew(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_
 // folded to one per word (one warp per row up to TILE_WARP_MAX tiles, then
 // one CTA per row with an n-bit shared-memory bitmap for max_n up to the
 // shared-memory limit, else copied as they are).
-void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t max_n,
-                     int sms, cudaStream_t st);
+void launch_capacity(const SlotTab &S, const InstTab &I, const WorkBufs &W, int sms,
+                     cudaStream_t st);
+void launch_capacity_big(const SlotTab &S, const InstTab &I, const WorkBufs &W, uint32_t max_n,
+                         int sms, cudaStream_t st);
 void launch_scatter(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);
 // Pack every appended row's new entries into tiles at the end of its tile list.
 void launch_pack(const SlotTab &S, const WorkBufs &W, int sms, cudaStream_t st);

@@ -31,12 +31,12 @@ enum { ST_CREATED = 0, ST_GRAMMAR = 1, ST_GRAPH = 2, ST_SOLVED = 3 };
 
 enum KernelId {
     KID_SYMBOLIC = 0, KID_BIN0, KID_BIN1, KID_BIN2, KID_BIN3, KID_COMMIT, KID_RESET,
-    KID_CAPACITY, KID_SCATTER, KID_PACK, KID_INIT, KID_REHASH, N_KID
+    KID_CAPACITY, KID_SCATTER, KID_PACK, KID_INIT, KID_REHASH, KID_CAPACITY_BIG, N_KID
 };
 const char *kKernelNames[N_KID] = {
     "k_symbolic", "k_spgemm_bin0", "k_spgemm_bin1", "k_spgemm_bin2", "k_spgemm_bin3",
     "k_commit", "k_reset_dnew", "k_capacity", "k_scatter", "k_pack", "k_init",
-    "k_rehash"};
+    "k_rehash", "k_capacity_big"};
 
 struct CudaError {
     cudaError_t e;
@@ -819,7 +819,10 @@ struct Runner {
             run(KID_RESET, [&] { launch_reset_dnew(S, W, sms, st); });
             run(KID_COMMIT, [&] { launch_commit(S, W, n_slots, sms, st); });
         }
-        if (stage <= 1) run(KID_CAPACITY, [&] { launch_capacity(S, I, W, max_n, sms, st); });
+        if (stage <= 1) {
+            run(KID_CAPACITY, [&] { launch_capacity(S, I, W, sms, st); });
+            run(KID_CAPACITY_BIG, [&] { launch_capacity_big(S, I, W, max_n, sms, st); });
+        }
         run(KID_SCATTER, [&] { launch_scatter(S, W, sms, st); });
         run(KID_PACK, [&] { launch_pack(S, W, sms, st); });
         launch_iter_end(S, I, W, d_ctl.p, n_slots, (uint32_t)cx.size(), count_iteration,
