@@ -247,6 +247,28 @@ __device__ __forceinline__ Work gathered_work(const SlotTab &S, uint32_t g, uint
     const uint32_t ow = S.occ_w[g], lx = S.local[g];
     const uint32_t bit = 1u << (lx & 31);
     Work w{0, 0};
+    if (qstep == 1) {
+        // one lane over all entries: four entries' loads in flight together
+        for (uint32_t q = q0; q < d; q += 4) {
+            uint32_t k[4], ob[4];
+            uint4 gd[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) k[t] = q + t < d ? pool[dstart + q + t] : 0u;
+#pragma unroll
+            for (int t = 0; t < 4; t++)
+                ob[t] = q + t < d ? oc[((size_t)o * n + k[t]) * ow + (lx >> 5)] & bit : 0u;
+#pragma unroll
+            for (int t = 0; t < 4; t++) gd[t] = ob[t] ? dg[k[t]] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                if (!ob[t]) continue;
+                const uint32_t nt = gd[t].y - (o ? (gd[t].w & DLAST_MASK) : 0u);
+                w.f += nt;
+                w.fb += 16ull + 8ull * nt;
+            }
+        }
+        return w;
+    }
     for (uint32_t q = q0; q < d; q += qstep) {
         const uint32_t k = pool[dstart + q];
         if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
@@ -323,6 +345,80 @@ __device__ __forceinline__ Work family_work(const SlotTab &S, uint32_t g0, uint3
     return w;
 }
 
+// Per-member product steps of a family on one delta row (thread tid of nth
+// working on it; members' gathered slots g0 .. g0+F-1, F <= 64): mf[i] and
+// mc[i] (zeroed by the caller, shared by the nth threads) get the tiles and
+// the referenced rows of member i.  Threads take the entries, four at a
+// time; the (entry, member) pairs whose occupancy bit is set are taken
+// FM_BATCH at a time across a lane's entries, their descriptors loading
+// together.
+// The members' descriptor arrays follow one another (the slots of one
+// instance are consecutive, 2n descriptors each), so member i's row k of
+// orientation o is S.desc[g0][(2i + o) n + k].
+constexpr int FM_BATCH = 4;
+
+__device__ __forceinline__ void family_members(const SlotTab &S, uint32_t g0, uint32_t F,
+                                               uint32_t o, uint32_t n, const uint32_t *pool,
+                                               uint32_t dstart, uint32_t d, uint32_t tid,
+                                               uint32_t nth, unsigned long long *mf,
+                                               uint32_t *mc) {
+    const uint32_t *oc = S.occ[g0];
+    const uint4 *dg = S.desc[g0];
+    const uint32_t ow = S.occ_w[g0], lx0 = S.local[g0];
+    const uint32_t w0 = lx0 >> 5, sh = lx0 & 31, wlast = (lx0 + F - 1) >> 5;
+    const unsigned long long fmask = F == 64 ? ~0ull : (1ull << F) - 1;
+    const size_t oo = (size_t)o * n;
+    for (uint32_t qb = 0; qb < d; qb += nth * 4) {
+        uint32_t k[4];
+        unsigned long long m[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const uint32_t q = qb + nth * t + tid;
+            k[t] = q < d ? pool[dstart + q] : 0u;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const uint32_t q = qb + nth * t + tid;
+            m[t] = 0;
+            if (q < d) {
+                const uint32_t *ok = oc + (oo + k[t]) * ow + w0;
+                const uint32_t x0 = ok[0];
+                const uint32_t x1 = w0 + 1 <= wlast ? ok[1] : 0u;
+                const uint32_t x2 = w0 + 2 <= wlast ? ok[2] : 0u;
+                const unsigned long long lo64 = ((unsigned long long)x1 << 32) | x0;
+                m[t] = ((lo64 >> sh) | (sh ? (unsigned long long)x2 << (64 - sh) : 0ull)) & fmask;
+            }
+        }
+        while (m[0] | m[1] | m[2] | m[3]) {
+            uint32_t mi[FM_BATCH], mk[FM_BATCH];
+            uint4 gd[FM_BATCH];
+#pragma unroll
+            for (int j = 0; j < FM_BATCH; j++) {
+                // the lowest pair left in the first entry with pairs left
+                const int t = m[0] ? 0 : m[1] ? 1 : m[2] ? 2 : m[3] ? 3 : 4;
+                const unsigned long long cur = t == 0 ? m[0] : t == 1 ? m[1] : t == 2 ? m[2]
+                                                                                  : m[3];
+                mi[j] = t < 4 ? (uint32_t)(__ffsll((long long)cur) - 1) : EMPTY32;
+                mk[j] = t == 0 ? k[0] : t == 1 ? k[1] : t == 2 ? k[2] : k[3];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (t == u) m[u] &= m[u] - 1;
+            }
+#pragma unroll
+            for (int j = 0; j < FM_BATCH; j++)
+                gd[j] = mi[j] != EMPTY32 ? dg[(size_t)(2 * mi[j]) * n + oo + mk[j]]
+                                         : make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int j = 0; j < FM_BATCH; j++) {
+                if (mi[j] == EMPTY32) continue;
+                const uint32_t nt = gd[j].y - (o ? (gd[j].w & DLAST_MASK) : 0u);
+                atomicAdd(&mf[mi[j]], (unsigned long long)nt);
+                atomicAdd(&mc[mi[j]], 1u);
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ Work warp_sum(Work w) {
     w.f = warp_sum64(w.f);
     w.fb = warp_sum64(w.fb);
@@ -330,11 +426,19 @@ __device__ __forceinline__ Work warp_sum(Work w) {
 }
 
 // prod_only >= 0 restricts the work list to one production (the plain form).
-__global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs W,
-                                                  int prod_only, Tuning T) {
+// Mode 0: a warp per touched row; a row whose delta has more than SYM_BIG_D
+// entries is listed for mode 1 (while the list has room) instead.  Mode 1: a
+// CTA per listed row, its threads sharing the entries (a long delta row on
+// one warp would hold the launch up long after the other warps finish).
+constexpr uint32_t SYM_BIG_D = 1024;
+
+__global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkBufs W,
+                                                     int prod_only, Tuning T, int mode) {
+    __shared__ Work red[8];
+    __shared__ unsigned long long mem_f[8][64];   // per-member sums of a family (a warp's)
+    __shared__ uint32_t mem_c[8][64];
     __shared__ uint2 stage[8][N_BINS][SYM_BUF];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const unsigned long long nw = (unsigned long long)gridDim.x * 8;
     const int par = *W.parity;
     const unsigned long long n_in = W.touched_n[par];
     const uint2 *t_in = W.touched[par];
@@ -354,6 +458,24 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         const unsigned long long pos = atomicAdd(&W.cnt->groups[b], 1ull);
         if (pos < W.group_cap[b]) W.groups[b][pos] = grp;
         else atomicOr(&W.cnt->overflow, OVF_GROUPS);
+    };
+    // warp-collective: each lane's group (bin b >= 0) appended, one atomic
+    // per bin
+    auto append_lanes = [&](int b, uint2 grp) {
+#pragma unroll
+        for (int bb = 0; bb < N_BINS; bb++) {
+            const unsigned m = __ballot_sync(FULL_MASK, b == bb);
+            if (!m) continue;
+            const int leader = __ffs(m) - 1;
+            unsigned long long pos = 0;
+            if (lane == leader) pos = atomicAdd(&W.cnt->groups[bb], (unsigned long long)__popc(m));
+            pos = __shfl_sync(FULL_MASK, pos, leader);
+            if (b == bb) {
+                pos += __popc(m & ((1u << lane) - 1));
+                if (pos < W.group_cap[bb]) W.groups[bb][pos] = grp;
+                else atomicOr(&W.cnt->overflow, OVF_GROUPS);
+            }
+        }
     };
 
     // classify one group of f product steps: mode, bin and table size;
@@ -400,6 +522,64 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                 const uint4 pr = P.prod[mp[i]];
                 return (fm.w == PART_A) ? pr.z : pr.y;
             };
+            if ((fm.z & FAM_CONSEC) && (qstep == 32 || qstep == 256) && fm.y <= 64) {
+                // a whole warp (or CTA) on the use: per-member sums first,
+                // then the family's group, or one group per member
+                const bool cta = qstep == 256;
+                auto group_sync = [&]() {
+                    if (cta) __syncthreads();
+                    else __syncwarp();
+                };
+                unsigned long long *mf = mem_f[cta ? 0 : wib];
+                uint32_t *mc = mem_c[cta ? 0 : wib];
+                for (uint32_t i = q0; i < fm.y; i += qstep) {
+                    mf[i] = 0;
+                    mc[i] = 0;
+                }
+                group_sync();
+                family_members(S, g0, fm.y, o, n, pool, dstart, d, q0, qstep, mf, mc);
+                group_sync();
+                Work wt{0, 0};
+                for (uint32_t i = q0; i < fm.y; i += qstep) {
+                    wt.f += mf[i];
+                    wt.fb += 16ull * mc[i] + 8ull * mf[i];
+                }
+                const Work wk = sum(wt);
+                if (wk.f) {
+                    uint2 grp;
+                    if (fm.z & FAM_CSHARED) {   // every member writes c: one mask row
+                        const uint32_t mt = S.desc[pr0.x][r].y;
+                        emit(classify(code, PART_F, idx, d, mt, 8ull * mt, wk.f, wk.fb, false,
+                                      grp),
+                             grp);
+                    } else if (wk.f <= T.limit[2]) {
+                        emit(classify(code, PART_F, idx, d, 0, 0, wk.f, wk.fb, true, grp), grp);
+                    } else {
+                        // too large for a hash bin: one group per member,
+                        // the threads taking the members
+                        const bool keep_acct = acct;
+                        acct = true;
+                        for (uint32_t i0 = 0; i0 < fm.y; i0 += qstep) {
+                            const uint32_t i = i0 + q0;
+                            int b = -1;
+                            uint2 mg = make_uint2(0, 0);
+                            if (i < fm.y && mf[i]) {
+                                const uint32_t mt = S.desc[P.prod[mp[i]].x][r].y;
+                                b = classify((mp[i] << 2) | fm.w, fm.w, idx, d, mt, 8ull * mt,
+                                             mf[i], 16ull * mc[i] + 8ull * mf[i], false, mg);
+                            }
+                            if (cta) {
+                                if (b >= 0) append(b, mg);
+                            } else {
+                                append_lanes(b, mg);
+                            }
+                        }
+                        acct = keep_acct;
+                    }
+                }
+                group_sync();
+                return;
+            }
             Work wk{0, 0};
             if (fm.z & FAM_CONSEC) {
                 wk = family_work(S, g0, fm.y, o, n, pool, dstart, d, q0, qstep);
@@ -419,6 +599,28 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                 emit(classify(code, PART_F, idx, d, mt, 8ull * mt, wk.f, wk.fb, false, grp), grp);
             } else if (wk.f <= T.limit[2]) {
                 emit(classify(code, PART_F, idx, d, 0, 0, wk.f, wk.fb, true, grp), grp);
+            } else if (qstep == 32) {
+                // too large for a hash bin: one group per member; with a
+                // whole warp on the use, the lanes take the members (each
+                // lane counts its member's products over all entries)
+                const bool keep_acct = acct;
+                acct = true;
+                for (uint32_t i0 = 0; i0 < fm.y; i0 += 32) {
+                    const uint32_t i = i0 + q0;
+                    int b = -1;
+                    uint2 mg = make_uint2(0, 0);
+                    if (i < fm.y) {
+                        const uint4 pr = P.prod[mp[i]];
+                        const uint32_t mt = S.desc[pr.x][r].y;
+                        const Work wi = gathered_work(S, (fm.w == PART_A) ? pr.z : pr.y, o, n,
+                                                      pool, dstart, d, 0, 1);
+                        if (wi.f)
+                            b = classify((mp[i] << 2) | fm.w, fm.w, idx, d, mt, 8ull * mt, wi.f,
+                                         wi.fb, false, mg);
+                    }
+                    append_lanes(b, mg);
+                }
+                acct = keep_acct;
             } else {               // too large for a hash bin: one group per member
                 for (uint32_t i = 0; i < fm.y; i++) {
                     const Work wi =
@@ -448,7 +650,47 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         emit(classify(code, part, idx, d, mt, 8ull * mt, wk.f, wk.fb, false, grp), grp);
     };
 
-    for (unsigned long long e = (unsigned long long)blockIdx.x * 8 + wib; e < n_in; e += nw) {
+    if (mode == 1) {
+        // a CTA per long delta row: the threads share its entries, sums over
+        // the CTA, thread 0 classifies and appends
+        const unsigned long long n_big = min(W.cnt->big_n, W.big_cap);
+        auto block_sum = [&](Work w) {
+            w = warp_sum(w);
+            __syncthreads();                 // red[] free from the last sum
+            if (lane == 0) red[wib] = w;
+            __syncthreads();
+            Work t{0, 0};
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                t.f += red[q].f;
+                t.fb += red[q].fb;
+            }
+            return t;
+        };
+        acct = threadIdx.x == 0;
+        for (unsigned long long e = blockIdx.x; e < n_big; e += gridDim.x) {
+            const uint2 t = W.big_rows[e];
+            const uint32_t xo = t.x, idx = t.y, slot = xo >> 1, o = xo & 1;
+            const uint32_t n = S.n[slot];
+            const uint4 dsc = S.desc[slot][(size_t)o * n + idx];
+            const uint32_t d = S.dn[slot][(size_t)o * n + idx].x;
+            const uint32_t dstart = dsc.x + tile_words(dsc.z);
+            const uint32_t *pool = S.pool[slot];
+            for (uint32_t u = P.use_off[xo]; u < P.use_off[xo + 1]; u++) {
+                const uint32_t code = P.use_code[u];
+                if (prod_only >= 0 && (code >> 2) != (uint32_t)prod_only) continue;
+                use_groups(code, o, n, idx, pool, dstart, d, threadIdx.x, 256, block_sum,
+                           [&](int bb, uint2 g) {
+                               if (threadIdx.x == 0) append(bb, g);
+                           });
+            }
+        }
+    }
+    // a warp per touched row, at a stride: rows the same merge touched lie
+    // together in the list and often cost alike (claiming runs of rows from
+    // a cursor was measured slower, more so the longer the runs)
+    for (unsigned long long e = (unsigned long long)blockIdx.x * 8 + wib; mode == 0 && e < n_in;
+         e += (unsigned long long)gridDim.x * 8) {
         const uint2 t = t_in[e];
         const uint32_t xo = t.x, idx = t.y, slot = xo >> 1, o = xo & 1;
         const uint32_t n = S.n[slot];
@@ -457,6 +699,16 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
         const uint32_t dstart = dsc.x + tile_words(dsc.z);
         const uint32_t *pool = S.pool[slot];
         const uint32_t u0 = P.use_off[xo], u1 = P.use_off[xo + 1];
+        if (d > SYM_BIG_D && u1 > u0) {
+            // listed for the CTA pass when there is room, else done here
+            unsigned long long pos = 0;
+            if (lane == 0) pos = atomicAdd(&W.cnt->big_n, 1ull);
+            pos = __shfl_sync(FULL_MASK, pos, 0);
+            if (pos < W.big_cap) {
+                if (lane == 0) W.big_rows[pos] = t;
+                continue;
+            }
+        }
         if (u1 - u0 >= 32 && d <= 16) {
             // many productions read this row, each with few products: one
             // lane per use, groups appended with one atomic per bin
@@ -484,20 +736,7 @@ __global__ void __launch_bounds__(256) k_symbolic(SlotTab S, ProdTab P, WorkBufs
                                    });
                     }
                 }
-#pragma unroll
-                for (int bb = 0; bb < N_BINS; bb++) {
-                    const unsigned m = __ballot_sync(FULL_MASK, b == bb);
-                    if (!m) continue;
-                    const int leader = __ffs(m) - 1;
-                    unsigned long long pos = 0;
-                    if (lane == leader) pos = atomicAdd(&W.cnt->groups[bb], (unsigned long long)__popc(m));
-                    pos = __shfl_sync(FULL_MASK, pos, leader);
-                    if (b == bb) {
-                        pos += __popc(m & ((1u << lane) - 1));
-                        if (pos < W.group_cap[bb]) W.groups[bb][pos] = grp;
-                        else atomicOr(&W.cnt->overflow, OVF_GROUPS);
-                    }
-                }
+                append_lanes(b, grp);
             }
             continue;
         }
@@ -2102,7 +2341,8 @@ static void set_smem_attrs() {
 
 void launch_symbolic(const SlotTab &S, const ProdTab &P, const WorkBufs &W, int prod_only,
                      const Tuning &T, int sms, cudaStream_t st) {
-    k_symbolic<<<sms * 8, 256, 0, st>>>(S, P, W, prod_only, T);
+    k_symbolic<<<sms * 8, 256, 0, st>>>(S, P, W, prod_only, T, 0);
+    k_symbolic<<<sms * 4, 256, 0, st>>>(S, P, W, prod_only, T, 1);
 }
 
 // The product bins, with the witness plumbing compiled in only when the

@@ -145,6 +145,7 @@ struct Counters {
     unsigned long long bytes_bin[N_BINS];
     unsigned long long bytes_sym;
     unsigned long long holes;       // reserved candidate entries left unused
+    unsigned long long big_n;       // delta rows listed for the CTA pass of k_symbolic
     unsigned int overflow;          // OVF_* bits
     unsigned int pad;
 };
@@ -174,6 +175,7 @@ struct WorkBufs {
     uint2 *cand_wit;                   // witness of each candidate (null: off)
     unsigned long long *delta_key; uint32_t *delta_slot;
     uint32_t *bitmap_scratch; unsigned long long bitmap_words;  // per CTA, global
+    uint2 *big_rows; unsigned long long big_cap;   // long delta rows (k_symbolic)
     Counters *cnt;
 };
 

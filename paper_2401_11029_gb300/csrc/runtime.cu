@@ -351,6 +351,7 @@ struct Runner {
     DevArr<unsigned long long> d_cand_key, d_delta_key;
     DevArr<uint32_t> d_cand_slot, d_delta_slot;
     DevArr<uint32_t> d_bitmap;
+    DevArr<uint2> d_big;                      // long delta rows for the symbolic CTA pass
     DevArr<Counters> d_cnt;
     DevArr<LoopCtl> d_ctl;
     DevArr<int> d_parity;
@@ -684,6 +685,8 @@ struct Runner {
         W.delta_key = d_delta_key.p; W.delta_slot = d_delta_slot.p;
         W.bitmap_scratch = d_bitmap.p;
         W.bitmap_words = (max_n + 31) / 32;
+        W.big_rows = d_big.p;
+        W.big_cap = d_big.n;
         W.cnt = d_cnt.p;
         return W;
     }
@@ -724,6 +727,9 @@ struct Runner {
         keep.release();
         d_touched[pin ^ 1].alloc(own, cap);
         touched_cap = cap;
+        // a listed row has more than 1024 delta entries, and the deltas of
+        // one iteration hold at most touched_cap entries
+        d_big.ensure(own, cap / 1024 + 1024);
         graph_valid = false;
     }
     void size_groups(int b, uint64_t cap) {
@@ -798,10 +804,12 @@ struct Runner {
                 for (int b = 0; b < N_BINS; b++)
                     run(KID_BIN0 + b,
                         [&] { launch_spgemm(b, S, P, W, max_n, tuning(), sms, st); });
-                // group counts and claim cursors (adjacent) start again
+                // group counts, claim cursors (adjacent) and the long-row
+                // list start again
                 ck(cudaMemsetAsync(d_cnt.p->groups, 0,
                                    sizeof(d_cnt.p->groups) + sizeof(d_cnt.p->claim), st),
                    "memset");
+                ck(cudaMemsetAsync(&d_cnt.p->big_n, 0, sizeof(d_cnt.p->big_n), st), "memset");
             }
         } else {
             run(KID_SYMBOLIC, [&] { launch_symbolic(S, P, W, -1, tuning(), sms, st); });
