@@ -14,7 +14,9 @@ After the timed steps the extracted pairs of every named non-terminal are
 fingerprinted and compared with the oracle's stored fingerprints.
 
 The default line also carries the other workloads, each with its own step
-time: the 64-field points-to solve (500 000 vertices), the 256 batched Dyck-3
+time: the 64-field points-to solve (500 000 vertices), the field-sensitive
+alias solve (142 fields, 41 652 vertices) and the context-sensitive
+value-flow solve (512 call sites, 100 000 vertices), the 256 batched Dyck-3
 instances (one batched CUDA-graph solve against each instance alone in the
 per-production form) and a short served Poisson stream of alias solves.
 
@@ -456,18 +458,22 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
     lib = cflr.load_library()
     import ctypes
     e2e_s = []
+    phases = {"create_grammar": [], "load_graph": [], "solve": [], "pairs_to_host": []}
     for k in range(args.steps + 1):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         c2 = cflr.cflr_create(device=local, stream=stream.cuda_stream,
                               form=cflr.CFLR_FORM_GRAPH, autotune_cache=TUNING_CACHE.encode())
         cflr.cflr_load_grammar(c2, text)
+        t1 = time.perf_counter()
         rc = lib.cflr_load_graph(c2, g.n, g.n_edges, h_src.data_ptr(), h_lab.data_ptr(),
                                  h_dst.data_ptr())
         assert rc == 0
         if not args.no_autotune:
             cflr.cflr_autotune(c2)          # the cached schedule of this workload
-        cflr.cflr_solve(c2)
+        t2 = time.perf_counter()
+        st2 = cflr.cflr_solve(c2)
+        t3 = time.perf_counter()
         tot = 0
         for x in range(n_named):
             n_p = ctypes.c_uint64()
@@ -476,10 +482,15 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
             assert rc == 0
             tot += n_p.value
         torch.cuda.synchronize(dev)
-        dt = time.perf_counter() - t0
+        t4 = time.perf_counter()
+        dt = t4 - t0
         cflr.cflr_destroy(c2)
         if k > 0:                                   # first call warms the allocator
             e2e_s.append(dt)
+            for key, a, b in (("create_grammar", t0, t1), ("load_graph", t1, t2),
+                              ("solve", t2, t3), ("pairs_to_host", t3, t4)):
+                phases[key].append(1e3 * (b - a))
+            fresh = {k: st2[k] for k in ("regrow_buffers", "regrow_sets", "regrow_pools")}
         assert tot == pairs
 
     ms = statistics.mean(step_ms)
@@ -498,7 +509,9 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
                        l2="flushed between steps (256 MiB write)"),
         "e2e": {"value": pairs_all / e2e_all, "unit": UNIT,
                 "h2d_bytes_per_step": int(12 * g.n_edges),
-                "d2h_bytes_per_step": int(8 * pairs)},
+                "d2h_bytes_per_step": int(8 * pairs),
+                "phases_ms": {k: round(statistics.mean(v), 2) for k, v in phases.items()},
+                "fresh_context_regrows": fresh},
         "gpu_launches": int(launches),
         "roofline": roofline_of(rows, "fsjpt_like" if kind == "fsjpt" else "fica_like"),
         "kernels": [{"name": r[3], "ms": round(r[0], 4), "launches": r[1],
@@ -526,7 +539,8 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
         sub.steps = max(1, min(args.steps, 5))
         sub.warmup = max(3, min(args.warmup, 3))
         sub.vertices = None
-        line["fsjpt_like_500k"] = run_fsjpt_sub(sub)
+        for name in EXTRA:
+            line[name] = run_extra(name, sub)
         line["dyck3_batch_256"] = run_dyck3_batch(sub, print_line=False)
         sub.requests = args.extra_requests
         sub.serve_warmup = 1.0
@@ -534,15 +548,35 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
     print(json.dumps(line), flush=True)
 
 
-def run_fsjpt_sub(args) -> dict:
-    """The field-sensitive points-to workload in the timed configuration:
-    step time, pairs/s, the roofline of its dominant kernel and parity."""
+# The other single-instance workloads of the default line: name -> (config,
+# graph, grammar text, stored oracle fingerprints)
+EXTRA = {
+    "fsjpt_like_500k": (FSJPT, lambda: workload_graph(FSJPT["seed"], None, "fsjpt"),
+                        lambda: grammar_of("fsjpt")),
+    "fsca_like_41k": ({"workload": "fsca_like field-sensitive alias (Fig. wcnf:fsca, 142 "
+                                   "fields; the shape of the imagick graph)",
+                       "n_vertices": 41_652, "forward_edges": 55_775, "reverse_edges": True,
+                       "seed": 6},
+                      lambda: gen.fsca_like(), lambda: gen.grammar_text("fsca", index_hi=141)),
+    "cscvf_like_100k": ({"workload": "cscvf_like context-sensitive value flow (Fig. "
+                                     "wcnf:cscvf, 512 call sites)",
+                         "n_vertices": 100_000, "edges": 168_000, "call_sites": 512,
+                         "seed": 7},
+                        lambda: gen.cscvf_like(n=100_000, n_edges=168_000, calls=512),
+                        lambda: gen.grammar_text("cscvf", index_hi=511)),
+}
+
+
+def run_extra(name, args) -> dict:
+    """One of the EXTRA workloads in the timed configuration: step time,
+    pairs/s, the roofline of its dominant kernel and parity."""
     import torch
     from paper_2401_11029_gb300 import cflr
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    g = workload_graph(FSJPT["seed"], None, "fsjpt")
-    text = grammar_of("fsjpt")
+    wl, make_graph, make_text = EXTRA[name]
+    g = make_graph()
+    text = make_text()
     ctx, tuning = timed_context(g, text, 0, stream.cuda_stream)
     n_nt, n_named, _ = cflr.cflr_grammar_sizes(ctx)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -559,16 +593,16 @@ def run_fsjpt_sub(args) -> dict:
     step_ms = timed_steps(ctx, n_named, out, flush, stream, args.steps, 1, pairs, last)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    parity = parity_record(ctx, golden_of("fsjpt_like_500k", g), out)
+    parity = parity_record(ctx, golden_of(name, g), out)
     rows = profiled_kernels(g, text, tuning, 0, stream.cuda_stream, n_named, out, flush,
                             args.steps, args.warmup, pairs)
     cflr.cflr_destroy(ctx)
     ms = statistics.mean(step_ms)
     return {"metric": METRIC, "value": pairs / (ms / 1e3), "unit": UNIT, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms,
-            "config": dict(FSJPT, edges=int(g.n_edges), pairs=int(pairs),
+            "config": dict(wl, edges=int(g.n_edges), pairs=int(pairs), nonterminals=n_nt,
                            l2="flushed between steps (256 MiB write)"),
-            "roofline": roofline_of(rows, "fsjpt_like"),
+            "roofline": roofline_of(rows, name.rsplit("_", 1)[0]),
             "kernels": [{"name": r[3], "ms": round(r[0], 4), "launches": r[1],
                          "gbs": round((r[2] / 1e9) / (r[0] / 1e3), 1) if r[0] > 0 else None}
                         for r in rows if r[1]][:6],
@@ -712,8 +746,26 @@ def run_serving(args, print_line: bool = True):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     srv_time = dict(srv.time)
-    srv.close()
     summ = summarize(done, warmup_s=args.serve_warmup)
+    # saturated (served below the arrival rate): the same requests again at
+    # 80 % of the rate served, to report latency where the server keeps up
+    sustained = None
+    if summ["req_per_s"] and summ["req_per_s"] < 0.95 * args.rate:
+        rate2 = 0.8 * summ["req_per_s"]
+        scale = args.rate / rate2
+        t1 = time.perf_counter()
+        done2 = srv.run([(r.rid, r.arrival_s * scale, g) for r, g in zip(reqs, graphs)])
+        wall2 = time.perf_counter() - t1
+        s2 = summarize(done2, warmup_s=args.serve_warmup * scale)
+        # keeping up: no queue builds, i.e. the last quarter of the requests
+        # waits about as long as the first quarter
+        lat = [f.latency_s for f in sorted(done2, key=lambda f: f.arrival_s)]
+        q = max(1, len(lat) // 4)
+        first, last = statistics.median(lat[:q]), statistics.median(lat[-q:])
+        sustained = dict(s2, rate_per_s=rate2, wall_s=wall2,
+                         first_quarter_median_s=first, last_quarter_median_s=last,
+                         keeps_up=bool(last <= 2 * first + 0.25))
+    srv.close()
     line = {"metric": "served CFL-r solves: throughput (pairs/s) with p50/p99 latency",
             "value": summ["pairs_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": len(done), "warmup": args.serve_warmup, "ms_per_step": None,
@@ -723,7 +775,12 @@ def run_serving(args, print_line: bool = True):
                        "rate_per_s": args.rate, "requests": args.requests,
                        "vertices": "log-uniform [5000, 300000]",
                        "mem_budget_gb": args.serve_budget_gb, "max_active": args.max_active},
-            "serving": dict(summ, wall_s=wall, warmup_s=args.serve_warmup, host_time=srv_time),
+            "serving": dict(summ, wall_s=wall, warmup_s=args.serve_warmup, host_time=srv_time,
+                            saturated=bool(summ["req_per_s"] and
+                                           summ["req_per_s"] < 0.95 * args.rate),
+                            # saturated, the rate served is the server's capacity
+                            capacity_req_per_s=summ["req_per_s"]),
+            "serving_below_capacity": sustained,
             "clocks": clk}
     if print_line:
         print(json.dumps(line), flush=True)

@@ -79,8 +79,10 @@ typedef struct {
                                    paths (every phase re-runs after a growth).      */
     uint32_t size_hint;         /* expected pairs per input edge of the finished
                                    closure over all non-terminals (0 = unknown): the
-                                   pair sets and the row pool start at that size, so
-                                   a fresh graph grows them rarely                  */
+                                   pair sets start with room for an even share of it
+                                   (three slots per expected pair) and the row pool
+                                   with six words per expected pair, so a fresh
+                                   graph grows them rarely                          */
     int stop_on_first_converged;/* nonzero: a batch led by this context stops after
                                    the first iteration in which some context reaches
                                    its fixpoint (CFLR_ELIMIT while others remain), so
@@ -117,6 +119,9 @@ typedef struct {
     uint64_t regrows;           /* buffer growths that re-ran a phase               */
     uint32_t converged;         /* 1 when the context has reached its fixpoint      */
     uint64_t groups[4];         /* work-list groups run by each product bin         */
+    uint64_t regrow_buffers;    /* of regrows: work buffers (work list, candidates)  */
+    uint64_t regrow_sets;       /* of regrows: pair sets (hash tables) moved          */
+    uint64_t regrow_pools;      /* of regrows: row pools moved                       */
 } cflr_stats;
 
 /* Schedule of the product kernels.  Each (production, delta row) group goes

@@ -78,7 +78,9 @@ class cflr_stats(ctypes.Structure):
                 ("solve_ms", ctypes.c_double), ("peak_device_bytes", ctypes.c_uint64),
                 ("ignored_edges", ctypes.c_uint64), ("flops", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("regrows", ctypes.c_uint64),
-                ("converged", ctypes.c_uint32), ("groups", ctypes.c_uint64 * 4)]
+                ("converged", ctypes.c_uint32), ("groups", ctypes.c_uint64 * 4),
+                ("regrow_buffers", ctypes.c_uint64), ("regrow_sets", ctypes.c_uint64),
+                ("regrow_pools", ctypes.c_uint64)]
 
     def to_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "groups"}

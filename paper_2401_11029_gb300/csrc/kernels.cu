@@ -1574,6 +1574,7 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
     const uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
     const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    unsigned long long moved = 0;           // tile bytes read and written (lane 0)
     for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + wib;
          e < n_t; e += nw) {
         const uint2 t = t_out[e];
@@ -1633,9 +1634,13 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
             base += __popc(m);
         }
         __syncwarp();
-        if (lane == 0) *dp = make_uint4((uint32_t)off, D, tcap, elog << ELOG_SHIFT);
+        if (lane == 0) {
+            *dp = make_uint4((uint32_t)off, D, tcap, elog << ELOG_SHIFT);
+            moved += 8ull * (dsc.y + D);
+        }
         __syncwarp();
     }
+    if (lane == 0 && moved) atomicAdd(&W.cnt->bytes_move[0], moved);
 }
 
 // The rows k_capacity leaves (more than TILE_WARP_MAX tiles): the CTA lists
@@ -1654,6 +1659,7 @@ __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, Work
     const int par = *W.parity;
     const uint2 *t_out = W.touched[par ^ 1];
     const unsigned long long n_t = min(W.touched_n[par ^ 1], W.touched_cap);
+    unsigned long long moved = 0;           // tile bytes read and written (thread 0)
     for (unsigned long long cb = (unsigned long long)blockIdx.x * 256; cb < n_t;
          cb += (unsigned long long)gridDim.x * 256) {
         if (threadIdx.x == 0) list_n = 0;
@@ -1726,11 +1732,15 @@ __global__ void __launch_bounds__(256) k_capacity_big(SlotTab S, InstTab I, Work
                         np[q] = pool[dsc.x + q];
                 }
                 __syncthreads();
-                if (threadIdx.x == 0) *dp = make_uint4((uint32_t)off, ntn, tcap, elog << ELOG_SHIFT);
+                if (threadIdx.x == 0) {
+                    *dp = make_uint4((uint32_t)off, ntn, tcap, elog << ELOG_SHIFT);
+                    moved += 8ull * (dsc.y + ntn);
+                }
             }
             __syncthreads();
         }
     }
+    if (threadIdx.x == 0 && moved) atomicAdd(&W.cnt->bytes_move[1], moved);
 }
 
 // Append the new pairs as single entries: (i, j) goes to the entry area of
@@ -1886,6 +1896,8 @@ __global__ void __launch_bounds__(256) k_iter_end(SlotTab S, InstTab I, WorkBufs
                 ctl->total_groups[b] += min(W.cnt->groups[b], W.group_cap[b]);
             }
             ctl->bytes_sym += W.cnt->bytes_sym;
+            ctl->bytes_move[0] += W.cnt->bytes_move[0];
+            ctl->bytes_move[1] += W.cnt->bytes_move[1];
         }
         *W.parity = par ^ 1;
         ctl->status = 0;

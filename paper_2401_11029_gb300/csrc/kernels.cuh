@@ -119,6 +119,7 @@ struct LoopCtl {
     unsigned long long bytes_bin[N_BINS];
     unsigned long long bytes_sym;
     unsigned long long total_groups[N_BINS];
+    unsigned long long bytes_move[2];
 };
 
 struct ProdTab {              // global production table of the batch
@@ -146,6 +147,8 @@ struct Counters {
     unsigned long long bytes_sym;
     unsigned long long holes;       // reserved candidate entries left unused
     unsigned long long big_n;       // delta rows listed for the CTA pass of k_symbolic
+    unsigned long long bytes_move[2];   // tile bytes read and written by moved rows
+                                        // (k_capacity, k_capacity_big)
     unsigned int overflow;          // OVF_* bits
     unsigned int pad;
 };

@@ -363,6 +363,7 @@ struct Runner {
     uint64_t cand_cap = 0, touched_cap = 0;
     uint64_t group_cap[N_BINS] = {};
     uint64_t regrows = 0;
+    uint64_t regrow_kind[3] = {};      // work buffers, pair sets, row pools
     // the iteration as one CUDA graph: a while-loop node around the body
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -417,6 +418,7 @@ struct Runner {
     void bind(std::vector<cflr_ctx *> ctxs) {
         cx = std::move(ctxs);
         regrows = 0;
+        regrow_kind[0] = regrow_kind[1] = regrow_kind[2] = 0;
         drop_graph();
         wit = false;
         for (auto *c : cx) wit |= c->cfg.witness != 0;
@@ -775,6 +777,7 @@ struct Runner {
         c->hval[x] = nv;
         c->hcap[x] = cap;
         regrows++;
+        regrow_kind[1]++;
     }
 
     void grow_pool(size_t k, uint64_t top) {
@@ -790,6 +793,7 @@ struct Runner {
         c->pool = np;       // rows address the pool by offset, so they stay valid
         c->pool_cap = cap;
         regrows++;
+        regrow_kind[2]++;
     }
 
     // ---- the iteration --------------------------------------------------
@@ -913,6 +917,7 @@ struct Runner {
                 size_touched(2 * cand_cap, *h_parity);
             }
             regrows++;
+            regrow_kind[0]++;
             return false;
         }
         const SlotTab S = slots();
@@ -1063,7 +1068,8 @@ struct Runner {
         own->k_bytes[KID_COMMIT] += 20 * h_ctl->total_cand + 20 * h_ctl->total_delta +
                                     8 * h_ctl->total_touched_out;
         own->k_bytes[KID_RESET] += 12 * h_ctl->total_touched_in;
-        own->k_bytes[KID_CAPACITY] += 24 * h_ctl->total_touched_out;
+        own->k_bytes[KID_CAPACITY] += 24 * h_ctl->total_touched_out + h_ctl->bytes_move[0];
+        own->k_bytes[KID_CAPACITY_BIG] += h_ctl->bytes_move[1];
         own->k_bytes[KID_SCATTER] += 60 * h_ctl->total_delta;
         own->k_bytes[KID_PACK] += 24 * h_ctl->total_delta + 24 * h_ctl->total_touched_out;
     }
@@ -1208,11 +1214,14 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
     if (c->cfg.initial_capacity)   // small first pool: the growth path runs early
         c->pool_cap = std::max<uint64_t>(8 * c->n_init / 5 + 4 * 2 * (uint64_t)nt, 64);
     // with a size hint, named non-terminals start with an even share of the
-    // expected closure (terminal wrappers only ever hold their edges)
+    // expected closure (terminal wrappers only ever hold their edges), with
+    // room for the candidates a pair set must also hold before they are
+    // deduplicated; the pool gets six words per expected pair (both forms'
+    // tiles and entries, and the segments rows leave behind when they move)
     const uint64_t expect = (uint64_t)c->cfg.size_hint * m;
     const uint64_t share = g.n_named ? expect / g.n_named : 0;
     if (expect && !c->cfg.initial_capacity)
-        c->pool_cap = std::min<uint64_t>(std::max<uint64_t>(c->pool_cap, 3 * expect),
+        c->pool_cap = std::min<uint64_t>(std::max<uint64_t>(c->pool_cap, 6 * expect),
                                          0xFFFFFFF0ull);
     c->pool = (uint32_t *)c->dalloc(c->pool_cap * 4);
     if (c->cfg.witness && nt > 32768)
@@ -1223,7 +1232,7 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
     c->nnz.assign(nt, 0);
     for (uint32_t A = 0; A < nt; A++) {
         uint64_t want = std::max<uint64_t>(4 * c->init_cnt[A], 1024);
-        if (A < g.n_named) want = std::max<uint64_t>(want, 2 * share);
+        if (A < g.n_named) want = std::max<uint64_t>(want, 3 * share);
         c->hcap[A] = next_pow2(want);
         c->htab[A] = (unsigned long long *)c->dalloc(c->hcap[A] * 8);
         if (c->cfg.witness) c->hval[A] = (uint2 *)c->dalloc(c->hcap[A] * 8);
@@ -1294,7 +1303,7 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
     ck(cudaEventCreate(&ev1), "event");
     ck(cudaEventRecord(ev0, own->stream), "event");
     int rc = CFLR_OK;
-    uint64_t flops = 0, cand = 0, regrows = 0, groups[4] = {0, 0, 0, 0};
+    uint64_t flops = 0, cand = 0, regrows = 0, groups[4] = {0, 0, 0, 0}, kinds[3] = {0, 0, 0};
     if (!active.empty()) {
         Runner &r = runner_of(own);
         r.bind(active);
@@ -1310,6 +1319,7 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
         cand = r.h_ctl->total_cand;
         for (int b = 0; b < 4; b++) groups[b] = r.h_ctl->total_groups[b];
         regrows = r.regrows;
+        for (int q = 0; q < 3; q++) kinds[q] = r.regrow_kind[q];
     }
     ck(cudaEventRecord(ev1, own->stream), "event");
     ck(cudaEventSynchronize(ev1), "event");
@@ -1328,6 +1338,9 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
         s.flops = flops;
         s.candidates = cand;
         s.regrows = regrows;
+        s.regrow_buffers = kinds[0];
+        s.regrow_sets = kinds[1];
+        s.regrow_pools = kinds[2];
         s.converged = c->touched_n == 0 ? 1u : 0u;
         for (int b = 0; b < 4; b++) s.groups[b] = groups[b];
         c->last = s;

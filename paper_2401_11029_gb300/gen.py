@@ -334,6 +334,77 @@ def fsjpt_like(n: int = 500_000, n_edges: int = 2_000_000, fields: int = 64, see
     return _with_reverses(g, rev)
 
 
+def fsca_like(n: int = 41_652, n_edges: int = 55_775, fields: int = 142, seed: int = 6,
+              window: int = DEFAULT_WINDOW, p_long: float = DEFAULT_P_LONG,
+              k_max: int = DEFAULT_K_MAX, field_s: float = 1.0) -> Graph:
+    """Field-sensitive C/C++ alias workload (Fig. "wcnf:fsca" labels).
+
+    Forward edges from the program-shaped sampler: 45 % 'a' (assignment),
+    25 % 'd' (dereference) and 30 % 'f_i' (access of field i, i drawn
+    Zipf(``field_s``) over ``fields`` fields); every edge also gets its
+    reverse (a_r, d_r, f_r_i).  The defaults take the shape of the paper's
+    imagick graph (41,652 vertices, 111,550 edges with reverses, 288 labels:
+    142 fields).
+    """
+    rng = _rng(seed)
+    loc = _Locality(rng, np.arange(n), window, p_long, k_max)
+    labels = ["a", "d"] + [f"f_{i}" for i in range(fields)]
+    L = len(labels)
+    n_a = n_edges * 45 // 100
+    n_d = n_edges * 25 // 100
+    n_f = n_edges - n_a - n_d
+    keys = [_distinct_edges(loc.sample, n_a, n, L, 0), _distinct_edges(loc.sample, n_d, n, L, 1)]
+    per_field = np.bincount(sample_cdf(rng, zipf_cdf(field_s, fields), n_f), minlength=fields)
+    for i in range(fields):
+        if per_field[i]:
+            keys.append(_distinct_edges(loc.sample, int(per_field[i]), n, L, 2 + i))
+    g = _keys_to_graph(n, labels, np.concatenate(keys),
+                       {"workload": "fsca_like", "seed": seed, "fields": fields,
+                        "window": window, "p_long": p_long, "k_max": k_max})
+    rev = {"a": "a_r", "d": "d_r"}
+    rev.update({f"f_{i}": f"f_r_{i}" for i in range(fields)})
+    return _with_reverses(g, rev)
+
+
+def cscvf_like(n: int = 346_034, n_edges: int = 581_210, calls: int = 5_655, seed: int = 7,
+               window: int = DEFAULT_WINDOW, p_long: float = DEFAULT_P_LONG,
+               k_max: int = DEFAULT_K_MAX, callee_s: float = 1.0) -> Graph:
+    """Context-sensitive C/C++ value-flow workload (Fig. "wcnf:cscvf" labels).
+
+    The vertices fall into procedures (the blocks of the program-shaped
+    sampler).  Intraprocedural flow is ``n_edges - 2 calls`` 'a' edges from the
+    sampler.  Call site i joins a caller procedure (uniform) and a callee
+    (Zipf(``callee_s``) over procedures, so a few functions are called from
+    many sites): 'call_i' from a vertex of the caller to the callee's first
+    vertex, and 'ret_i' from the callee's last vertex to a later vertex of the
+    caller (the call's result).  The defaults take the shape of the paper's
+    povray graph (346,034 vertices, 581,210 edges, 11,311 labels: 5,655 call
+    sites).
+    """
+    rng = _rng(seed)
+    loc = _Locality(rng, np.arange(n), window, p_long, k_max)
+    labels = ["a"] + [f"call_{i}" for i in range(calls)] + [f"ret_{i}" for i in range(calls)]
+    L = len(labels)
+    keys = [_distinct_edges(loc.sample, n_edges - 2 * calls, n, L, 0)]
+    W = max(1, int(window))
+    n_blocks = (n + W - 1) // W
+    caller = rng.integers(0, n_blocks, size=calls, dtype=np.int64)
+    callee = (sample_cdf(rng, zipf_cdf(callee_s, n_blocks), calls) +
+              rng.integers(0, n_blocks, size=calls, dtype=np.int64)) % n_blocks
+    b_lo = caller * W
+    b_len = np.minimum(b_lo + W, n) - b_lo
+    at = b_lo + rng.integers(0, 1 << 62, size=calls, dtype=np.int64) % b_len
+    back = at + rng.integers(0, 1 << 62, size=calls, dtype=np.int64) % (b_lo + b_len - at)
+    entry = callee * W
+    exit_ = np.minimum(entry + W, n) - 1
+    ci = np.arange(calls, dtype=np.int64)
+    keys.append((loc.order[at] * L + 1 + ci) * n + loc.order[entry])
+    keys.append((loc.order[exit_] * L + 1 + calls + ci) * n + loc.order[back])
+    return _keys_to_graph(n, labels, np.concatenate(keys),
+                          {"workload": "cscvf_like", "seed": seed, "calls": calls,
+                           "window": window, "p_long": p_long, "k_max": k_max})
+
+
 def log_uniform_int(rng: np.random.Generator, lo: int, hi: int) -> int:
     """An integer log-uniform in [lo, hi] (scalar math, rounded down)."""
     u = int(rng.integers(0, 1 << 53)) / float(1 << 53)

@@ -8,16 +8,20 @@ per iteration (inside one CUDA graph), until some request reaches its
 fixpoint or the tick's iteration cap is hit (cflr_solve_batch led by a
 context with stop_on_first_converged).  Between ticks the server retires
 the finished requests (their pairs are copied out and their device memory
-freed) and admits newly arrived ones while their estimated device footprint
-fits the memory budget.  A request's result is the same whether it is
-solved alone or in the mix: the batch only interleaves independent
-fixpoints.
+freed) and admits the requests that are loaded.  Loading (a context, the
+grammar, the graph's upload and renumbering, the terminal initialisation)
+runs on a second host thread, on each context's own stream, while ticks run:
+a request is taken for loading once it has arrived and its estimated device
+footprint fits the memory budget next to the requests in flight.  A
+request's result is the same whether it is solved alone or in the mix: the
+batch only interleaves independent fixpoints.
 
 This module only schedules; all CFL-r work runs in libcflr.so.
 """
 from __future__ import annotations
 
-import collections
+import queue
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -75,7 +79,8 @@ class Server:
         cflr.cflr_solve(self.leader)
         self.n_nt, self.n_named, _ = cflr.cflr_grammar_sizes(self.leader)
         self.term = {}
-        self.time = {"admit_s": 0.0, "tick_s": 0.0, "retire_s": 0.0, "ticks": 0, "regrows": 0}
+        self.time = {"admit_s": 0.0, "tick_s": 0.0, "retire_s": 0.0, "ticks": 0, "regrows": 0,
+                     "regrow_buffers": 0, "regrow_sets": 0, "regrow_pools": 0}
 
     def close(self):
         cflr.cflr_destroy(self.leader)
@@ -98,8 +103,9 @@ class Server:
         return np.asarray(out, dtype=np.uint32)
 
     def _admit(self, graph):
-        ctx = cflr.cflr_create(device=self.device, stream=self.stream, form=self.form,
-                               size_hint=self.size_hint)
+        # a private stream: the load overlaps the tick running on the
+        # leader's stream (the load ends synchronised with the host)
+        ctx = cflr.cflr_create(device=self.device, form=self.form, size_hint=self.size_hint)
         cflr.cflr_load_grammar(ctx, self.text)
         ids = self._label_ids(ctx, graph.labels)
         cflr.cflr_load_graph(ctx, graph.n, graph.src, ids[graph.lab], graph.dst)
@@ -121,49 +127,82 @@ class Server:
     def run(self, requests, clock=time.perf_counter) -> list:
         """Serve ``requests``: an iterable of (rid, arrival_s, graph), sorted
         by arrival.  Returns a list of ``Finished``."""
-        pending = collections.deque(requests)
-        active = []          # [ctx, rid, graph, arrival, admitted, footprint, iterations]
-        used = 0
-        done = []
+        requests = list(requests)
+        ready = queue.Queue()       # loaded requests waiting for the next tick
+        cond = threading.Condition()
+        inflight = {"used": 0, "n": 0}     # footprint and count being loaded or solved
+        failure = []
         t0 = clock()
-        while pending or active:
-            now = clock() - t0
-            while (pending and pending[0][1] <= now and len(active) < self.max_active):
-                rid, arr, g = pending[0]
-                fp = self.footprint(g)
-                if active and used + fp > self.budget:
-                    break                                  # wait for memory to free up
-                pending.popleft()
-                ta = clock()
-                ctx = self._admit(g)
-                self.time["admit_s"] += clock() - ta
-                active.append([ctx, rid, g, arr, clock() - t0, fp, 0])
-                used += fp
-            if not active:
-                wait = pending[0][1] - (clock() - t0)
-                if wait > 0:
-                    time.sleep(min(wait, 0.05))
-                continue
-            tt = clock()
-            stats = cflr.cflr_solve_batch([self.leader] + [a[0] for a in active],
-                                          allow_limit=True)
-            self.time["tick_s"] += clock() - tt
-            self.time["ticks"] += 1
-            still = []
-            self.time["regrows"] += stats[0]["regrows"]
-            for a, st in zip(active, stats[1:]):
-                a[6] = st["iterations"]
-                if st["converged"]:
-                    tr = clock()
-                    pairs, keys = self._retire(a[0], a)
-                    self.time["retire_s"] += clock() - tr
-                    used -= a[5]
-                    done.append(Finished(rid=a[1], n=a[2].n, edges=a[2].n_edges, pairs=pairs,
-                                         iterations=a[6], arrival_s=a[3], admitted_s=a[4],
-                                         done_s=clock() - t0, keys=keys))
-                else:
-                    still.append(a)
-            active = still
+
+        def loader():
+            try:
+                for rid, arr, g in requests:
+                    wait = arr - (clock() - t0)
+                    if wait > 0:
+                        time.sleep(wait)
+                    fp = self.footprint(g)
+                    with cond:
+                        # room: a slot, and the footprint within the budget
+                        # (a request alone is always taken)
+                        while inflight["n"] and (inflight["n"] >= self.max_active or
+                                                 inflight["used"] + fp > self.budget):
+                            cond.wait()
+                        inflight["used"] += fp
+                        inflight["n"] += 1
+                    ta = clock()
+                    ctx = self._admit(g)
+                    self.time["admit_s"] += clock() - ta
+                    ready.put([ctx, rid, g, arr, clock() - t0, fp, 0])
+            except BaseException as exc:        # handed to the serving thread
+                failure.append(exc)
+                ready.put(None)
+
+        th = threading.Thread(target=loader, name="cflr-loader", daemon=True)
+        th.start()
+        active = []          # [ctx, rid, graph, arrival, admitted, footprint, iterations]
+        done = []
+        try:
+            while len(done) < len(requests):
+                # admit what is loaded; wait for the loader when idle
+                block = not active
+                while True:
+                    try:
+                        item = ready.get(block=block, timeout=0.05 if block else None)
+                    except queue.Empty:
+                        break
+                    if item is None:
+                        raise failure[0]
+                    item[4] = clock() - t0
+                    active.append(item)
+                    block = False
+                if not active:
+                    continue
+                tt = clock()
+                stats = cflr.cflr_solve_batch([self.leader] + [a[0] for a in active],
+                                              allow_limit=True)
+                self.time["tick_s"] += clock() - tt
+                self.time["ticks"] += 1
+                still = []
+                for k in ("regrows", "regrow_buffers", "regrow_sets", "regrow_pools"):
+                    self.time[k] += stats[0][k]
+                for a, st in zip(active, stats[1:]):
+                    a[6] = st["iterations"]
+                    if st["converged"]:
+                        tr = clock()
+                        pairs, keys = self._retire(a[0], a)
+                        self.time["retire_s"] += clock() - tr
+                        with cond:
+                            inflight["used"] -= a[5]
+                            inflight["n"] -= 1
+                            cond.notify()
+                        done.append(Finished(rid=a[1], n=a[2].n, edges=a[2].n_edges,
+                                             pairs=pairs, iterations=a[6], arrival_s=a[3],
+                                             admitted_s=a[4], done_s=clock() - t0, keys=keys))
+                    else:
+                        still.append(a)
+                active = still
+        finally:
+            th.join(timeout=60)
         return done
 
 

@@ -27,16 +27,24 @@ WORKLOADS = {
     "dyck1_er_1000": ("dyck1", lambda: gen.dyck1_er()),
     "fica_like_200k": ("fica", lambda: gen.fica_like()),
     "fsjpt_like_500k": ("fsjpt", lambda: gen.fsjpt_like()),
+    # the imagick-shaped field-sensitive alias graph (142 fields)
+    "fsca_like_41k": (("fsca", 141), lambda: gen.fsca_like()),
+    # context-sensitive value flow, 100k vertices (povray's edge ratio), 512
+    # call sites
+    "cscvf_like_100k": (("cscvf", 511),
+                        lambda: gen.cscvf_like(n=100_000, n_edges=168_000, calls=512)),
 }
 
 
 def one(name, grammar, make):
     g = make()
-    text = gen.grammar_text(grammar)
+    # a grammar name, or (name, last index) for the indexed grammars
+    text = gen.grammar_text(*grammar) if isinstance(grammar, tuple) else gen.grammar_text(grammar)
     t0 = time.time()
     res = oracle.solve(text, g)
     pg = res.grammar
-    out = {"workload": name, "grammar": grammar, "n": g.n, "edges": g.n_edges,
+    out = {"workload": name, "grammar": list(grammar) if isinstance(grammar, tuple) else grammar,
+           "n": g.n, "edges": g.n_edges,
            "edge_digest": g.edge_digest(), "meta": {k: v for k, v in g.meta.items()
                                                     if isinstance(v, (int, float, str))},
            "oracle_seconds": round(res.seconds, 2), "total_pairs": res.total(),

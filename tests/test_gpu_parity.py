@@ -82,6 +82,7 @@ def test_growth_paths_give_identical_pairs():
     g = gen.fica_like(n=5000, n_a=10_000, n_d=3750, seed=11)
     st, _ = assert_parity(gen.grammar_text("fica"), g, initial_capacity=64)
     assert st["regrows"] > 0
+    assert st["regrow_buffers"] + st["regrow_sets"] + st["regrow_pools"] == st["regrows"]
 
 
 def test_batch_equals_alone_and_oracle():
@@ -622,3 +623,34 @@ def test_full_pair_set_stops_the_solve_and_context_stays_usable():
             want = oracle.solve(text, small)
             for x in want.grammar.nts:
                 assert np.array_equal(s.pairs(x), want.pairs[x]), x
+
+
+# ---------------------------------------------------------------------------
+# the field-sensitive alias and context-sensitive value-flow workloads
+# (Figs. wcnf:fsca and wcnf:cscvf: epsilon, unit productions, indexed
+# families over the full index range of the graph)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("form", [cflr.CFLR_FORM_PLAIN, cflr.CFLR_FORM_BATCHED,
+                                  cflr.CFLR_FORM_GRAPH])
+def test_fsca_program_graph_64_fields(form):
+    g = gen.fsca_like(n=3000, n_edges=4000, fields=64, seed=21)
+    st, want = assert_parity(gen.grammar_text("fsca", index_hi=63), g, form=form)
+    assert want.pairs["M"].size > 1000 and want.pairs["FV_63"].size > 0
+
+
+@pytest.mark.parametrize("form", [cflr.CFLR_FORM_PLAIN, cflr.CFLR_FORM_BATCHED,
+                                  cflr.CFLR_FORM_GRAPH])
+def test_cscvf_program_graph_256_call_sites(form):
+    g = gen.cscvf_like(n=4000, n_edges=6700, calls=256, seed=22)
+    st, want = assert_parity(gen.grammar_text("cscvf", index_hi=255), g, form=form)
+    assert want.pairs["AH"].size > 0
+
+
+def test_fsca_paper_shaped_142_fields():
+    """The imagick-shaped field-sensitive alias graph (41,652 vertices, 111,550
+    edges, 142 fields) in the timed launch configuration (graph form)."""
+    g = gen.fsca_like()
+    assert len(g.labels) == 288
+    assert_parity(gen.grammar_text("fsca", index_hi=141), g, include_wrappers=False,
+                  form=cflr.CFLR_FORM_GRAPH)
