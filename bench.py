@@ -522,7 +522,9 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
         "parity": parity,
         "solve": {"form": "graph", "iterations": solve_stats["iterations"],
                   "groups_per_bin": solve_stats["groups"],
-                  "flops": solve_stats["flops"], "candidates": solve_stats["candidates"],
+                  "flops": solve_stats["flops"], "flops_bin3": solve_stats["flops_bin3"],
+                  "mask_tiles_bin3": solve_stats["mask_tiles_bin3"],
+                  "candidates": solve_stats["candidates"],
                   "peak_device_bytes": solve_stats["peak_device_bytes"]},
         "roofline_note": "kernel times from the same steps replayed with per-kernel CUDA "
                          "events (host-launched iterations) right after the timed region",

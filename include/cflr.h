@@ -122,6 +122,8 @@ typedef struct {
     uint64_t regrow_buffers;    /* of regrows: work buffers (work list, candidates)  */
     uint64_t regrow_sets;       /* of regrows: pair sets (hash tables) moved          */
     uint64_t regrow_pools;      /* of regrows: row pools moved                       */
+    uint64_t flops_bin3;        /* of flops: product steps of the bitmap bin (3)     */
+    uint64_t mask_tiles_bin3;   /* mask-row tiles the bitmap bin's groups loaded     */
 } cflr_stats;
 
 /* Schedule of the product kernels.  Each (production, delta row) group goes

@@ -80,7 +80,8 @@ class cflr_stats(ctypes.Structure):
                 ("candidates", ctypes.c_uint64), ("regrows", ctypes.c_uint64),
                 ("converged", ctypes.c_uint32), ("groups", ctypes.c_uint64 * 4),
                 ("regrow_buffers", ctypes.c_uint64), ("regrow_sets", ctypes.c_uint64),
-                ("regrow_pools", ctypes.c_uint64)]
+                ("regrow_pools", ctypes.c_uint64), ("flops_bin3", ctypes.c_uint64),
+                ("mask_tiles_bin3", ctypes.c_uint64)]
 
     def to_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "groups"}

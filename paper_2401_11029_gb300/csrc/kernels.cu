@@ -445,6 +445,7 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkB
     int fill[N_BINS] = {0, 0, 0, 0};
     unsigned long long bytes[N_BINS] = {0, 0, 0, 0};
     unsigned long long flops = 0, sym_bytes = 0;
+    unsigned long long flops3 = 0, mask3 = 0;   // the bitmap bin's product and mask tiles
 
     auto flush = [&](int b) {   // lane 0 only
         unsigned long long pos = atomicAdd(&W.cnt->groups[b], (unsigned long long)fill[b]);
@@ -501,6 +502,10 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkB
             bytes[b] += 4ull * d + fbytes + (probe ? 0ull : mbytes + 16ull);
             sym_bytes += 20ull * d + 40ull;
             flops += f;
+            if (b == 3) {
+                flops3 += f;
+                mask3 += probe ? 0ull : mlen;
+            }
         }
         return b;
     };
@@ -760,12 +765,16 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkB
     for (int b = 0; b < N_BINS; b++) bytes[b] = warp_sum64(bytes[b]);
     flops = warp_sum64(flops);
     sym_bytes = warp_sum64(sym_bytes);
+    flops3 = warp_sum64(flops3);
+    mask3 = warp_sum64(mask3);
     if (lane == 0) {
         for (int b = 0; b < N_BINS; b++) {
             if (fill[b]) flush(b);
             if (bytes[b]) atomicAdd(&W.cnt->bytes_bin[b], bytes[b]);
         }
         if (flops) atomicAdd(&W.cnt->flops, flops);
+        if (flops3) atomicAdd(&W.cnt->tiles_bin3[0], flops3);
+        if (mask3) atomicAdd(&W.cnt->tiles_bin3[1], mask3);
         if (sym_bytes) atomicAdd(&W.cnt->bytes_sym, sym_bytes);
     }
 }
@@ -1385,7 +1394,12 @@ __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W, uint32_t 
     __shared__ uint32_t slot_new[COMMIT_SLOTS];
     __shared__ uint32_t n_new, n_touch;
     __shared__ unsigned long long base_new, base_touch;
-    if (W.cnt->overflow & OVF_STOP) return;    // the iteration is re-run after a growth
+    __shared__ unsigned stop;
+    // one read for the CTA (this kernel's own threads may set OVF_FULL, and
+    // every thread must take the same path to the barriers below)
+    if (threadIdx.x == 0) stop = W.cnt->overflow & OVF_STOP;
+    __syncthreads();
+    if (stop) return;                          // the iteration is re-run after a growth
     const int lane = threadIdx.x & 31;
     const int par = *W.parity;
     unsigned long long *out_n = &W.touched_n[par ^ 1];
@@ -1896,6 +1910,8 @@ __global__ void __launch_bounds__(256) k_iter_end(SlotTab S, InstTab I, WorkBufs
                 ctl->total_groups[b] += min(W.cnt->groups[b], W.group_cap[b]);
             }
             ctl->bytes_sym += W.cnt->bytes_sym;
+            ctl->tiles_bin3[0] += W.cnt->tiles_bin3[0];
+            ctl->tiles_bin3[1] += W.cnt->tiles_bin3[1];
             ctl->bytes_move[0] += W.cnt->bytes_move[0];
             ctl->bytes_move[1] += W.cnt->bytes_move[1];
         }

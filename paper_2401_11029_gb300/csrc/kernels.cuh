@@ -120,6 +120,7 @@ struct LoopCtl {
     unsigned long long bytes_sym;
     unsigned long long total_groups[N_BINS];
     unsigned long long bytes_move[2];
+    unsigned long long tiles_bin3[2];
 };
 
 struct ProdTab {              // global production table of the batch
@@ -149,6 +150,7 @@ struct Counters {
     unsigned long long big_n;       // delta rows listed for the CTA pass of k_symbolic
     unsigned long long bytes_move[2];   // tile bytes read and written by moved rows
                                         // (k_capacity, k_capacity_big)
+    unsigned long long tiles_bin3[2];   // product and mask tiles of the bitmap bin
     unsigned int overflow;          // OVF_* bits
     unsigned int pad;
 };

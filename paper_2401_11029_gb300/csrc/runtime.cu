@@ -1304,6 +1304,7 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
     ck(cudaEventRecord(ev0, own->stream), "event");
     int rc = CFLR_OK;
     uint64_t flops = 0, cand = 0, regrows = 0, groups[4] = {0, 0, 0, 0}, kinds[3] = {0, 0, 0};
+    uint64_t tiles3[2] = {0, 0};
     if (!active.empty()) {
         Runner &r = runner_of(own);
         r.bind(active);
@@ -1316,6 +1317,8 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
         r.download_state(true);
         r.export_touched();
         flops = r.h_ctl->total_flops;
+        tiles3[0] = r.h_ctl->tiles_bin3[0];
+        tiles3[1] = r.h_ctl->tiles_bin3[1];
         cand = r.h_ctl->total_cand;
         for (int b = 0; b < 4; b++) groups[b] = r.h_ctl->total_groups[b];
         regrows = r.regrows;
@@ -1341,6 +1344,8 @@ int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
         s.regrow_buffers = kinds[0];
         s.regrow_sets = kinds[1];
         s.regrow_pools = kinds[2];
+        s.flops_bin3 = tiles3[0];
+        s.mask_tiles_bin3 = tiles3[1];
         s.converged = c->touched_n == 0 ? 1u : 0u;
         for (int b = 0; b < 4; b++) s.groups[b] = groups[b];
         c->last = s;
