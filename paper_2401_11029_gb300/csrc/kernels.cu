@@ -2015,22 +2015,43 @@ __global__ void k_fill_u64(unsigned long long *p, unsigned long long count,
 
 // Split a batch's touched list back into per-instance lists with local
 // slot ids: first count the entries of every instance, then scatter.
+// (Lanes of one instance add their entries with one atomic per warp: the
+// rows of an instance lie together in the list.)
 __global__ void k_touched_count(const uint2 *in, unsigned long long n, const uint32_t *slot_inst,
                                 unsigned long long *cnt) {
-    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-         s < n; s += (unsigned long long)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[slot_inst[in[s].x >> 1]], 1ull);
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+         b < n; b += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long s = b + lane;
+        const uint32_t k = s < n ? slot_inst[in[s].x >> 1] : EMPTY32;
+        const unsigned same = __match_any_sync(FULL_MASK, k);
+        if (k != EMPTY32 && lane == __ffs(same) - 1)
+            atomicAdd(&cnt[k], (unsigned long long)__popc(same));
+    }
 }
 
 __global__ void k_touched_split(const uint2 *in, unsigned long long n, const uint32_t *slot_inst,
                                 const uint32_t *inst_base, uint2 *const *out,
                                 unsigned long long *cursor) {
-    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-         s < n; s += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint2 t = in[s];
-        const uint32_t k = slot_inst[t.x >> 1];
-        const unsigned long long pos = atomicAdd(&cursor[k], 1ull);
-        out[k][pos] = make_uint2(t.x - 2 * inst_base[k], t.y);
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+         b < n; b += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long s = b + lane;
+        uint2 t = make_uint2(0, 0);
+        uint32_t k = EMPTY32;
+        if (s < n) {
+            t = in[s];
+            k = slot_inst[t.x >> 1];
+        }
+        const unsigned same = __match_any_sync(FULL_MASK, k);
+        const int leader = __ffs(same) - 1;
+        unsigned long long pos = 0;
+        if (k != EMPTY32 && lane == leader) pos = atomicAdd(&cursor[k], (unsigned long long)__popc(same));
+        pos = __shfl_sync(FULL_MASK, pos, leader);
+        if (k != EMPTY32) {
+            pos += __popc(same & ((1u << lane) - 1));
+            out[k][pos] = make_uint2(t.x - 2 * inst_base[k], t.y);
+        }
     }
 }
 

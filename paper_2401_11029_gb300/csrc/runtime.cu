@@ -1028,6 +1028,22 @@ struct Runner {
             for (auto *c : cx) c->touched_n = 0;
             return;
         }
+        if (ni == 1) {
+            // one instance: its slots are the batch's, so the list is copied
+            // as it is (a split would serialise on one cursor)
+            cflr_ctx *c = cx[0];
+            if (n_in > c->touched_cap) {
+                if (c->touched) c->dfree(c->touched, c->touched_cap * sizeof(uint2));
+                c->touched = nullptr;
+                c->touched_cap = std::max<uint64_t>(n_in + n_in / 4, 1024);
+                c->touched = (uint2 *)alloc_for(c, c->touched_cap * sizeof(uint2));
+            }
+            c->touched_n = n_in;
+            ck(cudaMemcpyAsync(c->touched, d_touched[par].p, n_in * sizeof(uint2),
+                               cudaMemcpyDeviceToDevice, st), "D2D touched");
+            sync("export copy");
+            return;
+        }
         d_inst_cnt.ensure(own, ni);
         d_inst_base.ensure(own, ni);
         d_inst_out.ensure(own, ni);
