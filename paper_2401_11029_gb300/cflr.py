@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libcflr.so")
+# CFLR_LIBRARY=checked selects the bounds-checked build of the same library
+LIB_PATH = os.path.join(_HERE, "libcflr_checked.so" if os.environ.get("CFLR_LIBRARY") == "checked"
+                        else "libcflr.so")
 
 CFLR_OK = 0
 CFLR_EINVAL = -1

@@ -65,6 +65,20 @@ __device__ __forceinline__ uint32_t select_bit(uint32_t m, uint32_t n) {
     return pos;
 }
 
+// A row descriptor of `slot` that lies inside its instance's pool (checked
+// builds; always true otherwise): 16-byte aligned, tiles within the capacity,
+// tile and entry sections within the pool.
+__device__ __forceinline__ bool row_in_pool(const SlotTab &S, uint32_t slot, uint4 d,
+                                            unsigned *err) {
+#if defined(CFLR_CHECKED)
+    const unsigned long long end = (unsigned long long)d.x + tile_words(d.z) +
+                                   (d.z ? entry_cap(d) : 0ull);
+    return CFLR_CHECK((d.x & 3u) == 0 && d.y <= d.z && end <= S.pool_cap[S.inst[slot]], err);
+#else
+    return true;
+#endif
+}
+
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -130,13 +144,25 @@ __device__ __forceinline__ void clear_table(uint32_t *tab, uint32_t lg, uint32_t
 // n-bit bitmap of the row (bin 3).
 struct BitmapAcc {
     uint32_t *bm;
+#if defined(CFLR_CHECKED)
+    uint32_t words;     // the row's words (checked builds)
+    unsigned *err;
+#endif
     __device__ __forceinline__ uint32_t ins(uint32_t w, uint32_t b) const {
+#if defined(CFLR_CHECKED)
+        if (!CFLR_CHECK(w < words, err)) return 0;
+#endif
         const uint32_t ob = ((volatile uint32_t *)bm)[w];
         if ((ob & b) == b) return 0;
         return b & ~atomicOr(&bm[w], b);
     }
     // bits whose newness nobody asks (the mask row): one atomic, no read
-    __device__ __forceinline__ void set(uint32_t w, uint32_t b) const { atomicOr(&bm[w], b); }
+    __device__ __forceinline__ void set(uint32_t w, uint32_t b) const {
+#if defined(CFLR_CHECKED)
+        if (!CFLR_CHECK(w < words, err)) return;
+#endif
+        atomicOr(&bm[w], b);
+    }
 };
 
 // Whether a pair set holds `key`; a probe sequence that passes over the
@@ -241,7 +267,7 @@ struct Work {
 
 __device__ __forceinline__ Work gathered_work(const SlotTab &S, uint32_t g, uint32_t o, uint32_t n,
                                               const uint32_t *pool, uint32_t dstart, uint32_t d,
-                                              uint32_t q0, uint32_t qstep) {
+                                              uint32_t q0, uint32_t qstep, unsigned *err) {
     const uint4 *dg = S.desc[g] + (size_t)o * n;
     const uint32_t *oc = S.occ[g];
     const uint32_t ow = S.occ_w[g], lx = S.local[g];
@@ -253,7 +279,10 @@ __device__ __forceinline__ Work gathered_work(const SlotTab &S, uint32_t g, uint
             uint32_t k[4], ob[4];
             uint4 gd[4];
 #pragma unroll
-            for (int t = 0; t < 4; t++) k[t] = q + t < d ? pool[dstart + q + t] : 0u;
+            for (int t = 0; t < 4; t++) {
+                k[t] = q + t < d ? pool[dstart + q + t] : 0u;
+                if (!CFLR_CHECK(k[t] < n, err)) k[t] = 0;
+            }
 #pragma unroll
             for (int t = 0; t < 4; t++)
                 ob[t] = q + t < d ? oc[((size_t)o * n + k[t]) * ow + (lx >> 5)] & bit : 0u;
@@ -271,6 +300,7 @@ __device__ __forceinline__ Work gathered_work(const SlotTab &S, uint32_t g, uint
     }
     for (uint32_t q = q0; q < d; q += qstep) {
         const uint32_t k = pool[dstart + q];
+        if (!CFLR_CHECK(k < n, err)) continue;
         if (oc[((size_t)o * n + k) * ow + (lx >> 5)] & bit) {
             // column form (o = 1): A_old, the tiles before the last merge's
             const uint4 gd = dg[k];
@@ -287,7 +317,8 @@ __device__ __forceinline__ Work gathered_work(const SlotTab &S, uint32_t g, uint
 // are consecutive, so a few words per entry say which members have a row.
 __device__ __forceinline__ Work family_work(const SlotTab &S, uint32_t g0, uint32_t F, uint32_t o,
                                             uint32_t n, const uint32_t *pool, uint32_t dstart,
-                                            uint32_t d, uint32_t q0, uint32_t qstep) {
+                                            uint32_t d, uint32_t q0, uint32_t qstep,
+                                            unsigned *err) {
     const uint32_t *oc = S.occ[g0];
     const uint32_t ow = S.occ_w[g0], lx0 = S.local[g0];
     Work w{0, 0};
@@ -297,6 +328,7 @@ __device__ __forceinline__ Work family_work(const SlotTab &S, uint32_t g0, uint3
         // together instead of one after another on the entry's lane
         for (uint32_t q = 0; q < d; q++) {
             const uint32_t k = pool[dstart + q];
+            if (!CFLR_CHECK(k < n, err)) continue;
             const uint32_t *ok = oc + ((size_t)o * n + k) * ow;
             for (uint32_t i = q0; i < F; i += 32) {
                 const uint32_t x = lx0 + i;
@@ -312,6 +344,7 @@ __device__ __forceinline__ Work family_work(const SlotTab &S, uint32_t g0, uint3
     }
     for (uint32_t q = q0; q < d; q += qstep) {
         const uint32_t k = pool[dstart + q];
+        if (!CFLR_CHECK(k < n, err)) continue;
         const uint32_t *ok = oc + ((size_t)o * n + k) * ow;
         for (uint32_t wi = lx0 >> 5; wi <= (lx0 + F - 1) >> 5; wi++) {
             const uint32_t lo = wi * 32;
@@ -361,7 +394,7 @@ __device__ __forceinline__ void family_members(const SlotTab &S, uint32_t g0, ui
                                                uint32_t o, uint32_t n, const uint32_t *pool,
                                                uint32_t dstart, uint32_t d, uint32_t tid,
                                                uint32_t nth, unsigned long long *mf,
-                                               uint32_t *mc) {
+                                               uint32_t *mc, unsigned *err) {
     const uint32_t *oc = S.occ[g0];
     const uint4 *dg = S.desc[g0];
     const uint32_t ow = S.occ_w[g0], lx0 = S.local[g0];
@@ -375,12 +408,13 @@ __device__ __forceinline__ void family_members(const SlotTab &S, uint32_t g0, ui
         for (int t = 0; t < 4; t++) {
             const uint32_t q = qb + nth * t + tid;
             k[t] = q < d ? pool[dstart + q] : 0u;
+            if (!CFLR_CHECK(k[t] < n, err)) k[t] = d;   // skipped below
         }
 #pragma unroll
         for (int t = 0; t < 4; t++) {
             const uint32_t q = qb + nth * t + tid;
             m[t] = 0;
-            if (q < d) {
+            if (q < d && k[t] < n) {
                 const uint32_t *ok = oc + (oo + k[t]) * ow + w0;
                 const uint32_t x0 = ok[0];
                 const uint32_t x1 = w0 + 1 <= wlast ? ok[1] : 0u;
@@ -542,7 +576,8 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkB
                     mc[i] = 0;
                 }
                 group_sync();
-                family_members(S, g0, fm.y, o, n, pool, dstart, d, q0, qstep, mf, mc);
+                family_members(S, g0, fm.y, o, n, pool, dstart, d, q0, qstep, mf, mc,
+                               &W.cnt->overflow);
                 group_sync();
                 Work wt{0, 0};
                 for (uint32_t i = q0; i < fm.y; i += qstep) {
@@ -587,11 +622,12 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkB
             }
             Work wk{0, 0};
             if (fm.z & FAM_CONSEC) {
-                wk = family_work(S, g0, fm.y, o, n, pool, dstart, d, q0, qstep);
+                wk = family_work(S, g0, fm.y, o, n, pool, dstart, d, q0, qstep,
+                                 &W.cnt->overflow);
             } else {
                 for (uint32_t i = 0; i < fm.y; i++) {
                     const Work wi = gathered_work(S, member_slot(i), o, n, pool, dstart, d, q0,
-                                                  qstep);
+                                                  qstep, &W.cnt->overflow);
                     wk.f += wi.f;
                     wk.fb += wi.fb;
                 }
@@ -618,7 +654,7 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkB
                         const uint4 pr = P.prod[mp[i]];
                         const uint32_t mt = S.desc[pr.x][r].y;
                         const Work wi = gathered_work(S, (fm.w == PART_A) ? pr.z : pr.y, o, n,
-                                                      pool, dstart, d, 0, 1);
+                                                      pool, dstart, d, 0, 1, &W.cnt->overflow);
                         if (wi.f)
                             b = classify((mp[i] << 2) | fm.w, fm.w, idx, d, mt, 8ull * mt, wi.f,
                                          wi.fb, false, mg);
@@ -628,8 +664,8 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkB
                 acct = keep_acct;
             } else {               // too large for a hash bin: one group per member
                 for (uint32_t i = 0; i < fm.y; i++) {
-                    const Work wi =
-                        sum(gathered_work(S, member_slot(i), o, n, pool, dstart, d, q0, qstep));
+                    const Work wi = sum(gathered_work(S, member_slot(i), o, n, pool, dstart, d,
+                                                      q0, qstep, &W.cnt->overflow));
                     if (wi.f == 0) continue;
                     const uint32_t mt = S.desc[P.prod[mp[i]].x][r].y;
                     emit(classify((mp[i] << 2) | fm.w, fm.w, idx, d, mt, 8ull * mt, wi.f, wi.fb,
@@ -648,7 +684,7 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkB
         } else {
             // gathered rows: b's row form (PART_A) or a's column form (PART_B)
             wk = sum(gathered_work(S, (part == PART_A) ? pr.z : pr.y, o, n, pool, dstart, d, q0,
-                                   qstep));
+                                   qstep, &W.cnt->overflow));
         }
         if (wk.f == 0) return;
         uint2 grp;
@@ -826,11 +862,16 @@ __device__ __forceinline__ GroupInfo decode_group(const ProdTab &P, const SlotTa
 // The delta of a group: the entries the last merge added to a's row form
 // (PART_A, PART_U) or b's column form; returns {pool offset, count}.  A
 // family's shared operand is its members' a (PART_A) or b (PART_B).
-__device__ __forceinline__ uint2 owner_delta(const SlotTab &S, const GroupInfo &gi) {
+__device__ __forceinline__ uint2 owner_delta(const SlotTab &S, const GroupInfo &gi,
+                                             unsigned *err) {
     const uint32_t x = (gi.part == PART_B) ? gi.b : gi.a;
     const size_t r = (size_t)gi.o * gi.n + gi.idx;
     const uint4 dsc = S.desc[x][r];
-    return make_uint2(dsc.x + tile_words(dsc.z), S.dn[x][r].x);
+    const uint32_t d = S.dn[x][r].x;
+    if (!CFLR_CHECK(gi.idx < gi.n, err) || !row_in_pool(S, x, dsc, err) ||
+        !CFLR_CHECK(d <= (dsc.z ? entry_cap(dsc) : 0u), err))
+        return make_uint2(0, 0);
+    return make_uint2(dsc.x + tile_words(dsc.z), d);
 }
 
 __device__ __forceinline__ unsigned long long group_key(const GroupInfo &gi, uint32_t v) {
@@ -1114,8 +1155,10 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
             uint32_t nb = 0, wd = 0;
             if (e < d) {
                 const uint32_t v = pool[dstart + e];
-                wd = v >> 5;
-                nb = acc.ins(wd, 1u << (v & 31));
+                if (CFLR_CHECK(v < gi.n, &W.cnt->overflow)) {
+                    wd = v >> 5;
+                    nb = acc.ins(wd, 1u << (v & 31));
+                }
             }
             if (__any_sync(FULL_MASK, nb != 0)) emit_bits(nb, wd, 0u, 0u, 0u, 0u, 0u, 0u, 0, 0);
         }
@@ -1136,6 +1179,7 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
             uint32_t k = 0, mlo = 0, mhi = 0;
             if (e < hi_e) {
                 k = pool[dstart + e];
+                if (!CFLR_CHECK(k < gi.n, &W.cnt->overflow)) k = 0;
                 const uint32_t *ok = oc + (oo + k) * ow + w0;
                 const uint32_t x0 = ok[0];
                 const uint32_t x1 = w0 + 1 <= wlast ? ok[1] : 0u;
@@ -1169,8 +1213,10 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                     const uint32_t nth = f - (o_incl - o_cnt), plo = __popc(o_lo);
                     tag = nth < plo ? select_bit(o_lo, nth) : 32 + select_bit(o_hi, nth - plo);
                     const uint4 gd = S.desc[g0 + tag][oo + o_k];
-                    toff = gd.x;
-                    tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);
+                    if (row_in_pool(S, g0 + tag, gd, &W.cnt->overflow)) {
+                        toff = gd.x;
+                        tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);
+                    }
                 }
                 walk(toff, tn, tag, o_k);
             }
@@ -1191,11 +1237,14 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                 const uint4 pr = P.prod[P.fam_prod[gi.first + i]];
                 const uint32_t gs = (gi.part == PART_A) ? pr.z : pr.y;
                 const uint32_t lx = S.local[gs];
-                if ((S.occ[gs][(oo + k) * S.occ_w[gs] + (lx >> 5)] >> (lx & 31)) & 1u) {
+                if (CFLR_CHECK(k < gi.n, &W.cnt->overflow) &&
+                    ((S.occ[gs][(oo + k) * S.occ_w[gs] + (lx >> 5)] >> (lx & 31)) & 1u)) {
                     const uint4 gd = S.desc[gs][oo + k];
-                    toff = gd.x;
-                    tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);
-                    tag = i;
+                    if (row_in_pool(S, gs, gd, &W.cnt->overflow)) {
+                        toff = gd.x;
+                        tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);
+                        tag = i;
+                    }
                 }
             }
             walk(toff, tn, tag, k);
@@ -1210,9 +1259,13 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
         uint32_t toff = 0, tn = 0, k = 0;
         if (e < hi_e) {
             k = pool[dstart + e];
-            const uint4 gd = dg[k];
-            toff = gd.x;
-            tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);   // A_old for A . dB
+            if (CFLR_CHECK(k < gi.n, &W.cnt->overflow)) {
+                const uint4 gd = dg[k];
+                if (row_in_pool(S, g0, gd, &W.cnt->overflow)) {
+                    toff = gd.x;
+                    tn = gd.y - (gi.o ? (gd.w & DLAST_MASK) : 0u);   // A_old for A . dB
+                }
+            }
         }
         walk(toff, tn, 0, k);
     }
@@ -1223,8 +1276,10 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
 // thread tid of nth takes every nth tile.
 template <class Acc>
 __device__ __forceinline__ void preload_mask(const SlotTab &S, const GroupInfo &gi,
-                                             const Acc &acc, uint32_t tid, uint32_t nth) {
+                                             const Acc &acc, uint32_t tid, uint32_t nth,
+                                             unsigned *err) {
     const uint4 md = S.desc[gi.c][(size_t)gi.o * gi.n + gi.idx];
+    if (!row_in_pool(S, gi.c, md, err)) return;
     const uint32_t *tl = S.pool[gi.c] + md.x;
     // tile pairs (a tile section holds an even number of tiles)
     for (uint32_t q = tid; 2 * q < md.y; q += nth) {
@@ -1255,10 +1310,10 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS == 8 ? 4 : 3) k_spgemm_warp(
         __syncwarp();
         const HashAcc acc{tab, lg, &W.cnt->overflow};
         if (!gi.probe) {
-            preload_mask(S, gi, acc, lane, 32);
+            preload_mask(S, gi, acc, lane, 32, &W.cnt->overflow);
             __syncwarp();
         }
-        const uint2 own = owner_delta(S, gi);
+        const uint2 own = owner_delta(S, gi, &W.cnt->overflow);
         const uint32_t e =
             expand_rows<WIT, true, false, 2>(S, P, W, gi, own, 0, 1, lane, acc, ck);
         if (lane == 0 && e) {
@@ -1296,9 +1351,9 @@ __global__ void __launch_bounds__(256, LG == 12 ? 4 : 3) k_spgemm_cta(SlotTab S,
         }
         __syncthreads();
         const HashAcc acc{smem, lg, &W.cnt->overflow};
-        if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x);
+        if (!gi.probe) preload_mask(S, gi, acc, threadIdx.x, blockDim.x, &W.cnt->overflow);
         __syncthreads();
-        const uint2 own = owner_delta(S, gi);
+        const uint2 own = owner_delta(S, gi, &W.cnt->overflow);
         const uint32_t e = expand_rows<WIT, true, true, 2>(S, P, W, gi, own, wib,
                                                             blockDim.x >> 5, lane, acc, ck);
         if (lane == 0 && e) atomicAdd(&emitted_sh, e);
@@ -1336,7 +1391,11 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
     const unsigned long long n_groups = min(W.cnt->groups[bin], W.group_cap[bin]);
     uint32_t *bm = use_smem ? smem + (size_t)part * bm_stride
                             : W.bitmap_scratch + ((size_t)blockIdx.x * GPC + part) * W.bitmap_words;
+#if defined(CFLR_CHECKED)
+    BitmapAcc acc{bm, 0u, &W.cnt->overflow};
+#else
     const BitmapAcc acc{bm};
+#endif
     CandChunk ck{0, 0};
     unsigned long long bytes = 0;
     // each part claims groups one at a time from a cursor (their sizes vary
@@ -1348,6 +1407,9 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
     for (uint32_t q = 1; g < n_groups; q ^= 1) {
         const GroupInfo gi = decode_group(P, S, W.groups[bin][g]);
         const uint32_t words = (gi.n + 31) >> 5;
+#if defined(CFLR_CHECKED)
+        acc.words = words;
+#endif
         if (use_smem) {   // 16-byte stores: the stride is a multiple of four words
             uint4 *b4 = reinterpret_cast<uint4 *>(bm);
             for (uint32_t s = ptid; s < (words + 3) >> 2; s += TPG) b4[s] = make_uint4(0, 0, 0, 0);
@@ -1359,9 +1421,9 @@ __global__ void __launch_bounds__(256, 4) k_spgemm_bitmap(SlotTab S, ProdTab P, 
             next_sh[part][q] = atomicAdd(&W.cnt->claim[bin], 1ull);
         }
         psync();
-        if (!gi.probe) preload_mask(S, gi, acc, ptid, TPG);
+        if (!gi.probe) preload_mask(S, gi, acc, ptid, TPG, &W.cnt->overflow);
         psync();
-        const uint2 own = owner_delta(S, gi);
+        const uint2 own = owner_delta(S, gi, &W.cnt->overflow);
         const uint32_t e = expand_rows<WIT, false, true, 4>(S, P, W, gi, own, wib % (8 / GPC), 8 / GPC,
                                                      lane, acc, ck);
         if (lane == 0 && e) atomicAdd(&emitted_sh[part], e);
@@ -1419,6 +1481,11 @@ __global__ void __launch_bounds__(256) k_commit(SlotTab S, WorkBufs W, uint32_t 
             if (t < nc) slot = W.cand_slot[t];
             if (slot != EMPTY32) {            // not an unused reserved entry
                 key = W.cand_key[t];
+                if (!CFLR_CHECK((key >> 32) < S.n[slot] && (uint32_t)key < S.n[slot],
+                                &W.cnt->overflow))
+                    slot = EMPTY32;
+            }
+            if (slot != EMPTY32) {
                 unsigned long long *tab = S.htab[slot];
                 const unsigned long long m = S.hmask[slot];
                 unsigned long long h = pair_home(key, m);
@@ -1606,6 +1673,7 @@ __global__ void __launch_bounds__(256) k_capacity(SlotTab S, InstTab I, WorkBufs
         }
         if ((unsigned long long)dsc.y + w <= dsc.z && w <= entry_cap(dsc)) continue;
         if (dsc.y > TILE_WARP_MAX) continue;
+        if (!row_in_pool(S, slot, dsc, &W.cnt->overflow)) continue;
         uint32_t *pool = S.pool[slot];
         // fold into the table first (the count sizes the new segment) ...
         uint32_t lg = 5;
@@ -1773,10 +1841,14 @@ __global__ void __launch_bounds__(256) k_scatter(SlotTab S, WorkBufs W) {
         const uint32_t n = S.n[slot];
         const uint4 dr = dsc[i];
         const uint32_t pr = atomicAdd(&dn[i].y, 1u);
-        pool[(size_t)dr.x + tile_words(dr.z) + pr] = j;
+        if (row_in_pool(S, slot, dr, &W.cnt->overflow) &&
+            CFLR_CHECK(dr.z && pr < entry_cap(dr), &W.cnt->overflow))
+            pool[(size_t)dr.x + tile_words(dr.z) + pr] = j;
         const uint4 dc = dsc[(size_t)n + j];
         const uint32_t pc = atomicAdd(&dn[(size_t)n + j].y, 1u);
-        pool[(size_t)dc.x + tile_words(dc.z) + pc] = i;
+        if (row_in_pool(S, slot, dc, &W.cnt->overflow) &&
+            CFLR_CHECK(dc.z && pc < entry_cap(dc), &W.cnt->overflow))
+            pool[(size_t)dc.x + tile_words(dc.z) + pc] = i;
     }
 }
 
@@ -1801,6 +1873,9 @@ __global__ void __launch_bounds__(256) k_pack(SlotTab S, WorkBufs W) {
         uint4 *dp = &S.desc[slot][r];
         const uint4 dsc = *dp;
         const uint32_t w = S.dn[slot][r].x;
+        if (!row_in_pool(S, slot, dsc, &W.cnt->overflow) ||
+            !CFLR_CHECK(w <= entry_cap(dsc) && dsc.y + w <= dsc.z, &W.cnt->overflow))
+            continue;
         const uint32_t *ent = S.pool[slot] + dsc.x + tile_words(dsc.z);
         uint32_t *tl = S.pool[slot] + dsc.x;
         if (w == 1) {                  // one new pair: one tile, no table

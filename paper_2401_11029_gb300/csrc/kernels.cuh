@@ -96,6 +96,7 @@ struct SlotTab {              // per slot (device arrays, length n_slots)
     uint32_t **occ;
     uint32_t *occ_w;                // words per vertex and orientation
     uint32_t *local;                // non-terminal id of the slot in its instance
+    const unsigned long long *pool_cap;   // pool words of each instance (index: inst)
 };
 
 struct InstTab {              // per instance
@@ -162,8 +163,22 @@ constexpr unsigned OVF_TOUCHED = 8u;   // touched list overflow (cannot happen: 
 constexpr unsigned OVF_HASH = 16u;     // a pair set would pass half full (before the commit)
 constexpr unsigned OVF_FULL = 32u;     // a probe sequence passed over a whole hash table
                                        // (cannot happen while sets stay half full): fatal
+constexpr unsigned OVF_BOUNDS = 64u;   // an index failed its bounds check (checked
+                                       // builds only; the access was skipped): fatal
 constexpr unsigned OVF_PRE = OVF_GROUPS | OVF_CAND | OVF_HASH;   // iteration not committed
-constexpr unsigned OVF_STOP = OVF_PRE | OVF_FULL;   // the merge kernels do nothing
+constexpr unsigned OVF_STOP = OVF_PRE | OVF_FULL | OVF_BOUNDS;   // the merge kernels do nothing
+
+// Checked builds (CFLR_CHECKED defined; libcflr_checked.so) test the indices
+// that come from data (vertex ids read from rows, tile-list segments against
+// the pool, accumulator words against the row width, pair keys) before they
+// are used; a failed test sets OVF_BOUNDS in *err and the access is skipped,
+// so a layout bug ends the solve with CFLR_ECUDA instead of reading or
+// writing out of bounds.  In normal builds the tests compile to nothing.
+#if defined(CFLR_CHECKED)
+#define CFLR_CHECK(cond, err) ((cond) ? true : (atomicOr((err), OVF_BOUNDS), false))
+#else
+#define CFLR_CHECK(cond, err) true
+#endif
 
 struct WorkBufs {
     // touched rows {slot*2+o, idx}: touched[*parity] lists the rows whose

@@ -12,6 +12,8 @@
 #include "grammar.h"
 #include "kernels.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <array>
 #include <cstdio>
@@ -50,6 +52,16 @@ inline void ck(cudaError_t e, const char *what) {
 struct Status {
     int code;
     std::string msg;
+};
+
+// A named range on the host timeline for profilers (NVTX; costs nothing when
+// no tool is attached): the load, the renumbering, the terminal
+// initialisation, the solve and its iterations, growths and the extraction.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
 };
 
 inline uint64_t next_pow2(uint64_t x) {
@@ -656,6 +668,7 @@ struct Runner {
         S.htab = d_htab.p; S.hval = d_hval.p; S.hmask = d_hmask.p; S.cand = d_cand.p; S.delta = d_delta.p;
         S.nnz = d_nnz.p;
         S.occ = d_occ.p; S.occ_w = d_occw.p; S.local = d_local.p;
+        S.pool_cap = d_pool_cap.p;
         return S;
     }
     ProdTab prodtab() {
@@ -901,10 +914,13 @@ struct Runner {
     // Grow what the last (stopped) iteration overflowed and finish it.
     // Returns false when the iteration must be run again from its start.
     bool recover() {
+        Range range("cflr: grow buffers");
         const unsigned st_bits = h_ctl->status;
         if (st_bits & OVF_FULL)
             throw Status{CFLR_ECUDA, "a pair set filled up: a hash probe passed over the "
                                      "whole table (the pair sets were kept at their size)"};
+        if (st_bits & OVF_BOUNDS)
+            throw Status{CFLR_ECUDA, "an index failed its bounds check (checked build)"};
         if (st_bits & (OVF_GROUPS | OVF_CAND)) {       // nothing was committed
             for (int b = 0; b < N_BINS; b++) {
                 uint64_t want = h_cnt->groups[b] > group_cap[b] ? regrow_size(h_cnt->groups[b]) : 0;
@@ -953,6 +969,8 @@ struct Runner {
         if (h_ctl->status & OVF_FULL)
             throw Status{CFLR_ECUDA, "a pair set filled up: a hash probe passed over the "
                                      "whole table"};
+        if (h_ctl->status & OVF_BOUNDS)
+            throw Status{CFLR_ECUDA, "an index failed its bounds check (checked build)"};
         if (h_ctl->status) throw Status{CFLR_ECUDA, "internal: unexpected loop status"};
         return true;
     }
@@ -968,12 +986,15 @@ struct Runner {
         bool settled = graph_valid;
         for (;;) {
             if (use_graph && settled) {
+                Range range("cflr: closure loop (CUDA graph)");
                 ensure_graph();
                 ck(cudaGraphLaunch(gexec, st), "cudaGraphLaunch");
+                read_status();
             } else {
+                Range range("cflr: closure iteration");
                 launch_iteration(false, true);
+                read_status();
             }
-            read_status();
             prof.collect();
             settled = h_ctl->status == 0;
             if (h_ctl->status && !recover()) continue;
@@ -1195,6 +1216,7 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
         ck(cudaMemcpyAsync(c->e_dst, dst, m * 4, cudaMemcpyHostToDevice, st), "H2D edges");
     }
     if (!c->cfg.keep_vertex_order && n > 0) {
+        Range range("cflr: vertex renumbering");
         const std::vector<uint32_t> order = locality_order(n, m, src, dst);
         std::vector<uint32_t> perm(n);
         for (uint32_t k = 0; k < n; k++) perm[order[k]] = k;
@@ -1260,6 +1282,7 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
 // initial pairs go through the same commit and merge as the closure loop, so
 // afterwards every row's entries are its delta (M_old is empty).
 void reset_matrices(cflr_ctx *c) {
+    Range range("cflr: terminal initialisation");
     const Grammar &g = c->g;
     const uint32_t nt = (uint32_t)g.nts.size(), nterm = (uint32_t)g.terms.size();
     const uint32_t n = c->n;
@@ -1309,6 +1332,7 @@ int cuda_status(cflr_ctx *c, const CudaError &e) {
 }
 
 int solve_many(std::vector<cflr_ctx *> cx, cflr_stats *stats) {
+    Range range("cflr_solve");
     cflr_ctx *own = cx[0];
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     ck(cudaSetDevice(own->device), "cudaSetDevice");
@@ -1489,6 +1513,7 @@ int cflr_load_graph(cflr_ctx *c, uint32_t n_vertices, uint64_t n_edges, const ui
             return c->fail(CFLR_EGRAPH, "edge " + std::to_string(e) + " has a vertex id >= " +
                                             std::to_string(n_vertices));
     try {
+        Range range("cflr_load_graph");
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         c->free_graph();
         c->state = ST_GRAMMAR;
@@ -1562,6 +1587,7 @@ namespace {
 // arrays out_src/out_dst (row offsets by a device scan of the row lengths,
 // then one sort per row).
 void extract_device(cflr_ctx *c, uint32_t nt, uint32_t *out_src, uint32_t *out_dst) {
+    Range range("cflr: extraction");
     cudaStream_t st = c->stream;
     const uint32_t n = c->n;
     if (c->x_n < n || !c->x_len) {

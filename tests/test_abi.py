@@ -31,6 +31,15 @@ def test_library_builds_loads_and_exports_every_symbol():
     assert sorted(cflr.EXPORTS) == declared_entry_points()
 
 
+def test_checked_library_builds_and_exports_every_symbol():
+    """The bounds-checked build (CFLR_CHECKED) is the same library."""
+    from paper_2401_11029_gb300 import build
+    build.build()
+    lib = ctypes.CDLL(build.LIB_CHECKED)
+    for name in declared_entry_points():
+        assert hasattr(lib, name), name
+
+
 def test_binding_names_match_the_c_abi():
     import paper_2401_11029_gb300 as pkg
     from paper_2401_11029_gb300 import cflr
