@@ -907,6 +907,8 @@ __device__ __forceinline__ uint32_t expand_rows(const SlotTab &S, const ProdTab 
                                                 const WorkBufs &W, const GroupInfo &gi,
                                                 uint2 own, uint32_t warp_id, uint32_t nwarps,
                                                 int lane, const Acc &acc, CandChunk &ck) {
+    // the packed walk emits two windows' tiles per reservation
+    static_assert(!PACKED || WALK_U % 2 == 0, "the packed walk needs an even depth");
     const uint32_t dstart = own.x, d = own.y;
     const uint32_t *pool = S.pool[gi.c];
     const size_t oo = (size_t)gi.o * gi.n;
