@@ -5,8 +5,8 @@ One step is one pass of the whole hot path on the alias-analysis workload
 'a' and 150 000 'd' edges plus their reverses):
   terminal initialisation from the device-resident edges (cflr_reset),
   the semi-naive closure loop to its fixpoint (cflr_solve),
-  and the extraction of every non-terminal's sorted pairs into device
-  buffers (cflr_get_pairs_device).
+  and the extraction of every named non-terminal's sorted pairs into
+  device buffers, one after another (cflr_get_pairs_device_many).
 value = pairs of all named non-terminals / step time (CUDA events on the
 solve stream, L2 flushed between steps).  e2e repeats the step through the
 host-buffer API: grammar text and host edges in, host pair arrays out.
@@ -305,28 +305,28 @@ def device_step(ctx, n_named: int, out=None, last: dict | None = None) -> int:
     st = cflr.cflr_solve(ctx)
     if last is not None:
         last.update(st)
-    total = 0
-    for x in range(n_named):
-        cnt = cflr.cflr_get_pairs(ctx, x, count_only=True)
-        if cnt and out is not None:
-            cflr.cflr_get_pairs_device(ctx, x, out[0].data_ptr(), out[1].data_ptr(), cnt)
-        total += cnt
-    return total
+    ids = np.arange(n_named, dtype=np.uint32)
+    if out is None:
+        return int(cflr.cflr_get_pairs_many(ctx, ids, count_only=True)[-1])
+    off = cflr.cflr_get_pairs_device_many(ctx, ids, out[0].data_ptr(), out[1].data_ptr(),
+                                          min(out[0].numel(), out[1].numel()))
+    return int(off[-1])
 
 
 def device_fingerprints(ctx, names, out) -> dict:
     """Fingerprint of each named non-terminal's pairs as the device extraction
-    writes them (out: device buffers large enough for the largest)."""
+    writes them, all in one call (out: device buffers that hold them all)."""
     from paper_2401_11029_gb300 import cflr
+    ids = [cflr.cflr_symbol_id(ctx, name)[0] for name in names]
+    off = cflr.cflr_get_pairs_device_many(ctx, ids, out[0].data_ptr(), out[1].data_ptr(),
+                                          min(out[0].numel(), out[1].numel()))
+    total = int(off[-1])
+    s_all = out[0][:total].cpu().numpy().view(np.uint32)
+    d_all = out[1][:total].cpu().numpy().view(np.uint32)
     fps = {}
-    for name in names:
-        x, _ = cflr.cflr_symbol_id(ctx, name)
-        cnt = cflr.cflr_get_pairs(ctx, x, count_only=True)
-        if cnt:
-            cflr.cflr_get_pairs_device(ctx, x, out[0].data_ptr(), out[1].data_ptr(), cnt)
-        s = out[0][:cnt].cpu().numpy().view(np.uint32)
-        d = out[1][:cnt].cpu().numpy().view(np.uint32)
-        keys = gen.pair_keys(s, d)
+    for i, name in enumerate(names):
+        a, b = int(off[i]), int(off[i + 1])
+        keys = gen.pair_keys(s_all[a:b], d_all[a:b])
         if keys.size > 1 and not np.all(keys[1:] > keys[:-1]):
             fps[name] = "unsorted"
         else:
@@ -424,9 +424,8 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     last = {}
     pairs = device_step(ctx, n_named, None, last)
-    cap = max(cflr.cflr_get_pairs(ctx, x, count_only=True) for x in range(n_named))
-    out = (torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
-           torch.empty(max(cap, 1), dtype=torch.int32, device=dev))
+    out = (torch.empty(max(pairs, 1), dtype=torch.int32, device=dev),
+           torch.empty(max(pairs, 1), dtype=torch.int32, device=dev))
     for _ in range(max(0, args.warmup - 1)):
         device_step(ctx, n_named, out)
 
@@ -451,8 +450,10 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
     # end-to-end through the host-buffer API
     h_src = torch.from_numpy(g.src.astype(np.uint32).view(np.int32)).pin_memory()
     h_dst = torch.from_numpy(g.dst.astype(np.uint32).view(np.int32)).pin_memory()
-    h_out_s = torch.empty(cap, dtype=torch.int32).pin_memory()
-    h_out_d = torch.empty(cap, dtype=torch.int32).pin_memory()
+    h_out_s = torch.empty(max(pairs, 1), dtype=torch.int32).pin_memory()
+    h_out_d = torch.empty(max(pairs, 1), dtype=torch.int32).pin_memory()
+    h_out = (h_out_s.numpy().view(np.uint32), h_out_d.numpy().view(np.uint32))
+    ids = np.arange(n_named, dtype=np.uint32)
     lab_ids = label_array(ctx, g)
     h_lab = torch.from_numpy(lab_ids.view(np.int32)).pin_memory()
     lib = cflr.load_library()
@@ -474,13 +475,7 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
         t2 = time.perf_counter()
         st2 = cflr.cflr_solve(c2)
         t3 = time.perf_counter()
-        tot = 0
-        for x in range(n_named):
-            n_p = ctypes.c_uint64()
-            rc = lib.cflr_get_pairs(c2, x, h_out_s.data_ptr(), h_out_d.data_ptr(), cap,
-                                    ctypes.byref(n_p))
-            assert rc == 0
-            tot += n_p.value
+        tot = int(cflr.cflr_get_pairs_many(c2, ids, out=h_out)[2][-1])
         torch.cuda.synchronize(dev)
         t4 = time.perf_counter()
         dt = t4 - t0
@@ -584,9 +579,8 @@ def run_extra(name, args) -> dict:
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     last = {}
     pairs = device_step(ctx, n_named, None, last)
-    cap = max(cflr.cflr_get_pairs(ctx, x, count_only=True) for x in range(n_named))
-    out = (torch.empty(max(cap, 1), dtype=torch.int32, device=dev),
-           torch.empty(max(cap, 1), dtype=torch.int32, device=dev))
+    out = (torch.empty(max(pairs, 1), dtype=torch.int32, device=dev),
+           torch.empty(max(pairs, 1), dtype=torch.int32, device=dev))
     for _ in range(max(0, args.warmup - 1)):
         device_step(ctx, n_named, out)
     clocks = ClockSampler(0)

@@ -210,6 +210,29 @@ int cflr_get_pairs(const cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint3
 int cflr_get_pairs_device(const cflr_ctx *c, uint32_t nonterminal, uint32_t *d_src,
                           uint32_t *d_dst, uint64_t capacity, uint64_t *n_pairs);
 
+/* The pairs of several non-terminals in one call (the result of Algorithm 1
+ * for each of them, as cflr_get_pairs gives it).  nonterminals[0..count)
+ * (host array; an id may repeat) are written one after another into the host
+ * arrays src/dst, each non-terminal's pairs sorted by (src, dst).
+ * offsets (host array of count + 1 entries, required) receives where the
+ * pairs of nonterminals[i] start, and offsets[count] the total.  With
+ * src == dst == NULL only offsets are filled.  If capacity < total, nothing is
+ * copied, offsets are filled and CFLR_EINVAL is returned.  All extractions
+ * are queued at once and the copies to the host overlap them, so the call
+ * synchronises with the device once, not once per non-terminal.
+ * Errors: CFLR_ESTATE (no graph), CFLR_EINVAL (NULL offsets, a bad id,
+ * capacity), CFLR_ENOMEM, CFLR_ECUDA. */
+int cflr_get_pairs_many(const cflr_ctx *c, uint32_t count, const uint32_t *nonterminals,
+                        uint32_t *src, uint32_t *dst, uint64_t capacity, uint64_t *offsets);
+
+/* As cflr_get_pairs_many, but d_src/d_dst are device pointers (on this
+ * context's device) owned by the caller; offsets stays a host array.  The
+ * call returns after the last pair has been written on the context's
+ * stream. */
+int cflr_get_pairs_device_many(const cflr_ctx *c, uint32_t count, const uint32_t *nonterminals,
+                               uint32_t *d_src, uint32_t *d_dst, uint64_t capacity,
+                               uint64_t *offsets);
+
 /* Kinds of a derivation step (cflr_get_witness). */
 enum {
     CFLR_WIT_BINARY = 0,  /* nonterminal -> A B: (src, mid) in A, (mid, dst) in B    */

@@ -38,7 +38,8 @@ CFLR_FORM_GRAPH = 2
 # Every symbol include/cflr.h declares (checked by the CPU tests).
 EXPORTS = ["cflr_default_config", "cflr_create", "cflr_load_grammar", "cflr_symbol_id",
            "cflr_grammar_sizes", "cflr_load_graph", "cflr_solve", "cflr_get_pairs",
-           "cflr_get_pairs_device", "cflr_get_pairs_device_noalloc", "cflr_reset",
+           "cflr_get_pairs_device", "cflr_get_pairs_device_noalloc", "cflr_get_pairs_many",
+           "cflr_get_pairs_device_many", "cflr_reset",
            "cflr_solve_batch", "cflr_kernel_stats", "cflr_get_tuning", "cflr_set_tuning",
            "cflr_autotune", "cflr_get_witness", "cflr_last_error", "cflr_destroy"]
 
@@ -126,6 +127,10 @@ def load_library(path: str = LIB_PATH):
     lib.cflr_get_pairs_device.restype = i32
     lib.cflr_get_pairs_device_noalloc.argtypes = [vp, u32, vp, vp, u64, ctypes.POINTER(u64)]
     lib.cflr_get_pairs_device_noalloc.restype = i32
+    lib.cflr_get_pairs_many.argtypes = [vp, u32, vp, vp, vp, u64, vp]
+    lib.cflr_get_pairs_many.restype = i32
+    lib.cflr_get_pairs_device_many.argtypes = [vp, u32, vp, vp, vp, u64, vp]
+    lib.cflr_get_pairs_device_many.restype = i32
     lib.cflr_get_witness.argtypes = [vp, u32, u32, u32, ctypes.POINTER(i32), u32p, u32p, u32p]
     lib.cflr_get_witness.restype = i32
     lib.cflr_reset.argtypes = [vp]
@@ -251,6 +256,50 @@ def cflr_get_pairs_device(ctx, nonterminal: int, d_src: int, d_dst: int, capacit
                                                      ctypes.c_void_p(d_dst), int(capacity),
                                                      ctypes.byref(n)))
     return int(n.value)
+
+
+def cflr_get_pairs_many(ctx, nonterminals, count_only: bool = False, out=None):
+    """Pairs of several non-terminals in one call: (src, dst, offsets), the
+    pairs of nonterminals[i] being src[offsets[i]:offsets[i + 1]] (and dst
+    alike), each sorted by (src, dst).  With count_only, only the offsets.
+    `out` may give (src, dst) host arrays (uint32, C-contiguous) to write
+    into, e.g. views of pinned memory; they must hold the total."""
+    lib = load_library()
+    ids = np.ascontiguousarray(nonterminals, dtype=np.uint32)
+    off = np.empty(ids.size + 1, dtype=np.uint64)
+    _check(ctx, lib.cflr_get_pairs_many(ctx, ids.size, ids.ctypes.data, None, None, 0,
+                                        off.ctypes.data))
+    if count_only:
+        return off
+    total = int(off[-1])
+    if out is None:
+        src = np.empty(total, dtype=np.uint32)
+        dst = np.empty(total, dtype=np.uint32)
+    else:
+        src, dst = out
+        if src.dtype != np.uint32 or dst.dtype != np.uint32 or not (
+                src.flags.c_contiguous and dst.flags.c_contiguous):
+            raise ValueError("out arrays must be C-contiguous uint32")
+        if min(src.size, dst.size) < total:
+            raise ValueError(f"out arrays hold {min(src.size, dst.size)} pairs, need {total}")
+    if total:
+        _check(ctx, lib.cflr_get_pairs_many(ctx, ids.size, ids.ctypes.data, src.ctypes.data,
+                                            dst.ctypes.data, min(src.size, dst.size),
+                                            off.ctypes.data))
+    return src[:total], dst[:total], off
+
+
+def cflr_get_pairs_device_many(ctx, nonterminals, d_src: int, d_dst: int,
+                               capacity: int) -> np.ndarray:
+    """Write the pairs of several non-terminals one after another to
+    caller-owned device buffers (raw pointers); returns the offsets (uint64,
+    one more than the non-terminals)."""
+    ids = np.ascontiguousarray(nonterminals, dtype=np.uint32)
+    off = np.empty(ids.size + 1, dtype=np.uint64)
+    _check(ctx, load_library().cflr_get_pairs_device_many(
+        ctx, ids.size, ids.ctypes.data, ctypes.c_void_p(d_src), ctypes.c_void_p(d_dst),
+        int(capacity), off.ctypes.data))
+    return off
 
 
 def cflr_get_witness(ctx, nonterminal: int, src: int, dst: int):
@@ -381,6 +430,14 @@ class Solver:
         """Sorted uint64 keys src << 32 | dst of one non-terminal."""
         s, d = cflr_get_pairs(self.ctx, self.nt_id(name))
         return (s.astype(np.uint64) << np.uint64(32)) | d.astype(np.uint64)
+
+    def pairs_many(self, names) -> dict:
+        """Sorted uint64 keys of several non-terminals, read out in one call
+        (cflr_get_pairs_many): name -> keys."""
+        names = list(names)
+        s, d, off = cflr_get_pairs_many(self.ctx, [self.nt_id(x) for x in names])
+        keys = (s.astype(np.uint64) << np.uint64(32)) | d.astype(np.uint64)
+        return {x: keys[int(off[i]):int(off[i + 1])] for i, x in enumerate(names)}
 
     def count(self, name: str) -> int:
         return cflr_get_pairs(self.ctx, self.nt_id(name), count_only=True)

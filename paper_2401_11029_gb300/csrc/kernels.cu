@@ -461,10 +461,13 @@ __device__ __forceinline__ Work warp_sum(Work w) {
 
 // prod_only >= 0 restricts the work list to one production (the plain form).
 // Mode 0: a warp per touched row; a row whose delta has more than SYM_BIG_D
-// entries is listed for mode 1 (while the list has room) instead.  Mode 1: a
-// CTA per listed row, its threads sharing the entries (a long delta row on
-// one warp would hold the launch up long after the other warps finish).
-constexpr uint32_t SYM_BIG_D = 1024;
+// entries, or more than SYM_MIN_D entries and more than SYM_BIG_W descriptor
+// reads (entries times the members of its uses, a use of one production
+// counting as one), is listed for mode 1 (while the list has room) instead.
+// Mode 1: a CTA per listed row, its threads sharing the entries (a long
+// delta row on one warp would hold the launch up long after the other warps
+// finish).
+constexpr uint32_t SYM_BIG_D = 1024, SYM_MIN_D = 64, SYM_BIG_W = 32768;
 
 __global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkBufs W,
                                                      int prod_only, Tuning T, int mode) {
@@ -740,7 +743,16 @@ __global__ void __launch_bounds__(256, 4) k_symbolic(SlotTab S, ProdTab P, WorkB
         const uint32_t dstart = dsc.x + tile_words(dsc.z);
         const uint32_t *pool = S.pool[slot];
         const uint32_t u0 = P.use_off[xo], u1 = P.use_off[xo + 1];
-        if (d > SYM_BIG_D && u1 > u0) {
+        bool big = d > SYM_BIG_D;
+        if (!big && d > SYM_MIN_D) {
+            uint32_t w = 0;
+            for (uint32_t u = u0 + lane; u < u1; u += 32) {
+                const uint32_t code = P.use_code[u];
+                w += (code & 3) == PART_F ? P.fam[code >> 2].y : 1u;
+            }
+            big = (unsigned long long)__reduce_add_sync(FULL_MASK, w) * d > SYM_BIG_W;
+        }
+        if (big && u1 > u0) {
             // listed for the CTA pass when there is room, else done here
             unsigned long long pos = 0;
             if (lane == 0) pos = atomicAdd(&W.cnt->big_n, 1ull);
@@ -2174,6 +2186,80 @@ __global__ void k_permute_ids(uint32_t *a, unsigned long long m, const uint32_t 
 constexpr int EXTRACT_WARP_MAX = 1024;
 constexpr uint32_t EXTRACT_BATCH = 4;   // rows a warp takes per claim
 
+// Write one row of len <= EXTRACT_WARP_MAX pairs (warp-collective): its
+// nt tiles tl decoded into the warp's shared buffer s, the columns turned
+// into caller ids, sorted, and written as (src, column) pairs from o on.
+__device__ __forceinline__ void extract_row_warp(const uint32_t *tl, uint32_t nt, uint32_t len,
+                                                 uint32_t src, const uint32_t *iperm,
+                                                 unsigned long long o, uint32_t *out_src,
+                                                 uint32_t *out_dst, uint32_t *s, int lane) {
+    // each lane decodes one tile per round at its scan position
+    uint32_t base = 0;
+    for (uint32_t qb = 0; qb < nt; qb += 32) {
+        const uint32_t q = qb + lane;
+        const uint32_t w = q < nt ? tl[2 * q] : 0, b = q < nt ? tl[2 * q + 1] : 0;
+        const uint32_t c = __popc(b);
+        const uint32_t incl = warp_incl_scan(c, lane);
+        uint32_t pos = base + incl - c;
+        for (uint32_t rb = b; rb; rb &= rb - 1) s[pos++] = w * 32 + (__ffs(rb) - 1);
+        base += __shfl_sync(FULL_MASK, incl, 31);
+    }
+    __syncwarp();
+    // caller ids: one gather per entry, the whole warp's loads in
+    // flight together (per tile they would wait one after another)
+    if (iperm) {
+#pragma unroll 4
+        for (uint32_t t = lane; t < len; t += 32) s[t] = iperm[s[t]];
+    }
+    __syncwarp();
+    if (len <= 32) {
+        // bitonic network over the lanes: in each block of k lanes
+        // (ascending when lane & k is clear) the lower lane of every
+        // pair j apart keeps the minimum
+        uint32_t v = (uint32_t)lane < len ? s[lane] : EMPTY32;
+#pragma unroll
+        for (uint32_t k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                const uint32_t u = __shfl_xor_sync(FULL_MASK, v, j);
+                const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+                v = (lower == up) ? min(v, u) : max(v, u);
+            }
+        }
+        if ((uint32_t)lane < len) {
+            out_src[o + lane] = src;
+            out_dst[o + lane] = v;
+        }
+        __syncwarp();
+        return;
+    }
+    uint32_t P = 64;
+    while (P < len) P <<= 1;
+    for (uint32_t t = len + lane; t < P; t += 32) s[t] = EMPTY32;
+    __syncwarp();
+    // bitonic sort of P entries: every lane takes whole pairs (t, t + jj),
+    // t the q-th index with bit jj clear
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+            for (uint32_t q = lane; q < P / 2; q += 32) {
+                const uint32_t t = ((q & ~(jj - 1)) << 1) | (q & (jj - 1));
+                const uint32_t a = s[t], b = s[t | jj];
+                const bool up = (t & k) == 0;
+                if ((a > b) == up) {
+                    s[t] = b;
+                    s[t | jj] = a;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    for (uint32_t t = lane; t < len; t += 32) {
+        out_src[o + t] = src;
+        out_dst[o + t] = s[t];
+    }
+    __syncwarp();
+}
+
 // One warp per row: rows up to 32 entries are sorted in registers (one entry
 // per lane), longer ones up to 1024 entries by a bitonic sort in shared
 // memory; longer rows are listed for k_extract_big.  Warps claim rows
@@ -2207,78 +2293,70 @@ __global__ void __launch_bounds__(256) k_extract_small(const uint4 *desc, const 
                 if (lane == 0) big_rows[atomicAdd(&cursor[0], 1u)] = i;
                 continue;
             }
-            // each lane decodes one tile per round at its scan position
-            uint32_t base = 0;
-            for (uint32_t qb = 0; qb < nt; qb += 32) {
-                const uint32_t q = qb + lane;
-                const uint32_t w = q < nt ? tl[2 * q] : 0, b = q < nt ? tl[2 * q + 1] : 0;
-                const uint32_t c = __popc(b);
-                const uint32_t incl = warp_incl_scan(c, lane);
-                uint32_t pos = base + incl - c;
-                for (uint32_t rb = b; rb; rb &= rb - 1) s[pos++] = w * 32 + (__ffs(rb) - 1);
-                base += __shfl_sync(FULL_MASK, incl, 31);
-            }
-            __syncwarp();
-            // caller ids: one gather per entry, the whole warp's loads in
-            // flight together (per tile they would wait one after another)
-            if (iperm) {
-#pragma unroll 4
-                for (uint32_t t = lane; t < len; t += 32) s[t] = iperm[s[t]];
-            }
-            __syncwarp();
-            const unsigned long long o = row_out[i];
-            if (len <= 32) {
-                // bitonic network over the lanes: in each block of k lanes
-                // (ascending when lane & k is clear) the lower lane of every
-                // pair j apart keeps the minimum
-                uint32_t v = (uint32_t)lane < len ? s[lane] : EMPTY32;
-#pragma unroll
-                for (uint32_t k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-                    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                        const uint32_t u = __shfl_xor_sync(FULL_MASK, v, j);
-                        const bool up = (lane & k) == 0, lower = (lane & j) == 0;
-                        v = (lower == up) ? min(v, u) : max(v, u);
-                    }
-                }
-                if ((uint32_t)lane < len) {
-                    out_src[o + lane] = i;
-                    out_dst[o + lane] = v;
-                }
-                __syncwarp();
-                continue;
-            }
-            uint32_t P = 64;
-            while (P < len) P <<= 1;
-            for (uint32_t t = len + lane; t < P; t += 32) s[t] = EMPTY32;
-            __syncwarp();
-            // bitonic sort of P entries: every lane takes whole pairs (t, t + jj),
-            // t the q-th index with bit jj clear
-            for (uint32_t k = 2; k <= P; k <<= 1) {
-                for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
-                    for (uint32_t q = lane; q < P / 2; q += 32) {
-                        const uint32_t t = ((q & ~(jj - 1)) << 1) | (q & (jj - 1));
-                        const uint32_t a = s[t], b = s[t | jj];
-                        const bool up = (t & k) == 0;
-                        if ((a > b) == up) {
-                            s[t] = b;
-                            s[t | jj] = a;
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
-            for (uint32_t t = lane; t < len; t += 32) {
-                out_src[o + t] = i;
-                out_dst[o + t] = s[t];
-            }
-            __syncwarp();
+            extract_row_warp(tl, nt, len, i, iperm, row_out[i], out_src, out_dst, s, lane);
         }
     }
 }
 
-// One CTA per long row: mark the row's columns in an n-bit bitmap, then
-// write the set bits in increasing order.
+// One long row by the whole CTA (CTA-collective): its columns marked in an
+// n-bit bitmap bm (caller ids), then the set bits written in increasing
+// order as (src, column) pairs from o on.  scan: 256 words of shared memory.
+__device__ __forceinline__ void extract_row_cta(const uint32_t *tl, uint32_t ntiles, uint32_t n,
+                                                uint32_t src, const uint32_t *iperm,
+                                                unsigned long long o, uint32_t *out_src,
+                                                uint32_t *out_dst, uint32_t *bm,
+                                                uint32_t *scan) {
+    const uint32_t words = (n + 31) >> 5;
+    const uint32_t per = (words + blockDim.x - 1) / blockDim.x;
+    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < ntiles; q += blockDim.x) {
+        const uint32_t w = tl[2 * q];
+        // four bits of the tile at a time, their gathers in flight together
+        for (uint32_t rb = tl[2 * q + 1]; rb;) {
+            uint32_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                v[u] = rb ? w * 32 + (__ffs(rb) - 1) : EMPTY32;
+                rb &= rb - 1;
+            }
+            if (iperm) {
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (v[u] != EMPTY32) v[u] = iperm[v[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (v[u] != EMPTY32) atomicOr(&bm[v[u] >> 5], 1u << (v[u] & 31));
+        }
+    }
+    __syncthreads();
+    const uint32_t w0 = threadIdx.x * per, w1 = min(words, w0 + per);
+    uint32_t cnt = 0;
+    for (uint32_t w = w0; w < w1; w++) cnt += __popc(bm[w]);
+    scan[threadIdx.x] = cnt;
+    __syncthreads();
+    for (uint32_t off = 1; off < blockDim.x; off <<= 1) {
+        const uint32_t v = threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
+        __syncthreads();
+        scan[threadIdx.x] += v;
+        __syncthreads();
+    }
+    o += scan[threadIdx.x] - cnt;
+    for (uint32_t w = w0; w < w1; w++) {
+        uint32_t bits = bm[w];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            out_src[o] = src;
+            out_dst[o] = w * 32 + b;
+            o++;
+        }
+    }
+    __syncthreads();
+}
+
+// One CTA per long row listed by k_extract_small.
 __global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const uint32_t *pool,
                                                      uint32_t n, const uint32_t *perm,
                                                      const uint32_t *iperm,
@@ -2291,68 +2369,140 @@ __global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const ui
     __shared__ uint32_t scan[256];
     const uint32_t words = (n + 31) >> 5;
     uint32_t *bm = use_smem ? smem : gbitmap + (size_t)blockIdx.x * words;
-    const uint32_t per = (words + blockDim.x - 1) / blockDim.x;
     const uint32_t nb = *big_count;
     for (uint32_t r = blockIdx.x; r < nb; r += gridDim.x) {
         const uint32_t i = big_rows[r];
         const uint4 d = desc[stored_row(perm, i)];
-        const uint32_t *tl = pool + d.x;
-        for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0;
-        __syncthreads();
-        for (uint32_t q = threadIdx.x; q < d.y; q += blockDim.x) {
-            const uint32_t w = tl[2 * q];
-            // four bits of the tile at a time, their gathers in flight together
-            for (uint32_t rb = tl[2 * q + 1]; rb;) {
-                uint32_t v[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    v[u] = rb ? w * 32 + (__ffs(rb) - 1) : EMPTY32;
-                    rb &= rb - 1;
-                }
-                if (iperm) {
-#pragma unroll
-                    for (int u = 0; u < 4; u++)
-                        if (v[u] != EMPTY32) v[u] = iperm[v[u]];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (v[u] != EMPTY32) atomicOr(&bm[v[u] >> 5], 1u << (v[u] & 31));
-            }
-        }
-        __syncthreads();
-        const uint32_t w0 = threadIdx.x * per, w1 = min(words, w0 + per);
-        uint32_t cnt = 0;
-        for (uint32_t w = w0; w < w1; w++) cnt += __popc(bm[w]);
-        scan[threadIdx.x] = cnt;
-        __syncthreads();
-        for (uint32_t off = 1; off < blockDim.x; off <<= 1) {
-            const uint32_t v = threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
-            __syncthreads();
-            scan[threadIdx.x] += v;
-            __syncthreads();
-        }
-        unsigned long long o = row_out[i] + scan[threadIdx.x] - cnt;
-        for (uint32_t w = w0; w < w1; w++) {
-            uint32_t bits = bm[w];
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                out_src[o] = i;
-                out_dst[o] = w * 32 + b;
-                o++;
-            }
-        }
-        __syncthreads();
+        extract_row_cta(pool + d.x, d.y, n, i, iperm, row_out[i], out_src, out_dst, bm, scan);
     }
 }
 
 // ---------------------------------------------------------------------------
-// exclusive scan of uint32 counts into uint64 offsets (three phases)
+// Extraction of a list of non-terminals, one after another (the pairs of
+// several non-terminals in one call).  The rows of every listed
+// non-terminal, in caller order, are cut into units of rows_per_unit rows:
+// unit u = k * units_per_nt + c holds rows [c * rows_per_unit, ...) of
+// non-terminal nts[k].  The units follow the list order, so the exclusive
+// scan of their pair counts is each unit's first output position; within a
+// unit the rows follow one another.  Rows of more than EXTRACT_WARP_MAX
+// pairs are listed (row, k, output position) for a CTA each.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ const uint4 *list_desc(const ExtractList &L, uint32_t k) {
+    return L.desc + (size_t)L.nts[k] * 2 * L.n;   // row form of nts[k]
+}
+
+// Pairs of every unit (a warp per unit, its lanes over the rows).
+__global__ void __launch_bounds__(256) k_unit_lengths(ExtractList L,
+                                                      unsigned long long *unit_len) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long units = (unsigned long long)L.count * L.units_per_nt;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long u = (unsigned long long)blockIdx.x * (blockDim.x >> 5) +
+                                (threadIdx.x >> 5);
+         u < units; u += warps) {
+        const uint32_t k = (uint32_t)(u / L.units_per_nt), c = (uint32_t)(u % L.units_per_nt);
+        const uint4 *dk = list_desc(L, k);
+        const uint32_t r0 = c * L.rows_per_unit;
+        const uint32_t r1 = (uint32_t)min((unsigned long long)L.n,
+                                          (unsigned long long)r0 + L.rows_per_unit);
+        unsigned long long len = 0;
+        for (uint32_t i = r0 + lane; i < r1; i += 32) {
+            const uint4 d = dk[stored_row(L.perm, i)];
+            const uint32_t *tl = L.pool + d.x;
+            uint32_t c32 = 0;
+            for (uint32_t q = 0; q < d.y; q++) c32 += __popc(tl[2 * q + 1]);
+            len += c32;
+        }
+        len = warp_sum64(len);
+        if (lane == 0) unit_len[u] = len;
+    }
+}
+
+// The rows of every unit (a warp per unit, units claimed from cursor[1]):
+// the lanes read 32 rows' descriptors at once and the warp takes the
+// non-empty ones in order.  cursor[0] counts the listed long rows.
+__global__ void __launch_bounds__(256) k_extract_units(ExtractList L,
+                                                       const unsigned long long *unit_off,
+                                                       uint32_t *out_src, uint32_t *out_dst,
+                                                       uint4 *big, unsigned long long big_cap,
+                                                       unsigned long long *cursor,
+                                                       unsigned *err) {
+    __shared__ uint32_t sbuf[8][EXTRACT_WARP_MAX];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *s = sbuf[wib];
+    const unsigned long long units = (unsigned long long)L.count * L.units_per_nt;
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(&cursor[1], 1ull);
+        u = __shfl_sync(FULL_MASK, u, 0);
+        if (u >= units) break;
+        const uint32_t k = (uint32_t)(u / L.units_per_nt), c = (uint32_t)(u % L.units_per_nt);
+        const uint4 *dk = list_desc(L, k);
+        const uint32_t r0 = c * L.rows_per_unit;
+        const uint32_t r1 = (uint32_t)min((unsigned long long)L.n,
+                                          (unsigned long long)r0 + L.rows_per_unit);
+        unsigned long long o = unit_off[u];
+        for (uint32_t rb = r0; rb < r1; rb += 32) {
+            const uint32_t i = rb + lane;
+            const uint4 d = i < r1 ? dk[stored_row(L.perm, i)] : make_uint4(0, 0, 0, 0);
+            for (unsigned m = __ballot_sync(FULL_MASK, d.y != 0); m; m &= m - 1) {
+                const int l = __ffs(m) - 1;
+                const uint32_t nt = __shfl_sync(FULL_MASK, d.y, l);
+                const uint32_t *tl = L.pool + __shfl_sync(FULL_MASK, d.x, l);
+                uint32_t len = 0;
+                for (uint32_t q = lane; q < nt; q += 32) len += __popc(tl[2 * q + 1]);
+                len = __reduce_add_sync(FULL_MASK, len);
+                if (len == 0) continue;
+                if (o + len > L.limit) {
+                    // more pairs than the pair sets count: nothing is written
+                    // past the caller's arrays
+                    if (lane == 0) atomicOr(err, 2u);
+                } else if (len > EXTRACT_WARP_MAX) {
+                    if (lane == 0) {
+                        const unsigned long long pos = atomicAdd(&cursor[0], 1ull);
+                        if (pos < big_cap)
+                            big[pos] = make_uint4(rb + l, k, (uint32_t)o, (uint32_t)(o >> 32));
+                        else
+                            atomicOr(err, 1u);
+                    }
+                } else {
+                    extract_row_warp(tl, nt, len, rb + l, L.iperm, o, out_src, out_dst, s, lane);
+                }
+                o += len;
+            }
+        }
+    }
+}
+
+// One CTA per long row listed by k_extract_units.
+__global__ void __launch_bounds__(256) k_extract_units_big(ExtractList L, uint32_t *out_src,
+                                                           uint32_t *out_dst, const uint4 *big,
+                                                           unsigned long long big_cap,
+                                                           const unsigned long long *cursor,
+                                                           uint32_t *gbitmap, int use_smem) {
+    extern __shared__ uint32_t smem[];
+    __shared__ uint32_t scan[256];
+    const uint32_t words = (L.n + 31) >> 5;
+    uint32_t *bm = use_smem ? smem : gbitmap + (size_t)blockIdx.x * words;
+    const unsigned long long nb = min(cursor[0], big_cap);
+    for (unsigned long long r = blockIdx.x; r < nb; r += gridDim.x) {
+        const uint4 e = big[r];
+        const uint4 d = list_desc(L, e.y)[stored_row(L.perm, e.x)];
+        extract_row_cta(L.pool + d.x, d.y, L.n, e.x, L.iperm,
+                        ((unsigned long long)e.w << 32) | e.z, out_src, out_dst, bm, scan);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 or uint64 counts into uint64 offsets (three
+// phases; in place when in == out)
 // ---------------------------------------------------------------------------
 
 constexpr uint32_t SCAN_TILE = 1024;   // 256 threads x 4 elements
 
-__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *in, uint32_t n,
+template <typename T>
+__global__ void __launch_bounds__(256) k_scan_reduce(const T *in, unsigned long long n,
                                                      unsigned long long *bsum) {
     __shared__ unsigned long long sh[16];
     const unsigned long long base = (unsigned long long)blockIdx.x * SCAN_TILE + threadIdx.x * 4;
@@ -2380,12 +2530,13 @@ __global__ void __launch_bounds__(256) k_scan_top(unsigned long long *bsum, uint
     if (threadIdx.x == 0 && grand) *grand = carry;
 }
 
-__global__ void __launch_bounds__(256) k_scan_down(const uint32_t *in, uint32_t n,
+template <typename T>
+__global__ void __launch_bounds__(256) k_scan_down(const T *in, unsigned long long n,
                                                    const unsigned long long *bsum,
                                                    unsigned long long *out) {
     __shared__ unsigned long long sh[16];
     const unsigned long long base = (unsigned long long)blockIdx.x * SCAN_TILE + threadIdx.x * 4;
-    uint32_t x[4];
+    T x[4];
     unsigned long long v = 0;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
@@ -2405,9 +2556,19 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t n, unsigned long long *o
                            unsigned long long *bsum, unsigned long long *grand, cudaStream_t st) {
     if (!n) return;
     const uint32_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    k_scan_reduce<<<nb, 256, 0, st>>>(in, n, bsum);
+    k_scan_reduce<uint32_t><<<nb, 256, 0, st>>>(in, n, bsum);
     k_scan_top<<<1, 256, 0, st>>>(bsum, nb, grand);
-    k_scan_down<<<nb, 256, 0, st>>>(in, n, bsum, out);
+    k_scan_down<uint32_t><<<nb, 256, 0, st>>>(in, n, bsum, out);
+}
+
+void launch_exclusive_scan64(unsigned long long *in_out, unsigned long long n,
+                             unsigned long long *bsum, unsigned long long *grand,
+                             cudaStream_t st) {
+    if (!n) return;
+    const unsigned long long nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_reduce<unsigned long long><<<(unsigned)nb, 256, 0, st>>>(in_out, n, bsum);
+    k_scan_top<<<1, 256, 0, st>>>(bsum, (uint32_t)nb, grand);
+    k_scan_down<unsigned long long><<<(unsigned)nb, 256, 0, st>>>(in_out, n, bsum, in_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -2460,6 +2621,8 @@ static void set_smem_attrs() {
     set_bin_smem_attrs<false>();
     set_bin_smem_attrs<true>();
     cudaFuncSetAttribute(k_extract_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SMEM_BITMAP_MAX);
+    cudaFuncSetAttribute(k_extract_units_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)SMEM_BITMAP_MAX);
     cudaFuncSetAttribute(k_capacity_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)SMEM_BITMAP_MAX);
@@ -2632,6 +2795,34 @@ void launch_row_lengths(const uint4 *desc, const uint32_t *pool, uint32_t n,
                         const uint32_t *perm, uint32_t *len, cudaStream_t st) {
     if (!n) return;
     k_row_lengths<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(desc, pool, n, perm, len);
+}
+
+uint32_t extract_rows_per_unit(uint32_t count, uint32_t n, int sms) {
+    const unsigned long long target = (unsigned long long)sms * 64 * 8;   // resident warps x 8
+    const unsigned long long rows = (unsigned long long)count * n;
+    uint32_t r = 4;
+    while (r < 4096 && (unsigned long long)r * target < rows) r <<= 1;
+    return r;
+}
+
+void launch_extract_list(const ExtractList &L, uint32_t *out_src, uint32_t *out_dst,
+                         unsigned long long *units, unsigned long long *bsum,
+                         unsigned long long *total, uint4 *big, unsigned long long big_cap,
+                         unsigned long long *cursor, uint32_t *bitmap, unsigned *err, int sms,
+                         cudaStream_t st) {
+    const unsigned long long nu = L.units();
+    if (!nu || !L.n) return;
+    set_smem_attrs();
+    k_unit_lengths<<<grid_for(nu, 8, sms, 8), 256, 0, st>>>(L, units);
+    launch_exclusive_scan64(units, nu, bsum, total, st);
+    cudaMemsetAsync(cursor, 0, 2 * sizeof(unsigned long long), st);
+    k_extract_units<<<grid_for(nu, 8, sms, 8), 256, 0, st>>>(L, units, out_src, out_dst, big,
+                                                             big_cap, cursor, err);
+    const size_t bm_bytes = (size_t)((L.n + 31) / 32) * 4;
+    const bool sm = bm_bytes <= SMEM_BITMAP_MAX;
+    k_extract_units_big<<<sms * 4, 256, sm ? bm_bytes : 0, st>>>(L, out_src, out_dst, big,
+                                                                 big_cap, cursor, bitmap,
+                                                                 sm ? 1 : 0);
 }
 
 void launch_extract(const uint4 *desc, const uint32_t *pool, uint32_t n, const uint32_t *perm,

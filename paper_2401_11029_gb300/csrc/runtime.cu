@@ -141,9 +141,12 @@ struct cflr_ctx {
     std::vector<uint64_t> init_cnt;
     Runner *runner = nullptr;           // cached work buffers of solves led by this context
     // extraction scratch
-    uint32_t *x_len = nullptr, *x_big = nullptr, *x_bm = nullptr;
-    unsigned long long *x_off = nullptr, *x_bsum = nullptr;
-    size_t x_n = 0, x_bm_n = 0;
+    // (listed non-terminal ids, unit offsets and their block sums, counters
+    // and group totals, long-row list, row bitmaps)
+    uint32_t *x_nts = nullptr, *x_bm = nullptr;
+    unsigned long long *x_unit = nullptr, *x_bsum = nullptr, *x_misc = nullptr;
+    uint4 *x_bigl = nullptr;
+    size_t x_nts_n = 0, x_bm_n = 0, x_unit_n = 0, x_bsum_n = 0, x_misc_n = 0, x_bigl_n = 0;
     uint32_t *x_src = nullptr, *x_dst = nullptr;
     uint64_t x_out_cap = 0;
     // accounting
@@ -187,16 +190,31 @@ struct cflr_ctx {
         bytes_now -= std::min(bytes_now, (uint64_t)bytes);
     }
 
-    // extraction scratch (row lengths, offsets, long-row list, bitmaps)
+    // a device array of at least `need` elements (its contents are not kept)
+    template <typename T>
+    void scratch(T *&p, size_t &cap, size_t need) {
+        need = std::max<size_t>(need, 1);
+        if (p && cap >= need) return;
+        if (p) dfree(p, cap * sizeof(T));
+        p = nullptr;
+        cap = 0;
+        p = (T *)dalloc(need * sizeof(T));
+        cap = need;
+    }
+    template <typename T>
+    void drop(T *&p, size_t &cap) {
+        if (p) dfree(p, cap * sizeof(T));
+        p = nullptr;
+        cap = 0;
+    }
+    // extraction scratch
     void free_extract_scratch() {
-        if (x_len) dfree(x_len, x_n * 4);
-        if (x_big) dfree(x_big, (x_n + 2) * 4);
-        if (x_off) dfree(x_off, x_n * 8);
-        if (x_bsum) dfree(x_bsum, (x_n / 1024 + 2) * 8);
-        if (x_bm) dfree(x_bm, x_bm_n * 4);
-        x_len = x_big = x_bm = nullptr;
-        x_off = x_bsum = nullptr;
-        x_n = x_bm_n = 0;
+        drop(x_nts, x_nts_n);
+        drop(x_bm, x_bm_n);
+        drop(x_unit, x_unit_n);
+        drop(x_bsum, x_bsum_n);
+        drop(x_misc, x_misc_n);
+        drop(x_bigl, x_bigl_n);
     }
     // device staging of cflr_get_pairs's host output
     void free_extract_out() {
@@ -742,9 +760,9 @@ struct Runner {
         keep.release();
         d_touched[pin ^ 1].alloc(own, cap);
         touched_cap = cap;
-        // a listed row has more than 1024 delta entries, and the deltas of
+        // a listed row has more than 64 delta entries, and the deltas of
         // one iteration hold at most touched_cap entries
-        d_big.ensure(own, cap / 1024 + 1024);
+        d_big.ensure(own, cap / 64 + 1024);
         graph_valid = false;
     }
     void size_groups(int b, uint64_t cap) {
@@ -1594,32 +1612,112 @@ int cflr_reset(cflr_ctx *c) {
 
 namespace {
 
-// Write the pairs of one non-terminal, sorted by (src, dst), to device
-// arrays out_src/out_dst (row offsets by a device scan of the row lengths,
-// then one sort per row).
-void extract_device(cflr_ctx *c, uint32_t nt, uint32_t *out_src, uint32_t *out_dst) {
+// A stream and events that are destroyed on every way out of a call.
+struct CopyLane {
+    cudaStream_t s = nullptr;
+    std::vector<cudaEvent_t> ev;
+    ~CopyLane() {
+        if (s) cudaStreamSynchronize(s);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (s) cudaStreamDestroy(s);
+    }
+    cudaEvent_t record(cudaStream_t on) {
+        cudaEvent_t e;
+        ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        ev.push_back(e);
+        ck(cudaEventRecord(e, on), "cudaEventRecord");
+        return e;
+    }
+};
+
+// Write the pairs of the listed non-terminals (nts[0..count), output
+// positions offsets[0..count]) one after another into the device arrays
+// ws/wd, each non-terminal's sorted by (src, dst).  The non-empty ones are
+// extracted in groups by launch_extract_list; with host arrays hs/hd, a
+// group closes at COPY_CHUNK pairs and is copied out on a second stream as
+// soon as it is written, overlapping the extraction of the next group.
+// Checks each group's pair count against the pair sets' counts.
+void extract_many(cflr_ctx *c, uint32_t count, const uint32_t *nts, const uint64_t *offsets,
+                  uint32_t *ws, uint32_t *wd, uint32_t *hs, uint32_t *hd) {
     Range range("cflr: extraction");
+    constexpr uint64_t COPY_CHUNK = 1ull << 22;
     cudaStream_t st = c->stream;
     const uint32_t n = c->n;
-    if (c->x_n < n || !c->x_len) {
-        c->free_extract_scratch();
-        c->x_n = n;
-        c->x_len = (uint32_t *)c->dalloc((size_t)n * 4);
-        c->x_big = (uint32_t *)c->dalloc(((size_t)n + 2) * 4);
-        c->x_off = (unsigned long long *)c->dalloc((size_t)n * 8);
-        c->x_bsum = (unsigned long long *)c->dalloc(((size_t)n / 1024 + 2) * 8);
-        const size_t words = ((size_t)n + 31) / 32;
-        if (words * 4 > 200 * 1024) {
-            c->x_bm_n = words * (size_t)c->sms * 4;
-            c->x_bm = (uint32_t *)c->dalloc(c->x_bm_n * 4);
+    std::vector<uint32_t> ids;
+    std::vector<size_t> g_first;          // first entry of ids of each group
+    std::vector<uint64_t> g_pos, g_pairs; // output position and pairs of each group
+    for (uint32_t i = 0; i < count; i++) {
+        const uint64_t cnt = offsets[i + 1] - offsets[i];
+        if (!cnt) continue;
+        if (ids.empty() || (hs && g_pairs.back() >= COPY_CHUNK)) {
+            g_first.push_back(ids.size());
+            g_pos.push_back(offsets[i]);
+            g_pairs.push_back(0);
+        }
+        ids.push_back(nts[i]);
+        g_pairs.back() += cnt;
+    }
+    if (ids.empty()) return;
+    const size_t G = g_first.size();
+    g_first.push_back(ids.size());
+    std::vector<uint32_t> rows(G), upn(G);
+    uint64_t max_units = 0, max_pairs = 0;
+    for (size_t g = 0; g < G; g++) {
+        const uint32_t k = (uint32_t)(g_first[g + 1] - g_first[g]);
+        rows[g] = extract_rows_per_unit(k, n, c->sms);
+        upn[g] = (uint32_t)(((uint64_t)n + rows[g] - 1) / rows[g]);
+        max_units = std::max<uint64_t>(max_units, (uint64_t)k * upn[g]);
+        max_pairs = std::max(max_pairs, g_pairs[g]);
+    }
+    c->scratch(c->x_nts, c->x_nts_n, ids.size());
+    c->scratch(c->x_unit, c->x_unit_n, max_units + 1);
+    c->scratch(c->x_bsum, c->x_bsum_n, max_units / 1024 + 2);
+    c->scratch(c->x_misc, c->x_misc_n, 3 + G);      // cursors, error flag, group totals
+    c->scratch(c->x_bigl, c->x_bigl_n, max_pairs / 1024 + 1);
+    const size_t words = ((size_t)n + 31) / 32;
+    if (words * 4 > 200 * 1024) c->scratch(c->x_bm, c->x_bm_n, words * (size_t)c->sms * 4);
+    ck(cudaMemcpyAsync(c->x_nts, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
+    ck(cudaMemsetAsync(c->x_misc + 2, 0, 8, st), "memset");
+    unsigned *err = (unsigned *)(c->x_misc + 2);
+    CopyLane lane;
+    if (hs) ck(cudaStreamCreateWithFlags(&lane.s, cudaStreamNonBlocking), "cudaStreamCreate");
+    for (size_t g = 0; g < G; g++) {
+        ExtractList L{};
+        L.desc = c->desc;
+        L.pool = c->pool;
+        L.perm = c->perm;
+        L.iperm = c->iperm;
+        L.nts = c->x_nts + g_first[g];
+        L.n = n;
+        L.count = (uint32_t)(g_first[g + 1] - g_first[g]);
+        L.rows_per_unit = rows[g];
+        L.units_per_nt = upn[g];
+        L.limit = g_pairs[g];
+        launch_extract_list(L, ws + g_pos[g], wd + g_pos[g], c->x_unit, c->x_bsum,
+                            c->x_misc + 3 + g, c->x_bigl, c->x_bigl_n, c->x_misc, c->x_bm, err,
+                            c->sms, st);
+        ck(cudaGetLastError(), "extract");
+        if (hs) {
+            ck(cudaStreamWaitEvent(lane.s, lane.record(st), 0), "cudaStreamWaitEvent");
+            ck(cudaMemcpyAsync(hs + g_pos[g], ws + g_pos[g], g_pairs[g] * 4,
+                               cudaMemcpyDeviceToHost, lane.s), "D2H pairs");
+            ck(cudaMemcpyAsync(hd + g_pos[g], wd + g_pos[g], g_pairs[g] * 4,
+                               cudaMemcpyDeviceToHost, lane.s), "D2H pairs");
         }
     }
-    const uint4 *desc = c->desc + (size_t)nt * 2 * n;
-    launch_row_lengths(desc, c->pool, n, c->perm, c->x_len, st);
-    launch_exclusive_scan(c->x_len, n, c->x_off, c->x_bsum, nullptr, st);
-    launch_extract(desc, c->pool, n, c->perm, c->iperm, c->x_off, out_src, out_dst, c->x_big,
-                   c->x_big + n, c->x_bm, c->sms, st);
-    ck(cudaGetLastError(), "extract");
+    std::vector<unsigned long long> misc(3 + G);
+    ck(cudaMemcpyAsync(misc.data(), c->x_misc, (3 + G) * 8, cudaMemcpyDeviceToHost, st), "D2H");
+    if (hs) ck(cudaStreamSynchronize(lane.s), "sync copy");
+    ck(cudaStreamSynchronize(st), "sync extract");
+    if (misc[2] & 1)
+        throw Status{CFLR_ECUDA, "internal: the long-row list of the extraction overflowed"};
+    if (misc[2] & 2)
+        throw Status{CFLR_ECUDA, "internal: a row held more pairs than the pair sets count"};
+    for (size_t g = 0; g < G; g++)
+        if (misc[3 + g] != g_pairs[g])
+            throw Status{CFLR_ECUDA, "internal: extracted " + std::to_string(misc[3 + g]) +
+                                         " pairs where the pair sets hold " +
+                                         std::to_string(g_pairs[g])};
 }
 
 int get_pairs_common(cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint32_t *dst,
@@ -1635,10 +1733,9 @@ int get_pairs_common(cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint32_t 
     if (cnt == 0) return CFLR_OK;
     try {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
-        cudaStream_t st = c->stream;
+        const uint64_t off[2] = {0, cnt};
         if (on_device) {
-            extract_device(c, nonterminal, src, dst);
-            ck(cudaStreamSynchronize(st), "sync extract");
+            extract_many(c, 1, &nonterminal, off, src, dst, nullptr, nullptr);
             return CFLR_OK;
         }
         if (c->x_out_cap < cnt) {
@@ -1647,10 +1744,45 @@ int get_pairs_common(cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint32_t 
             c->x_dst = (uint32_t *)c->dalloc(cnt * 4);
             c->x_out_cap = cnt;
         }
-        extract_device(c, nonterminal, c->x_src, c->x_dst);
-        ck(cudaMemcpyAsync(src, c->x_src, cnt * 4, cudaMemcpyDeviceToHost, st), "D2H pairs");
-        ck(cudaMemcpyAsync(dst, c->x_dst, cnt * 4, cudaMemcpyDeviceToHost, st), "D2H pairs");
-        ck(cudaStreamSynchronize(st), "sync extract");
+        extract_many(c, 1, &nonterminal, off, c->x_src, c->x_dst, src, dst);
+        return CFLR_OK;
+    } catch (const Status &s) {
+        return finish_status(c, s);
+    } catch (const CudaError &e) {
+        return cuda_status(c, e);
+    }
+}
+
+// The pairs of several non-terminals, one after another (cflr_get_pairs_many
+// and cflr_get_pairs_device_many), with one synchronisation for the call.
+int get_pairs_many_common(cflr_ctx *c, uint32_t count, const uint32_t *nts, uint32_t *src,
+                          uint32_t *dst, uint64_t capacity, uint64_t *offsets, bool on_device) {
+    if (!c || !offsets || (count && !nts)) return CFLR_EINVAL;
+    if (c->state < ST_GRAPH) return c->fail(CFLR_ESTATE, "no graph loaded");
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < count; i++) {
+        if (nts[i] >= c->g.nts.size()) return c->fail(CFLR_EINVAL, "bad non-terminal id");
+        offsets[i] = total;
+        total += c->nnz[nts[i]];
+    }
+    offsets[count] = total;
+    if (!src && !dst) return CFLR_OK;
+    if (!src || !dst) return c->fail(CFLR_EINVAL, "src and dst must both be given");
+    if (capacity < total) return c->fail(CFLR_EINVAL, "capacity smaller than the pair count");
+    if (total == 0) return CFLR_OK;
+    try {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        if (on_device) {
+            extract_many(c, count, nts, offsets, src, dst, nullptr, nullptr);
+            return CFLR_OK;
+        }
+        if (c->x_out_cap < total) {
+            c->free_extract_out();
+            c->x_src = (uint32_t *)c->dalloc(total * 4);
+            c->x_dst = (uint32_t *)c->dalloc(total * 4);
+            c->x_out_cap = total;
+        }
+        extract_many(c, count, nts, offsets, c->x_src, c->x_dst, src, dst);
         return CFLR_OK;
     } catch (const Status &s) {
         return finish_status(c, s);
@@ -1662,6 +1794,19 @@ int get_pairs_common(cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint32_t 
 }  // namespace
 
 extern "C" {
+
+int cflr_get_pairs_many(const cflr_ctx *cc, uint32_t count, const uint32_t *nonterminals,
+                        uint32_t *src, uint32_t *dst, uint64_t capacity, uint64_t *offsets) {
+    return get_pairs_many_common(const_cast<cflr_ctx *>(cc), count, nonterminals, src, dst,
+                                 capacity, offsets, false);
+}
+
+int cflr_get_pairs_device_many(const cflr_ctx *cc, uint32_t count, const uint32_t *nonterminals,
+                               uint32_t *d_src, uint32_t *d_dst, uint64_t capacity,
+                               uint64_t *offsets) {
+    return get_pairs_many_common(const_cast<cflr_ctx *>(cc), count, nonterminals, d_src, d_dst,
+                                 capacity, offsets, true);
+}
 
 int cflr_get_pairs(const cflr_ctx *cc, uint32_t nonterminal, uint32_t *src, uint32_t *dst,
                    uint64_t capacity, uint64_t *n_pairs) {

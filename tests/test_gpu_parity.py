@@ -255,7 +255,7 @@ def _check_timed_configuration(kind, n_vertices):
         # the schedule is the cached one the bench line reports
         assert open(bench.TUNING_CACHE).read().count(f"_{g.n}_{g.n_edges} ") >= 1
         n_nt, n_named, _ = cflr.cflr_grammar_sizes(ctx)
-        cap = max(int(v.split(":")[0]) for v in gold["pairs"].values())
+        cap = gold["total_pairs"]
         out = (torch.empty(cap, dtype=torch.int32, device="cuda"),
                torch.empty(cap, dtype=torch.int32, device="cuda"))
         for _ in range(2):                       # second pass runs on reused buffers
