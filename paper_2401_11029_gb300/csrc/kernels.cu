@@ -21,6 +21,7 @@
 // All work is integer; the result does not depend on thread timing.
 #include "kernels.cuh"
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -2380,32 +2381,43 @@ __global__ void __launch_bounds__(256) k_extract_big(const uint4 *desc, const ui
 // ---------------------------------------------------------------------------
 // Extraction of a list of non-terminals, one after another (the pairs of
 // several non-terminals in one call).  The rows of every listed
-// non-terminal, in caller order, are cut into units of rows_per_unit rows:
-// unit u = k * units_per_nt + c holds rows [c * rows_per_unit, ...) of
-// non-terminal nts[k].  The units follow the list order, so the exclusive
-// scan of their pair counts is each unit's first output position; within a
-// unit the rows follow one another.  Rows of more than EXTRACT_WARP_MAX
-// pairs are listed (row, k, output position) for a CTA each.
+// non-terminal, in caller order, are cut into units of rows; the units
+// follow the list order, so the exclusive scan of their pair counts is each
+// unit's first output position; within a unit the rows follow one another.
+// Rows of more than EXTRACT_WARP_MAX pairs are listed (row, k, output
+// position) for a CTA each.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ const uint4 *list_desc(const ExtractList &L, uint32_t k) {
     return L.desc + (size_t)L.nts[k] * 2 * L.n;   // row form of nts[k]
 }
 
+// The listed non-terminal k owning unit u, and the unit's rows [r0, r1).
+__device__ __forceinline__ uint32_t unit_rows(const ExtractList &L, unsigned long long u,
+                                              uint32_t &r0, uint32_t &r1) {
+    uint32_t lo = 0, hi = L.count;          // unit_first[lo] <= u < unit_first[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (L.unit_first[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    const uint32_t R = L.rows_per[lo];
+    const unsigned long long a = (u - L.unit_first[lo]) * R;
+    r0 = (uint32_t)min(a, (unsigned long long)L.n);
+    r1 = (uint32_t)min(a + R, (unsigned long long)L.n);
+    return lo;
+}
+
 // Pairs of every unit (a warp per unit, its lanes over the rows).
 __global__ void __launch_bounds__(256) k_unit_lengths(ExtractList L,
                                                       unsigned long long *unit_len) {
     const int lane = threadIdx.x & 31;
-    const unsigned long long units = (unsigned long long)L.count * L.units_per_nt;
     const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     for (unsigned long long u = (unsigned long long)blockIdx.x * (blockDim.x >> 5) +
                                 (threadIdx.x >> 5);
-         u < units; u += warps) {
-        const uint32_t k = (uint32_t)(u / L.units_per_nt), c = (uint32_t)(u % L.units_per_nt);
-        const uint4 *dk = list_desc(L, k);
-        const uint32_t r0 = c * L.rows_per_unit;
-        const uint32_t r1 = (uint32_t)min((unsigned long long)L.n,
-                                          (unsigned long long)r0 + L.rows_per_unit);
+         u < L.units; u += warps) {
+        uint32_t r0, r1;
+        const uint4 *dk = list_desc(L, unit_rows(L, u, r0, r1));
         unsigned long long len = 0;
         for (uint32_t i = r0 + lane; i < r1; i += 32) {
             const uint4 d = dk[stored_row(L.perm, i)];
@@ -2431,17 +2443,14 @@ __global__ void __launch_bounds__(256) k_extract_units(ExtractList L,
     __shared__ uint32_t sbuf[8][EXTRACT_WARP_MAX];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *s = sbuf[wib];
-    const unsigned long long units = (unsigned long long)L.count * L.units_per_nt;
     for (;;) {
         unsigned long long u = 0;
         if (lane == 0) u = atomicAdd(&cursor[1], 1ull);
         u = __shfl_sync(FULL_MASK, u, 0);
-        if (u >= units) break;
-        const uint32_t k = (uint32_t)(u / L.units_per_nt), c = (uint32_t)(u % L.units_per_nt);
+        if (u >= L.units) break;
+        uint32_t r0, r1;
+        const uint32_t k = unit_rows(L, u, r0, r1);
         const uint4 *dk = list_desc(L, k);
-        const uint32_t r0 = c * L.rows_per_unit;
-        const uint32_t r1 = (uint32_t)min((unsigned long long)L.n,
-                                          (unsigned long long)r0 + L.rows_per_unit);
         unsigned long long o = unit_off[u];
         for (uint32_t rb = r0; rb < r1; rb += 32) {
             const uint32_t i = rb + lane;
@@ -2797,12 +2806,21 @@ void launch_row_lengths(const uint4 *desc, const uint32_t *pool, uint32_t n,
     k_row_lengths<<<grid_for(n, 256, 152, 8), 256, 0, st>>>(desc, pool, n, perm, len);
 }
 
-uint32_t extract_rows_per_unit(uint32_t count, uint32_t n, int sms) {
+void extract_plan(uint32_t count, uint32_t n, const uint64_t *pairs, int sms,
+                  uint32_t *rows_per, unsigned long long *unit_first) {
     const unsigned long long target = (unsigned long long)sms * 64 * 8;   // resident warps x 8
-    const unsigned long long rows = (unsigned long long)count * n;
-    uint32_t r = 4;
-    while (r < 4096 && (unsigned long long)r * target < rows) r <<= 1;
-    return r;
+    unsigned long long total = 0;
+    for (uint32_t k = 0; k < count; k++) total += pairs[k];
+    const unsigned long long share = std::max<unsigned long long>(256, total / target);
+    unit_first[0] = 0;
+    for (uint32_t k = 0; k < count; k++) {
+        unsigned long long u = std::max<unsigned long long>(((unsigned long long)n + 4095) / 4096,
+                                                            (pairs[k] + share - 1) / share);
+        u = std::max<unsigned long long>(1, std::min<unsigned long long>(u, n));
+        const uint32_t R = (uint32_t)(((unsigned long long)n + u - 1) / u);
+        rows_per[k] = std::max<uint32_t>(R, 1);
+        unit_first[k + 1] = unit_first[k] + ((unsigned long long)n + rows_per[k] - 1) / rows_per[k];
+    }
 }
 
 void launch_extract_list(const ExtractList &L, uint32_t *out_src, uint32_t *out_dst,
@@ -2810,7 +2828,7 @@ void launch_extract_list(const ExtractList &L, uint32_t *out_src, uint32_t *out_
                          unsigned long long *total, uint4 *big, unsigned long long big_cap,
                          unsigned long long *cursor, uint32_t *bitmap, unsigned *err, int sms,
                          cudaStream_t st) {
-    const unsigned long long nu = L.units();
+    const unsigned long long nu = L.units;
     if (!nu || !L.n) return;
     set_smem_attrs();
     k_unit_lengths<<<grid_for(nu, 8, sms, 8), 256, 0, st>>>(L, units);

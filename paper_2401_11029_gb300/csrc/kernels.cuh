@@ -282,27 +282,32 @@ void launch_extract(const uint4 *desc, const uint32_t *pool, uint32_t n, const u
                     uint32_t *bitmap, int sms, cudaStream_t st);
 
 // Extraction of a list of non-terminals, one after another, into out_src /
-// out_dst from position 0 (each non-terminal's pairs sorted by (src, dst)):
-// the non-terminal ids nts[0..count) are on the device, every listed one
-// non-empty.  Scratch: units (units() + 1 words; after the call units[u] is
-// unit u's first output position), bsum (units() / 1024 + 2 words), total
-// (one word: receives the pair count), big (big_cap long-row entries; big_cap
-// = total pairs / 1024 + 1 always suffices), cursor (two words), bitmap as
-// for launch_extract.  A long-row list that overflows sets bit 0 of *err, a
-// row that would end past `limit` pairs bit 1 (the row is not written).
+// out_dst from position 0 (each non-terminal's pairs sorted by (src, dst)).
+// The rows of listed non-terminal k are cut into units of rows_per[k] rows,
+// units unit_first[k] .. unit_first[k + 1] - 1; every listed one is
+// non-empty.  All tables are on the device.  Scratch: units (units + 1
+// words; after the call units[u] is unit u's first output position), bsum
+// (units / 1024 + 2 words), total (one word: receives the pair count), big
+// (big_cap long-row entries; big_cap = pairs / 1024 + 1 always suffices),
+// cursor (two words), bitmap as for launch_extract.  A long-row list that
+// overflows sets bit 0 of *err, a row that would end past `limit` pairs
+// bit 1 (the row is not written).
 struct ExtractList {
-    const uint4 *desc;            // every non-terminal's descriptors, 2 n each
+    const uint4 *desc;                  // every non-terminal's descriptors, 2 n each
     const uint32_t *pool;
     const uint32_t *perm, *iperm;
-    const uint32_t *nts;
+    const uint32_t *nts;                // listed non-terminal ids (count)
+    const uint32_t *rows_per;           // rows per unit of each (count)
+    const unsigned long long *unit_first;   // first unit of each (count + 1)
     uint32_t n, count;
-    uint32_t rows_per_unit, units_per_nt;
-    unsigned long long limit;     // room in out_src / out_dst (pairs)
-    unsigned long long units() const { return (unsigned long long)count * units_per_nt; }
+    unsigned long long units;           // unit_first[count]
+    unsigned long long limit;           // room in out_src / out_dst (pairs)
 };
-// rows_per_unit for `count` non-terminals of n rows: about eight units per
-// resident warp (a power of two from 4 to 4096)
-uint32_t extract_rows_per_unit(uint32_t count, uint32_t n, int sms);
+// Units of listed non-terminals with pairs[k] pairs each, n rows: about
+// eight units per resident warp in all, each with a like share of the pairs
+// and at most 4096 rows.  Fills rows_per and unit_first (count + 1).
+void extract_plan(uint32_t count, uint32_t n, const uint64_t *pairs, int sms,
+                  uint32_t *rows_per, unsigned long long *unit_first);
 void launch_extract_list(const ExtractList &L, uint32_t *out_src, uint32_t *out_dst,
                          unsigned long long *units, unsigned long long *bsum,
                          unsigned long long *total, uint4 *big, unsigned long long big_cap,

@@ -144,9 +144,11 @@ struct cflr_ctx {
     // (listed non-terminal ids, unit offsets and their block sums, counters
     // and group totals, long-row list, row bitmaps)
     uint32_t *x_nts = nullptr, *x_bm = nullptr;
-    unsigned long long *x_unit = nullptr, *x_bsum = nullptr, *x_misc = nullptr;
+    unsigned long long *x_first = nullptr, *x_unit = nullptr, *x_bsum = nullptr,
+                       *x_misc = nullptr;
     uint4 *x_bigl = nullptr;
-    size_t x_nts_n = 0, x_bm_n = 0, x_unit_n = 0, x_bsum_n = 0, x_misc_n = 0, x_bigl_n = 0;
+    size_t x_nts_n = 0, x_bm_n = 0, x_first_n = 0, x_unit_n = 0, x_bsum_n = 0, x_misc_n = 0,
+           x_bigl_n = 0;
     uint32_t *x_src = nullptr, *x_dst = nullptr;
     uint64_t x_out_cap = 0;
     // accounting
@@ -210,6 +212,7 @@ struct cflr_ctx {
     // extraction scratch
     void free_extract_scratch() {
         drop(x_nts, x_nts_n);
+        drop(x_first, x_first_n);
         drop(x_bm, x_bm_n);
         drop(x_unit, x_unit_n);
         drop(x_bsum, x_bsum_n);
@@ -1643,7 +1646,8 @@ void extract_many(cflr_ctx *c, uint32_t count, const uint32_t *nts, const uint64
     constexpr uint64_t COPY_CHUNK = 1ull << 22;
     cudaStream_t st = c->stream;
     const uint32_t n = c->n;
-    std::vector<uint32_t> ids;
+    std::vector<uint32_t> ids;            // the non-empty entries
+    std::vector<uint64_t> pairs;          // and their pair counts
     std::vector<size_t> g_first;          // first entry of ids of each group
     std::vector<uint64_t> g_pos, g_pairs; // output position and pairs of each group
     for (uint32_t i = 0; i < count; i++) {
@@ -1655,43 +1659,54 @@ void extract_many(cflr_ctx *c, uint32_t count, const uint32_t *nts, const uint64
             g_pairs.push_back(0);
         }
         ids.push_back(nts[i]);
+        pairs.push_back(cnt);
         g_pairs.back() += cnt;
     }
     if (ids.empty()) return;
     const size_t G = g_first.size();
     g_first.push_back(ids.size());
-    std::vector<uint32_t> rows(G), upn(G);
+    // unit tables of every group, one after another: rows per unit beside
+    // the ids, first units (count + 1 per group) in a 64-bit table
+    const size_t E = ids.size();
+    std::vector<uint32_t> tab(ids);
+    tab.resize(2 * E);
+    std::vector<unsigned long long> first(E + G);
     uint64_t max_units = 0, max_pairs = 0;
     for (size_t g = 0; g < G; g++) {
         const uint32_t k = (uint32_t)(g_first[g + 1] - g_first[g]);
-        rows[g] = extract_rows_per_unit(k, n, c->sms);
-        upn[g] = (uint32_t)(((uint64_t)n + rows[g] - 1) / rows[g]);
-        max_units = std::max<uint64_t>(max_units, (uint64_t)k * upn[g]);
+        extract_plan(k, n, pairs.data() + g_first[g], c->sms, tab.data() + E + g_first[g],
+                     first.data() + g_first[g] + g);
+        max_units = std::max<uint64_t>(max_units, first[g_first[g] + g + k]);
         max_pairs = std::max(max_pairs, g_pairs[g]);
     }
-    c->scratch(c->x_nts, c->x_nts_n, ids.size());
+    c->scratch(c->x_nts, c->x_nts_n, 2 * E);
+    c->scratch(c->x_first, c->x_first_n, E + G);
     c->scratch(c->x_unit, c->x_unit_n, max_units + 1);
     c->scratch(c->x_bsum, c->x_bsum_n, max_units / 1024 + 2);
     c->scratch(c->x_misc, c->x_misc_n, 3 + G);      // cursors, error flag, group totals
     c->scratch(c->x_bigl, c->x_bigl_n, max_pairs / 1024 + 1);
     const size_t words = ((size_t)n + 31) / 32;
     if (words * 4 > 200 * 1024) c->scratch(c->x_bm, c->x_bm_n, words * (size_t)c->sms * 4);
-    ck(cudaMemcpyAsync(c->x_nts, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
+    ck(cudaMemcpyAsync(c->x_nts, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
+    ck(cudaMemcpyAsync(c->x_first, first.data(), first.size() * 8, cudaMemcpyHostToDevice, st),
+       "H2D");
     ck(cudaMemsetAsync(c->x_misc + 2, 0, 8, st), "memset");
     unsigned *err = (unsigned *)(c->x_misc + 2);
     CopyLane lane;
     if (hs) ck(cudaStreamCreateWithFlags(&lane.s, cudaStreamNonBlocking), "cudaStreamCreate");
     for (size_t g = 0; g < G; g++) {
+        const uint32_t k = (uint32_t)(g_first[g + 1] - g_first[g]);
         ExtractList L{};
         L.desc = c->desc;
         L.pool = c->pool;
         L.perm = c->perm;
         L.iperm = c->iperm;
         L.nts = c->x_nts + g_first[g];
+        L.rows_per = c->x_nts + E + g_first[g];
+        L.unit_first = c->x_first + g_first[g] + g;
         L.n = n;
-        L.count = (uint32_t)(g_first[g + 1] - g_first[g]);
-        L.rows_per_unit = rows[g];
-        L.units_per_nt = upn[g];
+        L.count = k;
+        L.units = first[g_first[g] + g + k];
         L.limit = g_pairs[g];
         launch_extract_list(L, ws + g_pos[g], wd + g_pos[g], c->x_unit, c->x_bsum,
                             c->x_misc + 3 + g, c->x_bigl, c->x_bigl_n, c->x_misc, c->x_bm, err,
