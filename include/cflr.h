@@ -104,6 +104,14 @@ typedef struct {
                                    the table and report the full set, cflr_solve
                                    returns CFLR_ECUDA and the context needs a new
                                    graph (it stays usable)                          */
+    int order_on_device;        /* where the breadth-first vertex order is found
+                                   (unless keep_vertex_order): 0 (default) on the
+                                   GPU for graphs of at least 2^18 edges, on the
+                                   host below that; 1 on the GPU; -1 on the host.
+                                   Both give the same order.  The GPU search needs
+                                   fewer than 2^32 edges and no vertex with more
+                                   than 8192 edge ends; other graphs are ordered on
+                                   the host whatever this says                      */
 } cflr_config;
 
 typedef struct {
@@ -280,6 +288,14 @@ int cflr_get_witness(const cflr_ctx *c, uint32_t nonterminal, uint32_t src, uint
  *   - Arguments, output format and other errors as cflr_get_pairs_device. */
 int cflr_get_pairs_device_noalloc(const cflr_ctx *c, uint32_t nonterminal, uint32_t *d_src,
                                   uint32_t *d_dst, uint64_t capacity, uint64_t *n_pairs);
+
+/* The vertex order the context stores the loaded graph in: order[k]
+ * receives the caller's id of the vertex stored as row k (the identity with
+ * keep_vertex_order).  order is a host array of at least n_vertices entries
+ * (capacity).  The order only places rows in memory; results never depend
+ * on it.  Errors: CFLR_ESTATE (no graph), CFLR_EINVAL (NULL order, capacity
+ * below the vertex count), CFLR_ECUDA. */
+int cflr_get_vertex_order(const cflr_ctx *c, uint32_t *order, uint64_t capacity);
 
 /* Restore the matrices of the loaded graph to Algorithm 1's terminal
  * initialisation, from the copy of the edges cflr_load_graph keeps on the

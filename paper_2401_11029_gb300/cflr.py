@@ -39,7 +39,7 @@ CFLR_FORM_GRAPH = 2
 EXPORTS = ["cflr_default_config", "cflr_create", "cflr_load_grammar", "cflr_symbol_id",
            "cflr_grammar_sizes", "cflr_load_graph", "cflr_solve", "cflr_get_pairs",
            "cflr_get_pairs_device", "cflr_get_pairs_device_noalloc", "cflr_get_pairs_many",
-           "cflr_get_pairs_device_many", "cflr_reset",
+           "cflr_get_pairs_device_many", "cflr_get_vertex_order", "cflr_reset",
            "cflr_solve_batch", "cflr_kernel_stats", "cflr_get_tuning", "cflr_set_tuning",
            "cflr_autotune", "cflr_get_witness", "cflr_last_error", "cflr_destroy"]
 
@@ -64,7 +64,7 @@ class cflr_config(ctypes.Structure):
                 ("autotune_cache", ctypes.c_char_p), ("initial_capacity", ctypes.c_uint32),
                 ("size_hint", ctypes.c_uint32), ("stop_on_first_converged", ctypes.c_int),
                 ("keep_vertex_order", ctypes.c_int), ("witness", ctypes.c_int),
-                ("test_fixed_pair_sets", ctypes.c_int)]
+                ("test_fixed_pair_sets", ctypes.c_int), ("order_on_device", ctypes.c_int)]
 
 
 class cflr_tuning(ctypes.Structure):
@@ -127,6 +127,8 @@ def load_library(path: str = LIB_PATH):
     lib.cflr_get_pairs_device.restype = i32
     lib.cflr_get_pairs_device_noalloc.argtypes = [vp, u32, vp, vp, u64, ctypes.POINTER(u64)]
     lib.cflr_get_pairs_device_noalloc.restype = i32
+    lib.cflr_get_vertex_order.argtypes = [vp, vp, u64]
+    lib.cflr_get_vertex_order.restype = i32
     lib.cflr_get_pairs_many.argtypes = [vp, u32, vp, vp, vp, u64, vp]
     lib.cflr_get_pairs_many.restype = i32
     lib.cflr_get_pairs_device_many.argtypes = [vp, u32, vp, vp, vp, u64, vp]
@@ -324,6 +326,13 @@ def cflr_get_pairs_device_noalloc(ctx, nonterminal: int, d_src: int, d_dst: int,
         ctx, int(nonterminal), ctypes.c_void_p(d_src), ctypes.c_void_p(d_dst), int(capacity),
         ctypes.byref(n)))
     return int(n.value)
+
+
+def cflr_get_vertex_order(ctx, n_vertices: int) -> np.ndarray:
+    """The caller's id of the vertex stored as each row (uint32, n_vertices)."""
+    out = np.empty(max(int(n_vertices), 1), dtype=np.uint32)
+    _check(ctx, load_library().cflr_get_vertex_order(ctx, out.ctypes.data, out.size))
+    return out[:int(n_vertices)]
 
 
 def cflr_reset(ctx):

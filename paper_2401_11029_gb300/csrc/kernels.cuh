@@ -314,6 +314,48 @@ void launch_extract_list(const ExtractList &L, uint32_t *out_src, uint32_t *out_
                          unsigned long long *cursor, uint32_t *bitmap, unsigned *err, int sms,
                          cudaStream_t st);
 
+// Vertex renumbering on the device (renumber.cu): the breadth-first order of
+// the undirected edges a one-thread queue search gives.  The host runs, in
+// this order: launch_rn_adjacency (degrees deg[n], the largest into
+// *max_deg), an exclusive scan of deg into off[0..n], launch_rn_fill (the
+// adjacency lists adj[off[v] ..] of (edge << 32 | neighbour), sorted; every
+// list at most RENUM_LIST_MAX long; cur: n words, big: n words, big_n: one),
+// launch_rn_init, launch_rn_cc_pass until *more stays 0, launch_rn_count,
+// scans of cnt (component offsets) and is_root (root offsets, the root count
+// as total), launch_rn_roots (level 0), then per level launch_rn_claim, a
+// scan of won into woff[0..fsize], launch_rn_write (the next frontier into
+// F2, the next segment tables, perm and iperm), until the frontier is empty;
+// launch_rn_check sets *bad unless perm and iperm are inverse permutations.
+constexpr uint32_t RENUM_LIST_MAX = 8192;
+void launch_rn_adjacency(const uint32_t *src, const uint32_t *dst, unsigned long long m,
+                         uint32_t n, uint32_t *deg, uint32_t *max_deg, int sms, cudaStream_t st);
+void launch_rn_fill(const uint32_t *src, const uint32_t *dst, unsigned long long m, uint32_t n,
+                    const unsigned long long *off, unsigned long long *cur,
+                    unsigned long long *adj, uint32_t *big, uint32_t *big_n, uint32_t max_deg,
+                    int sms, cudaStream_t st);
+void launch_rn_init(uint32_t n, uint32_t *parent, uint32_t *lvl, unsigned long long *key,
+                    uint32_t *iperm, int sms, cudaStream_t st);
+void launch_rn_cc_pass(const uint32_t *src, const uint32_t *dst, unsigned long long m,
+                       uint32_t n, uint32_t *parent, unsigned *more, int sms, cudaStream_t st);
+void launch_rn_count(const uint32_t *parent, uint32_t n, uint32_t *cnt, uint32_t *is_root,
+                     int sms, cudaStream_t st);
+void launch_rn_roots(const uint32_t *parent, uint32_t n, const unsigned long long *roff,
+                     const unsigned long long *comp_off, uint32_t *F, uint32_t *lvl, uint32_t *sf,
+                     uint32_t *se, uint32_t *pc, uint32_t *perm, uint32_t *iperm, int sms,
+                     cudaStream_t st);
+void launch_rn_claim(const uint32_t *F, uint32_t fsize, const unsigned long long *off,
+                     const unsigned long long *adj, const uint32_t *lvl, unsigned long long *key,
+                     uint32_t *won, int sms, cudaStream_t st);
+void launch_rn_write(const uint32_t *F, uint32_t fsize, const unsigned long long *off,
+                     const unsigned long long *adj, uint32_t *lvl, const unsigned long long *key,
+                     const unsigned long long *woff, uint32_t *F2, uint32_t level,
+                     const uint32_t *parent, const unsigned long long *comp_off,
+                     const uint32_t *sf, const uint32_t *se, const uint32_t *pc, uint32_t *sf2,
+                     uint32_t *se2, uint32_t *pc2, uint32_t *perm, uint32_t *iperm, uint32_t n,
+                     int sms, cudaStream_t st);
+void launch_rn_check(const uint32_t *perm, const uint32_t *iperm, uint32_t n, unsigned *bad,
+                     int sms, cudaStream_t st);
+
 // a[e] <- perm[a[e]] for e < m (vertex renumbering of the loaded edges)
 void launch_permute_ids(uint32_t *a, unsigned long long m, const uint32_t *perm, int sms,
                         cudaStream_t st);

@@ -1217,6 +1217,112 @@ std::vector<uint32_t> locality_order(uint32_t n, uint64_t m, const uint32_t *src
     return order;
 }
 
+// Device arrays of one call, freed on every way out of it.
+struct TempArrays {
+    cflr_ctx *c;
+    std::vector<std::pair<void *, size_t>> held;
+    template <typename T>
+    T *get(size_t count) {
+        const size_t b = std::max<size_t>(count * sizeof(T), 16);
+        void *p = c->dalloc(b);
+        held.push_back({p, b});
+        return (T *)p;
+    }
+    ~TempArrays() {
+        for (auto &h : held) c->dfree(h.first, h.second);
+    }
+};
+
+// The order locality_order gives, found on the device from the uploaded
+// edges c->e_src / c->e_dst (caller ids) into c->perm / c->iperm (the
+// kernels' steps are described with launch_rn_adjacency).  Returns false,
+// with nothing to keep, for graphs it does not take: 2^32 edges or more, a
+// vertex with more than RENUM_LIST_MAX edge ends, or components that did not
+// settle in 128 passes.
+bool device_order(cflr_ctx *c, uint32_t n, uint64_t m) {
+    if (m >= (1ull << 32)) return false;
+    Range range("cflr: vertex renumbering (device)");
+    cudaStream_t st = c->stream;
+    const int sms = c->sms;
+    TempArrays tmp{c, {}};
+    uint32_t *word = tmp.get<uint32_t>(8);          // max degree, long lists, flags
+    unsigned long long *tot = tmp.get<unsigned long long>(2);
+    auto read_word = [&](const void *d, size_t bytes, void *to) {
+        ck(cudaMemcpyAsync(to, d, bytes, cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaStreamSynchronize(st), "sync renumbering");
+    };
+    uint32_t *deg = tmp.get<uint32_t>(n);
+    unsigned long long *off = tmp.get<unsigned long long>((size_t)n + 1);
+    unsigned long long *bsum = tmp.get<unsigned long long>((size_t)n / 1024 + 2);
+    launch_rn_adjacency(c->e_src, c->e_dst, m, n, deg, word, sms, st);
+    launch_exclusive_scan(deg, n, off, bsum, off + n, st);
+    ck(cudaGetLastError(), "renumbering: degrees");
+    uint32_t max_deg = 0;
+    read_word(word, 4, &max_deg);
+    if (max_deg > RENUM_LIST_MAX) return false;
+    unsigned long long *adj = tmp.get<unsigned long long>(2 * m);
+    unsigned long long *cur = tmp.get<unsigned long long>(n);
+    uint32_t *big = tmp.get<uint32_t>(n);
+    launch_rn_fill(c->e_src, c->e_dst, m, n, off, cur, adj, big, word + 1, max_deg, sms, st);
+    uint32_t *parent = tmp.get<uint32_t>(n);
+    uint32_t *lvl = tmp.get<uint32_t>(n);
+    unsigned long long *key = tmp.get<unsigned long long>(n);
+    launch_rn_init(n, parent, lvl, key, c->iperm, sms, st);
+    ck(cudaGetLastError(), "renumbering: adjacency");
+    for (int pass = 0;; pass++) {
+        if (pass == 128) return false;
+        launch_rn_cc_pass(c->e_src, c->e_dst, m, n, parent, (unsigned *)(word + 2), sms, st);
+        ck(cudaGetLastError(), "renumbering: components");
+        uint32_t more = 0;
+        read_word(word + 2, 4, &more);
+        if (!more) break;
+    }
+    uint32_t *cnt = tmp.get<uint32_t>(n);
+    uint32_t *is_root = tmp.get<uint32_t>(n);
+    unsigned long long *comp_off = tmp.get<unsigned long long>(n);
+    unsigned long long *roff = tmp.get<unsigned long long>(n);
+    launch_rn_count(parent, n, cnt, is_root, sms, st);
+    launch_exclusive_scan(cnt, n, comp_off, bsum, nullptr, st);
+    launch_exclusive_scan(is_root, n, roff, bsum, tot, st);
+    uint32_t *F = tmp.get<uint32_t>(n), *F2 = tmp.get<uint32_t>(n);
+    uint32_t *seg[2][3];      // per root: segment first, segment end, earlier count
+    for (int b = 0; b < 2; b++)
+        for (int k = 0; k < 3; k++) seg[b][k] = tmp.get<uint32_t>(n);
+    uint32_t *won = tmp.get<uint32_t>(n);
+    unsigned long long *woff = tmp.get<unsigned long long>((size_t)n + 1);
+    launch_rn_roots(parent, n, roff, comp_off, F, lvl, seg[0][0], seg[0][1], seg[0][2], c->perm,
+                    c->iperm, sms, st);
+    ck(cudaGetLastError(), "renumbering: roots");
+    unsigned long long fsize = 0;
+    read_word(tot, 8, &fsize);
+    uint64_t placed = 0;
+    int b = 0;
+    for (uint32_t level = 0; fsize; level++) {
+        if (level > n) throw Status{CFLR_ECUDA, "internal: the device search did not end"};
+        placed += fsize;
+        launch_rn_claim(F, (uint32_t)fsize, off, adj, lvl, key, won, sms, st);
+        launch_exclusive_scan(won, (uint32_t)fsize, woff, bsum, woff + fsize, st);
+        launch_rn_write(F, (uint32_t)fsize, off, adj, lvl, key, woff, F2, level, parent, comp_off,
+                        seg[b][0], seg[b][1], seg[b][2], seg[b ^ 1][0], seg[b ^ 1][1],
+                        seg[b ^ 1][2], c->perm, c->iperm, n, sms, st);
+        ck(cudaGetLastError(), "renumbering: level");
+        unsigned long long next = 0;
+        read_word(woff + fsize, 8, &next);
+        std::swap(F, F2);
+        b ^= 1;
+        fsize = next;
+    }
+    if (placed != n)
+        throw Status{CFLR_ECUDA, "internal: the device search placed " + std::to_string(placed) +
+                                     " of " + std::to_string(n) + " vertices"};
+    launch_rn_check(c->perm, c->iperm, n, (unsigned *)(word + 3), sms, st);
+    ck(cudaGetLastError(), "renumbering: check");
+    uint32_t bad = 0;
+    read_word(word + 3, 4, &bad);
+    if (bad) throw Status{CFLR_ECUDA, "internal: the device order is not a permutation"};
+    return true;
+}
+
 // Copy the graph to the device and size the matrices (cflr_load_graph).
 void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *lab,
                   const uint32_t *dst) {
@@ -1248,20 +1354,25 @@ void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, cons
         ck(cudaMemcpyAsync(c->e_dst, dst, m * 4, cudaMemcpyHostToDevice, st), "H2D edges");
     }
     if (!c->cfg.keep_vertex_order && n > 0) {
-        Range range("cflr: vertex renumbering");
-        const std::vector<uint32_t> order = locality_order(n, m, src, dst);
-        std::vector<uint32_t> perm(n);
-        for (uint32_t k = 0; k < n; k++) perm[order[k]] = k;
         c->perm = (uint32_t *)c->dalloc((size_t)n * 4);
         c->iperm = (uint32_t *)c->dalloc((size_t)n * 4);
-        ck(cudaMemcpyAsync(c->perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st),
-           "H2D order");
-        ck(cudaMemcpyAsync(c->iperm, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st),
-           "H2D order");
+        const int where = c->cfg.order_on_device;
+        const bool on_device = where > 0 || (where == 0 && m >= (1u << 18));
+        if (!on_device || !device_order(c, n, m)) {
+            Range range("cflr: vertex renumbering (host)");
+            const std::vector<uint32_t> order = locality_order(n, m, src, dst);
+            std::vector<uint32_t> perm(n);
+            for (uint32_t k = 0; k < n; k++) perm[order[k]] = k;
+            ck(cudaMemcpyAsync(c->perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st),
+               "H2D order");
+            ck(cudaMemcpyAsync(c->iperm, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice,
+                               st),
+               "H2D order");
+            // the host vectors die here: wait for the copies that read them
+            ck(cudaStreamSynchronize(st), "sync order");
+        }
         launch_permute_ids(c->e_src, m, c->perm, c->sms, st);
         launch_permute_ids(c->e_dst, m, c->perm, c->sms, st);
-        // the host vectors die here: wait for the copies that read them
-        ck(cudaStreamSynchronize(st), "sync order");
     }
     std::vector<uint32_t> toff(1, 0), tslot;
     for (uint32_t l = 0; l < nterm; l++) {
@@ -1591,6 +1702,27 @@ int cflr_solve_batch(cflr_ctx *const *ctxs, int n, cflr_stats *stats) {
         return finish_status(cx[0], s);
     } catch (const CudaError &e) {
         return cuda_status(cx[0], e);
+    }
+}
+
+int cflr_get_vertex_order(const cflr_ctx *cc, uint32_t *order, uint64_t capacity) {
+    cflr_ctx *c = const_cast<cflr_ctx *>(cc);
+    if (!c) return CFLR_EINVAL;
+    if (c->state < ST_GRAPH) return c->fail(CFLR_ESTATE, "no graph loaded");
+    if (!order) return c->fail(CFLR_EINVAL, "order is NULL");
+    if (capacity < c->n) return c->fail(CFLR_EINVAL, "capacity smaller than the vertex count");
+    if (!c->iperm) {
+        for (uint32_t k = 0; k < c->n; k++) order[k] = k;
+        return CFLR_OK;
+    }
+    try {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        ck(cudaMemcpyAsync(order, c->iperm, (size_t)c->n * 4, cudaMemcpyDeviceToHost, c->stream),
+           "D2H order");
+        ck(cudaStreamSynchronize(c->stream), "sync order");
+        return CFLR_OK;
+    } catch (const CudaError &e) {
+        return cuda_status(c, e);
     }
 }
 
