@@ -520,7 +520,9 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
                   "flops": solve_stats["flops"], "flops_bin3": solve_stats["flops_bin3"],
                   "mask_tiles_bin3": solve_stats["mask_tiles_bin3"],
                   "candidates": solve_stats["candidates"],
-                  "peak_device_bytes": solve_stats["peak_device_bytes"]},
+                  "peak_device_bytes": solve_stats["peak_device_bytes"],
+                  "regrows_last_step": solve_stats["regrows"]},
+        "steps_ms": [round(t, 3) for t in step_ms],
         "roofline_note": "kernel times from the same steps replayed with per-kernel CUDA "
                          "events (host-launched iterations) right after the timed region",
     }
@@ -604,7 +606,8 @@ def run_extra(name, args) -> dict:
                         for r in rows if r[1]][:6],
             "clocks": clk, "tuning": tuning, "parity": parity,
             "solve": {"form": "graph", "iterations": last["iterations"],
-                      "groups_per_bin": last["groups"]}}
+                      "groups_per_bin": last["groups"], "regrows_last_step": last["regrows"]},
+            "steps_ms": [round(t, 3) for t in step_ms]}
 
 
 def run_dyck3_batch(args, print_line: bool = True):
