@@ -2445,13 +2445,13 @@ __global__ void __launch_bounds__(256) k_extract_units(ExtractList L,
     uint32_t *s = sbuf[wib];
     for (;;) {
         unsigned long long u = 0;
-        if (lane == 0) u = atomicAdd(&cursor[1], 1ull);
+        if (lane == 0) u = L.u_begin + atomicAdd(&cursor[1], 1ull);
         u = __shfl_sync(FULL_MASK, u, 0);
-        if (u >= L.units) break;
+        if (u >= L.u_end) break;
         uint32_t r0, r1;
         const uint32_t k = unit_rows(L, u, r0, r1);
         const uint4 *dk = list_desc(L, k);
-        unsigned long long o = unit_off[u];
+        unsigned long long o = unit_off[u];     // absolute; written at o - L.base
         for (uint32_t rb = r0; rb < r1; rb += 32) {
             const uint32_t i = rb + lane;
             const uint4 d = i < r1 ? dk[stored_row(L.perm, i)] : make_uint4(0, 0, 0, 0);
@@ -2470,13 +2470,15 @@ __global__ void __launch_bounds__(256) k_extract_units(ExtractList L,
                 } else if (len > EXTRACT_WARP_MAX) {
                     if (lane == 0) {
                         const unsigned long long pos = atomicAdd(&cursor[0], 1ull);
+                        const unsigned long long ro = o - L.base;
                         if (pos < big_cap)
-                            big[pos] = make_uint4(rb + l, k, (uint32_t)o, (uint32_t)(o >> 32));
+                            big[pos] = make_uint4(rb + l, k, (uint32_t)ro, (uint32_t)(ro >> 32));
                         else
                             atomicOr(err, 1u);
                     }
                 } else {
-                    extract_row_warp(tl, nt, len, rb + l, L.iperm, o, out_src, out_dst, s, lane);
+                    extract_row_warp(tl, nt, len, rb + l, L.iperm, o - L.base, out_src, out_dst,
+                                     s, lane);
                 }
                 o += len;
             }
@@ -2823,16 +2825,22 @@ void extract_plan(uint32_t count, uint32_t n, const uint64_t *pairs, int sms,
     }
 }
 
-void launch_extract_list(const ExtractList &L, uint32_t *out_src, uint32_t *out_dst,
-                         unsigned long long *units, unsigned long long *bsum,
-                         unsigned long long *total, uint4 *big, unsigned long long big_cap,
-                         unsigned long long *cursor, uint32_t *bitmap, unsigned *err, int sms,
-                         cudaStream_t st) {
+void launch_extract_count(const ExtractList &L, unsigned long long *units,
+                          unsigned long long *bsum, unsigned long long *total, int sms,
+                          cudaStream_t st) {
     const unsigned long long nu = L.units;
     if (!nu || !L.n) return;
-    set_smem_attrs();
     k_unit_lengths<<<grid_for(nu, 8, sms, 8), 256, 0, st>>>(L, units);
     launch_exclusive_scan64(units, nu, bsum, total, st);
+}
+
+void launch_extract_write(const ExtractList &L, uint32_t *out_src, uint32_t *out_dst,
+                          const unsigned long long *units, uint4 *big,
+                          unsigned long long big_cap, unsigned long long *cursor,
+                          uint32_t *bitmap, unsigned *err, int sms, cudaStream_t st) {
+    const unsigned long long nu = L.u_end > L.u_begin ? L.u_end - L.u_begin : 0;
+    if (!nu || !L.n) return;
+    set_smem_attrs();
     cudaMemsetAsync(cursor, 0, 2 * sizeof(unsigned long long), st);
     k_extract_units<<<grid_for(nu, 8, sms, 8), 256, 0, st>>>(L, units, out_src, out_dst, big,
                                                              big_cap, cursor, err);

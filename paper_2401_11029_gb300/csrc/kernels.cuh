@@ -281,17 +281,20 @@ void launch_extract(const uint4 *desc, const uint32_t *pool, uint32_t n, const u
                     uint32_t *out_dst, uint32_t *big_rows, uint32_t *big_count,
                     uint32_t *bitmap, int sms, cudaStream_t st);
 
-// Extraction of a list of non-terminals, one after another, into out_src /
-// out_dst from position 0 (each non-terminal's pairs sorted by (src, dst)).
-// The rows of listed non-terminal k are cut into units of rows_per[k] rows,
-// units unit_first[k] .. unit_first[k + 1] - 1; every listed one is
-// non-empty.  All tables are on the device.  Scratch: units (units + 1
-// words; after the call units[u] is unit u's first output position), bsum
-// (units / 1024 + 2 words), total (one word: receives the pair count), big
-// (big_cap long-row entries; big_cap = pairs / 1024 + 1 always suffices),
-// cursor (two words), bitmap as for launch_extract.  A long-row list that
-// overflows sets bit 0 of *err, a row that would end past `limit` pairs
-// bit 1 (the row is not written).
+// Extraction of a list of non-terminals, one after another (each
+// non-terminal's pairs sorted by (src, dst)).  The rows of listed
+// non-terminal k are cut into units of rows_per[k] rows, units unit_first[k]
+// .. unit_first[k + 1] - 1; every listed one is non-empty.  All tables are on
+// the device.
+// launch_extract_count: units (units + 1 words) receives every unit's first
+// output position (an exclusive scan of the units' pair counts in list
+// order), *total the pair count; bsum: units / 1024 + 2 words.
+// launch_extract_write: the rows of units u_begin .. u_end - 1, a pair at
+// output position o written at out_src / out_dst[o - base]; a row that
+// would end past position `limit` is not written (bit 1 of *err).  Long rows
+// are listed in big (big_cap entries: the range's pairs / 1024 + 1 always
+// suffice; an overflow sets bit 0 of *err); cursor: two words; bitmap as for
+// launch_extract.
 struct ExtractList {
     const uint4 *desc;                  // every non-terminal's descriptors, 2 n each
     const uint32_t *pool;
@@ -301,18 +304,21 @@ struct ExtractList {
     const unsigned long long *unit_first;   // first unit of each (count + 1)
     uint32_t n, count;
     unsigned long long units;           // unit_first[count]
-    unsigned long long limit;           // room in out_src / out_dst (pairs)
+    unsigned long long u_begin, u_end;  // units written by launch_extract_write
+    unsigned long long base, limit;     // output positions: written at o - base, o < limit
 };
 // Units of listed non-terminals with pairs[k] pairs each, n rows: about
 // eight units per resident warp in all, each with a like share of the pairs
 // and at most 4096 rows.  Fills rows_per and unit_first (count + 1).
 void extract_plan(uint32_t count, uint32_t n, const uint64_t *pairs, int sms,
                   uint32_t *rows_per, unsigned long long *unit_first);
-void launch_extract_list(const ExtractList &L, uint32_t *out_src, uint32_t *out_dst,
-                         unsigned long long *units, unsigned long long *bsum,
-                         unsigned long long *total, uint4 *big, unsigned long long big_cap,
-                         unsigned long long *cursor, uint32_t *bitmap, unsigned *err, int sms,
-                         cudaStream_t st);
+void launch_extract_count(const ExtractList &L, unsigned long long *units,
+                          unsigned long long *bsum, unsigned long long *total, int sms,
+                          cudaStream_t st);
+void launch_extract_write(const ExtractList &L, uint32_t *out_src, uint32_t *out_dst,
+                          const unsigned long long *units, uint4 *big,
+                          unsigned long long big_cap, unsigned long long *cursor,
+                          uint32_t *bitmap, unsigned *err, int sms, cudaStream_t st);
 
 // Vertex renumbering on the device (renumber.cu): the breadth-first order of
 // the undirected edges a one-thread queue search gives.  The host runs, in

@@ -1772,57 +1772,40 @@ struct CopyLane {
 };
 
 // Write the pairs of the listed non-terminals (nts[0..count), output
-// positions offsets[0..count]) one after another into the device arrays
-// ws/wd, each non-terminal's sorted by (src, dst).  The non-empty ones are
-// extracted in groups by launch_extract_list; with host arrays hs/hd, a
-// group closes at COPY_CHUNK pairs and is copied out on a second stream as
-// soon as it is written, overlapping the extraction of the next group.
-// Checks each group's pair count against the pair sets' counts.
+// positions offsets[0..count]) one after another, each non-terminal's
+// sorted by (src, dst): into the device arrays ws/wd, or into the host
+// arrays hs/hd through two device staging buffers of at most STAGE pairs.
+// For the host, the units' first positions are read back after the count,
+// the units are cut into ranges that fit a buffer, and each range is written
+// into one buffer while the other is copied out on a second stream.
+// Checks the extracted count against the pair sets' counts.
 void extract_many(cflr_ctx *c, uint32_t count, const uint32_t *nts, const uint64_t *offsets,
                   uint32_t *ws, uint32_t *wd, uint32_t *hs, uint32_t *hd) {
     Range range("cflr: extraction");
-    constexpr uint64_t COPY_CHUNK = 1ull << 22;
+    constexpr uint64_t STAGE = 1ull << 24;
     cudaStream_t st = c->stream;
     const uint32_t n = c->n;
-    std::vector<uint32_t> ids;            // the non-empty entries
-    std::vector<uint64_t> pairs;          // and their pair counts
-    std::vector<size_t> g_first;          // first entry of ids of each group
-    std::vector<uint64_t> g_pos, g_pairs; // output position and pairs of each group
+    std::vector<uint32_t> tab;            // the non-empty entries, then their rows per unit
+    std::vector<uint64_t> pairs;
     for (uint32_t i = 0; i < count; i++) {
         const uint64_t cnt = offsets[i + 1] - offsets[i];
         if (!cnt) continue;
-        if (ids.empty() || (hs && g_pairs.back() >= COPY_CHUNK)) {
-            g_first.push_back(ids.size());
-            g_pos.push_back(offsets[i]);
-            g_pairs.push_back(0);
-        }
-        ids.push_back(nts[i]);
+        tab.push_back(nts[i]);
         pairs.push_back(cnt);
-        g_pairs.back() += cnt;
     }
-    if (ids.empty()) return;
-    const size_t G = g_first.size();
-    g_first.push_back(ids.size());
-    // unit tables of every group, one after another: rows per unit beside
-    // the ids, first units (count + 1 per group) in a 64-bit table
-    const size_t E = ids.size();
-    std::vector<uint32_t> tab(ids);
-    tab.resize(2 * E);
-    std::vector<unsigned long long> first(E + G);
-    uint64_t max_units = 0, max_pairs = 0;
-    for (size_t g = 0; g < G; g++) {
-        const uint32_t k = (uint32_t)(g_first[g + 1] - g_first[g]);
-        extract_plan(k, n, pairs.data() + g_first[g], c->sms, tab.data() + E + g_first[g],
-                     first.data() + g_first[g] + g);
-        max_units = std::max<uint64_t>(max_units, first[g_first[g] + g + k]);
-        max_pairs = std::max(max_pairs, g_pairs[g]);
-    }
-    c->scratch(c->x_nts, c->x_nts_n, 2 * E);
-    c->scratch(c->x_first, c->x_first_n, E + G);
-    c->scratch(c->x_unit, c->x_unit_n, max_units + 1);
-    c->scratch(c->x_bsum, c->x_bsum_n, max_units / 1024 + 2);
-    c->scratch(c->x_misc, c->x_misc_n, 3 + G);      // cursors, error flag, group totals
-    c->scratch(c->x_bigl, c->x_bigl_n, max_pairs / 1024 + 1);
+    if (tab.empty()) return;
+    const uint32_t E = (uint32_t)tab.size();
+    uint64_t total = 0;
+    for (uint64_t p : pairs) total += p;
+    tab.resize(2 * (size_t)E);
+    std::vector<unsigned long long> first(E + 1);
+    extract_plan(E, n, pairs.data(), c->sms, tab.data() + E, first.data());
+    const uint64_t U = first[E];
+    c->scratch(c->x_nts, c->x_nts_n, 2 * (size_t)E);
+    c->scratch(c->x_first, c->x_first_n, (size_t)E + 1);
+    c->scratch(c->x_unit, c->x_unit_n, U + 1);
+    c->scratch(c->x_bsum, c->x_bsum_n, U / 1024 + 2);
+    c->scratch(c->x_misc, c->x_misc_n, 4);       // cursors, error flag, total
     const size_t words = ((size_t)n + 31) / 32;
     if (words * 4 > 200 * 1024) c->scratch(c->x_bm, c->x_bm_n, words * (size_t)c->sms * 4);
     ck(cudaMemcpyAsync(c->x_nts, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st), "H2D");
@@ -1830,47 +1813,88 @@ void extract_many(cflr_ctx *c, uint32_t count, const uint32_t *nts, const uint64
        "H2D");
     ck(cudaMemsetAsync(c->x_misc + 2, 0, 8, st), "memset");
     unsigned *err = (unsigned *)(c->x_misc + 2);
-    CopyLane lane;
-    if (hs) ck(cudaStreamCreateWithFlags(&lane.s, cudaStreamNonBlocking), "cudaStreamCreate");
-    for (size_t g = 0; g < G; g++) {
-        const uint32_t k = (uint32_t)(g_first[g + 1] - g_first[g]);
-        ExtractList L{};
-        L.desc = c->desc;
-        L.pool = c->pool;
-        L.perm = c->perm;
-        L.iperm = c->iperm;
-        L.nts = c->x_nts + g_first[g];
-        L.rows_per = c->x_nts + E + g_first[g];
-        L.unit_first = c->x_first + g_first[g] + g;
-        L.n = n;
-        L.count = k;
-        L.units = first[g_first[g] + g + k];
-        L.limit = g_pairs[g];
-        launch_extract_list(L, ws + g_pos[g], wd + g_pos[g], c->x_unit, c->x_bsum,
-                            c->x_misc + 3 + g, c->x_bigl, c->x_bigl_n, c->x_misc, c->x_bm, err,
-                            c->sms, st);
-        ck(cudaGetLastError(), "extract");
-        if (hs) {
-            ck(cudaStreamWaitEvent(lane.s, lane.record(st), 0), "cudaStreamWaitEvent");
-            ck(cudaMemcpyAsync(hs + g_pos[g], ws + g_pos[g], g_pairs[g] * 4,
-                               cudaMemcpyDeviceToHost, lane.s), "D2H pairs");
-            ck(cudaMemcpyAsync(hd + g_pos[g], wd + g_pos[g], g_pairs[g] * 4,
-                               cudaMemcpyDeviceToHost, lane.s), "D2H pairs");
-        }
-    }
-    std::vector<unsigned long long> misc(3 + G);
-    ck(cudaMemcpyAsync(misc.data(), c->x_misc, (3 + G) * 8, cudaMemcpyDeviceToHost, st), "D2H");
-    if (hs) ck(cudaStreamSynchronize(lane.s), "sync copy");
-    ck(cudaStreamSynchronize(st), "sync extract");
-    if (misc[2] & 1)
-        throw Status{CFLR_ECUDA, "internal: the long-row list of the extraction overflowed"};
-    if (misc[2] & 2)
-        throw Status{CFLR_ECUDA, "internal: a row held more pairs than the pair sets count"};
-    for (size_t g = 0; g < G; g++)
-        if (misc[3 + g] != g_pairs[g])
-            throw Status{CFLR_ECUDA, "internal: extracted " + std::to_string(misc[3 + g]) +
+    ExtractList L{};
+    L.desc = c->desc;
+    L.pool = c->pool;
+    L.perm = c->perm;
+    L.iperm = c->iperm;
+    L.nts = c->x_nts;
+    L.rows_per = c->x_nts + E;
+    L.unit_first = c->x_first;
+    L.n = n;
+    L.count = E;
+    L.units = U;
+    launch_extract_count(L, c->x_unit, c->x_bsum, c->x_misc + 3, c->sms, st);
+    ck(cudaGetLastError(), "extract count");
+    unsigned long long misc[4] = {0, 0, 0, 0};
+    auto check = [&]() {
+        ck(cudaMemcpyAsync(misc, c->x_misc, sizeof(misc), cudaMemcpyDeviceToHost, st), "D2H");
+        ck(cudaStreamSynchronize(st), "sync extract");
+        if (misc[2] & 1)
+            throw Status{CFLR_ECUDA, "internal: the long-row list of the extraction overflowed"};
+        if (misc[2] & 2)
+            throw Status{CFLR_ECUDA, "internal: a row held more pairs than the pair sets count"};
+        if (misc[3] != total)
+            throw Status{CFLR_ECUDA, "internal: extracted " + std::to_string(misc[3]) +
                                          " pairs where the pair sets hold " +
-                                         std::to_string(g_pairs[g])};
+                                         std::to_string(total)};
+    };
+    if (!hs) {
+        c->scratch(c->x_bigl, c->x_bigl_n, total / 1024 + 1);
+        L.u_begin = 0;
+        L.u_end = U;
+        L.base = 0;
+        L.limit = total;
+        launch_extract_write(L, ws, wd, c->x_unit, c->x_bigl, c->x_bigl_n, c->x_misc, c->x_bm,
+                             err, c->sms, st);
+        ck(cudaGetLastError(), "extract");
+        check();
+        return;
+    }
+    // ranges of units that fit a staging buffer (a unit larger than that
+    // makes a range of its own and sizes the buffers)
+    std::vector<unsigned long long> uoff(U + 1);
+    ck(cudaMemcpyAsync(uoff.data(), c->x_unit, U * 8, cudaMemcpyDeviceToHost, st), "D2H");
+    ck(cudaStreamSynchronize(st), "sync extract count");
+    uoff[U] = total;
+    std::vector<uint64_t> cut(1, 0);
+    uint64_t cap = 0;
+    for (uint64_t u = 1; u <= U; u++) {
+        if (uoff[u] - uoff[cut.back()] > STAGE && u - 1 > cut.back()) cut.push_back(u - 1);
+        if (u == U) cut.push_back(U);
+    }
+    for (size_t r = 0; r + 1 < cut.size(); r++)
+        cap = std::max<uint64_t>(cap, uoff[cut[r + 1]] - uoff[cut[r]]);
+    cap = std::max<uint64_t>(cap, 1);
+    if (c->x_out_cap < 2 * cap) {
+        c->free_extract_out();
+        c->x_src = (uint32_t *)c->dalloc(2 * cap * 4);
+        c->x_dst = (uint32_t *)c->dalloc(2 * cap * 4);
+        c->x_out_cap = 2 * cap;
+    }
+    c->scratch(c->x_bigl, c->x_bigl_n, cap / 1024 + 1);
+    CopyLane lane;
+    ck(cudaStreamCreateWithFlags(&lane.s, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaEvent_t copied[2] = {nullptr, nullptr};   // the last copy out of each buffer
+    for (size_t r = 0; r + 1 < cut.size(); r++) {
+        const int b = (int)(r & 1);
+        if (copied[b]) ck(cudaStreamWaitEvent(st, copied[b], 0), "cudaStreamWaitEvent");
+        L.u_begin = cut[r];
+        L.u_end = cut[r + 1];
+        L.base = uoff[cut[r]];
+        L.limit = uoff[cut[r + 1]];
+        uint32_t *bs = c->x_src + b * cap, *bd = c->x_dst + b * cap;
+        launch_extract_write(L, bs, bd, c->x_unit, c->x_bigl, c->x_bigl_n, c->x_misc, c->x_bm,
+                             err, c->sms, st);
+        ck(cudaGetLastError(), "extract");
+        ck(cudaStreamWaitEvent(lane.s, lane.record(st), 0), "cudaStreamWaitEvent");
+        const uint64_t k = L.limit - L.base;
+        ck(cudaMemcpyAsync(hs + L.base, bs, k * 4, cudaMemcpyDeviceToHost, lane.s), "D2H pairs");
+        ck(cudaMemcpyAsync(hd + L.base, bd, k * 4, cudaMemcpyDeviceToHost, lane.s), "D2H pairs");
+        copied[b] = lane.record(lane.s);
+    }
+    ck(cudaStreamSynchronize(lane.s), "sync copy");
+    check();
 }
 
 int get_pairs_common(cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint32_t *dst,
@@ -1891,13 +1915,7 @@ int get_pairs_common(cflr_ctx *c, uint32_t nonterminal, uint32_t *src, uint32_t 
             extract_many(c, 1, &nonterminal, off, src, dst, nullptr, nullptr);
             return CFLR_OK;
         }
-        if (c->x_out_cap < cnt) {
-            c->free_extract_out();
-            c->x_src = (uint32_t *)c->dalloc(cnt * 4);
-            c->x_dst = (uint32_t *)c->dalloc(cnt * 4);
-            c->x_out_cap = cnt;
-        }
-        extract_many(c, 1, &nonterminal, off, c->x_src, c->x_dst, src, dst);
+        extract_many(c, 1, &nonterminal, off, nullptr, nullptr, src, dst);
         return CFLR_OK;
     } catch (const Status &s) {
         return finish_status(c, s);
@@ -1929,13 +1947,7 @@ int get_pairs_many_common(cflr_ctx *c, uint32_t count, const uint32_t *nts, uint
             extract_many(c, count, nts, offsets, src, dst, nullptr, nullptr);
             return CFLR_OK;
         }
-        if (c->x_out_cap < total) {
-            c->free_extract_out();
-            c->x_src = (uint32_t *)c->dalloc(total * 4);
-            c->x_dst = (uint32_t *)c->dalloc(total * 4);
-            c->x_out_cap = total;
-        }
-        extract_many(c, count, nts, offsets, c->x_src, c->x_dst, src, dst);
+        extract_many(c, count, nts, offsets, nullptr, nullptr, src, dst);
         return CFLR_OK;
     } catch (const Status &s) {
         return finish_status(c, s);

@@ -114,3 +114,31 @@ def test_many_before_a_graph_is_a_state_error():
         with pytest.raises(CflrError) as e:
             cflr.cflr_get_pairs_many(s.ctx, [0])
         assert e.value.code == cflr.CFLR_ESTATE
+
+
+def test_pinned_host_arrays():
+    # pinned host arrays (the copies run asynchronously on a second stream)
+    # get what pageable ones get
+    import torch
+    text = gen.grammar_text("fica")
+    g = gen.fica_like(n=6000, n_a=12000, n_d=4500, seed=34)
+    with _solved(text, g) as s:
+        ids = list(range(s.n_named))
+        src, dst, off = cflr.cflr_get_pairs_many(s.ctx, ids)          # pageable
+        total = int(off[-1])
+        ps = torch.full((total + 3,), -1, dtype=torch.int32).pin_memory()
+        pd = torch.full((total + 3,), -1, dtype=torch.int32).pin_memory()
+        out = (ps.numpy().view(np.uint32), pd.numpy().view(np.uint32))
+        s2, d2, off2 = cflr.cflr_get_pairs_many(s.ctx, ids, out=out)
+        assert np.array_equal(off2, off) and np.array_equal(s2, src) and np.array_equal(d2, dst)
+        assert np.all(out[0][total:] == 0xFFFFFFFF)
+        # one non-terminal into a pinned array at an offset inside it
+        x = int(np.argmax(np.diff(off.astype(np.int64))))
+        a, b = int(off[x]), int(off[x + 1])
+        lib = cflr.load_library()
+        import ctypes
+        n_p = ctypes.c_uint64()
+        assert lib.cflr_get_pairs(s.ctx, ids[x], ps.data_ptr() + 12, pd.data_ptr() + 12, b - a,
+                                  ctypes.byref(n_p)) == 0
+        assert np.array_equal(out[0][3:3 + b - a], src[a:b])
+        assert np.array_equal(out[1][3:3 + b - a], dst[a:b])
