@@ -810,7 +810,12 @@ struct Runner {
                           &d_cnt.p->overflow, sms, st);
         });
         own->k_bytes[KID_REHASH] += c->hcap[x] * 8 + need * 8;
-        sync("rehash");
+        // the old table is freed on the context's stream: when that is the
+        // batch stream the free is ordered after the rehash and no wait is
+        // needed (the rehash reports through the loop status read next; a
+        // points-to solve grows hundreds of sets, and one wait each had cost
+        // about 30 % of its first solve)
+        if (c->stream != st) sync("rehash");
         c->dfree(c->htab[x], c->hcap[x] * 8);
         if (c->hval[x]) c->dfree(c->hval[x], c->hcap[x] * 8);
         c->htab[x] = nt;
@@ -828,7 +833,7 @@ struct Runner {
             throw Status{CFLR_ENOMEM, "row pool exceeds 2^32 entries"};
         uint32_t *np = (uint32_t *)alloc_for(c, cap * 4);
         ck(cudaMemcpyAsync(np, c->pool, c->pool_cap * 4, cudaMemcpyDeviceToDevice, st), "D2D");
-        sync("pool copy");
+        if (c->stream != st) sync("pool copy");    // the free runs on the context's stream
         c->dfree(c->pool, c->pool_cap * 4);
         c->pool = np;       // rows address the pool by offset, so they stay valid
         c->pool_cap = cap;
@@ -1324,19 +1329,63 @@ bool device_order(cflr_ctx *c, uint32_t n, uint64_t m) {
     return true;
 }
 
+// One pass over the input edges on up to eight host threads (contiguous
+// ranges): the first edge with a vertex id >= n (m when there is none), the
+// edges per label a production uses, and the other edges.
+struct EdgeScan {
+    uint64_t bad = 0;
+    std::vector<uint64_t> per_label;
+    uint64_t ignored = 0;
+};
+EdgeScan scan_edges(const Grammar &g, uint32_t n, uint64_t m, const uint32_t *src,
+                    const uint32_t *lab, const uint32_t *dst) {
+    const uint32_t nterm = (uint32_t)g.terms.size();
+    std::vector<uint8_t> used(nterm);
+    for (uint32_t l = 0; l < nterm; l++) used[l] = !g.term_nts[l].empty();
+    unsigned T = std::min(std::max(1u, std::thread::hardware_concurrency()), 8u);
+    if (m < (1u << 18)) T = 1;
+    std::vector<EdgeScan> part(T);
+    auto work = [&](unsigned t) {
+        EdgeScan &r = part[t];
+        const uint64_t e0 = m * t / T, e1 = m * (t + 1) / T;
+        r.bad = m;
+        r.per_label.assign(nterm, 0);
+        for (uint64_t e = e0; e < e1; e++) {
+            if ((src[e] >= n || dst[e] >= n) && r.bad == m) r.bad = e;
+            if (lab[e] < nterm && used[lab[e]]) r.per_label[lab[e]]++;
+            else r.ignored++;
+        }
+    };
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < T; t++) {
+        try {
+            th.emplace_back(work, t);
+        } catch (const std::system_error &) {
+            work(t);                 // no thread to be had: that range here
+        }
+    }
+    work(0);
+    for (auto &x : th) x.join();
+    EdgeScan out;
+    out.bad = m;
+    out.per_label.assign(nterm, 0);
+    for (auto &r : part) {
+        out.bad = std::min(out.bad, r.bad);
+        out.ignored += r.ignored;
+        for (uint32_t l = 0; l < nterm; l++) out.per_label[l] += r.per_label[l];
+    }
+    return out;
+}
+
 // Copy the graph to the device and size the matrices (cflr_load_graph).
 void upload_graph(cflr_ctx *c, uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *lab,
-                  const uint32_t *dst) {
+                  const uint32_t *dst, const EdgeScan &scan) {
     const Grammar &g = c->g;
     const uint32_t nt = (uint32_t)g.nts.size(), nterm = (uint32_t)g.terms.size();
     cudaStream_t st = c->stream;
     // per-label edge counts -> per-non-terminal initial counts
-    std::vector<uint64_t> per_label(nterm, 0);
-    uint64_t ignored = 0;
-    for (uint64_t e = 0; e < m; e++) {
-        if (lab[e] < nterm && !g.term_nts[lab[e]].empty()) per_label[lab[e]]++;
-        else ignored++;
-    }
+    const std::vector<uint64_t> &per_label = scan.per_label;
+    const uint64_t ignored = scan.ignored;
     c->init_cnt.assign(nt, 0);
     for (uint32_t l = 0; l < nterm; l++)
         for (uint32_t A : g.term_nts[l]) c->init_cnt[A] += per_label[l];
@@ -1657,16 +1706,16 @@ int cflr_load_graph(cflr_ctx *c, uint32_t n_vertices, uint64_t n_edges, const ui
     const long double bound = (long double)nt * n_vertices * (long double)n_vertices;
     if (bound >= 4.6e18L || n_vertices >= 0xFFFFFFF0u)
         return c->fail(CFLR_EGRAPH, "too many vertices for 64-bit pair keys");
-    for (uint64_t e = 0; e < n_edges; e++)
-        if (src[e] >= n_vertices || dst[e] >= n_vertices)
-            return c->fail(CFLR_EGRAPH, "edge " + std::to_string(e) + " has a vertex id >= " +
-                                            std::to_string(n_vertices));
+    const EdgeScan scan = scan_edges(c->g, n_vertices, n_edges, src, label, dst);
+    if (scan.bad < n_edges)
+        return c->fail(CFLR_EGRAPH, "edge " + std::to_string(scan.bad) + " has a vertex id >= " +
+                                        std::to_string(n_vertices));
     try {
         Range range("cflr_load_graph");
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         c->free_graph();
         c->state = ST_GRAMMAR;
-        upload_graph(c, n_vertices, n_edges, src, label, dst);
+        upload_graph(c, n_vertices, n_edges, src, label, dst, scan);
         reset_matrices(c);
         c->state = ST_GRAPH;
         c->err.clear();
