@@ -487,6 +487,17 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
                 phases[key].append(1e3 * (b - a))
             fresh = {k: st2[k] for k in ("regrow_buffers", "regrow_sets", "regrow_pools")}
         assert tot == pairs
+    # a bare copy of the same bytes into the same pinned arrays, for context:
+    # the host copy bandwidth differs between boxes and runs
+    bare = []
+    for k in range(4):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h_out_s.copy_(out[0], non_blocking=True)
+        h_out_d.copy_(out[1], non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if k:
+            bare.append(1e3 * (time.perf_counter() - t0))
 
     ms = statistics.mean(step_ms)
     ms_all, pairs_all, e2e_all = aggregate(dist, dev, ms, pairs, statistics.mean(e2e_s))
@@ -506,6 +517,8 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
                 "h2d_bytes_per_step": int(12 * g.n_edges),
                 "d2h_bytes_per_step": int(8 * pairs),
                 "phases_ms": {k: round(statistics.mean(v), 2) for k, v in phases.items()},
+                "pairs_to_host_each_ms": [round(v, 2) for v in phases["pairs_to_host"]],
+                "bare_d2h_copy_ms": round(statistics.median(bare), 2),
                 "fresh_context_regrows": fresh},
         "gpu_launches": int(launches),
         "roofline": roofline_of(rows, "fsjpt_like" if kind == "fsjpt" else "fica_like"),
