@@ -501,7 +501,9 @@ def run_cflr(args, kind: str = "fica", extras: bool = False):
 
     ms = statistics.mean(step_ms)
     ms_all, pairs_all, e2e_all = aggregate(dist, dev, ms, pairs, statistics.mean(e2e_s))
-    launches = sum(r[1] for r in rows) + args.steps * n_named * 6   # + extraction kernels
+    # + the read-out of each step: unit counts, a three-kernel scan, the rows,
+    # the long rows (one list extraction of every named non-terminal)
+    launches = sum(r[1] for r in rows) + args.steps * 6
     if rank != 0:
         cflr.cflr_destroy(ctx)
         return
