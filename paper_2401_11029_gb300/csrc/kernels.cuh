@@ -269,8 +269,10 @@ void launch_exclusive_scan(const uint32_t *in, uint32_t n, unsigned long long *o
                            unsigned long long *bsum, unsigned long long *grand, cudaStream_t st);
 
 // Extraction of one non-terminal's pairs, sorted by (src, dst), in the
-// caller's vertex ids: perm maps a caller id to its stored row, iperm a
-// stored id back (both null when the vertices kept their input order).
+// caller's vertex ids, with caller-provided scratch (the allocation-free
+// read-out; the other read-outs use the list extraction below): perm maps a
+// caller id to its stored row, iperm a stored id back (both null when the
+// vertices kept their input order).
 void launch_row_lengths(const uint4 *desc, const uint32_t *pool, uint32_t n,
                         const uint32_t *perm, uint32_t *len, cudaStream_t st);
 // big_rows: scratch of n uint32 followed by two counters (big_count points
