@@ -1243,10 +1243,23 @@ struct TempArrays {
 // edges c->e_src / c->e_dst (caller ids) into c->perm / c->iperm (the
 // kernels' steps are described with launch_rn_adjacency).  Returns false,
 // with nothing to keep, for graphs it does not take: 2^32 edges or more, a
-// vertex with more than RENUM_LIST_MAX edge ends, or components that did not
-// settle in 128 passes.
+// vertex with more than RENUM_LIST_MAX edge ends, components that did not
+// settle in 128 passes, or scratch beyond the context's memory budget.
+bool device_order_steps(cflr_ctx *c, uint32_t n, uint64_t m);
+
 bool device_order(cflr_ctx *c, uint32_t n, uint64_t m) {
     if (m >= (1ull << 32)) return false;
+    try {
+        return device_order_steps(c, n, m);
+    } catch (const Status &s) {
+        // no room for the search's scratch under the memory budget: the host
+        // search needs none (the scratch is freed on the way out)
+        if (s.code == CFLR_ENOMEM) return false;
+        throw;
+    }
+}
+
+bool device_order_steps(cflr_ctx *c, uint32_t n, uint64_t m) {
     Range range("cflr: vertex renumbering (device)");
     cudaStream_t st = c->stream;
     const int sms = c->sms;
