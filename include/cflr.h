@@ -225,17 +225,20 @@ int cflr_get_pairs_device(const cflr_ctx *c, uint32_t nonterminal, uint32_t *d_s
  * offsets (host array of count + 1 entries, required) receives where the
  * pairs of nonterminals[i] start, and offsets[count] the total.  With
  * src == dst == NULL only offsets are filled.  If capacity < total, nothing is
- * copied, offsets are filled and CFLR_EINVAL is returned.  All extractions
- * are queued at once and the copies to the host overlap them, so the call
- * synchronises with the device once, not once per non-terminal.
+ * copied, offsets are filled and CFLR_EINVAL is returned.  All listed
+ * non-terminals are extracted together (not one call's work per
+ * non-terminal): the pairs pass through two device staging buffers of at
+ * most 16 Mi pairs, each copied to the host while the next range is written.
+ * The call waits for the device twice: after counting and at the end.
  * Errors: CFLR_ESTATE (no graph), CFLR_EINVAL (NULL offsets, a bad id,
  * capacity), CFLR_ENOMEM, CFLR_ECUDA. */
 int cflr_get_pairs_many(const cflr_ctx *c, uint32_t count, const uint32_t *nonterminals,
                         uint32_t *src, uint32_t *dst, uint64_t capacity, uint64_t *offsets);
 
 /* As cflr_get_pairs_many, but d_src/d_dst are device pointers (on this
- * context's device) owned by the caller; offsets stays a host array.  The
- * call returns after the last pair has been written on the context's
+ * context's device) owned by the caller; offsets stays a host array.  No
+ * staging: the kernels write the caller's arrays, and the call waits for the
+ * device once, after the last pair has been written on the context's
  * stream. */
 int cflr_get_pairs_device_many(const cflr_ctx *c, uint32_t count, const uint32_t *nonterminals,
                                uint32_t *d_src, uint32_t *d_dst, uint64_t capacity,
